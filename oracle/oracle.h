@@ -1,0 +1,101 @@
+/*
+ * FP64 CPU oracle for the monodomain finite-volume step of Del Corso,
+ * Verzicco & Viola, "A fast computational model for the electrophysiology of
+ * the whole human heart".
+ *
+ * TEST INFRASTRUCTURE ONLY. This library is the correctness reference the
+ * CUDA path is checked against. Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg load it; the product never does. It shares no
+ * code, header, table or constant with the CUDA library.
+ *
+ * It follows the paper's algorithm stage by stage, in plain per-cell loops:
+ *   - geometry of the cell-centred tetrahedral FV mesh (Sec. 3.2);
+ *   - S1 inverse-distance node values, S2 face values and Gauss-Green cell
+ *     gradients, S3 interpolated face gradient with the directional-derivative
+ *     correction of Eq. 8, flux A_f (D_f grad v_f).n_f summed over the four
+ *     faces, zero on boundary faces (Eq. 7);
+ *   - conductivity tensors rotated into the fibre frame (Eqs. 2-3);
+ *   - ionic models (ten Tusscher-Panfilov 2006, Courtemanche 1998,
+ *     Stewart 2009) advanced by Rush-Larsen for gates and forward Euler for
+ *     everything else, all evaluated at (V^n, s^n) (Sec. 3.2);
+ *   - the stimulus of Eq. 4 and the activation time (first upward crossing of
+ *     a threshold, Sec. 4);
+ *   - the 1D vertex-based FV Purkinje graph and its junctions (Sec. 3.2, 3.3).
+ *
+ * Units: V in mV, t in ms, D in mm^2/ms, currents in uA/uF.
+ */
+#ifndef EP_ORACLE_H
+#define EP_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MAXVAR 24
+
+enum { ORC_TP06 = 0, ORC_CRN = 1, ORC_STEWART = 2 };
+
+typedef struct {
+    int32_t model;      /* ORC_TP06 / ORC_CRN / ORC_STEWART */
+    int32_t variant;    /* TP06: 0 epi, 1 mid, 2 endo */
+    double D_l, D_t;    /* monodomain diffusivity along / across the fibre, mm^2/ms */
+    double gks_scale, gkr_scale;
+    double K_o;         /* extracellular K+, mM */
+} orc_cellparams;
+
+typedef struct {
+    double amplitude;   /* uA/uF; negative depolarises (enters like I_ion) */
+    double t_on, duration, period;  /* ms; period 0 = single pulse */
+} orc_stim;
+
+/* ---- geometry and the diffusion operator (fv3d.c) ---- */
+typedef struct orc_mesh orc_mesh;
+orc_mesh *orc_mesh_create(int64_t n_nodes, const double *xyz, int64_t n_cells,
+                          const int32_t *tet, int *err);
+void orc_mesh_destroy(orc_mesh *m);
+int64_t orc_mesh_n_boundary_faces(const orc_mesh *m);
+void orc_mesh_cell_info(const orc_mesh *m, double *centroid, double *volume,
+                        int32_t *neighbour);
+void orc_node_values(const orc_mesh *m, const double *v, double *vn);
+void orc_cell_gradients(const orc_mesh *m, const double *vn, double *grad);
+void orc_diffusion(const orc_mesh *m, const double *D, const double *v, double *out);
+void orc_diffusion_twopoint(const orc_mesh *m, const double *D, const double *v, double *out);
+void orc_conductivity(const double *fibre, double D_l, double D_t, double *D);
+
+/* ---- cell models (tp06.c, crn.c, stewart.c) ---- */
+int orc_model_nvar(int model);
+const char *orc_model_varname(int model, int var);
+void orc_model_init(const orc_cellparams *p, double *s);
+double orc_model_step(double *s, double dt, double i_stim, const orc_cellparams *p);
+/* single-cell run: V recorded every record_every steps (n_steps/record_every values) */
+void orc_cell_run(const orc_cellparams *p, double dt, int64_t n_steps,
+                  const orc_stim *stim, int64_t record_every, double *v_out,
+                  double *state_inout);
+
+/* ---- tissue simulation (tissue.c) ---- */
+typedef struct orc_sim orc_sim;
+orc_sim *orc_sim_create(int64_t n_nodes, const double *xyz, int64_t n_cells,
+                        const int32_t *tet, const double *fibre,
+                        const uint8_t *param_set, const uint8_t *stim_mask,
+                        int n_sets, const orc_cellparams *sets,
+                        int n_stim, const orc_stim *stim,
+                        double dt, double threshold, int *err);
+void orc_sim_destroy(orc_sim *s);
+void orc_sim_run(orc_sim *s, int64_t n_steps);
+int64_t orc_sim_step_index(const orc_sim *s);
+void orc_sim_get_var(const orc_sim *s, int var, double *out);
+void orc_sim_set_var(orc_sim *s, int var, const double *in);
+void orc_sim_get_act(const orc_sim *s, double *out);
+void orc_sim_set_step_index(orc_sim *s, int64_t n);
+void orc_sim_diffusion(const orc_sim *s, const double *v, double *out);
+const orc_mesh *orc_sim_mesh(const orc_sim *s);
+int orc_stim_active(const orc_stim *st, double dt, int64_t n);
+
+/* ---- Purkinje graph (purkinje.c) ---- */
+typedef struct orc_purk orc_purk;
+
+#ifdef __cplusplus
+}
+#endif
+#endif

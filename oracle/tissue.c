@@ -1,0 +1,210 @@
+/*
+ * Oracle (test infrastructure only): the operator-split monodomain time step
+ * on the tetrahedral mesh, and the single-cell driver.
+ *
+ * One step from t^n = n dt (Sec. 3.2, Eq. 7 divided by chi C_m V_c):
+ *   diff_c   = (1/V_c) sum_j A_fj (D_fj grad v_fj) . n_fj        (fv3d.c)
+ *   I_s,c    = sum of the amplitudes of the stimulus protocols (Eq. 4) that
+ *              cover cell c and are on at step n
+ *   s^{n+1}  = cell-model update at (V^n, s^n)  (RL gates, FE the rest)
+ *   V^{n+1}  = V^n + dt (diff_c - I_ion(V^n, s^n) - I_s,c)
+ *   activation time: at the first step with V^n < theta <= V^{n+1},
+ *              t_act = t^n + dt (theta - V^n) / (V^{n+1} - V^n)
+ *
+ * A stimulus protocol is on at step n when n >= n_on and
+ * (n - n_on) mod n_period < n_dur (single pulse: n < n_on + n_dur), with
+ * n_on, n_dur, n_period the onset, duration and period rounded to whole
+ * steps.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include "oracle.h"
+
+int orc_tp06_nvar(void);
+const char *orc_tp06_varname(int v);
+void orc_tp06_init(int variant, double *s);
+double orc_tp06_step(double *s, double dt, double i_stim, const orc_cellparams *p);
+int orc_crn_nvar(void);
+const char *orc_crn_varname(int v);
+void orc_crn_init(double *s);
+double orc_crn_step(double *s, double dt, double i_stim, const orc_cellparams *p);
+int orc_stewart_nvar(void);
+const char *orc_stewart_varname(int v);
+void orc_stewart_init(double *s);
+double orc_stewart_step(double *s, double dt, double i_stim, const orc_cellparams *p);
+
+int orc_model_nvar(int model) {
+    switch (model) {
+    case ORC_TP06: return orc_tp06_nvar();
+    case ORC_CRN: return orc_crn_nvar();
+    case ORC_STEWART: return orc_stewart_nvar();
+    }
+    return 0;
+}
+
+const char *orc_model_varname(int model, int var) {
+    switch (model) {
+    case ORC_TP06: return orc_tp06_varname(var);
+    case ORC_CRN: return orc_crn_varname(var);
+    case ORC_STEWART: return orc_stewart_varname(var);
+    }
+    return 0;
+}
+
+void orc_model_init(const orc_cellparams *p, double *s) {
+    for (int k = 0; k < ORC_MAXVAR; ++k) s[k] = 0.0;
+    switch (p->model) {
+    case ORC_TP06: orc_tp06_init(p->variant, s); break;
+    case ORC_CRN: orc_crn_init(s); break;
+    case ORC_STEWART: orc_stewart_init(s); break;
+    }
+}
+
+/* Advances every state variable except V (index 0); returns I_ion(V^n, s^n). */
+double orc_model_step(double *s, double dt, double i_stim, const orc_cellparams *p) {
+    switch (p->model) {
+    case ORC_TP06: return orc_tp06_step(s, dt, i_stim, p);
+    case ORC_CRN: return orc_crn_step(s, dt, i_stim, p);
+    case ORC_STEWART: return orc_stewart_step(s, dt, i_stim, p);
+    }
+    return 0.0;
+}
+
+int orc_stim_active(const orc_stim *st, double dt, int64_t n) {
+    int64_t n_on = llround(st->t_on / dt);
+    int64_t n_dur = llround(st->duration / dt);
+    int64_t n_per = llround(st->period / dt);
+    if (n < n_on) return 0;
+    if (n_per <= 0) return n < n_on + n_dur;
+    return ((n - n_on) % n_per) < n_dur;
+}
+
+void orc_cell_run(const orc_cellparams *p, double dt, int64_t n_steps,
+                  const orc_stim *stim, int64_t record_every, double *v_out,
+                  double *state_inout) {
+    double s[ORC_MAXVAR];
+    memcpy(s, state_inout, sizeof(s));
+    int64_t r = 0;
+    for (int64_t n = 0; n < n_steps; ++n) {
+        double is = (stim && orc_stim_active(stim, dt, n)) ? stim->amplitude : 0.0;
+        double vn = s[0];
+        double iion = orc_model_step(s, dt, is, p);
+        s[0] = vn + dt * (-iion - is);
+        if (record_every > 0 && (n + 1) % record_every == 0) v_out[r++] = s[0];
+    }
+    memcpy(state_inout, s, sizeof(s));
+}
+
+struct orc_sim {
+    orc_mesh *m;
+    int64_t n_cells;
+    uint8_t *pset, *smask;
+    int n_sets;
+    orc_cellparams sets[256];
+    int n_stim;
+    orc_stim stim[8];
+    double dt, theta;
+    int64_t step;
+    double *state;   /* [n_cells][ORC_MAXVAR] */
+    double *D;       /* [n_cells][9] */
+    double *act;
+    double *v, *diff;
+};
+
+orc_sim *orc_sim_create(int64_t n_nodes, const double *xyz, int64_t n_cells,
+                        const int32_t *tet, const double *fibre,
+                        const uint8_t *param_set, const uint8_t *stim_mask,
+                        int n_sets, const orc_cellparams *sets,
+                        int n_stim, const orc_stim *stim,
+                        double dt, double threshold, int *err) {
+    if (n_sets < 1 || n_sets > 256 || n_stim < 0 || n_stim > 8) { *err = 10; return NULL; }
+    for (int64_t c = 0; c < n_cells; ++c)
+        if (param_set[c] >= n_sets) { *err = 11; return NULL; }
+    orc_mesh *m = orc_mesh_create(n_nodes, xyz, n_cells, tet, err);
+    if (!m) return NULL;
+    orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
+    s->m = m;
+    s->n_cells = n_cells;
+    s->pset = (uint8_t *)malloc(n_cells);
+    memcpy(s->pset, param_set, n_cells);
+    s->smask = (uint8_t *)malloc(n_cells);
+    if (stim_mask) memcpy(s->smask, stim_mask, n_cells);
+    else memset(s->smask, 0, n_cells);
+    s->n_sets = n_sets;
+    memcpy(s->sets, sets, sizeof(orc_cellparams) * n_sets);
+    s->n_stim = n_stim;
+    if (n_stim) memcpy(s->stim, stim, sizeof(orc_stim) * n_stim);
+    s->dt = dt;
+    s->theta = threshold;
+    s->step = 0;
+    s->state = (double *)malloc(sizeof(double) * ORC_MAXVAR * n_cells);
+    s->D = (double *)malloc(sizeof(double) * 9 * n_cells);
+    s->act = (double *)malloc(sizeof(double) * n_cells);
+    s->v = (double *)malloc(sizeof(double) * n_cells);
+    s->diff = (double *)malloc(sizeof(double) * n_cells);
+    for (int64_t c = 0; c < n_cells; ++c) {
+        const orc_cellparams *p = &s->sets[s->pset[c]];
+        orc_model_init(p, s->state + ORC_MAXVAR * c);
+        double f[3] = {1.0, 0.0, 0.0};
+        if (fibre) { f[0] = fibre[3 * c]; f[1] = fibre[3 * c + 1]; f[2] = fibre[3 * c + 2]; }
+        orc_conductivity(f, p->D_l, p->D_t, s->D + 9 * c);
+        s->act[c] = INFINITY;
+    }
+    *err = 0;
+    return s;
+}
+
+void orc_sim_destroy(orc_sim *s) {
+    if (!s) return;
+    orc_mesh_destroy(s->m);
+    free(s->pset); free(s->smask); free(s->state); free(s->D); free(s->act);
+    free(s->v); free(s->diff);
+    free(s);
+}
+
+void orc_sim_run(orc_sim *s, int64_t n_steps) {
+    for (int64_t it = 0; it < n_steps; ++it) {
+        const int64_t n = s->step;
+        double amp[8];
+        for (int k = 0; k < s->n_stim; ++k)
+            amp[k] = orc_stim_active(&s->stim[k], s->dt, n) ? s->stim[k].amplitude : 0.0;
+        for (int64_t c = 0; c < s->n_cells; ++c) s->v[c] = s->state[ORC_MAXVAR * c];
+        orc_diffusion(s->m, s->D, s->v, s->diff);
+#pragma omp parallel for schedule(static)
+        for (int64_t c = 0; c < s->n_cells; ++c) {
+            double *st = s->state + ORC_MAXVAR * c;
+            double is = 0.0;
+            for (int k = 0; k < s->n_stim; ++k)
+                if (s->smask[c] & (1u << k)) is += amp[k];
+            const double vn = st[0];
+            const double iion = orc_model_step(st, s->dt, is, &s->sets[s->pset[c]]);
+            const double vnew = vn + s->dt * (s->diff[c] - iion - is);
+            st[0] = vnew;
+            if (isinf(s->act[c]) && vn < s->theta && vnew >= s->theta)
+                s->act[c] = (double)n * s->dt + s->dt * (s->theta - vn) / (vnew - vn);
+        }
+        s->step = n + 1;
+    }
+}
+
+int64_t orc_sim_step_index(const orc_sim *s) { return s->step; }
+void orc_sim_set_step_index(orc_sim *s, int64_t n) { s->step = n; }
+
+void orc_sim_get_var(const orc_sim *s, int var, double *out) {
+    for (int64_t c = 0; c < s->n_cells; ++c) out[c] = s->state[ORC_MAXVAR * c + var];
+}
+
+void orc_sim_set_var(orc_sim *s, int var, const double *in) {
+    for (int64_t c = 0; c < s->n_cells; ++c) s->state[ORC_MAXVAR * c + var] = in[c];
+}
+
+void orc_sim_get_act(const orc_sim *s, double *out) {
+    memcpy(out, s->act, sizeof(double) * s->n_cells);
+}
+
+void orc_sim_diffusion(const orc_sim *s, const double *v, double *out) {
+    orc_diffusion(s->m, s->D, v, out);
+}
+
+const orc_mesh *orc_sim_mesh(const orc_sim *s) { return s->m; }

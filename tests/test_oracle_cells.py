@@ -1,0 +1,135 @@
+"""Physiological pins of the oracle's cell models (Sec. 3.1, Sec. 5) and of
+the Rush-Larsen / forward-Euler scheme (Sec. 3.2).
+
+Parity with the published model traces is unpinned (the model papers' figures
+and code are not available); these tests pin what the method paper and the
+models' physiology fix: resting potentials, action-potential duration and
+plateau, automaticity, and the time-integration properties."""
+import numpy as np
+import pytest
+
+import workloads as w
+
+DT = 0.02
+
+
+def _apd(v, dt, frac):
+    rest, peak = v[0], v.max()
+    ip = int(v.argmax())
+    up = int(np.argmax(v > 0.5 * (rest + peak)))
+    thr = peak - frac * (peak - rest)
+    i = ip
+    while i < len(v) and v[i] > thr:
+        i += 1
+    return (i - up) * dt
+
+
+def _paced(orc, ps, amp, dur, beats=6, bcl=1000.0, dt=DT):
+    stim = orc.Stim(amp, 0.0, dur, bcl)
+    n_beat = int(round(bcl / dt))
+    v, st = orc.cell_run(ps, dt, n_beat * beats, stim, 1)
+    return v[-n_beat - 1:], st
+
+
+@pytest.fixture(scope="module")
+def tp06_beats(orc):
+    return {var: _paced(orc, w.ParamSet(model=0, variant=var), -52.0, 1.0)
+            for var in (0, 1, 2)}
+
+
+def test_tp06_rest_and_peak(tp06_beats):
+    """TP06 rests near -85 mV (Sec. 5) with an overshooting upstroke."""
+    for var, (v, _) in tp06_beats.items():
+        assert -87.0 <= v[0] <= -84.0
+        assert 25.0 <= v.max() <= 50.0
+
+
+def test_tp06_apd_and_variant_order(tp06_beats):
+    """Plateau of about 300 ms (Sec. 5); the M cell has the longest APD; the
+    epi cell has a deeper early-repolarisation notch than the endo cell."""
+    apd = {k: _apd(v, DT, 0.9) for k, (v, _) in tp06_beats.items()}
+    assert 260.0 <= apd[0] <= 340.0
+    assert apd[1] > apd[0] + 40.0 and apd[1] > apd[2] + 40.0
+    assert abs(apd[2] - apd[0]) < 20.0
+    notch = {}
+    for k in (0, 2):
+        v = tp06_beats[k][0]
+        ip = int(v.argmax())
+        notch[k] = v[ip:ip + int(30 / DT)].min()
+    assert notch[0] < notch[2] - 5.0
+
+
+def test_tp06_unstimulated_stays_at_rest(orc):
+    v, _ = orc.cell_run(w.ParamSet(model=0), DT, 50000, None, 100)
+    assert np.all((v > -87.0) & (v < -84.0))
+
+
+def test_courtemanche_rest_and_repolarisation(orc):
+    """Courtemanche rests near -80 mV and repolarises within a few hundred ms
+    (Sec. 5)."""
+    v, _ = _paced(orc, w.ParamSet(model=1), -20.0, 2.0)
+    assert -82.0 <= v[0] <= -79.0
+    assert v.max() > 10.0
+    assert 120.0 <= _apd(v, DT, 0.5) <= 260.0
+    assert _apd(v, DT, 0.9) <= 360.0
+
+
+def test_stewart_high_peak_plateau_and_automaticity(orc):
+    """Stewart Purkinje cell: high depolarisation peak and a plateau of about
+    250 ms (Sec. 5); unstimulated, I_f makes it fire on its own."""
+    v, _ = _paced(orc, w.ParamSet(model=2), -52.0, 1.0)
+    assert v.max() > 40.0
+    assert 150.0 <= _apd(v, DT, 0.5) <= 320.0
+    v, _ = orc.cell_run(w.ParamSet(model=2), DT, 150000, None, 1)
+    up = np.flatnonzero((v[:-1] < 0.0) & (v[1:] >= 0.0))
+    assert len(up) >= 1
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_rush_larsen_exact_for_frozen_voltage(orc, model):
+    """With V frozen, the RL update of a gate is its exact exponential
+    solution, so 1 step of 4*dt equals 4 steps of dt for every gate whose
+    rates depend on V only (the FE variables do not have this property)."""
+    ps = w.ParamSet(model=model)
+    names = orc.model_varnames(model)
+    gates = {0: ["m", "h", "j", "xr1", "xr2", "xs", "r", "s", "d", "f", "f2"],
+             1: ["m", "h", "j", "oa", "oi", "ua", "ui", "xr", "xs", "d", "f"],
+             2: ["m", "h", "j", "xr1", "xr2", "xs", "r", "s", "d", "f", "f2", "y"]}[model]
+    s0 = orc.model_init(ps)
+    s0[0] = -20.0
+    a = s0.copy()
+    for _ in range(4):
+        orc.model_step(a, 0.01, 0.0, ps)
+    b = s0.copy()
+    orc.model_step(b, 0.04, 0.0, ps)
+    for g in gates:
+        k = names.index(g)
+        assert a[k] == pytest.approx(b[k], rel=1e-12, abs=1e-15), g
+
+
+def test_first_order_in_time(orc):
+    """FE/RL is first order in dt (Sec. 4): the error of V at a fixed time
+    halves when dt halves."""
+    ps = w.ParamSet(model=0)
+    T = 30.0
+
+    def v_at(dt):
+        n = int(round(T / dt))
+        v, _ = orc.cell_run(ps, dt, n, orc.Stim(-52.0, 0.0, 1.0, 0.0), n)
+        return v[-1]
+
+    ref = v_at(0.000625)
+    e = [abs(v_at(dt) - ref) for dt in (0.02, 0.01, 0.005)]
+    r1, r2 = e[0] / e[1], e[1] / e[2]
+    assert 1.6 < r1 < 2.6 and 1.6 < r2 < 2.6
+
+
+def test_stimulus_schedule(orc):
+    """Eq. 4 with whole steps: on for round(S_d/dt) steps from the onset,
+    repeating every round(period/dt) steps."""
+    s = orc.Stim(-52.0, 0.0, 1.0, 0.0)
+    on = [orc.stim_active(s, 0.02, n) for n in range(60)]
+    assert on == [True] * 50 + [False] * 10
+    s = orc.Stim(-52.0, 2.0, 0.5, 10.0)
+    on = [orc.stim_active(s, 0.5, n) for n in range(30)]
+    assert [n for n in range(30) if on[n]] == [4, 24]
