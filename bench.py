@@ -1,0 +1,335 @@
+"""Benchmark of the monodomain finite-volume step on one B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (``ours``): the ventricular wedge slab, 50 x 50 x 10 mm at 0.25 mm
+(200 x 200 x 40 cubes x 6 tets = 9.6M cells), fibre angle rotating from -60
+deg (endocardium) to +60 deg (epicardium), TP06 endo / M / epi variants in
+depth thirds, corner stimulus, dt = 0.02 ms; seeded synthetic input shaped
+like the paper's slab benchmark (Sec. 4). A "step" is one time step of every
+cell: the node-value launch and the fused cell launch. ``value`` is
+cell-updates/s of the FP32 path (FP64 accumulation of [Na]i, [K]i, [Ca]SR)
+with the state resident in HBM; the plain FP64 path is timed beside it on the
+same workload. Under torchrun each rank runs its own replica (the path has no
+exchange step); ``value`` sums the ranks' cell-updates over the slowest
+rank's time.
+
+``--impl reference`` times the FP64 CPU oracle as it stands on this host's
+cores, on a bounded crop of the same workload (same construction, fewer
+cubes), one oracle time step per bench step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as w  # noqa: E402
+
+METRIC = "cell-updates/s FP32 batched vs FP64 plain (same GPU, ≤1 mV); p50/p99 job latency"
+UNIT = "cell-updates/s"
+WEDGE = dict(nx=200, ny=200, nz=40, h=0.25)
+CROP = dict(nx=50, ny=50, nz=10, h=0.25)       # oracle sample: same construction, 150k cells
+OUTPUT_EVERY = 250                              # V read back every 5 ms of simulated time (e2e)
+# algorithmic bytes per cell-update of the fused cell kernel (TP06, FP32 mixed):
+#   per-cell coefficients and indices: nodes_a, nodes_b, nbr (3 x int4), wa, wb, q (3 x float4) = 96
+#   own V read 4, pset + stim mask 2, state read 15 x 4 + 3 x 8 = 84
+#   V^{n+1} write 4, state write 84
+# (node-value and neighbour-potential gathers are L2 hits by design and not counted)
+CELL_BYTES = 96 + 4 + 2 + 84 + 4 + 84
+# node kernel: sliced-ELL entries (4-byte cell index + 4-byte weight) per incidence (4 per cell),
+# plus the node-value write (N_nodes / N_cells x 4 bytes)
+NODE_BYTES_PER_INCIDENCE = 8
+
+
+def wedge_case(dims):
+    return w.wedge_case(nx=dims["nx"], ny=dims["ny"], nz=dims["nz"], h=dims["h"], n_steps=20000)
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2112_12854_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(n_cells):
+    """DRAM bytes per cell of the cell kernel from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "cell_kernel_wedge.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram_bytes_per_cell:\s*([0-9.]+)", txt)
+    if not m_hash or not m_b or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_b.group(1)) * n_cells
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, smax, reasons = [], [], set()
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 8:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if r[4 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def oracle_throughput(dims, budget_s, max_steps=None):
+    """Time the FP64 oracle on a crop of the workload; returns (cell-updates/s, steps, cells, cores)."""
+    import oracle
+    case = wedge_case(dims)
+    s = oracle.Sim(case)
+    s.run(1)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        s.run(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_steps and steps >= max_steps):
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return case.n_cells * steps / el, steps, case.n_cells, cores
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    case = wedge_case(CROP)
+    s = oracle.Sim(case)
+    for _ in range(args.warmup):
+        s.run(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.run(1)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    val = case.n_cells * args.steps / el
+    sample = (f"oracle (FP64 C, OpenMP) on a crop of the wedge workload: {CROP['nx']}x{CROP['ny']}x{CROP['nz']} "
+              f"cubes x 6 = {case.n_cells} cells, one time step per bench step")
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": "ventricular wedge slab crop (oracle sample)",
+                                            "cells": case.n_cells, "dt_ms": case.dt},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--small", action="store_true", help="debug: 1/8-volume crop instead of the full wedge")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_2112_12854_b300 import ep
+    dims = dict(nx=100, ny=100, nz=20, h=0.25) if args.small else WEDGE
+    case = wedge_case(dims)
+    N = case.n_cells
+    ctx = ep.Context()
+    job = ep.job_from_case(ctx, case, precision=ep.EP_FP32_MIXED)
+    info = job.info()
+    stream = torch.cuda.current_stream()
+    nvar = len(ep.model_varnames(ep.EP_TP06))
+    host_state = [torch.empty(N, dtype=torch.float64, pin_memory=True).numpy() for _ in range(nvar)]
+    for v in range(nvar):
+        job.read(v, out=host_state[v])
+
+    # warm-up, then the timed region: K steps (captured-graph replay) bracketed by barrier + sync
+    job.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    job.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N * args.steps / (ms * 1e-3)
+    finite = job.check_finite()
+
+    # per-kernel device time (CUDA events on the launching stream, direct launches)
+    node_ms, cell_ms = ep.time_kernels([job], min(args.steps, 200))
+    peak, peak_kind = measured_peaks()
+    incid = 4.0 * N
+    cell_gbs = CELL_BYTES * N / (cell_ms * 1e-3) / 1e9
+    node_bytes = NODE_BYTES_PER_INCIDENCE * incid + 4.0 * info["n_nodes"]
+    traffic = traffic_from_profile(N)
+    roofline = {"bound": "hbm", "kernel": "cell_kernel<float>", "achieved": cell_gbs, "peak": peak,
+                "unit": "GB/s", "frac": cell_gbs / peak, "traffic": traffic,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy)" if peak_kind == "measured"
+                else "fallback 6.4 TB/s",
+                "algorithmic_bytes_per_cell": CELL_BYTES, "cell_kernel_ms": cell_ms, "node_kernel_ms": node_ms,
+                "node_kernel_gbs": node_bytes / (node_ms * 1e-3) / 1e9,
+                "step_gbs": (CELL_BYTES * N + node_bytes) / ((cell_ms + node_ms) * 1e-3) / 1e9}
+
+    # end to end through the public API with host buffers: the initial state uploaded from pinned
+    # host memory, K steps, V read back every OUTPUT_EVERY steps, the activation map at the end
+    e2e = None
+    if not args.no_e2e:
+        vout = torch.empty(N, dtype=torch.float64, pin_memory=True).numpy()
+        aout = torch.empty(N, dtype=torch.float64, pin_memory=True).numpy()
+        job.reset_activation()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        job.step_index = 0
+        for v in range(nvar):
+            job.write(v, host_state[v])
+        done, reads = 0, 0
+        while done < args.steps:
+            k = min(OUTPUT_EVERY, args.steps - done)
+            job.step(k)
+            done += k
+            job.read(0, out=vout)
+            reads += 1
+        job.activation_times(out=aout)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        barrier()
+        e2e = {"value": world * N * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": nvar * 8 * N / args.steps,
+               "d2h_bytes_per_step": (reads + 1) * 8 * N / args.steps,
+               "note": f"state uploaded from pinned host memory, V read back every {OUTPUT_EVERY} steps, "
+                       "activation map at the end"}
+    job.destroy()
+
+    # plain FP64 path on the same workload
+    job64 = ep.job_from_case(ctx, case, precision=ep.EP_FP64_PLAIN)
+    job64.step(3)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    job64.step(args.fp64_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    fp64 = {"value": N * args.fp64_steps / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps,
+            "steps": args.fp64_steps}
+    job64.destroy()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, st, cells, cores = oracle_throughput(CROP, args.cpu_budget)
+        cpu = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"oracle on a {CROP['nx']}x{CROP['ny']}x{CROP['nz']}-cube crop of the wedge "
+                         f"({cells} cells), {st} steps"}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": f"ventricular wedge slab {dims['nx']}x{dims['ny']}x{dims['nz']} cubes "
+                                      f"of {dims['h']} mm x 6 tets, TP06 endo/M/epi, fibres -60..+60 deg",
+                          "cells": N, "nodes": info["n_nodes"], "dt_ms": case.dt,
+                          "precision": "FP32 with FP64 [Na]i/[K]i/[Ca]SR accumulation",
+                          "l2": f"inputs larger than L2 ({info['device_bytes'] / 1e9:.2f} GB resident, "
+                                f"~{(CELL_BYTES * N + node_bytes) / 1e9:.2f} GB moved per step > 126 MB)",
+                          "parallelism": f"replicas x{world}", "graph_replay": True},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+               "gpu_launches": 2 * args.steps, "fp64_plain": fp64,
+               "speedup_vs_fp64_plain": value / world / fp64["value"], "state_finite": finite}
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,261 @@
+/*
+ * ep.h - C ABI of the B300 monodomain finite-volume library.
+ *
+ * The library advances the operator-split monodomain equation on a
+ * tetrahedral cell-centred finite-volume mesh, the method of Del Corso,
+ * Verzicco & Viola, "A fast computational model for the electrophysiology of
+ * the whole human heart":
+ *
+ *   dV_c/dt = (1/V_c) sum_{j=1..4} A_fj (D_fj grad v_fj) . n_fj  -  I_ion(V_c, s_c)  -  I_s,c
+ *
+ * (Eq. 7 divided by chi C_m V_c, with D = M / (chi C_m) in mm^2/ms and the
+ * currents in uA/uF), the face gradient built from inverse-distance node
+ * values, Gauss-Green cell gradients and the directional-derivative
+ * correction of Eq. 8 (Sec. 3.2), the conductivity tensor rotated into the
+ * fibre frame (Eqs. 2-3), and the cell state advanced by Rush-Larsen for the
+ * gating variables and forward Euler for everything else (Sec. 3.2), with the
+ * stimulus of Eq. 4. A 1D vertex-based finite-volume Purkinje graph (Sec. 3.2)
+ * couples to the myocardium at junctions (Sec. 3.3).
+ *
+ * Units everywhere: length mm, time ms, potential mV, current uA/uF,
+ * diffusivity mm^2/ms, concentration mM.
+ *
+ * Conventions common to every entry point
+ *   - Return value: EP_OK (0) or one of the negative-free error codes below;
+ *     no C++ exception ever crosses this interface. On error the call has no
+ *     effect and ep_last_error() describes it.
+ *   - Host buffers passed in belong to the caller and are copied before the
+ *     call returns; host buffers passed out are written before it returns.
+ *   - Device memory belongs to the library. It is obtained through the
+ *     context's allocator callbacks (for example a framework's caching
+ *     allocator), or from cudaMalloc when none are given, and returned
+ *     through them by ep_job_destroy / ep_context_destroy.
+ *   - Cell and node arrays passed in or out are in the CALLER's numbering;
+ *     the library renumbers internally (reverse Cuthill-McKee) and undoes it.
+ *   - Threading: a context and its jobs are used by one host thread at a time.
+ *     Device work is enqueued on the context's stream and is asynchronous,
+ *     except where an entry point says it synchronises.
+ */
+#ifndef EP_H
+#define EP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+enum {
+    EP_OK = 0,
+    EP_EINVAL = 1,      /* bad argument (NULL pointer, size mismatch, out-of-range id) */
+    EP_ENOMEM = 2,      /* the allocator callback (or cudaMalloc) returned no memory */
+    EP_EMESH = 3,       /* degenerate tet, node index out of range, face shared by >2 tets */
+    EP_EUNSTABLE = 4,   /* dt above the explicit stability bound of the diffusion operator */
+    EP_ENONFINITE = 5,  /* a NaN/Inf was found in the state */
+    EP_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
+    EP_ECUDA = 7,       /* a CUDA runtime call failed (message in ep_last_error) */
+    EP_ESTATE = 8       /* call not valid in the object's current state (e.g. no params set) */
+};
+
+/* ---- cell models (Sec. 3.1) ---- */
+enum {
+    EP_TP06 = 0,        /* ten Tusscher-Panfilov 2006 ventricular myocyte, 19 state variables */
+    EP_CRN = 1,         /* Courtemanche-Ramirez-Nattel 1998 atrial myocyte, 21 state variables */
+    EP_STEWART = 2      /* Stewart et al. 2009 Purkinje cell, 20 state variables */
+};
+#define EP_N_MODELS 3
+
+/* ---- arithmetic of a job ---- */
+enum {
+    EP_FP32_MIXED = 0,  /* FP32 gates, currents, V and diffusion; [Na]i, [K]i and the
+                           SR calcium accumulated in FP64 */
+    EP_FP64_PLAIN = 1   /* everything in FP64 */
+};
+
+/* ---- Purkinje-muscle junction coupling (Sec. 3.3) ---- */
+enum {
+    EP_PMJ_RESISTIVE = 0, /* current (V_p - V_m)/R into both sides, scaled by each side's capacitance */
+    EP_PMJ_TRIGGERED = 1  /* threshold crossing at one side stimulates the other after a delay */
+};
+
+#define EP_MAX_PARAM_SETS 16
+#define EP_MAX_STIMULI 8
+#define EP_VAR_V 0        /* variable 0 of every model is the transmembrane potential */
+
+typedef struct ep_context ep_context;
+typedef struct ep_job ep_job;
+
+/* Device allocator callbacks. alloc returns a device pointer aligned to at
+ * least 256 bytes, or NULL when out of memory; free releases it. */
+typedef void *(*ep_alloc_fn)(size_t bytes, void *user);
+typedef void (*ep_free_fn)(void *ptr, size_t bytes, void *user);
+
+/* Mesh of one job. xyz: 3*n_nodes doubles (mm), node k at xyz[3k..3k+2].
+ * tet: 4*n_cells node indices; either orientation is accepted (the library
+ * orders each tet positively). cell_model: n_cells bytes, EP_TP06 / EP_CRN /
+ * EP_STEWART, or NULL for all EP_TP06. param_set: n_cells bytes indexing
+ * ep_params.sets, or NULL for all 0. stim_mask: n_cells bytes, bit k set
+ * = stimulus protocol k covers the cell, or NULL for none. fibre: 3*n_cells
+ * doubles, the fibre direction of each cell (need not be normalised), or
+ * NULL for isotropic tissue with diffusivity D_l. */
+typedef struct {
+    int64_t n_nodes;
+    const double *xyz;
+    int64_t n_cells;
+    const int32_t *tet;
+    const uint8_t *cell_model;
+    const uint8_t *param_set;
+    const uint8_t *stim_mask;
+    const double *fibre;
+} ep_mesh_desc;
+
+/* Parameters of one parameter set. variant (TP06 only): 0 epicardial,
+ * 1 mid-myocardial (M), 2 endocardial. D_l, D_t: monodomain diffusivity
+ * along and across the fibre, mm^2/ms (Eq. 7: D = M/(chi C_m), M the half
+ * harmonic mean of the intra- and extracellular conductivities). gks_scale,
+ * gkr_scale multiply the maximal I_Ks and I_Kr conductances; K_o is the
+ * extracellular potassium concentration (mM). */
+typedef struct {
+    int32_t variant;
+    int32_t reserved;
+    double D_l, D_t;
+    double gks_scale, gkr_scale;
+    double K_o;
+} ep_cell_params;
+
+/* Stimulus protocol (Eq. 4): amplitude (uA/uF, negative depolarises, it
+ * enters the equation like I_ion), onset, duration, period (ms; period 0 = one
+ * pulse). Times are rounded to whole steps: on at step n when
+ * n >= round(t_on/dt) and (n - round(t_on/dt)) mod round(period/dt) <
+ * round(duration/dt). */
+typedef struct {
+    double amplitude, t_on, duration, period;
+} ep_stimulus;
+
+typedef struct {
+    double dt;                          /* time step, ms */
+    int32_t precision;                  /* EP_FP32_MIXED or EP_FP64_PLAIN */
+    int32_t n_sets;                     /* 1..EP_MAX_PARAM_SETS */
+    ep_cell_params sets[EP_MAX_PARAM_SETS];
+    int32_t n_stim;                     /* 0..EP_MAX_STIMULI */
+    int32_t reserved;
+    ep_stimulus stim[EP_MAX_STIMULI];
+    double threshold;                   /* activation threshold, mV (Sec. 4 uses 0 mV) */
+} ep_params;
+
+/* ---------------------------------------------------------------------- */
+
+/* Create a context bound to one CUDA device (the current one) and stream.
+ * alloc/free may both be NULL (then cudaMalloc/cudaFree are used); user is
+ * passed back to them. cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream). *out receives the context. Errors: EP_EINVAL, EP_ECUDA. */
+int ep_context_create(ep_alloc_fn alloc, ep_free_fn free_fn, void *user,
+                      void *cuda_stream, ep_context **out);
+
+/* Change the stream later work is enqueued on. */
+int ep_context_set_stream(ep_context *ctx, void *cuda_stream);
+
+/* Destroys the context; every job of the context must have been destroyed. */
+int ep_context_destroy(ep_context *ctx);
+
+/* Text of the last error on this context (never NULL; "" when none). With a
+ * NULL context, the last error of a failed ep_context_create. */
+const char *ep_last_error(const ep_context *ctx);
+
+/* Build one job's mesh (Sec. 3.2): validate the tets, order them positively,
+ * match faces, renumber cells and nodes in reverse Cuthill-McKee order
+ * (grouped by cell model), build the node-to-cell table of the
+ * inverse-distance interpolation and upload the topology. Synchronises.
+ * Errors: EP_EINVAL, EP_EMESH, EP_ENOMEM, EP_ECUDA. */
+int ep_mesh_create(ep_context *ctx, const ep_mesh_desc *desc, ep_job **out);
+
+/* Set (or replace) the job's parameters: precision, dt, parameter sets,
+ * stimuli, threshold. Computes in FP64 the geometry, the conductivity
+ * tensors (Eqs. 2-3) and the folded per-cell flux coefficients of Eqs. 7-8,
+ * rounds them once to the job's precision and uploads them. On the first
+ * call (or when the precision changes) it also allocates the state and sets
+ * it to each model's published resting state, the activation times to +inf
+ * and the step counter to 0. Rejects a dt at or above the explicit stability
+ * bound of the diffusion operator with EP_EUNSTABLE. Synchronises. */
+int ep_params_set(ep_job *job, const ep_params *params);
+
+/* Advance n_jobs jobs of one context by n_steps time steps each. All jobs are
+ * advanced together: every step is one node-value launch and one fused
+ * cell launch covering every resident cell of every job of the same
+ * precision. Repeated calls with the same job list replay a captured CUDA
+ * graph. Asynchronous on the context's stream. Errors: EP_EINVAL (jobs of
+ * another context, repeated job, job without params), EP_ECUDA. */
+int ep_step(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps);
+
+/* Copy variable var of cell model `model` to host_out (n = number of cells,
+ * caller's order). Cells of another model receive NaN, except for
+ * EP_VAR_V, which every cell has. Synchronises the context's stream. */
+int ep_read_state(ep_job *job, int32_t model, int32_t var, double *host_out, int64_t n);
+
+/* Overwrite variable var of cells of `model` from host_in (n cells, caller's
+ * order; entries of cells of other models are ignored, except for EP_VAR_V).
+ * With ep_read_state and ep_set_step_index this checkpoints and resumes a job
+ * exactly. Synchronises. */
+int ep_write_state(ep_job *job, int32_t model, int32_t var, const double *host_in, int64_t n);
+
+/* Activation times (ms): the first upward crossing of the threshold,
+ * t^n + dt (theta - V^n)/(V^{n+1} - V^n) (Sec. 4); +inf where the cell has not
+ * activated. n = number of cells, caller's order. Synchronises. */
+int ep_activation_times(ep_job *job, double *host_out, int64_t n);
+
+/* Reset activation times to +inf (a new beat). Asynchronous. */
+int ep_reset_activation(ep_job *job);
+
+/* Steps taken so far (synchronises) / set the step counter (t^n = n dt). */
+int ep_step_index(ep_job *job, int64_t *out);
+int ep_set_step_index(ep_job *job, int64_t n);
+
+/* Scan the job's state for NaN/Inf on the device. Returns EP_OK or
+ * EP_ENONFINITE. Synchronises. */
+int ep_check_finite(ep_job *job);
+
+/* Job information: cells, nodes, interior faces, device bytes held. */
+int ep_job_info(const ep_job *job, int64_t *n_cells, int64_t *n_nodes,
+                int64_t *n_interior_faces, int64_t *device_bytes);
+
+/* Device bytes a job of this size would hold (planner estimate used for
+ * admission by free memory). */
+int64_t ep_estimate_bytes(int64_t n_cells, int64_t n_nodes, int32_t precision);
+
+/* Release the job's device memory (after its queued work completes). */
+int ep_job_destroy(ep_job *job);
+
+/* Profiling hook: advance the jobs by n_steps with direct launches (no
+ * graph), recording CUDA events on the context's stream around each launch,
+ * and return the mean device time per step of the node-value kernel and of
+ * the fused cell kernel (ms, summed over the jobs' precision groups).
+ * Synchronises. The results equal those of ep_step. */
+int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double *node_ms, double *cell_ms);
+
+/* Host-only inspection of the planner (no device work, no GPU needed): run
+ * the mesh ingest and the FP64 coefficient folding of ep_mesh_create +
+ * ep_params_set and return the folded operator, so that it can be checked
+ * against a face-by-face evaluation of Eqs. 7-8. Output arrays are
+ * caller-allocated: cell_order[n_cells] (internal position -> caller cell),
+ * tet/opp/nbr/wa/wb/q[4 n_cells] in internal numbering (opp/nbr -1 on the
+ * boundary), n2c_ptr[n_nodes + 1], n2c[4 n_cells], nw[4 n_cells] (node ->
+ * cell inverse-distance weights). The diffusion term of internal cell c is
+ *   sum_k wa[4c+k] vn[tet[4c+k]] + wb[4c+k] vn[opp[4c+k]] + q[4c+k] (V[nbr[4c+k]] - V[c]),
+ *   vn[n] = sum_{j in [n2c_ptr[n], n2c_ptr[n+1])} nw[j] V[n2c[j]].
+ * *rho_bound receives the Gershgorin bound of the operator's spectral radius.
+ * Any output pointer may be NULL. */
+int ep_plan_inspect(const ep_mesh_desc *desc, const ep_params *params, int64_t *cell_order, int32_t *tet,
+                    int32_t *opp, int32_t *nbr, double *wa, double *wb, double *q, int64_t *n2c_ptr,
+                    int32_t *n2c, double *nw, double *rho_bound);
+
+/* Number of state variables of a model and the name of each
+ * (e.g. "V", "Ca_i", "Na_i", "m"). */
+int32_t ep_model_nvar(int32_t model);
+const char *ep_model_varname(int32_t model, int32_t var);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EP_H */

@@ -1,0 +1,826 @@
+// C-ABI entry points (include/ep.h): contexts, jobs, batched stepping with
+// CUDA-graph replay, state transfer. Host-side runtime only; every step of
+// the method runs in the kernels of kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <set>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ep.h"
+#include "devtypes.h"
+#include "kernels.h"
+#include "planner.h"
+#include "varmap.h"
+
+using namespace ep;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+constexpr int kGraphSteps = 32;       // steps per captured graph
+constexpr int kGraphMinSteps = 64;    // below this, launch directly
+
+struct Plan {
+    std::vector<ep_job *> jobs;
+    std::vector<uint64_t> versions;
+    struct Group {
+        int precision;
+        int n_jobs;
+        DevBuf jobtab, node_tiles, cell_tiles, done;
+        StepLaunch L;
+    };
+    std::vector<Group> groups;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+};
+
+}  // namespace
+
+struct ep_context {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;
+    ep_alloc_fn alloc = nullptr;
+    ep_free_fn free_fn = nullptr;
+    void *user = nullptr;
+    std::string err;
+    std::set<ep_job *> jobs;
+    std::vector<std::unique_ptr<Plan>> plans;
+    int sm_count = 148;
+};
+
+struct ep_job {
+    ep_context *ctx = nullptr;
+    HostMesh mesh;
+    Sell sell;
+    bool has_params = false;
+    ep_params params{};
+    int precision = -1;
+    uint64_t version = 1;
+    DevJob dj{};
+    DevBuf dj_dev;
+    DevBuf step_dev;
+    const int *perm_dev = nullptr;  // internal cell -> caller cell
+    std::vector<DevBuf> topo;     // precision-independent device arrays
+    std::vector<DevBuf> prec;     // precision-dependent device arrays
+    std::vector<Tile> cell_tiles, node_tiles;
+    int64_t device_bytes = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(ep_context *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(ep_context *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, EP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int dalloc(ep_context *ctx, size_t bytes, DevBuf *b) {
+    bytes = std::max<size_t>(bytes, 256);
+    void *p = nullptr;
+    if (ctx->alloc) {
+        p = ctx->alloc(bytes, ctx->user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (!p) return fail(ctx, EP_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    b->p = p;
+    b->bytes = bytes;
+    return EP_OK;
+}
+
+void dfree(ep_context *ctx, DevBuf *b) {
+    if (!b->p) return;
+    if (ctx->free_fn) ctx->free_fn(b->p, b->bytes, ctx->user);
+    else cudaFree(b->p);
+    b->p = nullptr;
+    b->bytes = 0;
+}
+
+template <class T>
+int upload(ep_context *ctx, const std::vector<T> &v, std::vector<DevBuf> *pool, void **out) {
+    DevBuf b;
+    int rc = dalloc(ctx, v.size() * sizeof(T), &b);
+    if (rc) return rc;
+    pool->push_back(b);
+    if (!v.empty()) {
+        cudaError_t e = cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
+        e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
+    }
+    *out = b.p;
+    return EP_OK;
+}
+
+void free_plan(ep_context *ctx, Plan *p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (auto &g : p->groups) {
+        dfree(ctx, &g.jobtab);
+        dfree(ctx, &g.node_tiles);
+        dfree(ctx, &g.cell_tiles);
+        dfree(ctx, &g.done);
+    }
+}
+
+void drop_plans_with(ep_context *ctx, ep_job *job) {
+    auto &pl = ctx->plans;
+    for (size_t i = 0; i < pl.size();) {
+        if (std::find(pl[i]->jobs.begin(), pl[i]->jobs.end(), job) != pl[i]->jobs.end()) {
+            free_plan(ctx, pl[i].get());
+            pl.erase(pl.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+void free_job_arrays(ep_job *j, std::vector<DevBuf> *pool) {
+    for (auto &b : *pool) dfree(j->ctx, &b);
+    pool->clear();
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Tiles of at most kCellThreads consecutive cells inside one model region,
+// kNodeThreads consecutive nodes (starting on a 32-node slice).
+void build_tiles(ep_job *j) {
+    j->cell_tiles.clear();
+    j->node_tiles.clear();
+    for (int m = 0; m < EP_N_MODELS; ++m)
+        for (int64_t s = j->mesh.model_off[m]; s < j->mesh.model_off[m + 1]; s += kCellThreads)
+            j->cell_tiles.push_back(Tile{0, m, int(s), int(std::min<int64_t>(kCellThreads, j->mesh.model_off[m + 1] - s))});
+    for (int64_t s = 0; s < j->mesh.n_nodes; s += kNodeThreads)
+        j->node_tiles.push_back(Tile{0, 0, int(s), int(std::min<int64_t>(kNodeThreads, j->mesh.n_nodes - s))});
+}
+
+}  // namespace
+
+extern "C" {
+
+int ep_context_create(ep_alloc_fn alloc, ep_free_fn free_fn, void *user, void *cuda_stream, ep_context **out) {
+    if (!out || (alloc == nullptr) != (free_fn == nullptr)) {
+        g_create_error = "ep_context_create: out is NULL or only one of alloc/free given";
+        return EP_EINVAL;
+    }
+    try {
+        auto *ctx = new ep_context();
+        cudaError_t e = cudaGetDevice(&ctx->device);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            g_create_error = std::string("ep_context_create: ") + cudaGetErrorString(e);
+            delete ctx;
+            return EP_ECUDA;
+        }
+        ctx->alloc = alloc;
+        ctx->free_fn = free_fn;
+        ctx->user = user;
+        ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+        *out = ctx;
+        return EP_OK;
+    } catch (...) {
+        g_create_error = "ep_context_create: out of host memory";
+        return EP_ENOMEM;
+    }
+}
+
+int ep_context_set_stream(ep_context *ctx, void *cuda_stream) {
+    if (!ctx) return EP_EINVAL;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    return EP_OK;
+}
+
+int ep_context_destroy(ep_context *ctx) {
+    if (!ctx) return EP_EINVAL;
+    if (!ctx->jobs.empty()) return fail(ctx, EP_ESTATE, "ep_context_destroy: jobs still alive");
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &p : ctx->plans) free_plan(ctx, p.get());
+    ctx->plans.clear();
+    if (ctx->capture) cudaStreamDestroy(ctx->capture);
+    delete ctx;
+    return EP_OK;
+}
+
+const char *ep_last_error(const ep_context *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+int32_t ep_model_nvar(int32_t model) { return model_nvar(model); }
+
+const char *ep_model_varname(int32_t model, int32_t var) {
+    if (var < 0 || var >= model_nvar(model)) return nullptr;
+    return model_vars(model)[var].name;
+}
+
+int64_t ep_estimate_bytes(int64_t n_cells, int64_t n_nodes, int32_t precision) {
+    const int64_t r = precision == EP_FP64_PLAIN ? 8 : 4;
+    // topology: nodes_a/b, nbr (3 int4), pset, smask, sell columns (~4.3 per cell)
+    int64_t b = n_cells * (48 + 2) + int64_t(4.4 * n_cells) * 4;
+    // coefficients (3 x vec4), V x2, act, sell weights, node values
+    b += n_cells * (12 * r + 3 * r) + int64_t(4.4 * n_cells) * r + n_nodes * r;
+    // state: up to 16 compute-type + 4 FP64 variables
+    b += n_cells * (16 * r + 4 * 8);
+    return b + (1 << 20);
+}
+
+int ep_mesh_create(ep_context *ctx, const ep_mesh_desc *desc, ep_job **out) {
+    if (!ctx || !desc || !out) return fail(ctx, EP_EINVAL, "ep_mesh_create: NULL argument");
+    DeviceGuard g(ctx->device);
+    try {
+        std::unique_ptr<ep_job> j(new ep_job());
+        j->ctx = ctx;
+        std::string err;
+        int rc = build_mesh(desc, &j->mesh, &err);
+        if (rc) return fail(ctx, rc, err);
+        build_sell(j->mesh, &j->sell);
+        const HostMesh &m = j->mesh;
+        const int64_t N = m.n_cells;
+        std::vector<int4> na(N), nb(N), nc(N);
+        for (int64_t c = 0; c < N; ++c) {
+            const int32_t *t = &m.tet[4 * c];
+            na[c] = make_int4(t[0], t[1], t[2], t[3]);
+            int o[4], q[4];
+            for (int k = 0; k < 4; ++k) {
+                o[k] = m.opp[4 * c + k] >= 0 ? m.opp[4 * c + k] : t[0];
+                q[k] = m.nbr[4 * c + k] >= 0 ? m.nbr[4 * c + k] : int(c);
+            }
+            nb[c] = make_int4(o[0], o[1], o[2], o[3]);
+            nc[c] = make_int4(q[0], q[1], q[2], q[3]);
+        }
+        void *p;
+        if ((rc = upload(ctx, na, &j->topo, &p))) return rc;
+        j->dj.nodes_a = static_cast<const int4 *>(p);
+        if ((rc = upload(ctx, nb, &j->topo, &p))) return rc;
+        j->dj.nodes_b = static_cast<const int4 *>(p);
+        if ((rc = upload(ctx, nc, &j->topo, &p))) return rc;
+        j->dj.nbr = static_cast<const int4 *>(p);
+        if ((rc = upload(ctx, m.pset, &j->topo, &p))) return rc;
+        j->dj.pset = static_cast<const uint8_t *>(p);
+        if ((rc = upload(ctx, m.smask, &j->topo, &p))) return rc;
+        j->dj.smask = static_cast<const uint8_t *>(p);
+        std::vector<long long> sp(j->sell.slice_ptr.begin(), j->sell.slice_ptr.end());
+        if ((rc = upload(ctx, sp, &j->topo, &p))) return rc;
+        j->dj.slice_ptr = static_cast<const long long *>(p);
+        if ((rc = upload(ctx, j->sell.col, &j->topo, &p))) return rc;
+        j->dj.ncol = static_cast<const int *>(p);
+        if ((rc = upload(ctx, m.cell_new2old, &j->topo, &p))) return rc;
+        j->perm_dev = static_cast<const int *>(p);
+        DevBuf b;
+        if ((rc = dalloc(ctx, sizeof(long long), &b))) return rc;
+        j->step_dev = b;
+        cudaMemsetAsync(b.p, 0, sizeof(long long), ctx->stream);
+        j->dj.step = static_cast<long long *>(b.p);
+        if ((rc = dalloc(ctx, sizeof(DevJob), &b))) return rc;
+        j->dj_dev = b;
+        j->dj.n_cells = N;
+        j->dj.n_nodes = m.n_nodes;
+        build_tiles(j.get());
+        for (auto &t : j->topo) j->device_bytes += t.bytes;
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_mesh_create");
+        ctx->jobs.insert(j.get());
+        *out = j.release();
+        return EP_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(ctx, EP_ENOMEM, "ep_mesh_create: out of host memory");
+    }
+}
+
+int ep_params_set(ep_job *job, const ep_params *p) {
+    if (!job || !p) return EP_EINVAL;
+    ep_context *ctx = job->ctx;
+    if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return fail(ctx, EP_EINVAL, "ep_params_set: dt must be > 0");
+    if (p->precision != EP_FP32_MIXED && p->precision != EP_FP64_PLAIN)
+        return fail(ctx, EP_EINVAL, "ep_params_set: unknown precision");
+    if (p->n_sets < 1 || p->n_sets > EP_MAX_PARAM_SETS || p->n_stim < 0 || p->n_stim > EP_MAX_STIMULI)
+        return fail(ctx, EP_EINVAL, "ep_params_set: n_sets must be 1..16 and n_stim 0..8");
+    for (int s = 0; s < p->n_sets; ++s) {
+        const ep_cell_params &c = p->sets[s];
+        if (!(c.D_l >= 0.0) || !(c.D_t >= 0.0) || !(c.K_o > 0.0) || c.variant < 0 || c.variant > 2)
+            return fail(ctx, EP_EINVAL, "ep_params_set: bad parameter set " + std::to_string(s));
+    }
+    DeviceGuard g(ctx->device);
+    try {
+        std::string err;
+        Coeffs cf;
+        int rc = build_coeffs(job->mesh, p, &cf, &err);
+        if (rc) return fail(ctx, rc, err);
+        // explicit stability of the diffusion part: dt * rho(L) < 2
+        double rho = cf.gershgorin;
+        if (p->dt * rho >= 1.9) rho = 1.05 * power_radius(job->mesh, cf, 60);
+        if (p->dt * rho >= 2.0)
+            return fail(ctx, EP_EUNSTABLE,
+                        "ep_params_set: dt = " + std::to_string(p->dt) + " ms exceeds the explicit stability bound " +
+                            std::to_string(2.0 / rho) + " ms of the diffusion operator");
+        const bool fresh = !job->has_params || job->precision != p->precision;
+        cudaStreamSynchronize(ctx->stream);
+        drop_plans_with(ctx, job);
+        const HostMesh &m = job->mesh;
+        const int64_t N = m.n_cells;
+        std::vector<DevBuf> newprec;
+        DevJob dj = job->dj;
+        auto put = [&](auto &vec, void **dst) { return upload(ctx, vec, &newprec, dst); };
+        auto coeff_upload = [&](const std::vector<double> &v, const void **dst) -> int {
+            void *q = nullptr;
+            int r;
+            if (p->precision == EP_FP64_PLAIN) {
+                r = put(v, &q);
+            } else {
+                std::vector<float> f(v.begin(), v.end());
+                r = put(f, &q);
+            }
+            *dst = q;
+            return r;
+        };
+        std::vector<double> nwd(job->sell.col.size());
+        for (size_t k = 0; k < nwd.size(); ++k) nwd[k] = job->sell.src[k] >= 0 ? cf.nw[job->sell.src[k]] : 0.0;
+        if ((rc = coeff_upload(cf.wa, &dj.wa)) || (rc = coeff_upload(cf.wb, &dj.wb)) || (rc = coeff_upload(cf.q, &dj.q)) ||
+            (rc = coeff_upload(nwd, &dj.nw))) {
+            for (auto &b : newprec) dfree(ctx, &b);
+            return rc;
+        }
+        std::vector<DevBuf> keep;
+        if (fresh) {
+            const size_t r = p->precision == EP_FP64_PLAIN ? 8 : 4;
+            DevBuf b;
+            auto grab = [&](size_t bytes, void **dst) {
+                int r2 = dalloc(ctx, bytes, &b);
+                if (!r2) {
+                    newprec.push_back(b);
+                    *dst = b.p;
+                }
+                return r2;
+            };
+            rc = grab(N * r, &dj.V[0]);
+            if (!rc) rc = grab(N * r, &dj.V[1]);
+            if (!rc) rc = grab(N * r, &dj.act);
+            if (!rc) rc = grab(m.n_nodes * r, &dj.vn);
+            for (int md = 0; md < EP_N_MODELS && !rc; ++md) {
+                DevRegion &rg = dj.reg[md];
+                rg.off = m.model_off[md];
+                rg.n = m.model_off[md + 1] - m.model_off[md];
+                rg.stride = round_up(std::max<int64_t>(rg.n, 1), 64);
+                rg.r = nullptr;
+                rg.a = nullptr;
+                if (rg.n == 0) continue;
+                void *q = nullptr;
+                rc = grab(size_t(model_nr(md)) * rg.stride * r, &rg.r);
+                if (!rc) rc = grab(size_t(model_na(md)) * rg.stride * 8, &q);
+                rg.a = static_cast<double *>(q);
+            }
+            if (rc) {
+                for (auto &bb : newprec) dfree(ctx, &bb);
+                return rc;
+            }
+        } else {
+            // keep the state arrays (V, act, vn, regions): they are the last entries of prec
+            // coefficient arrays of the previous call are replaced
+        }
+        // parameters and stimuli
+        for (int s = 0; s < EP_MAX_PARAM_SETS; ++s) {
+            const ep_cell_params &c = p->sets[s < p->n_sets ? s : 0];
+            dj.params[s] = DevParams{c.variant, 0, c.gks_scale, c.gkr_scale, c.K_o};
+        }
+        dj.n_stim = p->n_stim;
+        for (int k = 0; k < p->n_stim; ++k) {
+            const ep_stimulus &s = p->stim[k];
+            dj.stim[k] = DevStim{s.amplitude, std::llround(s.t_on / p->dt), std::llround(s.duration / p->dt),
+                                 std::llround(s.period / p->dt)};
+        }
+        dj.precision = p->precision;
+        dj.dt = p->dt;
+        dj.threshold = p->threshold;
+        // swap in: coefficient arrays always new; state arrays new only when fresh
+        if (fresh) {
+            free_job_arrays(job, &job->prec);
+            job->prec = newprec;
+        } else {
+            // replace the 4 coefficient buffers (first 4 of prec), keep state buffers
+            for (int k = 0; k < 4; ++k) dfree(ctx, &job->prec[k]);
+            for (int k = 0; k < 4; ++k) job->prec[k] = newprec[k];
+        }
+        job->dj = dj;
+        cudaError_t e = cudaMemcpyAsync(job->dj_dev.p, &job->dj, sizeof(DevJob), cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_params_set");
+        if (fresh) {
+            cudaMemsetAsync(job->step_dev.p, 0, sizeof(long long), ctx->stream);
+            e = launch_init(p->precision, static_cast<const DevJob *>(job->dj_dev.p), N, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_params_set: init");
+        }
+        e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_params_set");
+        job->params = *p;
+        job->precision = p->precision;
+        job->has_params = true;
+        job->version++;
+        job->device_bytes = 0;
+        for (auto &t : job->topo) job->device_bytes += t.bytes;
+        for (auto &t : job->prec) job->device_bytes += t.bytes;
+        return EP_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(ctx, EP_ENOMEM, "ep_params_set: out of host memory");
+    }
+}
+
+static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
+    pl->jobs.assign(jobs, jobs + n);
+    for (int i = 0; i < n; ++i) pl->versions.push_back(jobs[i]->version);
+    for (int prec : {EP_FP32_MIXED, EP_FP64_PLAIN}) {
+        std::vector<DevJob> tab;
+        std::vector<Tile> nt, ct;
+        for (int i = 0; i < n; ++i) {
+            if (jobs[i]->precision != prec) continue;
+            const int jid = int(tab.size());
+            tab.push_back(jobs[i]->dj);
+            for (Tile t : jobs[i]->node_tiles) nt.push_back(Tile{jid, t.model, t.start, t.count});
+            for (Tile t : jobs[i]->cell_tiles) ct.push_back(Tile{jid, t.model, t.start, t.count});
+        }
+        if (tab.empty()) continue;
+        Plan::Group g{};
+        g.precision = prec;
+        g.n_jobs = int(tab.size());
+        std::vector<DevBuf> tmp;
+        void *p;
+        int rc;
+        if ((rc = upload(ctx, tab, &tmp, &p))) return rc;
+        g.jobtab = tmp.back();
+        if ((rc = upload(ctx, nt, &tmp, &p))) return rc;
+        g.node_tiles = tmp.back();
+        if ((rc = upload(ctx, ct, &tmp, &p))) return rc;
+        g.cell_tiles = tmp.back();
+        if ((rc = dalloc(ctx, sizeof(unsigned), &g.done))) return rc;
+        cudaMemsetAsync(g.done.p, 0, sizeof(unsigned), ctx->stream);
+        g.L.jobs = static_cast<const DevJob *>(g.jobtab.p);
+        g.L.n_jobs = g.n_jobs;
+        g.L.node_tiles = static_cast<const Tile *>(g.node_tiles.p);
+        g.L.n_node_tiles = int(nt.size());
+        g.L.cell_tiles = static_cast<const Tile *>(g.cell_tiles.p);
+        g.L.n_cell_tiles = int(ct.size());
+        g.L.done = static_cast<unsigned *>(g.done.p);
+        g.L.node_grid = std::max(1, std::min<int>(int(nt.size()), ctx->sm_count * node_blocks_per_sm(prec)));
+        g.L.cell_grid = std::max(1, std::min<int>(int(ct.size()), ctx->sm_count * cell_blocks_per_sm(prec)));
+        pl->groups.push_back(g);
+    }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? EP_OK : cuda_fail(ctx, e, "plan");
+}
+
+static cudaError_t enqueue_steps(Plan *pl, int64_t steps, cudaStream_t s) {
+    for (int64_t it = 0; it < steps; ++it)
+        for (auto &g : pl->groups) {
+            cudaError_t e = launch_step(g.precision, g.L, s);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+static int check_jobs(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, const char *who) {
+    ep_context *ctx = jobs[0]->ctx;
+    if (n_steps < 0) return fail(ctx, EP_EINVAL, std::string(who) + ": n_steps < 0");
+    for (int i = 0; i < n_jobs; ++i) {
+        if (!jobs[i] || jobs[i]->ctx != ctx) return fail(ctx, EP_EINVAL, std::string(who) + ": jobs of different contexts");
+        if (!jobs[i]->has_params) return fail(ctx, EP_ESTATE, std::string(who) + ": a job has no parameters");
+        for (int k = 0; k < i; ++k)
+            if (jobs[k] == jobs[i]) return fail(ctx, EP_EINVAL, std::string(who) + ": job listed twice");
+    }
+    return EP_OK;
+}
+
+// The cached plan (job tables, tiles, graph) of this exact job list, built on first use.
+static int get_plan(ep_context *ctx, ep_job *const *jobs, int32_t n_jobs, Plan **out) {
+    for (size_t k = 0; k < ctx->plans.size(); ++k) {
+        Plan *p = ctx->plans[k].get();
+        if (int(p->jobs.size()) != n_jobs || !std::equal(p->jobs.begin(), p->jobs.end(), jobs)) continue;
+        bool same = true;
+        for (int i = 0; i < n_jobs; ++i) same = same && p->versions[i] == jobs[i]->version;
+        if (same) {
+            *out = p;
+            return EP_OK;
+        }
+        free_plan(ctx, p);
+        ctx->plans.erase(ctx->plans.begin() + k);
+        break;
+    }
+    std::unique_ptr<Plan> np(new Plan());
+    int rc = build_plan(ctx, jobs, n_jobs, np.get());
+    if (rc) {
+        free_plan(ctx, np.get());
+        return rc;
+    }
+    if (ctx->plans.size() >= 8) {
+        free_plan(ctx, ctx->plans.front().get());
+        ctx->plans.erase(ctx->plans.begin());
+    }
+    ctx->plans.push_back(std::move(np));
+    *out = ctx->plans.back().get();
+    return EP_OK;
+}
+
+int ep_step(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps) {
+    if (!jobs || n_jobs <= 0 || !jobs[0]) return EP_EINVAL;
+    ep_context *ctx = jobs[0]->ctx;
+    int rc = check_jobs(jobs, n_jobs, n_steps, "ep_step");
+    if (rc) return rc;
+    if (n_steps == 0) return EP_OK;
+    DeviceGuard g(ctx->device);
+    try {
+        Plan *pl = nullptr;
+        if ((rc = get_plan(ctx, jobs, n_jobs, &pl))) return rc;
+        int64_t left = n_steps;
+        if (n_steps >= kGraphMinSteps) {
+            if (!pl->exec) {
+                cudaError_t e = cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t e2 = enqueue_steps(pl, kGraphSteps, ctx->capture);
+                    e = cudaStreamEndCapture(ctx->capture, &pl->graph);
+                    if (e2 != cudaSuccess) e = e2;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_step: graph capture");
+            }
+            for (; left >= kGraphSteps; left -= kGraphSteps) {
+                cudaError_t e = cudaGraphLaunch(pl->exec, ctx->stream);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_step: graph launch");
+            }
+        }
+        cudaError_t e = enqueue_steps(pl, left, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_step: launch");
+        return EP_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(ctx, EP_ENOMEM, "ep_step: out of host memory");
+    }
+}
+
+int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double *node_ms, double *cell_ms) {
+    if (!jobs || n_jobs <= 0 || !jobs[0] || !node_ms || !cell_ms) return EP_EINVAL;
+    ep_context *ctx = jobs[0]->ctx;
+    int rc = check_jobs(jobs, n_jobs, n_steps, "ep_time_kernels");
+    if (rc) return rc;
+    *node_ms = *cell_ms = 0.0;
+    if (n_steps == 0) return EP_OK;
+    DeviceGuard g(ctx->device);
+    try {
+        Plan *pl = nullptr;
+        if ((rc = get_plan(ctx, jobs, n_jobs, &pl))) return rc;
+        const size_t ng = pl->groups.size();
+        std::vector<cudaEvent_t> ev(3 * ng * n_steps, nullptr);
+        cudaError_t e = cudaSuccess;
+        for (auto &x : ev)
+            if (e == cudaSuccess) e = cudaEventCreate(&x);
+        size_t k = 0;
+        for (int64_t it = 0; it < n_steps && e == cudaSuccess; ++it)
+            for (auto &gr : pl->groups) {
+                e = cudaEventRecord(ev[k++], ctx->stream);
+                if (e == cudaSuccess) e = launch_node(gr.precision, gr.L, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(ev[k++], ctx->stream);
+                if (e == cudaSuccess) e = launch_cell(gr.precision, gr.L, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(ev[k++], ctx->stream);
+            }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        double tn = 0.0, tc = 0.0;
+        for (size_t i = 0; i + 2 < k + 1 && e == cudaSuccess; i += 3) {
+            float a = 0.f, b = 0.f;
+            e = cudaEventElapsedTime(&a, ev[i], ev[i + 1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[i + 1], ev[i + 2]);
+            tn += a;
+            tc += b;
+        }
+        for (auto &x : ev)
+            if (x) cudaEventDestroy(x);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_time_kernels");
+        *node_ms = tn / double(n_steps);
+        *cell_ms = tc / double(n_steps);
+        return EP_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(ctx, EP_ENOMEM, "ep_time_kernels: out of host memory");
+    }
+}
+
+static int check_io(ep_job *job, int64_t n, const void *buf) {
+    if (!job) return EP_EINVAL;
+    if (!buf || n != job->mesh.n_cells)
+        return fail(job->ctx, EP_EINVAL, "buffer is NULL or its length differs from the number of cells");
+    if (!job->has_params) return fail(job->ctx, EP_ESTATE, "job has no parameters (no state yet)");
+    return EP_OK;
+}
+
+static int transfer_state(ep_job *job, int32_t model, int32_t var, double *host, int64_t n, bool write) {
+    int rc = check_io(job, n, host);
+    if (rc) return rc;
+    ep_context *ctx = job->ctx;
+    if (model < 0 || model >= EP_N_MODELS || var < 0 || var >= model_nvar(model))
+        return fail(ctx, EP_EINVAL, "unknown model or variable id");
+    DeviceGuard g(ctx->device);
+    DevBuf b;
+    if ((rc = dalloc(ctx, n * sizeof(double), &b))) return rc;
+    cudaError_t e = cudaSuccess;
+    const DevJob *dj = static_cast<const DevJob *>(job->dj_dev.p);
+    double *buf = static_cast<double *>(b.p);
+    if (write) {
+        e = cudaMemcpyAsync(buf, host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = launch_scatter(job->precision, dj, job->perm_dev, n, model, var, buf, ctx->stream);
+    } else {
+        e = launch_gather(job->precision, dj, job->perm_dev, n, model, var, buf, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host, buf, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, &b);
+    return e == cudaSuccess ? EP_OK : cuda_fail(ctx, e, write ? "ep_write_state" : "ep_read_state");
+}
+
+int ep_read_state(ep_job *job, int32_t model, int32_t var, double *host_out, int64_t n) {
+    try {
+        return transfer_state(job, model, var, host_out, n, false);
+    } catch (const std::bad_alloc &) {
+        return fail(job->ctx, EP_ENOMEM, "ep_read_state: out of host memory");
+    }
+}
+
+int ep_write_state(ep_job *job, int32_t model, int32_t var, const double *host_in, int64_t n) {
+    try {
+        return transfer_state(job, model, var, const_cast<double *>(host_in), n, true);
+    } catch (const std::bad_alloc &) {
+        return fail(job->ctx, EP_ENOMEM, "ep_write_state: out of host memory");
+    }
+}
+
+int ep_activation_times(ep_job *job, double *host_out, int64_t n) {
+    int rc = check_io(job, n, host_out);
+    if (rc) return rc;
+    ep_context *ctx = job->ctx;
+    DeviceGuard g(ctx->device);
+    DevBuf b;
+    if ((rc = dalloc(ctx, n * sizeof(double), &b))) return rc;
+    cudaError_t e = launch_gather_act(job->precision, static_cast<const DevJob *>(job->dj_dev.p), job->perm_dev, n,
+                                      static_cast<double *>(b.p), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, b.p, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, &b);
+    return e == cudaSuccess ? EP_OK : cuda_fail(ctx, e, "ep_activation_times");
+}
+
+int ep_reset_activation(ep_job *job) {
+    if (!job) return EP_EINVAL;
+    if (!job->has_params) return fail(job->ctx, EP_ESTATE, "job has no parameters");
+    DeviceGuard g(job->ctx->device);
+    cudaError_t e = launch_reset_act(job->precision, static_cast<const DevJob *>(job->dj_dev.p), job->mesh.n_cells,
+                                     job->ctx->stream);
+    return e == cudaSuccess ? EP_OK : cuda_fail(job->ctx, e, "ep_reset_activation");
+}
+
+int ep_step_index(ep_job *job, int64_t *out) {
+    if (!job || !out) return EP_EINVAL;
+    DeviceGuard g(job->ctx->device);
+    long long v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, job->step_dev.p, sizeof(v), cudaMemcpyDeviceToHost, job->ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(job->ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(job->ctx, e, "ep_step_index");
+    *out = v;
+    return EP_OK;
+}
+
+int ep_set_step_index(ep_job *job, int64_t n) {
+    if (!job || n < 0) return EP_EINVAL;
+    DeviceGuard g(job->ctx->device);
+    // V lives in buffer (step & 1): move it when the parity changes
+    int64_t cur = 0;
+    int rc = ep_step_index(job, &cur);
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    if (job->has_params && ((cur ^ n) & 1)) {
+        const size_t bytes = job->mesh.n_cells * (job->precision == EP_FP64_PLAIN ? 8 : 4);
+        e = cudaMemcpyAsync(job->dj.V[n & 1], job->dj.V[cur & 1], bytes, cudaMemcpyDeviceToDevice, job->ctx->stream);
+    }
+    long long v = n;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(job->step_dev.p, &v, sizeof(v), cudaMemcpyHostToDevice, job->ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(job->ctx->stream);
+    return e == cudaSuccess ? EP_OK : cuda_fail(job->ctx, e, "ep_set_step_index");
+}
+
+int ep_check_finite(ep_job *job) {
+    if (!job) return EP_EINVAL;
+    if (!job->has_params) return fail(job->ctx, EP_ESTATE, "job has no parameters");
+    ep_context *ctx = job->ctx;
+    DeviceGuard g(ctx->device);
+    DevBuf b;
+    int rc = dalloc(ctx, sizeof(unsigned), &b);
+    if (rc) return rc;
+    unsigned cnt = 0;
+    cudaError_t e = cudaMemsetAsync(b.p, 0, sizeof(unsigned), ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_check_finite(job->precision, static_cast<const DevJob *>(job->dj_dev.p), job->mesh.n_cells,
+                                static_cast<unsigned *>(b.p), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, b.p, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, &b);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_check_finite");
+    if (cnt) return fail(ctx, EP_ENONFINITE, std::to_string(cnt) + " non-finite state values");
+    return EP_OK;
+}
+
+int ep_job_info(const ep_job *job, int64_t *n_cells, int64_t *n_nodes, int64_t *n_interior_faces,
+                int64_t *device_bytes) {
+    if (!job) return EP_EINVAL;
+    if (n_cells) *n_cells = job->mesh.n_cells;
+    if (n_nodes) *n_nodes = job->mesh.n_nodes;
+    if (n_interior_faces) *n_interior_faces = job->mesh.n_interior_faces;
+    if (device_bytes) *device_bytes = job->device_bytes;
+    return EP_OK;
+}
+
+int ep_job_destroy(ep_job *job) {
+    if (!job) return EP_EINVAL;
+    ep_context *ctx = job->ctx;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    drop_plans_with(ctx, job);
+    free_job_arrays(job, &job->prec);
+    free_job_arrays(job, &job->topo);
+    dfree(ctx, &job->dj_dev);
+    dfree(ctx, &job->step_dev);
+    ctx->jobs.erase(job);
+    delete job;
+    return EP_OK;
+}
+
+int ep_plan_inspect(const ep_mesh_desc *desc, const ep_params *params, int64_t *cell_order, int32_t *tet,
+                    int32_t *opp, int32_t *nbr, double *wa, double *wb, double *q, int64_t *n2c_ptr,
+                    int32_t *n2c, double *nw, double *rho_bound) {
+    if (!desc || !params) {
+        g_create_error = "ep_plan_inspect: NULL argument";
+        return EP_EINVAL;
+    }
+    try {
+        HostMesh m;
+        std::string err;
+        int rc = build_mesh(desc, &m, &err);
+        if (!rc) {
+            Coeffs cf;
+            if (params->n_sets < 1 || params->n_sets > EP_MAX_PARAM_SETS) {
+                err = "ep_plan_inspect: n_sets must be 1..16";
+                rc = EP_EINVAL;
+            } else {
+                rc = build_coeffs(m, params, &cf, &err);
+            }
+            if (!rc) {
+                const int64_t N = m.n_cells;
+                auto cp = [](auto *dst, const auto &src) {
+                    if (dst) std::copy(src.begin(), src.end(), dst);
+                };
+                if (cell_order)
+                    for (int64_t i = 0; i < N; ++i) cell_order[i] = m.cell_new2old[i];
+                cp(tet, m.tet);
+                cp(opp, m.opp);
+                cp(nbr, m.nbr);
+                cp(wa, cf.wa);
+                cp(wb, cf.wb);
+                cp(q, cf.q);
+                cp(n2c_ptr, m.n2c_ptr);
+                cp(n2c, m.n2c);
+                cp(nw, cf.nw);
+                if (rho_bound) *rho_bound = cf.gershgorin;
+                return EP_OK;
+            }
+        }
+        g_create_error = err;
+        return rc;
+    } catch (const std::bad_alloc &) {
+        g_create_error = "ep_plan_inspect: out of host memory";
+        return EP_ENOMEM;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,171 @@
+// Device cell model: Courtemanche, Ramirez & Nattel 1998 human atrial
+// myocyte (Sec. 3.1, atria and 1D bundles). One step: currents at
+// (V^n, s^n), the 15 gates by Rush-Larsen, the concentrations by forward
+// Euler with the model's differential buffering factors; [Na]i, [K]i and the
+// SR compartments (Ca_up, Ca_rel) accumulated in FP64 (Sec. 3.2).
+//
+// Storage: compute-type slots 0 Ca_i, 1 m, 2 h, 3 j, 4 oa, 5 oi, 6 ua, 7 ui,
+// 8 xr, 9 xs, 10 d, 11 f, 12 fCa, 13 u, 14 v, 15 w; FP64 slots 0 Na_i, 1 K_i,
+// 2 Ca_up, 3 Ca_rel.
+#pragma once
+#include "cellmath.cuh"
+#include "devtypes.h"
+
+namespace ep {
+
+constexpr int kCRNnr = 16, kCRNna = 4;
+
+// x / (1 - exp(-x/k)) and x / (exp(x/k) - 1), both equal to k at x = 0.
+template <class R>
+__device__ __forceinline__ R lin_over_1mexp(R x, R k) {
+    const R y = x / k;
+    return y == R(0) ? k : k * y / (-fexpm1(-y));
+}
+template <class R>
+__device__ __forceinline__ R lin_over_expm1(R x, R k) {
+    const R y = x / k;
+    return y == R(0) ? k : k * y / fexpm1(y);
+}
+
+template <class R>
+__device__ __forceinline__ R crn_step(const DevRegion &rg, long long i, const DevParams &P, R V, R dt) {
+    R *x = static_cast<R *>(rg.r) + i;
+    double *a = rg.a + i;
+    const long long st = rg.stride;
+    const R Cai = x[0], m = x[st], h = x[2 * st], jj = x[3 * st], oa = x[4 * st], oi = x[5 * st];
+    const R ua = x[6 * st], ui = x[7 * st], xr = x[8 * st], xs = x[9 * st], d = x[10 * st];
+    const R f = x[11 * st], fCa = x[12 * st], u = x[13 * st], vv = x[14 * st], w = x[15 * st];
+    const double Nai64 = a[0], Ki64 = a[st], Caup64 = a[2 * st], Carel64 = a[3 * st];
+    const R Nai = R(Nai64), Ki = R(Ki64), Caup = R(Caup64), Carel = R(Carel64);
+
+    const R Fc = R(96.4867);
+    const R RTF = R(8.3143 * 310.0 / 96.4867), FRT = R(96.4867 / (8.3143 * 310.0));
+    const R Cm = R(100), Vi = R(13668), Vup = R(1109.52), Vrel = R(96.48);
+    const R Nao = R(140), Cao = R(1.8), Ko = R(P.K_o);
+
+    const R ENa = RTF * flog(Nao / Nai);
+    const R EK = RTF * flog(Ko / Ki);
+    const R ECa = R(0.5) * RTF * flog(Cao / Cai);
+
+    const R INa = R(7.8) * m * m * m * h * jj * (V - ENa);
+    const R IK1 = R(0.09) * (V - EK) * logistic(R(0.07) * (V + R(80)));
+    const R Ito = R(0.1652) * oa * oa * oa * oi * (V - EK);
+    const R gKur = R(0.005) + R(0.05) * logistic(-(V - R(15)) * R(1.0 / 13.0));
+    const R IKur = gKur * ua * ua * ua * ui * (V - EK);
+    const R IKr = R(0.0294) * R(P.gkr_scale) * xr * (V - EK) * logistic((V + R(15)) * R(1.0 / 22.4));
+    const R IKs = R(0.129) * R(P.gks_scale) * xs * xs * (V - EK);
+    const R ICaL = R(0.1238) * d * f * fCa * (V - R(65));
+    const R sigma = (fexp(Nao * R(1.0 / 67.3)) - R(1)) * R(1.0 / 7.0);
+    const R fNaK = R(1) / (R(1) + R(0.1245) * fexp(R(-0.1) * V * FRT) + R(0.0365) * sigma * fexp(-V * FRT));
+    const R rN = R(10) / Nai;
+    const R INaK = R(0.59933874) * fNaK / (R(1) + rN * fsqrt(rN)) * Ko / (Ko + R(1.5));
+    const R egm1 = fexp(R(-0.65) * V * FRT);
+    const R INaCa = R(1600) * (fexp(R(0.35) * V * FRT) * Nai * Nai * Nai * Cao - egm1 * Nao * Nao * Nao * Cai) /
+                    ((R(87.5 * 87.5 * 87.5) + Nao * Nao * Nao) * (R(1.38) + Cao) * (R(1) + R(0.1) * egm1));
+    const R IbCa = R(0.00113) * (V - ECa);
+    const R IbNa = R(0.000674) * (V - ENa);
+    const R IpCa = R(0.275) * Cai / (R(0.0005) + Cai);
+    const R Iion = INa + IK1 + Ito + IKur + IKr + IKs + ICaL + INaK + INaCa + IbCa + IbNa + IpCa;
+
+    const R Irel = R(30) * u * u * vv * w * (Carel - Cai);
+    const R Itr = (Caup - Carel) * R(1.0 / 180.0);
+    const R Iup = R(0.005) / (R(1) + R(0.00092) / Cai);
+    const R Iupleak = R(0.005) * Caup * R(1.0 / 15.0);
+
+    const R dNai = (R(-3) * INaK - R(3) * INaCa - IbNa - INa) * (Cm / (Vi * Fc));
+    const R dKi = (R(2) * INaK - IK1 - Ito - IKur - IKr - IKs) * (Cm / (Vi * Fc));
+    const R B1 = (R(2) * INaCa - IpCa - ICaL - IbCa) * (Cm / (R(2) * Vi * Fc)) + (Vup * (Iupleak - Iup) + Irel * Vrel) / Vi;
+    const R B2 = R(1) + R(0.07 * 0.0005) / ((Cai + R(0.0005)) * (Cai + R(0.0005))) +
+                 R(0.05 * 0.00238) / ((Cai + R(0.00238)) * (Cai + R(0.00238)));
+    const R dCaup = Iup - Iupleak - Itr * (Vrel / Vup);
+    const R dCarel = (Itr - Irel) / (R(1) + R(10 * 0.8) / ((Carel + R(0.8)) * (Carel + R(0.8))));
+
+    // ---- gates ----
+    R al, be;
+    al = R(0.32) * lin_over_1mexp(V + R(47.13), R(10));
+    be = R(0.08) * fexp(-V * R(1.0 / 11.0));
+    x[st] = rush_larsen(m, al / (al + be), R(1) / (al + be), dt);
+    if (V >= R(-40)) {
+        al = R(0);
+        be = R(1) / (R(0.13) * (R(1) + fexp(-(V + R(10.66)) * R(1.0 / 11.1))));
+    } else {
+        al = R(0.135) * fexp(-(V + R(80)) * R(1.0 / 6.8));
+        be = R(3.56) * fexp(R(0.079) * V) + R(3.1e5) * fexp(R(0.35) * V);
+    }
+    x[2 * st] = rush_larsen(h, al / (al + be), R(1) / (al + be), dt);
+    if (V >= R(-40)) {
+        al = R(0);
+        be = R(0.3) * fexp(R(-2.535e-7) * V) * logistic(R(-0.1) * (V + R(32)));
+    } else {
+        al = (R(-127140) * fexp(R(0.2444) * V) - R(3.474e-5) * fexp(R(-0.04391) * V)) * (V + R(37.78)) *
+             logistic(R(0.311) * (V + R(79.23)));
+        be = R(0.1212) * fexp(R(-0.01052) * V) * logistic(R(-0.1378) * (V + R(40.14)));
+    }
+    x[3 * st] = rush_larsen(jj, al / (al + be), R(1) / (al + be), dt);
+    // oa and ua share their rate functions
+    al = R(0.65) / (fexp(-(V + R(10)) * R(1.0 / 8.5)) + fexp(-(V - R(30)) * R(1.0 / 59.0)));
+    be = R(0.65) / (R(2.5) + fexp((V + R(82)) * R(1.0 / 17.0)));
+    const R tau_a = R(1) / ((al + be) * R(3));
+    x[4 * st] = rush_larsen(oa, logistic(-(V + R(20.47)) * R(1.0 / 17.54)), tau_a, dt);
+    x[6 * st] = rush_larsen(ua, logistic(-(V + R(30.3)) * R(1.0 / 9.6)), tau_a, dt);
+    al = R(1) / (R(18.53) + fexp((V + R(113.7)) * R(1.0 / 10.95)));
+    be = R(1) / (R(35.56) + fexp(-(V + R(1.26)) * R(1.0 / 7.44)));
+    x[5 * st] = rush_larsen(oi, logistic((V + R(43.1)) * R(1.0 / 5.3)), R(1) / ((al + be) * R(3)), dt);
+    al = R(1) / (R(21) + fexp(-(V - R(185)) * R(1.0 / 28.0)));
+    be = fexp((V - R(158)) * R(1.0 / 16.0));
+    x[7 * st] = rush_larsen(ui, logistic((V - R(99.45)) * R(1.0 / 27.48)), R(1) / ((al + be) * R(3)), dt);
+    al = R(0.0003) * lin_over_1mexp(V + R(14.1), R(5));
+    be = R(7.3898e-5) * lin_over_expm1(V - R(3.3328), R(5.1237));
+    x[8 * st] = rush_larsen(xr, logistic(-(V + R(14.1)) * R(1.0 / 6.5)), R(1) / (al + be), dt);
+    al = R(4e-5) * lin_over_1mexp(V - R(19.9), R(17));
+    be = R(3.5e-5) * lin_over_expm1(V - R(19.9), R(9));
+    x[9 * st] = rush_larsen(xs, R(1) / fsqrt(R(1) + fexp(-(V - R(19.9)) * R(1.0 / 12.7))), R(0.5) / (al + be), dt);
+    {
+        const R yv = (V + R(10)) * R(1.0 / 6.24);
+        const R g = yv == R(0) ? R(1) : -fexpm1(-yv) / yv;
+        const R tau = g / (R(6.24 * 0.035) * (R(1) + fexp(-yv)));
+        x[10 * st] = rush_larsen(d, logistic(-(V + R(10)) * R(0.125)), tau, dt);
+    }
+    {
+        const R tau = R(9) / (R(0.0197) * fexp(R(-0.0337 * 0.0337) * (V + R(10)) * (V + R(10))) + R(0.02));
+        x[11 * st] = rush_larsen(f, logistic((V + R(28)) * R(1.0 / 6.9)), tau, dt);
+    }
+    x[12 * st] = rush_larsen(fCa, R(1) / (R(1) + Cai * R(1.0 / 0.00035)), R(2), dt);
+    {
+        const R Fn = R(1e-12) * Vrel * Irel - R(5e-13) / Fc * (R(0.5) * ICaL - R(0.2) * INaCa) * Cm;
+        const R su = logistic(-(Fn - R(3.4175e-13)) * R(1.0 / 13.67e-16));
+        x[13 * st] = rush_larsen(u, su, R(8), dt);
+        const R vinf = R(1) - logistic(-(Fn - R(6.835e-14)) * R(1.0 / 13.67e-16));
+        x[14 * st] = rush_larsen(vv, vinf, R(1.91) + R(2.09) * su, dt);
+        const R yw = (V - R(7.9)) * R(0.2);
+        const R g = yw == R(0) ? R(1) : -fexpm1(-yw) / yw;
+        const R tau = R(6) * g / (R(5) * (R(1) + R(0.3) * fexp(-yw)));
+        x[15 * st] = rush_larsen(w, R(1) - logistic(-(V - R(40)) * R(1.0 / 17.0)), tau, dt);
+    }
+
+    // ---- concentrations ----
+    x[0] = Cai + dt * (B1 / B2);
+    a[0] = Nai64 + double(dt * dNai);
+    a[st] = Ki64 + double(dt * dKi);
+    a[2 * st] = Caup64 + double(dt * dCaup);
+    a[3 * st] = Carel64 + double(dt * dCarel);
+    return Iion;
+}
+
+template <class R>
+__device__ __forceinline__ void crn_init(const DevRegion &rg, long long i, R *V) {
+    R *x = static_cast<R *>(rg.r) + i;
+    double *a = rg.a + i;
+    const long long st = rg.stride;
+    *V = R(-81.18);
+    const R v[kCRNnr] = {R(1.013e-4), R(2.908e-3), R(9.649e-1), R(9.775e-1), R(3.043e-2), R(9.992e-1),
+                         R(4.966e-3), R(9.986e-1), R(3.296e-5), R(1.869e-2), R(1.367e-4), R(9.996e-1),
+                         R(7.755e-1), R(0), R(1), R(9.992e-1)};
+    for (int k = 0; k < kCRNnr; ++k) x[k * st] = v[k];
+    a[0] = 11.17;
+    a[st] = 139.0;
+    a[2 * st] = 1.488;
+    a[3 * st] = 1.488;
+}
+
+}  // namespace ep

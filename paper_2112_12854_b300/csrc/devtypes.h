@@ -1,0 +1,69 @@
+// Plain-data structures shared by the host runtime and the kernels: one
+// DevJob per resident job (the job table of the batched launch) and the tile
+// tables that map thread blocks onto cells and nodes.
+#pragma once
+#include <cstdint>
+#include <vector_types.h>
+
+#include "../../include/ep.h"
+
+namespace ep {
+
+// Stimulus protocol in whole steps (Eq. 4).
+struct DevStim {
+    double amp;
+    long long n_on, n_dur, n_per;
+};
+
+struct DevParams {
+    int variant;
+    int pad;
+    double gks_scale, gkr_scale, K_o;
+};
+
+// State of the cells of one cell model inside a job: n_r arrays of the
+// job's compute type (float or double) followed, in a second allocation, by
+// n_a double arrays. Variable v of local cell i is r[v * stride + i].
+struct DevRegion {
+    void *r;
+    double *a;
+    long long stride;
+    long long off;   // first cell of the region in the job's numbering
+    long long n;
+};
+
+struct DevJob {
+    const int4 *nodes_a;      // the cell's 4 vertices
+    const int4 *nodes_b;      // vertex of the neighbour opposite each face (own vertex 0 on the boundary)
+    const int4 *nbr;          // neighbour across each face (the cell itself on the boundary)
+    const void *wa, *wb, *q;  // float4 or double4 per cell (folded Eqs. 7-8 coefficients / V_c)
+    const uint8_t *pset;
+    const uint8_t *smask;
+    void *V[2];               // double-buffered transmembrane potential
+    void *vn;                 // node values (scratch of the step)
+    void *act;                // activation times
+    const long long *slice_ptr;  // sliced-ELL node -> cell table
+    const int *ncol;
+    const void *nw;
+    long long n_cells, n_nodes;
+    DevRegion reg[EP_N_MODELS];
+    DevParams params[EP_MAX_PARAM_SETS];
+    DevStim stim[EP_MAX_STIMULI];
+    int n_stim;
+    int precision;
+    double dt, threshold;
+    long long *step;          // steps taken (device counter)
+};
+
+// A tile is a run of consecutive cells (or nodes) of one job and one model.
+struct Tile {
+    int job;
+    int model;
+    int start;
+    int count;
+};
+
+constexpr int kCellThreads = 256;
+constexpr int kNodeThreads = 256;
+
+}  // namespace ep

@@ -1,0 +1,306 @@
+// Device kernels of the monodomain finite-volume step (Sec. 3.2).
+//
+// One step of every resident job is two launches:
+//   node_kernel  S1: v_n = sum_k w_nk V_k over the cells around each node
+//                (inverse-distance weights, sliced-ELL table, coalesced);
+//   cell_kernel  S2 + S3 + the cell model, fused: the diffusion term of
+//                Eqs. 7-8 from eight node values and four neighbour
+//                potentials with folded FP64-derived coefficients, then the
+//                cell model (Rush-Larsen / forward Euler at (V^n, s^n)),
+//                the stimulus of Eq. 4, V^{n+1} and the activation time.
+// Both kernels are persistent (grid-stride over tiles of one job and one
+// model) and serve every job of the batch in one launch. The last block of
+// the cell launch advances the jobs' step counters, which select the V
+// buffer (double-buffered by step parity) and the time t^n = n dt.
+#include <cmath>
+
+#include "crncell.cuh"
+#include "kernels.h"
+#include "ttcells.cuh"
+#include "varmap.h"
+
+namespace ep {
+
+template <class R> struct Vec4T;
+template <> struct Vec4T<float> { using type = float4; };
+template <> struct Vec4T<double> { using type = double4_32a; };
+
+template <class R>
+__device__ __forceinline__ R stimulus(const DevJob &J, unsigned mask, long long n) {
+    R is = R(0);
+    for (int k = 0; k < J.n_stim; ++k) {
+        if (!((mask >> k) & 1u)) continue;
+        const DevStim &s = J.stim[k];
+        bool on;
+        if (n < s.n_on) on = false;
+        else if (s.n_per <= 0) on = n < s.n_on + s.n_dur;
+        else on = ((n - s.n_on) % s.n_per) < s.n_dur;
+        if (on) is += R(s.amp);
+    }
+    return is;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kNodeThreads) node_kernel(const DevJob *__restrict__ jobs,
+                                                            const Tile *__restrict__ tiles, int n_tiles) {
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        const DevJob &J = jobs[tl.job];
+        const int i = threadIdx.x;
+        if (i >= tl.count) continue;
+        const long long node = (long long)tl.start + i;
+        const long long n = *J.step;
+        const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
+        const R *__restrict__ w = static_cast<const R *>(J.nw);
+        const long long s = node >> 5;
+        const long long b = J.slice_ptr[s] + (node & 31), e = J.slice_ptr[s + 1];
+        R acc = R(0);
+        for (long long k = b; k < e; k += 32) acc += w[k] * V[J.ncol[k]];
+        static_cast<R *>(J.vn)[node] = acc;
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void cell_update(const DevJob &J, int model, long long c) {
+    using R4 = typename Vec4T<R>::type;
+    const long long n = *J.step;
+    const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
+    R *__restrict__ Vnext = static_cast<R *>(J.V[(n & 1) ^ 1]);
+    const R *__restrict__ vn = static_cast<const R *>(J.vn);
+    const int4 na = J.nodes_a[c], nb = J.nodes_b[c], nc = J.nbr[c];
+    const R4 wa = static_cast<const R4 *>(J.wa)[c];
+    const R4 wb = static_cast<const R4 *>(J.wb)[c];
+    const R4 q = static_cast<const R4 *>(J.q)[c];
+    const R Vc = V[c];
+    // diffusion term of Eq. 7 (S2 + S3 folded): eight node values, four neighbours
+    R diff = wa.x * vn[na.x] + wa.y * vn[na.y] + wa.z * vn[na.z] + wa.w * vn[na.w];
+    diff += wb.x * vn[nb.x] + wb.y * vn[nb.y] + wb.z * vn[nb.z] + wb.w * vn[nb.w];
+    diff += q.x * (V[nc.x] - Vc) + q.y * (V[nc.y] - Vc) + q.z * (V[nc.z] - Vc) + q.w * (V[nc.w] - Vc);
+
+    const unsigned mask = J.smask[c];
+    const R is = mask ? stimulus<R>(J, mask, n) : R(0);
+    const DevParams &P = J.params[J.pset[c]];
+    const R dt = R(J.dt);
+    const DevRegion &rg = J.reg[model];
+    const long long li = c - rg.off;
+    R iion;
+    if (model == EP_TP06) iion = tt_step<R, false>(rg, li, P, Vc, dt, is);
+    else if (model == EP_STEWART) iion = tt_step<R, true>(rg, li, P, Vc, dt, is);
+    else iion = crn_step<R>(rg, li, P, Vc, dt);
+    const R Vn = Vc + dt * (diff - iion - is);
+    Vnext[c] = Vn;
+    const R th = R(J.threshold);
+    if (Vc < th && Vn >= th) {
+        R *act = static_cast<R *>(J.act);
+        if (isinf(act[c])) act[c] = R(double(n) * J.dt) + dt * (th - Vc) / (Vn - Vc);
+    }
+}
+
+template <class R>
+__global__ void __launch_bounds__(kCellThreads) cell_kernel(const DevJob *__restrict__ jobs,
+                                                            const Tile *__restrict__ tiles, int n_tiles,
+                                                            unsigned *done, int n_jobs) {
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        if (threadIdx.x < tl.count) cell_update<R>(jobs[tl.job], tl.model, (long long)tl.start + threadIdx.x);
+    }
+    // Every block has read the step counters; the last one to finish advances them.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(done, 1u);
+        if (prev == gridDim.x - 1) {
+            for (int j = 0; j < n_jobs; ++j) *jobs[j].step += 1;
+            *done = 0u;
+            __threadfence();
+        }
+    }
+}
+
+template <class R>
+__global__ void init_kernel(const DevJob *__restrict__ job, long long n_cells) {
+    const DevJob &J = *job;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n_cells;
+         c += (long long)gridDim.x * blockDim.x) {
+        int model = 0;
+        while (model < EP_N_MODELS - 1 && c >= J.reg[model].off + J.reg[model].n) ++model;
+        const DevRegion &rg = J.reg[model];
+        R v;
+        if (model == EP_TP06) tt_init<R, false>(rg, c - rg.off, &v);
+        else if (model == EP_STEWART) tt_init<R, true>(rg, c - rg.off, &v);
+        else crn_init<R>(rg, c - rg.off, &v);
+        static_cast<R *>(J.V[0])[c] = v;
+        static_cast<R *>(J.V[1])[c] = v;
+        static_cast<R *>(J.act)[c] = R(INFINITY);
+    }
+}
+
+struct DevVarLoc {
+    int kind, slot;
+};
+
+// out / in are in the caller's cell order: internal cell c is caller cell perm[c].
+template <class R>
+__global__ void gather_kernel(const DevJob *__restrict__ job, const int *__restrict__ perm, long long n_cells,
+                              int model, DevVarLoc loc, double *buf, int write) {
+    const DevJob &J = *job;
+    const long long n = *J.step;
+    R *V = static_cast<R *>(J.V[n & 1]);
+    const DevRegion &rg = J.reg[model];
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n_cells;
+         c += (long long)gridDim.x * blockDim.x) {
+        double &x = buf[perm[c]];
+        if (loc.kind == kVarV) {
+            if (write) V[c] = R(x);
+            else x = double(V[c]);
+            continue;
+        }
+        if (c < rg.off || c >= rg.off + rg.n) {
+            if (!write) x = NAN;
+            continue;
+        }
+        const long long i = c - rg.off;
+        if (loc.kind == kVarR) {
+            R *p = static_cast<R *>(rg.r) + loc.slot * rg.stride + i;
+            if (write) *p = R(x);
+            else x = double(*p);
+        } else {
+            double *p = rg.a + loc.slot * rg.stride + i;
+            if (write) *p = x;
+            else x = *p;
+        }
+    }
+}
+
+template <class R>
+__global__ void act_kernel(const DevJob *__restrict__ job, const int *__restrict__ perm, long long n_cells,
+                           double *out) {
+    R *act = static_cast<R *>(job->act);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n_cells;
+         c += (long long)gridDim.x * blockDim.x) {
+        if (out) out[perm[c]] = double(act[c]);
+        else act[c] = R(INFINITY);
+    }
+}
+
+template <class R>
+__global__ void finite_kernel(const DevJob *__restrict__ job, long long n_cells, unsigned *count) {
+    const DevJob &J = *job;
+    const long long n = *J.step;
+    const R *V = static_cast<const R *>(J.V[n & 1]);
+    unsigned bad = 0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n_cells;
+         c += (long long)gridDim.x * blockDim.x) {
+        if (!isfinite(V[c])) ++bad;
+        int model = 0;
+        while (model < EP_N_MODELS - 1 && c >= J.reg[model].off + J.reg[model].n) ++model;
+        const DevRegion &rg = J.reg[model];
+        const long long i = c - rg.off;
+        for (int k = 0; k < model_nr(model); ++k)
+            if (!isfinite(static_cast<const R *>(rg.r)[k * rg.stride + i])) ++bad;
+        for (int k = 0; k < model_na(model); ++k)
+            if (!isfinite(rg.a[k * rg.stride + i])) ++bad;
+    }
+    if (bad) atomicAdd(count, bad);
+}
+
+static int grid_for(long long n, int threads) {
+    long long g = (n + threads - 1) / threads;
+    return int(g < 1 ? 1 : (g > 148 * 16 ? 148 * 16 : g));
+}
+
+template <class R>
+static cudaError_t step_impl(const StepLaunch &L, cudaStream_t s) {
+    node_kernel<R><<<L.node_grid, kNodeThreads, 0, s>>>(L.jobs, L.node_tiles, L.n_node_tiles);
+    cell_kernel<R><<<L.cell_grid, kCellThreads, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done, L.n_jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(int precision, const StepLaunch &L, cudaStream_t s) {
+    return precision == EP_FP64_PLAIN ? step_impl<double>(L, s) : step_impl<float>(L, s);
+}
+
+cudaError_t launch_init(int precision, const DevJob *job, long long n_cells, cudaStream_t s) {
+    if (precision == EP_FP64_PLAIN) init_kernel<double><<<grid_for(n_cells, 256), 256, 0, s>>>(job, n_cells);
+    else init_kernel<float><<<grid_for(n_cells, 256), 256, 0, s>>>(job, n_cells);
+    return cudaGetLastError();
+}
+
+static cudaError_t gather_impl(int precision, const DevJob *job, const int *perm, long long n_cells, int model,
+                               int var, double *buf, int write, cudaStream_t s) {
+    const VarLoc &v = model_vars(model)[var];
+    DevVarLoc loc{v.kind, v.slot};
+    if (precision == EP_FP64_PLAIN)
+        gather_kernel<double><<<grid_for(n_cells, 256), 256, 0, s>>>(job, perm, n_cells, model, loc, buf, write);
+    else
+        gather_kernel<float><<<grid_for(n_cells, 256), 256, 0, s>>>(job, perm, n_cells, model, loc, buf, write);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(int precision, const DevJob *job, const int *perm, long long n_cells, int model, int var,
+                          double *out, cudaStream_t s) {
+    return gather_impl(precision, job, perm, n_cells, model, var, out, 0, s);
+}
+
+cudaError_t launch_scatter(int precision, const DevJob *job, const int *perm, long long n_cells, int model, int var,
+                           const double *in, cudaStream_t s) {
+    return gather_impl(precision, job, perm, n_cells, model, var, const_cast<double *>(in), 1, s);
+}
+
+cudaError_t launch_gather_act(int precision, const DevJob *job, const int *perm, long long n_cells, double *out,
+                              cudaStream_t s) {
+    if (precision == EP_FP64_PLAIN)
+        act_kernel<double><<<grid_for(n_cells, 256), 256, 0, s>>>(job, perm, n_cells, out);
+    else
+        act_kernel<float><<<grid_for(n_cells, 256), 256, 0, s>>>(job, perm, n_cells, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_act(int precision, const DevJob *job, long long n_cells, cudaStream_t s) {
+    return launch_gather_act(precision, job, nullptr, n_cells, nullptr, s);
+}
+
+cudaError_t launch_node(int precision, const StepLaunch &L, cudaStream_t s) {
+    if (precision == EP_FP64_PLAIN)
+        node_kernel<double><<<L.node_grid, kNodeThreads, 0, s>>>(L.jobs, L.node_tiles, L.n_node_tiles);
+    else
+        node_kernel<float><<<L.node_grid, kNodeThreads, 0, s>>>(L.jobs, L.node_tiles, L.n_node_tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell(int precision, const StepLaunch &L, cudaStream_t s) {
+    if (precision == EP_FP64_PLAIN)
+        cell_kernel<double><<<L.cell_grid, kCellThreads, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done,
+                                                                L.n_jobs);
+    else
+        cell_kernel<float><<<L.cell_grid, kCellThreads, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done,
+                                                               L.n_jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(int precision, const DevJob *job, long long n_cells, unsigned *count,
+                                cudaStream_t s) {
+    if (precision == EP_FP64_PLAIN) finite_kernel<double><<<grid_for(n_cells, 256), 256, 0, s>>>(job, n_cells, count);
+    else finite_kernel<float><<<grid_for(n_cells, 256), 256, 0, s>>>(job, n_cells, count);
+    return cudaGetLastError();
+}
+
+int cell_blocks_per_sm(int precision) {
+    int nb = 0;
+    if (precision == EP_FP64_PLAIN)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_kernel<double>, kCellThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_kernel<float>, kCellThreads, 0);
+    return nb < 1 ? 1 : nb;
+}
+
+int node_blocks_per_sm(int precision) {
+    int nb = 0;
+    if (precision == EP_FP64_PLAIN)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, node_kernel<double>, kNodeThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, node_kernel<float>, kNodeThreads, 0);
+    return nb < 1 ? 1 : nb;
+}
+
+}  // namespace ep

@@ -1,0 +1,51 @@
+// Launch wrappers of the device kernels (kernels.cu), callable from host C++.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "devtypes.h"
+
+namespace ep {
+
+struct StepLaunch {
+    const DevJob *jobs;        // device job table
+    int n_jobs;
+    const Tile *node_tiles;
+    int n_node_tiles;
+    const Tile *cell_tiles;
+    int n_cell_tiles;
+    unsigned *done;            // device counter used to advance the step counters
+    int node_grid, cell_grid;  // persistent grid sizes
+};
+
+// One time step of every job in the table: node values, then the fused
+// diffusion + cell-model + activation update.
+cudaError_t launch_step(int precision, const StepLaunch &L, cudaStream_t s);
+
+// Set the state of every cell to its model's resting state, activation
+// times to +inf (job given by a device pointer to its DevJob).
+cudaError_t launch_init(int precision, const DevJob *job, long long n_cells, cudaStream_t s);
+
+// The two launches of launch_step, separately (for timing).
+cudaError_t launch_node(int precision, const StepLaunch &L, cudaStream_t s);
+cudaError_t launch_cell(int precision, const StepLaunch &L, cudaStream_t s);
+
+// Copy variable `var` of `model` (all cells for var 0 = V) into out[n_cells]
+// in the caller's cell order (internal cell c -> out[perm[c]]; cells of other
+// models get NaN), and the reverse.
+cudaError_t launch_gather(int precision, const DevJob *job, const int *perm, long long n_cells, int model, int var,
+                          double *out, cudaStream_t s);
+cudaError_t launch_scatter(int precision, const DevJob *job, const int *perm, long long n_cells, int model, int var,
+                           const double *in, cudaStream_t s);
+cudaError_t launch_gather_act(int precision, const DevJob *job, const int *perm, long long n_cells, double *out,
+                              cudaStream_t s);
+cudaError_t launch_reset_act(int precision, const DevJob *job, long long n_cells, cudaStream_t s);
+
+// Count non-finite values of the job's state into *count (device int).
+cudaError_t launch_check_finite(int precision, const DevJob *job, long long n_cells, unsigned *count,
+                                cudaStream_t s);
+
+// Kernel attributes for sizing persistent grids.
+int cell_blocks_per_sm(int precision);
+int node_blocks_per_sm(int precision);
+
+}  // namespace ep

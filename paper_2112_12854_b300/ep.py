@@ -1,0 +1,353 @@
+"""Python binding of ``libep.so`` (include/ep.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module
+converts numpy arrays and Python values to the C structures, routes device
+allocations to PyTorch's caching allocator and passes PyTorch's current CUDA
+stream. If the library is missing it raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libep.so")
+
+EP_OK, EP_EINVAL, EP_ENOMEM, EP_EMESH, EP_EUNSTABLE, EP_ENONFINITE, EP_ETIMEOUT, EP_ECUDA, EP_ESTATE = range(9)
+EP_TP06, EP_CRN, EP_STEWART = 0, 1, 2
+EP_FP32_MIXED, EP_FP64_PLAIN = 0, 1
+MAX_SETS, MAX_STIM = 16, 8
+_STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "EMESH", 4: "EUNSTABLE", 5: "ENONFINITE", 6: "ETIMEOUT",
+           7: "ECUDA", 8: "ESTATE"}
+
+
+class EPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ep error {code} ({_STATUS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("xyz", ctypes.c_void_p), ("n_cells", ctypes.c_int64),
+                ("tet", ctypes.c_void_p), ("cell_model", ctypes.c_void_p), ("param_set", ctypes.c_void_p),
+                ("stim_mask", ctypes.c_void_p), ("fibre", ctypes.c_void_p)]
+
+
+class CellParams(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("reserved", ctypes.c_int32), ("D_l", ctypes.c_double),
+                ("D_t", ctypes.c_double), ("gks_scale", ctypes.c_double), ("gkr_scale", ctypes.c_double),
+                ("K_o", ctypes.c_double)]
+
+
+class Stimulus(ctypes.Structure):
+    _fields_ = [("amplitude", ctypes.c_double), ("t_on", ctypes.c_double), ("duration", ctypes.c_double),
+                ("period", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("precision", ctypes.c_int32), ("n_sets", ctypes.c_int32),
+                ("sets", CellParams * MAX_SETS), ("n_stim", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("stim", Stimulus * MAX_STIM), ("threshold", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+# every symbol declared in include/ep.h
+EXPORTS = ["ep_context_create", "ep_context_set_stream", "ep_context_destroy", "ep_last_error",
+           "ep_mesh_create", "ep_params_set", "ep_step", "ep_read_state", "ep_write_state",
+           "ep_activation_times", "ep_reset_activation", "ep_step_index", "ep_set_step_index",
+           "ep_check_finite", "ep_job_info", "ep_estimate_bytes", "ep_job_destroy", "ep_model_nvar",
+           "ep_model_varname", "ep_plan_inspect", "ep_time_kernels"]
+
+_lib = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+
+
+def load():
+    """Load libep.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run `python -m paper_2112_12854_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "ep_context_create": ([ALLOC_FN, FREE_FN, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+        "ep_context_set_stream": ([_P, _P], ctypes.c_int),
+        "ep_context_destroy": ([_P], ctypes.c_int),
+        "ep_last_error": ([_P], ctypes.c_char_p),
+        "ep_mesh_create": ([_P, ctypes.POINTER(MeshDesc), ctypes.POINTER(_P)], ctypes.c_int),
+        "ep_params_set": ([_P, ctypes.POINTER(Params)], ctypes.c_int),
+        "ep_step": ([ctypes.POINTER(_P), ctypes.c_int32, _I64], ctypes.c_int),
+        "ep_read_state": ([_P, ctypes.c_int32, ctypes.c_int32, _P, _I64], ctypes.c_int),
+        "ep_write_state": ([_P, ctypes.c_int32, ctypes.c_int32, _P, _I64], ctypes.c_int),
+        "ep_activation_times": ([_P, _P, _I64], ctypes.c_int),
+        "ep_reset_activation": ([_P], ctypes.c_int),
+        "ep_step_index": ([_P, ctypes.POINTER(_I64)], ctypes.c_int),
+        "ep_set_step_index": ([_P, _I64], ctypes.c_int),
+        "ep_check_finite": ([_P], ctypes.c_int),
+        "ep_job_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                         ctypes.POINTER(_I64)], ctypes.c_int),
+        "ep_estimate_bytes": ([_I64, _I64, ctypes.c_int32], _I64),
+        "ep_job_destroy": ([_P], ctypes.c_int),
+        "ep_model_nvar": ([ctypes.c_int32], ctypes.c_int32),
+        "ep_model_varname": ([ctypes.c_int32, ctypes.c_int32], ctypes.c_char_p),
+        "ep_time_kernels": ([ctypes.POINTER(_P), ctypes.c_int32, _I64, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "ep_plan_inspect": ([ctypes.POINTER(MeshDesc), ctypes.POINTER(Params)] + [_P] * 10
+                            + [ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def model_varnames(model: int) -> list[str]:
+    L = load()
+    return [L.ep_model_varname(model, k).decode() for k in range(L.ep_model_nvar(model))]
+
+
+def estimate_bytes(n_cells: int, n_nodes: int, precision: int = EP_FP32_MIXED) -> int:
+    return int(load().ep_estimate_bytes(n_cells, n_nodes, precision))
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Context:
+    """A library context on the current CUDA device. Device memory comes from
+    PyTorch's caching allocator (or cudaMalloc with ``torch_allocator=False``);
+    work is enqueued on ``stream`` (default: PyTorch's current stream)."""
+
+    def __init__(self, stream=None, torch_allocator: bool = True):
+        import torch
+        L = load()
+        self._torch = torch
+        self.device = torch.cuda.current_device()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self._stream_ptr = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        if torch_allocator:
+            dev, st = self.device, stream
+
+            def _alloc(nbytes, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
+                except Exception:  # out of memory: the library reports EP_ENOMEM
+                    return None
+
+            def _free(ptr, nbytes, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc, self._free = ALLOC_FN(_alloc), FREE_FN(_free)
+        else:
+            self._alloc, self._free = ctypes.cast(None, ALLOC_FN), ctypes.cast(None, FREE_FN)
+        h = _P()
+        rc = L.ep_context_create(self._alloc, self._free, None, self._stream_ptr, ctypes.byref(h))
+        if rc:
+            raise EPError(rc, L.ep_last_error(None).decode())
+        self._h = h
+        self.jobs = set()
+
+    def check(self, rc):
+        if rc:
+            raise EPError(rc, load().ep_last_error(self._h).decode())
+
+    def close(self):
+        for j in list(self.jobs):
+            j.destroy()
+        if getattr(self, "_h", None):
+            self.check(load().ep_context_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def mesh(self, xyz, tets, *, cell_model=None, param_set=None, stim_mask=None, fibre=None) -> "Job":
+        return Job(self, xyz, tets, cell_model=cell_model, param_set=param_set, stim_mask=stim_mask,
+                   fibre=fibre)
+
+
+def make_params(dt, sets, stimuli=(), *, precision=EP_FP32_MIXED, threshold=-20.0) -> Params:
+    """sets: objects with variant, D_l, D_t, gks_scale, gkr_scale, K_o;
+    stimuli: objects with amplitude, t_on, duration, period."""
+    p = Params()
+    p.dt = float(dt)
+    p.precision = int(precision)
+    p.n_sets = len(sets)
+    if not 1 <= len(sets) <= MAX_SETS or len(stimuli) > MAX_STIM:
+        raise ValueError("1..16 parameter sets and at most 8 stimuli")
+    for k, s in enumerate(sets):
+        p.sets[k] = CellParams(int(getattr(s, "variant", 0)), 0, float(s.D_l), float(s.D_t),
+                               float(getattr(s, "gks_scale", 1.0)), float(getattr(s, "gkr_scale", 1.0)),
+                               float(getattr(s, "K_o", 5.4)))
+    p.n_stim = len(stimuli)
+    for k, s in enumerate(stimuli):
+        p.stim[k] = Stimulus(float(s.amplitude), float(s.t_on), float(s.duration), float(getattr(s, "period", 0.0)))
+    p.threshold = float(threshold)
+    return p
+
+
+class Job:
+    def __init__(self, ctx: Context, xyz, tets, *, cell_model=None, param_set=None, stim_mask=None, fibre=None):
+        L = load()
+        self.ctx = ctx
+        self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        self._tets = np.ascontiguousarray(tets, dtype=np.int32)
+        n = self._tets.shape[0]
+        self._arrays = {}
+        d = MeshDesc()
+        d.n_nodes = self._xyz.shape[0]
+        d.xyz = _ptr(self._xyz)
+        d.n_cells = n
+        d.tet = _ptr(self._tets)
+        for name, arr, dt, width in (("cell_model", cell_model, np.uint8, 1), ("param_set", param_set, np.uint8, 1),
+                                     ("stim_mask", stim_mask, np.uint8, 1), ("fibre", fibre, np.float64, 3)):
+            if arr is None:
+                setattr(d, name, None)
+                continue
+            a = np.ascontiguousarray(arr, dtype=dt)
+            if a.size != n * width:
+                raise ValueError(f"{name} must have {n * width} entries")
+            self._arrays[name] = a
+            setattr(d, name, _ptr(a))
+        h = _P()
+        ctx.check(L.ep_mesh_create(ctx._h, ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.n_cells = n
+        self._arrays.clear()
+        ctx.jobs.add(self)
+
+    def set_params(self, params: Params):
+        self.ctx.check(load().ep_params_set(self._h, ctypes.byref(params)))
+
+    def step(self, n_steps: int):
+        step([self], n_steps)
+
+    def read(self, var, model: int = EP_TP06, out=None) -> np.ndarray:
+        if isinstance(var, str):
+            var = model_varnames(model).index(var)
+        if out is None:
+            out = np.empty(self.n_cells, np.float64)
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == self.n_cells
+        self.ctx.check(load().ep_read_state(self._h, model, var, _ptr(out), self.n_cells))
+        return out
+
+    def write(self, var, values, model: int = EP_TP06):
+        if isinstance(var, str):
+            var = model_varnames(model).index(var)
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        self.ctx.check(load().ep_write_state(self._h, model, var, _ptr(v), self.n_cells))
+
+    @property
+    def V(self) -> np.ndarray:
+        return self.read(0)
+
+    def activation_times(self, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.n_cells, np.float64)
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == self.n_cells
+        self.ctx.check(load().ep_activation_times(self._h, _ptr(out), self.n_cells))
+        return out
+
+    def reset_activation(self):
+        self.ctx.check(load().ep_reset_activation(self._h))
+
+    @property
+    def step_index(self) -> int:
+        v = _I64()
+        self.ctx.check(load().ep_step_index(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    @step_index.setter
+    def step_index(self, n):
+        self.ctx.check(load().ep_set_step_index(self._h, int(n)))
+
+    def check_finite(self) -> bool:
+        rc = load().ep_check_finite(self._h)
+        if rc == EP_ENONFINITE:
+            return False
+        self.ctx.check(rc)
+        return True
+
+    def info(self) -> dict:
+        a, b, c, d = _I64(), _I64(), _I64(), _I64()
+        self.ctx.check(load().ep_job_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                          ctypes.byref(d)))
+        return dict(n_cells=a.value, n_nodes=b.value, n_interior_faces=c.value, device_bytes=d.value)
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            self.ctx.check(load().ep_job_destroy(self._h))
+            self._h = None
+            self.ctx.jobs.discard(self)
+
+
+def step(jobs, n_steps: int):
+    """Advance all jobs by n_steps in shared batched launches (ep_step)."""
+    arr = (_P * len(jobs))(*[j._h for j in jobs])
+    jobs[0].ctx.check(load().ep_step(arr, len(jobs), int(n_steps)))
+
+
+def time_kernels(jobs, n_steps: int):
+    """Advance the jobs by n_steps with CUDA events around each launch;
+    returns the mean (node_ms, cell_ms) device time per step."""
+    arr = (_P * len(jobs))(*[j._h for j in jobs])
+    a, b = ctypes.c_double(), ctypes.c_double()
+    jobs[0].ctx.check(load().ep_time_kernels(arr, len(jobs), int(n_steps), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def job_from_case(ctx: Context, case, *, precision=EP_FP32_MIXED, cell_model=None) -> Job:
+    """Create a job from a ``workloads.TissueCase`` and set its parameters."""
+    if cell_model is None:
+        cell_model = np.array([case.param_sets[k].model for k in range(len(case.param_sets))],
+                              np.uint8)[case.param_set]
+    j = ctx.mesh(case.xyz, case.tets, cell_model=cell_model, param_set=case.param_set,
+                 stim_mask=case.stim_mask, fibre=case.fibre)
+    j.set_params(make_params(case.dt, case.param_sets, case.stimuli, precision=precision,
+                             threshold=case.threshold))
+    return j
+
+
+def plan_inspect(xyz, tets, params: Params, *, cell_model=None, param_set=None, fibre=None) -> dict:
+    """Run the host planner only (no GPU) and return its folded operator."""
+    L = load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    n, nn = tets.shape[0], xyz.shape[0]
+    keep = []
+    d = MeshDesc()
+    d.n_nodes, d.xyz, d.n_cells, d.tet = nn, _ptr(xyz), n, _ptr(tets)
+    for name, arr, dt in (("cell_model", cell_model, np.uint8), ("param_set", param_set, np.uint8),
+                          ("fibre", fibre, np.float64)):
+        if arr is None:
+            setattr(d, name, None)
+        else:
+            a = np.ascontiguousarray(arr, dtype=dt)
+            keep.append(a)
+            setattr(d, name, _ptr(a))
+    d.stim_mask = None
+    out = dict(cell_order=np.zeros(n, np.int64), tet=np.zeros(4 * n, np.int32), opp=np.zeros(4 * n, np.int32),
+               nbr=np.zeros(4 * n, np.int32), wa=np.zeros(4 * n), wb=np.zeros(4 * n), q=np.zeros(4 * n),
+               n2c_ptr=np.zeros(nn + 1, np.int64), n2c=np.zeros(4 * n, np.int32), nw=np.zeros(4 * n))
+    rho = ctypes.c_double(0.0)
+    rc = L.ep_plan_inspect(ctypes.byref(d), ctypes.byref(params), *[_ptr(out[k]) for k in
+                           ("cell_order", "tet", "opp", "nbr", "wa", "wb", "q", "n2c_ptr", "n2c", "nw")],
+                           ctypes.byref(rho))
+    if rc:
+        raise EPError(rc, L.ep_last_error(None).decode())
+    out["rho_bound"] = rho.value
+    return out

@@ -1,0 +1,156 @@
+"""Host-side checks of the CUDA library that need no GPU: the shared library
+loads and exports the C ABI, and its planner's folded FP64 operator equals
+the oracle's face-by-face evaluation of Eqs. 7-8 (an identity, not shared
+code: the planner folds S1-S3 into per-cell coefficients independently)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as w
+from paper_2112_12854_b300 import ep
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "ep.h")
+
+
+def _declared():
+    src = open(HDR).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ep_[a-z_0-9]+)\s*\(", src)) - {"ep_alloc_fn", "ep_free_fn"})
+
+
+def test_library_exports_every_declared_symbol():
+    L = ep.load()
+    names = _declared()
+    assert "ep_step" in names and "ep_mesh_create" in names
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(ep.EXPORTS)
+
+
+def test_model_variable_tables():
+    assert len(ep.model_varnames(ep.EP_TP06)) == 19
+    assert len(ep.model_varnames(ep.EP_CRN)) == 21
+    assert len(ep.model_varnames(ep.EP_STEWART)) == 20
+    import oracle
+    for m in range(3):
+        assert ep.model_varnames(m) == oracle.model_varnames(m)
+
+
+def _params(sets, dt=0.02):
+    return ep.make_params(dt, sets, [])
+
+
+def _apply(plan, V):
+    n = V.size
+    vn = np.add.reduceat(plan["nw"] * V[plan["n2c"]], plan["n2c_ptr"][:-1]) if plan["n2c"].size else None
+    # reduceat of empty rows returns the next value: guard rows with no cells
+    empty = plan["n2c_ptr"][1:] == plan["n2c_ptr"][:-1]
+    vn[empty] = 0.0
+    tet, opp, nbr = plan["tet"].reshape(n, 4), plan["opp"].reshape(n, 4), plan["nbr"].reshape(n, 4)
+    wa, wb, q = plan["wa"].reshape(n, 4), plan["wb"].reshape(n, 4), plan["q"].reshape(n, 4)
+    out = (wa * vn[tet]).sum(1)
+    out += np.where(opp >= 0, wb * vn[np.maximum(opp, 0)], 0.0).sum(1)
+    out += np.where(nbr >= 0, q * (V[np.maximum(nbr, 0)] - V[:, None]), 0.0).sum(1)
+    return out
+
+
+def _compare(xyz, tets, fibre, sets, pset, seed=0):
+    import oracle
+    plan = ep.plan_inspect(xyz, tets, _params(sets), param_set=pset, fibre=fibre)
+    order = plan["cell_order"]
+    assert np.array_equal(np.sort(order), np.arange(tets.shape[0]))
+    m = oracle.Mesh(xyz, tets)
+    D = np.stack([oracle.conductivity(fibre[c], sets[pset[c]].D_l, sets[pset[c]].D_t).ravel()
+                  for c in range(tets.shape[0])])
+    rng = np.random.default_rng(seed)
+    for _ in range(3):
+        v = rng.uniform(-90, 40, tets.shape[0])
+        ref = m.diffusion(D, v)
+        got = np.empty_like(ref)
+        got[order] = _apply(plan, v[order])
+        scale = np.abs(ref).max()
+        assert np.abs(got - ref).max() < 1e-11 * scale
+    return plan
+
+
+def test_folded_operator_equals_face_by_face_kuhn():
+    xyz, tets = w.kuhn_box(6, 5, 3, 0.25)
+    rng = np.random.default_rng(1)
+    fib = rng.standard_normal((tets.shape[0], 3))
+    sets = [w.ParamSet(D_l=0.154, D_t=0.0385), w.ParamSet(D_l=0.0953, D_t=0.0126)]
+    pset = rng.integers(0, 2, tets.shape[0]).astype(np.uint8)
+    _compare(xyz, tets, fib, sets, pset)
+
+
+def test_folded_operator_equals_face_by_face_jittered_and_inverted():
+    """A jittered (non-symmetric) mesh with randomly inverted tets and
+    shuffled numbering exercises the alpha weights, the orientation fix and
+    the renumbering."""
+    xyz, tets = w.kuhn_box(5, 4, 4, 0.5)
+    rng = np.random.default_rng(2)
+    xyz = xyz + rng.uniform(-0.08, 0.08, xyz.shape)
+    flip = rng.uniform(size=tets.shape[0]) < 0.5
+    tets = tets.copy()
+    tets[flip] = tets[flip][:, [0, 2, 1, 3]]
+    perm = rng.permutation(tets.shape[0])
+    tets = tets[perm]
+    nperm = rng.permutation(xyz.shape[0])
+    inv = np.argsort(nperm)
+    xyz = xyz[nperm]
+    tets = inv[tets].astype(np.int32)
+    fib = rng.standard_normal((tets.shape[0], 3))
+    _compare(xyz, tets, fib, [w.ParamSet()], np.zeros(tets.shape[0], np.uint8))
+
+
+def test_rcm_reduces_bandwidth_and_groups_models():
+    xyz, tets = w.kuhn_box(12, 6, 3, 0.5)
+    rng = np.random.default_rng(3)
+    perm = rng.permutation(tets.shape[0])
+    tets = tets[perm]
+    models = rng.integers(0, 3, tets.shape[0]).astype(np.uint8)
+    plan = ep.plan_inspect(xyz, tets, _params([w.ParamSet()]), cell_model=models)
+    order = plan["cell_order"]
+    assert np.all(np.diff(models[order].astype(int)) >= 0)          # model-major
+    plan1 = ep.plan_inspect(xyz, tets, _params([w.ParamSet()]))
+    nbr = plan1["nbr"].reshape(-1, 4)
+    c = np.repeat(np.arange(nbr.shape[0]), 4)
+    bw_rcm = np.abs(nbr.ravel() - c)[nbr.ravel() >= 0].max()
+    import oracle
+    _, _, nb0 = oracle.Mesh(xyz, tets).cell_info()
+    bw0 = np.abs(nb0.ravel() - np.repeat(np.arange(nb0.shape[0]), 4))[nb0.ravel() >= 0].max()
+    assert bw_rcm < bw0 / 4
+
+
+def test_gershgorin_bounds_spectrum():
+    xyz, tets = w.kuhn_box(4, 3, 3, 0.25)
+    plan = ep.plan_inspect(xyz, tets, _params([w.ParamSet()]), fibre=w.fibres_uniform(tets.shape[0]))
+    n = tets.shape[0]
+    L = np.stack([_apply(plan, np.eye(n)[k]) for k in range(n)], axis=1)
+    rho = np.abs(np.linalg.eigvals(L)).max()
+    assert rho <= plan["rho_bound"] * (1 + 1e-12)
+    assert plan["rho_bound"] < 2.0 * rho
+
+
+@pytest.mark.parametrize("case", ["degenerate", "range", "nonmanifold"])
+def test_planner_rejects_bad_meshes(case):
+    if case == "degenerate":
+        xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], float)
+        tets = np.array([[0, 1, 2, 3]])
+    elif case == "range":
+        xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+        tets = np.array([[0, 1, 2, 7]])
+    else:
+        xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [0, 0, -1], [1, 1, 1]], float)
+        tets = np.array([[0, 1, 2, 3], [0, 1, 2, 4], [0, 1, 2, 5]])
+    with pytest.raises(ep.EPError) as e:
+        ep.plan_inspect(xyz, tets, _params([w.ParamSet()]))
+    assert e.value.code == ep.EP_EMESH
+
+
+def test_planner_rejects_missing_param_set():
+    xyz, tets = w.kuhn_box(2, 2, 2, 0.5)
+    with pytest.raises(ep.EPError) as e:
+        ep.plan_inspect(xyz, tets, _params([w.ParamSet()]), param_set=np.full(tets.shape[0], 3, np.uint8))
+    assert e.value.code == ep.EP_EINVAL
