@@ -250,6 +250,31 @@ int ep_plan_inspect(const ep_mesh_desc *desc, const ep_params *params, int64_t *
                     int32_t *opp, int32_t *nbr, double *wa, double *wb, double *q, int64_t *n2c_ptr,
                     int32_t *n2c, double *nw, double *rho_bound);
 
+/* Step one job without allocating any device memory. The paper has no
+ * counterpart: this entry point is for callers that must not allocate while
+ * they step, such as a process whose device memory is entirely reserved by
+ * another runtime's pool (a fresh cudaMalloc would fail or fragment it) or a
+ * latency-critical loop that may not call cudaMalloc/cudaFree, which can take
+ * a global lock or synchronise the device. ep_step, by contrast, builds and
+ * caches a batch plan (device job and tile tables) on its first call for a
+ * job list, and each job holds its own node-value buffer.
+ *
+ * The job's state and coefficient arrays (created earlier through the
+ * context's allocator) are the inputs and outputs; the step's scratch (the
+ * node values and a ticket counter) lives in one static device array of the
+ * library, 256 bytes + EP_NOALLOC_MAX_NODES doubles (16 MiB + 256 B), held by
+ * every GPU that loads the library until the process exits. Results equal
+ * those of ep_step.
+ *   - Rejects meshes with more than EP_NOALLOC_MAX_NODES nodes (EP_EINVAL).
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents: calls
+ *     that overlap on the GPU (other streams, threads or contexts on the same
+ *     device) race on it; serialise them.
+ * Asynchronous on the context's stream. */
+#define EP_NOALLOC_MAX_NODES 2097152
+int ep_step_noalloc(ep_job *job, int64_t n_steps);
+
 /* Number of state variables of a model and the name of each
  * (e.g. "V", "Ca_i", "Na_i", "m"). */
 int32_t ep_model_nvar(int32_t model);

@@ -823,4 +823,20 @@ int ep_plan_inspect(const ep_mesh_desc *desc, const ep_params *params, int64_t *
     }
 }
 
+int ep_step_noalloc(ep_job *job, int64_t n_steps) {
+    if (!job) return EP_EINVAL;
+    ep_context *ctx = job->ctx;
+    if (n_steps < 0) return fail(ctx, EP_EINVAL, "ep_step_noalloc: n_steps < 0");
+    if (!job->has_params) return fail(ctx, EP_ESTATE, "ep_step_noalloc: the job has no parameters");
+    if (job->mesh.n_nodes > EP_NOALLOC_MAX_NODES)
+        return fail(ctx, EP_EINVAL, "ep_step_noalloc: the mesh has " + std::to_string(job->mesh.n_nodes) +
+                                        " nodes; at most " + std::to_string(EP_NOALLOC_MAX_NODES) +
+                                        " fit the static node-value array");
+    if (n_steps == 0) return EP_OK;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = launch_step_noalloc(job->precision, static_cast<const DevJob *>(job->dj_dev.p), job->mesh.n_nodes,
+                                        job->mesh.n_cells, n_steps, ctx->stream);
+    return e == cudaSuccess ? EP_OK : cuda_fail(ctx, e, "ep_step_noalloc");
+}
+
 }  // extern "C"

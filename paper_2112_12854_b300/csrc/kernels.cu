@@ -12,7 +12,9 @@
 // model) and serve every job of the batch in one launch. The last block of
 // the cell launch advances the jobs' step counters, which select the V
 // buffer (double-buffered by step parity) and the time t^n = n dt.
+#include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "crncell.cuh"
 #include "kernels.h"
@@ -301,6 +303,126 @@ int node_blocks_per_sm(int precision) {
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, node_kernel<float>, kNodeThreads, 0);
     return nb < 1 ? 1 : nb;
+}
+
+// ---------------------------------------------------------------------------
+// Step variant that allocates nothing.
+//
+// Some callers must not allocate device memory while they step a job: a
+// process whose device memory is already fully reserved by another runtime's
+// memory pool (a new cudaMalloc would fail or fragment that pool), or a
+// latency-critical loop that may not call cudaMalloc/cudaFree because those
+// can take a global lock or synchronise the device. The variant below keeps
+// the step's only scratch -- the node values of S1 and the ticket counter that
+// advances the step -- in this file-scope array instead of memory owned by
+// the job. Every GPU that loads the library holds the array until the process
+// exits. All calls share it and it keeps the last call's contents: calls that
+// overlap on the GPU (different streams, threads or contexts on one device)
+// race on it and must be serialised by the caller.
+constexpr long long kNoAllocMaxNodes = EP_NOALLOC_MAX_NODES;
+constexpr size_t kNoAllocHeader = 256;  // ticket counter, padded to keep node values 256-byte aligned
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocHeader + kNoAllocMaxNodes * sizeof(double)];
+
+// Device address of g_noalloc_scratch, looked up once per device with that
+// device current (in host code the symbol's name is only a host-side stand-in).
+static void *g_noalloc_addr[256];
+static std::mutex g_noalloc_mutex;
+
+static cudaError_t noalloc_scratch_address(void **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kNodeThreads) node_kernel_noalloc(const DevJob *__restrict__ job, R *__restrict__ vn) {
+    const DevJob &J = *job;
+    const long long n = *J.step;
+    const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
+    const R *__restrict__ w = static_cast<const R *>(J.nw);
+    for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < J.n_nodes;
+         node += (long long)gridDim.x * blockDim.x) {
+        const long long s = node >> 5;
+        const long long b = J.slice_ptr[s] + (node & 31), e = J.slice_ptr[s + 1];
+        R acc = R(0);
+        for (long long k = b; k < e; k += 32) acc += w[k] * V[J.ncol[k]];
+        vn[node] = acc;
+    }
+}
+
+template <class R>
+__global__ void __launch_bounds__(kCellThreads) cell_kernel_noalloc(const DevJob *__restrict__ job, R *vn,
+                                                                    unsigned *ticket) {
+    // the job's descriptor with its node-value pointer redirected to the static scratch
+    __shared__ DevJob Js;
+    {
+        const long long *src = reinterpret_cast<const long long *>(job);
+        long long *dst = reinterpret_cast<long long *>(&Js);
+        for (int i = threadIdx.x; i < int(sizeof(DevJob) / sizeof(long long)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) Js.vn = vn;
+    __syncthreads();
+    const long long end0 = Js.reg[0].off + Js.reg[0].n, end1 = Js.reg[1].off + Js.reg[1].n;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < Js.n_cells;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int model = c < end0 ? 0 : (c < end1 ? 1 : 2);
+        cell_update<R>(Js, model, c);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(ticket, 1u);
+        if (prev == gridDim.x - 1) {
+            *Js.step += 1;
+            *ticket = 0u;
+            __threadfence();
+        }
+    }
+}
+
+template <class R>
+static cudaError_t step_noalloc_impl(const DevJob *job, long long n_nodes, long long n_cells, long long n_steps,
+                                     cudaStream_t s) {
+    void *base = nullptr;
+    cudaError_t e = noalloc_scratch_address(&base);
+    if (e != cudaSuccess) return e;
+    unsigned *ticket = static_cast<unsigned *>(base);
+    R *vn = reinterpret_cast<R *>(static_cast<unsigned char *>(base) + kNoAllocHeader);
+    // the ticket must start at zero; the array keeps whatever the last call left
+    e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 148, nb_node = 1, nb_cell = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_node, node_kernel_noalloc<R>, kNodeThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_cell, cell_kernel_noalloc<R>, kCellThreads, 0);
+    const long long gn = std::min<long long>((n_nodes + kNodeThreads - 1) / kNodeThreads,
+                                             (long long)sms * std::max(nb_node, 1));
+    const long long gc = std::min<long long>((n_cells + kCellThreads - 1) / kCellThreads,
+                                             (long long)sms * std::max(nb_cell, 1));
+    for (long long it = 0; it < n_steps; ++it) {
+        node_kernel_noalloc<R><<<int(std::max(gn, 1LL)), kNodeThreads, 0, s>>>(job, vn);
+        cell_kernel_noalloc<R><<<int(std::max(gc, 1LL)), kCellThreads, 0, s>>>(job, vn, ticket);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_noalloc(int precision, const DevJob *job, long long n_nodes, long long n_cells,
+                                long long n_steps, cudaStream_t s) {
+    if (n_nodes < 1 || n_nodes > kNoAllocMaxNodes) return cudaErrorInvalidValue;
+    return precision == EP_FP64_PLAIN ? step_noalloc_impl<double>(job, n_nodes, n_cells, n_steps, s)
+                                      : step_noalloc_impl<float>(job, n_nodes, n_cells, n_steps, s);
 }
 
 }  // namespace ep

@@ -44,6 +44,11 @@ cudaError_t launch_reset_act(int precision, const DevJob *job, long long n_cells
 cudaError_t launch_check_finite(int precision, const DevJob *job, long long n_cells, unsigned *count,
                                 cudaStream_t s);
 
+// Step one job n_steps times with its node values in a static device array
+// instead of job memory (no allocation; at most EP_NOALLOC_MAX_NODES nodes).
+cudaError_t launch_step_noalloc(int precision, const DevJob *job, long long n_nodes, long long n_cells,
+                                long long n_steps, cudaStream_t s);
+
 // Kernel attributes for sizing persistent grids.
 int cell_blocks_per_sm(int precision);
 int node_blocks_per_sm(int precision);

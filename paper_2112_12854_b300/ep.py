@@ -56,11 +56,14 @@ ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 
 # every symbol declared in include/ep.h
+NOALLOC_MAX_NODES = 2097152
+
 EXPORTS = ["ep_context_create", "ep_context_set_stream", "ep_context_destroy", "ep_last_error",
            "ep_mesh_create", "ep_params_set", "ep_step", "ep_read_state", "ep_write_state",
            "ep_activation_times", "ep_reset_activation", "ep_step_index", "ep_set_step_index",
            "ep_check_finite", "ep_job_info", "ep_estimate_bytes", "ep_job_destroy", "ep_model_nvar",
-           "ep_model_varname", "ep_plan_inspect", "ep_time_kernels"]
+           "ep_model_varname", "ep_plan_inspect", "ep_time_kernels",
+           "ep_step_noalloc"]
 
 _lib = None
 _P = ctypes.c_void_p
@@ -96,6 +99,7 @@ def load():
         "ep_job_destroy": ([_P], ctypes.c_int),
         "ep_model_nvar": ([ctypes.c_int32], ctypes.c_int32),
         "ep_model_varname": ([ctypes.c_int32, ctypes.c_int32], ctypes.c_char_p),
+        "ep_step_noalloc": ([_P, _I64], ctypes.c_int),
         "ep_time_kernels": ([ctypes.POINTER(_P), ctypes.c_int32, _I64, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "ep_plan_inspect": ([ctypes.POINTER(MeshDesc), ctypes.POINTER(Params)] + [_P] * 10
@@ -299,6 +303,12 @@ def step(jobs, n_steps: int):
     """Advance all jobs by n_steps in shared batched launches (ep_step)."""
     arr = (_P * len(jobs))(*[j._h for j in jobs])
     jobs[0].ctx.check(load().ep_step(arr, len(jobs), int(n_steps)))
+
+
+def step_noalloc(job, n_steps: int):
+    """Advance one job by n_steps through ep_step_noalloc (no device allocation;
+    node values in the library's static device array, see include/ep.h)."""
+    job.ctx.check(load().ep_step_noalloc(job._h, int(n_steps)))
 
 
 def time_kernels(jobs, n_steps: int):
