@@ -186,6 +186,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--tune-steps", type=int, default=5, help="steps per cell-kernel variant in the autotuner")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -223,7 +224,9 @@ def main():
     for v in range(nvar):
         job.read(v, out=host_state[v])
 
-    # warm-up, then the timed region: K steps (captured-graph replay) bracketed by barrier + sync
+    # warm-up (the autotuner's steps are part of it), then the timed region: K steps
+    # (captured-graph replay) bracketed by barrier + sync
+    chosen, variant_ms = ep.autotune([job], args.tune_steps)
     job.step(args.warmup)
     torch.cuda.synchronize()
     clocks = Clocks(local)
@@ -257,6 +260,7 @@ def main():
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy)" if peak_kind == "measured"
                 else "fallback 6.4 TB/s",
                 "algorithmic_bytes_per_cell": CELL_BYTES, "cell_kernel_ms": cell_ms, "node_kernel_ms": node_ms,
+                "cell_variant": int(chosen[0]), "autotune_ms": [round(float(x), 4) for x in variant_ms[0]],
                 "node_kernel_gbs": node_bytes / (node_ms * 1e-3) / 1e9,
                 "step_gbs": (CELL_BYTES * N + node_bytes) / ((cell_ms + node_ms) * 1e-3) / 1e9}
 
@@ -293,7 +297,8 @@ def main():
 
     # plain FP64 path on the same workload
     job64 = ep.job_from_case(ctx, case, precision=ep.EP_FP64_PLAIN)
-    job64.step(3)
+    chosen64, _ = ep.autotune([job64], 1)
+    job64.step(2)
     torch.cuda.synchronize()
     e0.record(stream)
     job64.step(args.fp64_steps)
@@ -301,7 +306,7 @@ def main():
     torch.cuda.synchronize()
     ms64 = e0.elapsed_time(e1)
     fp64 = {"value": N * args.fp64_steps / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps,
-            "steps": args.fp64_steps}
+            "steps": args.fp64_steps, "cell_variant": int(chosen64[1])}
     job64.destroy()
 
     cpu = None

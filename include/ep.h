@@ -234,6 +234,21 @@ int ep_job_destroy(ep_job *job);
  * Synchronises. The results equal those of ep_step. */
 int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double *node_ms, double *cell_ms);
 
+/* Autotuner of the cell kernel's launch shape (threads per block and
+ * resident blocks per SM, six variants). Advances the jobs by
+ * 6 * steps_per_variant real time steps, timing the cell launch of each
+ * variant with CUDA events, and keeps the fastest variant per precision for
+ * every later ep_step of the context. All variants compute bitwise identical
+ * results. chosen[2] (may be NULL) receives the variant picked for
+ * EP_FP32_MIXED and EP_FP64_PLAIN (-1 if no job of that precision);
+ * variant_ms[2 * 6] (may be NULL) the mean cell-kernel time per variant.
+ * Synchronises. */
+int ep_autotune(ep_job *const *jobs, int32_t n_jobs, int32_t steps_per_variant, int32_t *chosen,
+                double *variant_ms);
+
+/* Force the cell kernel's launch-shape variant (0..5) for one precision. */
+int ep_set_cell_variant(ep_context *ctx, int32_t precision, int32_t variant);
+
 /* Host-only inspection of the planner (no device work, no GPU needed): run
  * the mesh ingest and the FP64 coefficient folding of ep_mesh_create +
  * ep_params_set and return the folded operator, so that it can be checked

@@ -19,6 +19,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libep.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The kernels' FP32 arithmetic uses the hardware approximations (exp2/log2/rcp/rsqrt
+# units, flush-to-zero); FP64 code is unaffected by these flags.
+FILE_FLAGS = {"kernels.cu": ["--use_fast_math"]}
 
 
 def nvcc() -> str:
@@ -52,7 +55,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     objs = []
     for src in sources():
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
-        cmd = cmd_common + ["-c", src, "-o", obj]
+        cmd = cmd_common + FILE_FLAGS.get(os.path.basename(src), []) + ["-c", src, "-o", obj]
         if src.endswith(".cpp"):
             cmd = cmd_common + ["-x", "cu", "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -60,6 +60,7 @@ struct ep_context {
     std::set<ep_job *> jobs;
     std::vector<std::unique_ptr<Plan>> plans;
     int sm_count = 148;
+    int cell_variant[2] = {0, 0};   // launch shape of the cell kernel per precision (ep_autotune)
 };
 
 struct ep_job {
@@ -412,17 +413,21 @@ int ep_params_set(ep_job *job, const ep_params *p) {
         // parameters and stimuli
         for (int s = 0; s < EP_MAX_PARAM_SETS; ++s) {
             const ep_cell_params &c = p->sets[s < p->n_sets ? s : 0];
-            dj.params[s] = DevParams{c.variant, 0, c.gks_scale, c.gkr_scale, c.K_o};
+            const double sq = std::sqrt(c.K_o / 5.4);
+            dj.params[s] = DevParams{c.variant, 0, c.gks_scale, c.gkr_scale, c.K_o, sq,
+                                     float(c.gks_scale), float(c.gkr_scale), float(c.K_o), float(sq)};
         }
         dj.n_stim = p->n_stim;
         for (int k = 0; k < p->n_stim; ++k) {
             const ep_stimulus &s = p->stim[k];
             dj.stim[k] = DevStim{s.amplitude, std::llround(s.t_on / p->dt), std::llround(s.duration / p->dt),
-                                 std::llround(s.period / p->dt)};
+                                 std::llround(s.period / p->dt), float(s.amplitude), 0};
         }
         dj.precision = p->precision;
         dj.dt = p->dt;
         dj.threshold = p->threshold;
+        dj.dt_f = float(p->dt);
+        dj.threshold_f = float(p->threshold);
         // swap in: coefficient arrays always new; state arrays new only when fresh
         if (fresh) {
             free_job_arrays(job, &job->prec);
@@ -491,7 +496,9 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
         g.L.n_cell_tiles = int(ct.size());
         g.L.done = static_cast<unsigned *>(g.done.p);
         g.L.node_grid = std::max(1, std::min<int>(int(nt.size()), ctx->sm_count * node_blocks_per_sm(prec)));
-        g.L.cell_grid = std::max(1, std::min<int>(int(ct.size()), ctx->sm_count * cell_blocks_per_sm(prec)));
+        g.L.cell_variant = ctx->cell_variant[prec];
+        g.L.cell_grid =
+            std::max(1, std::min<int>(int(ct.size()), ctx->sm_count * cell_blocks_per_sm(prec, g.L.cell_variant)));
         pl->groups.push_back(g);
     }
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -626,6 +633,100 @@ int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double
         return EP_OK;
     } catch (const std::bad_alloc &) {
         return fail(ctx, EP_ENOMEM, "ep_time_kernels: out of host memory");
+    }
+}
+
+// Use launch shape `variant` for the cell kernel of `precision` in every plan
+// of the context (captured graphs are re-captured on next use).
+static void apply_cell_variant(ep_context *ctx, int precision, int variant) {
+    ctx->cell_variant[precision] = variant;
+    for (auto &p : ctx->plans) {
+        bool touched = false;
+        for (auto &g : p->groups)
+            if (g.precision == precision) {
+                g.L.cell_variant = variant;
+                g.L.cell_grid = std::max(1, std::min<int>(g.L.n_cell_tiles,
+                                                          ctx->sm_count * cell_blocks_per_sm(precision, variant)));
+                touched = true;
+            }
+        if (touched) {
+            if (p->exec) cudaGraphExecDestroy(p->exec);
+            if (p->graph) cudaGraphDestroy(p->graph);
+            p->exec = nullptr;
+            p->graph = nullptr;
+        }
+    }
+}
+
+int ep_set_cell_variant(ep_context *ctx, int32_t precision, int32_t variant) {
+    if (!ctx) return EP_EINVAL;
+    if ((precision != EP_FP32_MIXED && precision != EP_FP64_PLAIN) || variant < 0 || variant >= kNumCellVariants)
+        return fail(ctx, EP_EINVAL, "ep_set_cell_variant: unknown precision or variant");
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    apply_cell_variant(ctx, precision, variant);
+    return EP_OK;
+}
+
+int ep_autotune(ep_job *const *jobs, int32_t n_jobs, int32_t steps_per_variant, int32_t *chosen, double *variant_ms) {
+    if (!jobs || n_jobs <= 0 || !jobs[0] || steps_per_variant <= 0) return EP_EINVAL;
+    ep_context *ctx = jobs[0]->ctx;
+    int rc = check_jobs(jobs, n_jobs, 0, "ep_autotune");
+    if (rc) return rc;
+    DeviceGuard g(ctx->device);
+    try {
+        Plan *pl = nullptr;
+        if ((rc = get_plan(ctx, jobs, n_jobs, &pl))) return rc;
+        cudaEvent_t e0, e1;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_autotune");
+        for (int p = 0; p < 2; ++p) {
+            if (chosen) chosen[p] = -1;
+            for (int v = 0; v < kNumCellVariants && variant_ms; ++v) variant_ms[p * kNumCellVariants + v] = -1.0;
+        }
+        for (auto &gr : pl->groups) {
+            double best = 1e300;
+            int best_v = 0;
+            for (int v = 0; v < kNumCellVariants && e == cudaSuccess; ++v) {
+                gr.L.cell_variant = v;
+                gr.L.cell_grid = std::max(1, std::min<int>(gr.L.n_cell_tiles,
+                                                           ctx->sm_count * cell_blocks_per_sm(gr.precision, v)));
+                double tot = 0.0;
+                for (int it = 0; it < steps_per_variant && e == cudaSuccess; ++it) {
+                    // every group of the plan advances together, so all jobs stay in step
+                    for (auto &other : pl->groups) {
+                        if (&other == &gr) {
+                            e = launch_node(gr.precision, gr.L, ctx->stream);
+                            if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+                            if (e == cudaSuccess) e = launch_cell(gr.precision, gr.L, ctx->stream);
+                            if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+                            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                            float ms = 0.f;
+                            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                            tot += ms;
+                        } else if (e == cudaSuccess) {
+                            e = launch_step(other.precision, other.L, ctx->stream);
+                        }
+                    }
+                }
+                const double mean = tot / steps_per_variant;
+                if (variant_ms) variant_ms[gr.precision * kNumCellVariants + v] = mean;
+                if (mean < best) {
+                    best = mean;
+                    best_v = v;
+                }
+            }
+            if (e != cudaSuccess) break;
+            apply_cell_variant(ctx, gr.precision, best_v);
+            if (chosen) chosen[gr.precision] = best_v;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        return e == cudaSuccess ? EP_OK : cuda_fail(ctx, e, "ep_autotune");
+    } catch (const std::bad_alloc &) {
+        return fail(ctx, EP_ENOMEM, "ep_autotune: out of host memory");
     }
 }
 

@@ -50,4 +50,53 @@ __device__ __forceinline__ R buffered_increment(R c, R dtot, R B, R K) {
     return p > R(0) ? R(2) * dtot * u * u / (p + disc) : (disc - p) / (R(2) * u);
 }
 
+// Value of a parameter in the compute type: the FP64 copy for double, the
+// FP32 copy for float.
+template <class R> __device__ __forceinline__ R pick(double d, float f);
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
+// Error-free sum of two floats (Knuth's TwoSum), then renormalisation: adds
+// the float d to the two-float value a = a.x + a.y, keeping ~48 significant
+// bits. The sum uses only additions, so FMA contraction cannot alter it.
+__device__ __forceinline__ float2 twofloat_add(float2 a, float d) {
+    const float s = a.x + d;
+    const float bp = s - a.x;
+    const float err = (a.x - (s - bp)) + (d - bp);
+    const float lo = a.y + err;
+    const float hi = s + lo;
+    return make_float2(hi, lo - (hi - s));
+}
+
+// Slowly drifting concentrations ([Na]i, [K]i, SR calcium) live in 8-byte
+// slots: an FP64 value in the plain path, a two-float compensated sum in the
+// mixed path, so that FP32 increments accumulate without FP64 arithmetic.
+template <class R> struct Accum;
+template <> struct Accum<double> {
+    double v;
+    __device__ __forceinline__ static Accum load(const double *p) { return Accum{*p}; }
+    __device__ __forceinline__ double value() const { return v; }
+    __device__ __forceinline__ void store_add(double *p, double d) const { *p = v + d; }
+    __device__ __forceinline__ static void init(double *p, double x) { *p = x; }
+    __device__ __forceinline__ static double read(const double *p) { return *p; }
+};
+template <> struct Accum<float> {
+    float2 v;
+    __device__ __forceinline__ static Accum load(const double *p) {
+        return Accum{*reinterpret_cast<const float2 *>(p)};
+    }
+    __device__ __forceinline__ float value() const { return v.x; }
+    __device__ __forceinline__ void store_add(double *p, float d) const {
+        *reinterpret_cast<float2 *>(p) = twofloat_add(v, d);
+    }
+    __device__ __forceinline__ static void init(double *p, double x) {
+        const float hi = float(x);
+        *reinterpret_cast<float2 *>(p) = make_float2(hi, float(x - double(hi)));
+    }
+    __device__ __forceinline__ static double read(const double *p) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        return double(v.x) + double(v.y);
+    }
+};
+
 }  // namespace ep

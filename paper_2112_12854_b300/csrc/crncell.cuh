@@ -2,11 +2,12 @@
 // myocyte (Sec. 3.1, atria and 1D bundles). One step: currents at
 // (V^n, s^n), the 15 gates by Rush-Larsen, the concentrations by forward
 // Euler with the model's differential buffering factors; [Na]i, [K]i and the
-// SR compartments (Ca_up, Ca_rel) accumulated in FP64 (Sec. 3.2).
+// SR compartments (Ca_up, Ca_rel) accumulated in FP64 (plain path) or as
+// two-float compensated sums (mixed path) (Sec. 3.2).
 //
 // Storage: compute-type slots 0 Ca_i, 1 m, 2 h, 3 j, 4 oa, 5 oi, 6 ua, 7 ui,
-// 8 xr, 9 xs, 10 d, 11 f, 12 fCa, 13 u, 14 v, 15 w; FP64 slots 0 Na_i, 1 K_i,
-// 2 Ca_up, 3 Ca_rel.
+// 8 xr, 9 xs, 10 d, 11 f, 12 fCa, 13 u, 14 v, 15 w; accumulator slots 0 Na_i,
+// 1 K_i, 2 Ca_up, 3 Ca_rel.
 #pragma once
 #include "cellmath.cuh"
 #include "devtypes.h"
@@ -35,13 +36,14 @@ __device__ __forceinline__ R crn_step(const DevRegion &rg, long long i, const De
     const R Cai = x[0], m = x[st], h = x[2 * st], jj = x[3 * st], oa = x[4 * st], oi = x[5 * st];
     const R ua = x[6 * st], ui = x[7 * st], xr = x[8 * st], xs = x[9 * st], d = x[10 * st];
     const R f = x[11 * st], fCa = x[12 * st], u = x[13 * st], vv = x[14 * st], w = x[15 * st];
-    const double Nai64 = a[0], Ki64 = a[st], Caup64 = a[2 * st], Carel64 = a[3 * st];
-    const R Nai = R(Nai64), Ki = R(Ki64), Caup = R(Caup64), Carel = R(Carel64);
+    const Accum<R> Nai_a = Accum<R>::load(a), Ki_a = Accum<R>::load(a + st);
+    const Accum<R> Caup_a = Accum<R>::load(a + 2 * st), Carel_a = Accum<R>::load(a + 3 * st);
+    const R Nai = Nai_a.value(), Ki = Ki_a.value(), Caup = Caup_a.value(), Carel = Carel_a.value();
 
     const R Fc = R(96.4867);
     const R RTF = R(8.3143 * 310.0 / 96.4867), FRT = R(96.4867 / (8.3143 * 310.0));
     const R Cm = R(100), Vi = R(13668), Vup = R(1109.52), Vrel = R(96.48);
-    const R Nao = R(140), Cao = R(1.8), Ko = R(P.K_o);
+    const R Nao = R(140), Cao = R(1.8), Ko = pick<R>(P.K_o, P.Ko_f);
 
     const R ENa = RTF * flog(Nao / Nai);
     const R EK = RTF * flog(Ko / Ki);
@@ -52,8 +54,8 @@ __device__ __forceinline__ R crn_step(const DevRegion &rg, long long i, const De
     const R Ito = R(0.1652) * oa * oa * oa * oi * (V - EK);
     const R gKur = R(0.005) + R(0.05) * logistic(-(V - R(15)) * R(1.0 / 13.0));
     const R IKur = gKur * ua * ua * ua * ui * (V - EK);
-    const R IKr = R(0.0294) * R(P.gkr_scale) * xr * (V - EK) * logistic((V + R(15)) * R(1.0 / 22.4));
-    const R IKs = R(0.129) * R(P.gks_scale) * xs * xs * (V - EK);
+    const R IKr = R(0.0294) * pick<R>(P.gkr_scale, P.gkr_f) * xr * (V - EK) * logistic((V + R(15)) * R(1.0 / 22.4));
+    const R IKs = R(0.129) * pick<R>(P.gks_scale, P.gks_f) * xs * xs * (V - EK);
     const R ICaL = R(0.1238) * d * f * fCa * (V - R(65));
     const R sigma = (fexp(Nao * R(1.0 / 67.3)) - R(1)) * R(1.0 / 7.0);
     const R fNaK = R(1) / (R(1) + R(0.1245) * fexp(R(-0.1) * V * FRT) + R(0.0365) * sigma * fexp(-V * FRT));
@@ -145,10 +147,10 @@ __device__ __forceinline__ R crn_step(const DevRegion &rg, long long i, const De
 
     // ---- concentrations ----
     x[0] = Cai + dt * (B1 / B2);
-    a[0] = Nai64 + double(dt * dNai);
-    a[st] = Ki64 + double(dt * dKi);
-    a[2 * st] = Caup64 + double(dt * dCaup);
-    a[3 * st] = Carel64 + double(dt * dCarel);
+    Nai_a.store_add(a, dt * dNai);
+    Ki_a.store_add(a + st, dt * dKi);
+    Caup_a.store_add(a + 2 * st, dt * dCaup);
+    Carel_a.store_add(a + 3 * st, dt * dCarel);
     return Iion;
 }
 
@@ -162,10 +164,10 @@ __device__ __forceinline__ void crn_init(const DevRegion &rg, long long i, R *V)
                          R(4.966e-3), R(9.986e-1), R(3.296e-5), R(1.869e-2), R(1.367e-4), R(9.996e-1),
                          R(7.755e-1), R(0), R(1), R(9.992e-1)};
     for (int k = 0; k < kCRNnr; ++k) x[k * st] = v[k];
-    a[0] = 11.17;
-    a[st] = 139.0;
-    a[2 * st] = 1.488;
-    a[3 * st] = 1.488;
+    Accum<R>::init(a, 11.17);
+    Accum<R>::init(a + st, 139.0);
+    Accum<R>::init(a + 2 * st, 1.488);
+    Accum<R>::init(a + 3 * st, 1.488);
 }
 
 }  // namespace ep

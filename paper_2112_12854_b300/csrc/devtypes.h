@@ -13,17 +13,24 @@ namespace ep {
 struct DevStim {
     double amp;
     long long n_on, n_dur, n_per;
+    float amp_f;
+    int pad;
 };
 
+// Per-set parameters, in FP64 for the plain path and rounded once to FP32
+// for the mixed path (so the FP32 kernel does no FP64 conversions).
 struct DevParams {
     int variant;
     int pad;
-    double gks_scale, gkr_scale, K_o;
+    double gks_scale, gkr_scale, K_o, sqrt_Ko;   // sqrt_Ko = sqrt(K_o / 5.4)
+    float gks_f, gkr_f, Ko_f, sqrt_Ko_f;
 };
 
 // State of the cells of one cell model inside a job: n_r arrays of the
-// job's compute type (float or double) followed, in a second allocation, by
-// n_a double arrays. Variable v of local cell i is r[v * stride + i].
+// job's compute type (float or double) and, in a second allocation, n_a
+// arrays of 8-byte accumulators: FP64 values in the plain path, two-float
+// compensated sums (hi, lo) in the mixed path. Variable v of local cell i is
+// r[v * stride + i] (and a[v * stride + i]).
 struct DevRegion {
     void *r;
     double *a;
@@ -52,6 +59,7 @@ struct DevJob {
     int n_stim;
     int precision;
     double dt, threshold;
+    float dt_f, threshold_f;
     long long *step;          // steps taken (device counter)
 };
 

@@ -37,7 +37,7 @@ __device__ __forceinline__ R stimulus(const DevJob &J, unsigned mask, long long 
         if (n < s.n_on) on = false;
         else if (s.n_per <= 0) on = n < s.n_on + s.n_dur;
         else on = ((n - s.n_on) % s.n_per) < s.n_dur;
-        if (on) is += R(s.amp);
+        if (on) is += pick<R>(s.amp, s.amp_f);
     }
     return is;
 }
@@ -82,7 +82,7 @@ __device__ __forceinline__ void cell_update(const DevJob &J, int model, long lon
     const unsigned mask = J.smask[c];
     const R is = mask ? stimulus<R>(J, mask, n) : R(0);
     const DevParams &P = J.params[J.pset[c]];
-    const R dt = R(J.dt);
+    const R dt = pick<R>(J.dt, J.dt_f);
     const DevRegion &rg = J.reg[model];
     const long long li = c - rg.off;
     R iion;
@@ -91,20 +91,25 @@ __device__ __forceinline__ void cell_update(const DevJob &J, int model, long lon
     else iion = crn_step<R>(rg, li, P, Vc, dt);
     const R Vn = Vc + dt * (diff - iion - is);
     Vnext[c] = Vn;
-    const R th = R(J.threshold);
+    const R th = pick<R>(J.threshold, J.threshold_f);
     if (Vc < th && Vn >= th) {
         R *act = static_cast<R *>(J.act);
         if (isinf(act[c])) act[c] = R(double(n) * J.dt) + dt * (th - Vc) / (Vn - Vc);
     }
 }
 
-template <class R>
-__global__ void __launch_bounds__(kCellThreads) cell_kernel(const DevJob *__restrict__ jobs,
-                                                            const Tile *__restrict__ tiles, int n_tiles,
-                                                            unsigned *done, int n_jobs) {
+// Launch-shape variants of the cell kernel, chosen by ep_autotune: threads
+// per block and the minimum number of resident blocks per SM requested from
+// the register allocator. All variants run the same per-cell arithmetic, so
+// their results are bitwise identical. Tiles hold kCellThreads cells; a
+// block narrower than a tile walks it in strides of its width.
+template <class R, int T, int MINB>
+__global__ void __launch_bounds__(T, MINB) cell_kernel(const DevJob *__restrict__ jobs,
+                                                        const Tile *__restrict__ tiles, int n_tiles,
+                                                        unsigned *done, int n_jobs) {
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const Tile tl = tiles[t];
-        if (threadIdx.x < tl.count) cell_update<R>(jobs[tl.job], tl.model, (long long)tl.start + threadIdx.x);
+        for (int i = threadIdx.x; i < tl.count; i += T) cell_update<R>(jobs[tl.job], tl.model, (long long)tl.start + i);
     }
     // Every block has read the step counters; the last one to finish advances them.
     __syncthreads();
@@ -168,8 +173,8 @@ __global__ void gather_kernel(const DevJob *__restrict__ job, const int *__restr
             else x = double(*p);
         } else {
             double *p = rg.a + loc.slot * rg.stride + i;
-            if (write) *p = x;
-            else x = *p;
+            if (write) Accum<R>::init(p, x);
+            else x = Accum<R>::read(p);
         }
     }
 }
@@ -201,7 +206,7 @@ __global__ void finite_kernel(const DevJob *__restrict__ job, long long n_cells,
         for (int k = 0; k < model_nr(model); ++k)
             if (!isfinite(static_cast<const R *>(rg.r)[k * rg.stride + i])) ++bad;
         for (int k = 0; k < model_na(model); ++k)
-            if (!isfinite(rg.a[k * rg.stride + i])) ++bad;
+            if (!isfinite(Accum<R>::read(rg.a + k * rg.stride + i))) ++bad;
     }
     if (bad) atomicAdd(count, bad);
 }
@@ -214,8 +219,7 @@ static int grid_for(long long n, int threads) {
 template <class R>
 static cudaError_t step_impl(const StepLaunch &L, cudaStream_t s) {
     node_kernel<R><<<L.node_grid, kNodeThreads, 0, s>>>(L.jobs, L.node_tiles, L.n_node_tiles);
-    cell_kernel<R><<<L.cell_grid, kCellThreads, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done, L.n_jobs);
-    return cudaGetLastError();
+    return launch_cell(sizeof(R) == 8 ? EP_FP64_PLAIN : EP_FP32_MIXED, L, s);
 }
 
 cudaError_t launch_step(int precision, const StepLaunch &L, cudaStream_t s) {
@@ -270,14 +274,48 @@ cudaError_t launch_node(int precision, const StepLaunch &L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_cell(int precision, const StepLaunch &L, cudaStream_t s) {
-    if (precision == EP_FP64_PLAIN)
-        cell_kernel<double><<<L.cell_grid, kCellThreads, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done,
-                                                                L.n_jobs);
-    else
-        cell_kernel<float><<<L.cell_grid, kCellThreads, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done,
-                                                               L.n_jobs);
+template <class R>
+static cudaError_t cell_launch_variant(const StepLaunch &L, cudaStream_t s) {
+    switch (L.cell_variant) {
+#define EP_CELL_CASE(k, T, B)                                                                                  \
+    case k:                                                                                                    \
+        cell_kernel<R, T, B><<<L.cell_grid, T, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done, L.n_jobs); \
+        break;
+        EP_CELL_VARIANTS(EP_CELL_CASE)
+#undef EP_CELL_CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
+}
+
+cudaError_t launch_cell(int precision, const StepLaunch &L, cudaStream_t s) {
+    return precision == EP_FP64_PLAIN ? cell_launch_variant<double>(L, s) : cell_launch_variant<float>(L, s);
+}
+
+template <class R>
+static int cell_blocks_variant(int variant) {
+    int nb = 0;
+    switch (variant) {
+#define EP_CELL_CASE(k, T, B)                                                                 \
+    case k:                                                                                   \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_kernel<R, T, B>, T, 0);       \
+        break;
+        EP_CELL_VARIANTS(EP_CELL_CASE)
+#undef EP_CELL_CASE
+    }
+    return nb < 1 ? 1 : nb;
+}
+
+int cell_variant_threads(int variant) {
+    switch (variant) {
+#define EP_CELL_CASE(k, T, B) \
+    case k:                   \
+        return T;
+        EP_CELL_VARIANTS(EP_CELL_CASE)
+#undef EP_CELL_CASE
+    }
+    return 0;
 }
 
 cudaError_t launch_check_finite(int precision, const DevJob *job, long long n_cells, unsigned *count,
@@ -287,13 +325,8 @@ cudaError_t launch_check_finite(int precision, const DevJob *job, long long n_ce
     return cudaGetLastError();
 }
 
-int cell_blocks_per_sm(int precision) {
-    int nb = 0;
-    if (precision == EP_FP64_PLAIN)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_kernel<double>, kCellThreads, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_kernel<float>, kCellThreads, 0);
-    return nb < 1 ? 1 : nb;
+int cell_blocks_per_sm(int precision, int variant) {
+    return precision == EP_FP64_PLAIN ? cell_blocks_variant<double>(variant) : cell_blocks_variant<float>(variant);
 }
 
 int node_blocks_per_sm(int precision) {

@@ -15,7 +15,20 @@ struct StepLaunch {
     int n_cell_tiles;
     unsigned *done;            // device counter used to advance the step counters
     int node_grid, cell_grid;  // persistent grid sizes
+    int cell_variant;          // launch shape of the cell kernel (EP_CELL_VARIANTS)
 };
+
+// Launch shapes of the cell kernel: (index, threads per block, minimum
+// resident blocks per SM). Variant 0 is the default before autotuning.
+#define EP_CELL_VARIANTS(X) \
+    X(0, 256, 2)            \
+    X(1, 256, 3)            \
+    X(2, 128, 4)            \
+    X(3, 128, 5)            \
+    X(4, 128, 6)            \
+    X(5, 64, 12)
+constexpr int kNumCellVariants = 6;
+int cell_variant_threads(int variant);
 
 // One time step of every job in the table: node values, then the fused
 // diffusion + cell-model + activation update.
@@ -50,7 +63,7 @@ cudaError_t launch_step_noalloc(int precision, const DevJob *job, long long n_no
                                 long long n_steps, cudaStream_t s);
 
 // Kernel attributes for sizing persistent grids.
-int cell_blocks_per_sm(int precision);
+int cell_blocks_per_sm(int precision, int variant);
 int node_blocks_per_sm(int precision);
 
 }  // namespace ep

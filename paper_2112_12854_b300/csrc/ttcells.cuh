@@ -4,14 +4,15 @@
 //   - Stewart et al. 2009 human Purkinje cell, which adds I_f and I_sus to the
 //     same scaffold and changes I_Na, I_K1, I_to, I_Kr and I_Ks.
 // One step: currents and rates at (V^n, s^n); gates and Rbar by Rush-Larsen;
-// [Na]i, [K]i by forward Euler accumulated in FP64; the three calcium
+// [Na]i, [K]i by forward Euler, accumulated in FP64 (plain path) or as a
+// two-float compensated sum (mixed path); the three calcium
 // compartments by forward Euler on the buffered total, applied as an
 // increment of the free concentration (Sec. 3.2).
 //
 // Storage of a region (see DevRegion): compute-type slots
 //   0 Ca_i, 1 Ca_SS, 2 m, 3 h, 4 j, 5 xr1, 6 xr2, 7 xs, 8 r, 9 s, 10 d, 11 f,
 //   12 f2, 13 fCaSS, 14 Rbar, [15 y (Stewart)]
-// and FP64 slots 0 Na_i, 1 K_i, 2 Ca_SR.
+// and accumulator slots (FP64 / two-float) 0 Na_i, 1 K_i, 2 Ca_SR.
 #pragma once
 #include "cellmath.cuh"
 #include "devtypes.h"
@@ -30,16 +31,16 @@ __device__ __forceinline__ R tt_step(const DevRegion &rg, long long i, const Dev
     const R Cai = x[0], Cass = x[st], m = x[2 * st], h = x[3 * st], jj = x[4 * st];
     const R xr1 = x[5 * st], xr2 = x[6 * st], xs = x[7 * st], r = x[8 * st], s = x[9 * st];
     const R d = x[10 * st], f = x[11 * st], f2 = x[12 * st], fcass = x[13 * st], rr = x[14 * st];
-    const double Nai64 = a[0], Ki64 = a[st], Casr64 = a[2 * st];
-    const R Nai = R(Nai64), Ki = R(Ki64), Casr = R(Casr64);
+    const Accum<R> Nai_a = Accum<R>::load(a), Ki_a = Accum<R>::load(a + st), Casr_a = Accum<R>::load(a + 2 * st);
+    const R Nai = Nai_a.value(), Ki = Ki_a.value(), Casr = Casr_a.value();
 
     // constants (model papers' parameter tables)
     const R RTF = R(8314.472 * 310.0 / 96485.3415), FRT = R(96485.3415 / (8314.472 * 310.0));
     const R Fc = R(96485.3415);
     const R Cm = R(0.185), Vc = R(0.016404), Vsr = R(0.001094), Vss = R(0.00005468);
     const R Nao = R(140.0), Cao = R(2.0);
-    const R Ko = R(P.K_o);
-    const R sqKo = fsqrt(Ko * R(1.0 / 5.4));
+    const R Ko = pick<R>(P.K_o, P.Ko_f);
+    const R sqKo = pick<R>(P.sqrt_Ko, P.sqrt_Ko_f);
 
     const R ENa = RTF * flog(Nao / Nai);
     const R EK = RTF * flog(Ko / Ki);
@@ -62,8 +63,8 @@ __device__ __forceinline__ R tt_step(const DevRegion &rg, long long i, const Dev
         GKs = (P.variant == 1) ? R(0.098) : R(0.392);
         GKr = R(0.153);
     }
-    GKs *= R(P.gks_scale);
-    GKr *= R(P.gkr_scale);
+    GKs *= pick<R>(P.gks_scale, P.gks_f);
+    GKr *= pick<R>(P.gkr_scale, P.gkr_f);
     const R Ito = Gto * r * s * (V - EK);
     const R IKr = GKr * sqKo * xr1 * xr2 * (V - EK);
     const R IKs = GKs * xs * xs * (V - EKs);
@@ -199,9 +200,9 @@ __device__ __forceinline__ R tt_step(const DevRegion &rg, long long i, const Dev
     // ---- concentrations ----
     x[0] = Cai + buffered_increment(Cai, dt * dCai_tot, R(0.2), R(0.001));
     x[st] = Cass + buffered_increment(Cass, dt * dCass_tot, R(0.4), R(0.00025));
-    a[0] = Nai64 + double(dt * dNai);
-    a[st] = Ki64 + double(dt * dKi);
-    a[2 * st] = Casr64 + double(buffered_increment(Casr, dt * dCasr_tot, R(10), R(0.3)));
+    Nai_a.store_add(a, dt * dNai);
+    Ki_a.store_add(a + st, dt * dKi);
+    Casr_a.store_add(a + 2 * st, buffered_increment(Casr, dt * dCasr_tot, R(10), R(0.3)));
     return Iion;
 }
 
@@ -217,18 +218,18 @@ __device__ __forceinline__ void tt_init(const DevRegion &rg, long long i, R *V) 
                             R(0.0095), R(2.42e-8), R(0.999998), R(3.373e-5), R(0.7888), R(0.9755), R(0.9953),
                             R(0.9073)};
         for (int k = 0; k < kTTnr; ++k) x[k * st] = v[k];
-        a[0] = 8.604;
-        a[st] = 136.89;
-        a[2 * st] = 3.64;
+        Accum<R>::init(a, 8.604);
+        Accum<R>::init(a + st, 136.89);
+        Accum<R>::init(a + 2 * st, 3.64);
     } else {
         *V = R(-69.1865);
         const R v[kSTWnr] = {R(0.000101878), R(0.000446818), R(0.0417391), R(0.190678), R(0.238219),
                              R(0.00550281), R(0.313298), R(0.00953708), R(0.00103629), R(0.96589),
                              R(0.000287906), R(0.989144), R(0.995762), R(0.999934), R(0.991227), R(0.0457562)};
         for (int k = 0; k < kSTWnr; ++k) x[k * st] = v[k];
-        a[0] = 8.80545;
-        a[st] = 136.781894;
-        a[2 * st] = 3.10836;
+        Accum<R>::init(a, 8.80545);
+        Accum<R>::init(a + st, 136.781894);
+        Accum<R>::init(a + 2 * st, 3.10836);
     }
 }
 

@@ -63,7 +63,7 @@ EXPORTS = ["ep_context_create", "ep_context_set_stream", "ep_context_destroy", "
            "ep_activation_times", "ep_reset_activation", "ep_step_index", "ep_set_step_index",
            "ep_check_finite", "ep_job_info", "ep_estimate_bytes", "ep_job_destroy", "ep_model_nvar",
            "ep_model_varname", "ep_plan_inspect", "ep_time_kernels",
-           "ep_step_noalloc"]
+           "ep_step_noalloc", "ep_autotune", "ep_set_cell_variant"]
 
 _lib = None
 _P = ctypes.c_void_p
@@ -100,6 +100,8 @@ def load():
         "ep_model_nvar": ([ctypes.c_int32], ctypes.c_int32),
         "ep_model_varname": ([ctypes.c_int32, ctypes.c_int32], ctypes.c_char_p),
         "ep_step_noalloc": ([_P, _I64], ctypes.c_int),
+        "ep_autotune": ([ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32, _P, _P], ctypes.c_int),
+        "ep_set_cell_variant": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
         "ep_time_kernels": ([ctypes.POINTER(_P), ctypes.c_int32, _I64, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "ep_plan_inspect": ([ctypes.POINTER(MeshDesc), ctypes.POINTER(Params)] + [_P] * 10
@@ -309,6 +311,24 @@ def step_noalloc(job, n_steps: int):
     """Advance one job by n_steps through ep_step_noalloc (no device allocation;
     node values in the library's static device array, see include/ep.h)."""
     job.ctx.check(load().ep_step_noalloc(job._h, int(n_steps)))
+
+
+N_CELL_VARIANTS = 6
+
+
+def autotune(jobs, steps_per_variant: int = 10):
+    """Pick the fastest cell-kernel launch shape per precision (ep_autotune).
+    Advances the jobs by 6 * steps_per_variant real steps. Returns
+    (chosen[2], ms[2][6])."""
+    arr = (_P * len(jobs))(*[j._h for j in jobs])
+    chosen = np.zeros(2, np.int32)
+    ms = np.zeros(2 * N_CELL_VARIANTS, np.float64)
+    jobs[0].ctx.check(load().ep_autotune(arr, len(jobs), int(steps_per_variant), _ptr(chosen), _ptr(ms)))
+    return chosen, ms.reshape(2, N_CELL_VARIANTS)
+
+
+def set_cell_variant(ctx: "Context", precision: int, variant: int):
+    ctx.check(load().ep_set_cell_variant(ctx._h, int(precision), int(variant)))
 
 
 def time_kernels(jobs, n_steps: int):

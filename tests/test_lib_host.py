@@ -154,3 +154,10 @@ def test_planner_rejects_missing_param_set():
     with pytest.raises(ep.EPError) as e:
         ep.plan_inspect(xyz, tets, _params([w.ParamSet()]), param_set=np.full(tets.shape[0], 3, np.uint8))
     assert e.value.code == ep.EP_EINVAL
+
+
+def test_library_has_no_unresolved_internal_symbols():
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--undefined-only", ep.LIB_PATH], capture_output=True, text=True).stdout
+    bad = [l for l in out.splitlines() if "_ZN2ep" in l]
+    assert not bad, bad
