@@ -179,6 +179,45 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_serving(ctx, args, capacity_cups, rank, world, dist):
+    """Two serving runs of the job-stream workload (sizes log-uniform 20k-4M
+    cells, 100-800 ms simulated, 70 % slabs / 30 % whole-heart topology at
+    1/4 scale, Poisson arrivals): at args.serve_load x the measured capacity,
+    where latencies are meaningful, and at the configured args.serve_rate
+    jobs/s, which offers about 3.4e11 cell-updates/s, an order of magnitude
+    above one B300's capacity, so it runs overloaded by construction and is
+    cut off at a time limit. Requests are sharded across ranks by id."""
+    from paper_2112_12854_b300.serving import LibBackend, Server, config5_requests, summarize
+    probe = config5_requests(1.0, 400.0, seed=99)           # the job mix, for its mean work per job
+    mean_work = float(np.mean([r.n_cells * r.n_steps for r in probe]))
+    cap_jobs = capacity_cups / mean_work
+    out = {"capacity_jobs_per_s": cap_jobs, "mean_job_cell_updates": mean_work}
+    for name, rate, limit in (("load_%.2f" % args.serve_load, args.serve_load * cap_jobs * world,
+                               args.serve_window + 90.0),
+                              ("configured_%g_per_s" % args.serve_rate, args.serve_rate, args.serve_window)):
+        reqs = config5_requests(rate, args.serve_window, seed=1 if name.startswith("conf") else 0)
+        srv = Server(LibBackend(ctx), steps_per_iter=250, workers=4, rank=rank, world=world)
+        t0 = time.perf_counter()
+        res = srv.run(reqs, time_limit=limit)
+        wall = time.perf_counter() - t0
+        if dist is not None:
+            allr = [None] * world
+            dist.all_gather_object(allr, [(r.latency, r.n_cells * r.n_steps, r.error) for r in res])
+            flat = [x for part in allr for x in part]
+            lat = np.array([x[0] for x in flat if x[2] is None])
+            work = sum(x[1] for x in flat if x[2] is None)
+            summ = {"completed": len(lat), "cell_updates_per_s": work / wall,
+                    "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
+                    "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None}
+        else:
+            summ = summarize(res, wall, srv.log)
+        summ.update({"offered_jobs_per_s": rate, "arrivals": len(reqs), "window_s": args.serve_window,
+                     "time_limit_s": limit, "wall_s": wall, "unfinished": len(srv.unfinished) * world,
+                     "max_resident": max((x["resident"] for x in srv.log), default=0)})
+        out[name] = summ
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -191,6 +230,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="debug: 1/8-volume crop instead of the full wedge")
+    ap.add_argument("--serve-window", type=float, default=40.0,
+                    help="seconds of Poisson arrivals in each serving run (0 = no serving leg)")
+    ap.add_argument("--serve-load", type=float, default=0.7, help="offered load of the first serving run, "
+                    "as a fraction of the measured capacity")
+    ap.add_argument("--serve-rate", type=float, default=20.0, help="arrival rate of the configured (overloaded) run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -309,6 +353,10 @@ def main():
             "steps": args.fp64_steps, "cell_variant": int(chosen64[1])}
     job64.destroy()
 
+    serving = None
+    if args.serve_window > 0:
+        serving = run_serving(ctx, args, value / world, rank, world, dist)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, st, cells, cores = oracle_throughput(CROP, args.cpu_budget)
@@ -329,7 +377,8 @@ def main():
                           "parallelism": f"replicas x{world}", "graph_replay": True},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": 2 * args.steps, "fp64_plain": fp64,
-               "speedup_vs_fp64_plain": value / world / fp64["value"], "state_finite": finite}
+               "speedup_vs_fp64_plain": value / world / fp64["value"], "state_finite": finite,
+               "serving": serving}
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist is not None:

@@ -86,6 +86,7 @@ enum {
 
 typedef struct ep_context ep_context;
 typedef struct ep_job ep_job;
+typedef struct ep_plan ep_plan;
 
 /* Device allocator callbacks. alloc returns a device pointer aligned to at
  * least 256 bytes, or NULL when out of memory; free releases it. */
@@ -180,6 +181,26 @@ int ep_mesh_create(ep_context *ctx, const ep_mesh_desc *desc, ep_job **out);
  * and the step counter to 0. Rejects a dt at or above the explicit stability
  * bound of the diffusion operator with EP_EUNSTABLE. Synchronises. */
 int ep_params_set(ep_job *job, const ep_params *params);
+
+/* Two-phase job creation, for servers that overlap host preparation with
+ * device work.
+ * ep_plan_create does all host work of ep_mesh_create (+ ep_params_set when
+ * params is not NULL): validation, renumbering, face matching, the FP64
+ * folding and the stability check. It touches no device, needs no context
+ * and may run concurrently in several host threads. Errors as
+ * ep_mesh_create / ep_params_set; the message is in ep_last_error(NULL) of
+ * the calling thread.
+ * ep_plan_bytes: device bytes a job created from the plan will hold (the
+ * admission estimate).
+ * ep_job_create uploads a plan into a new job of ctx on a private upload
+ * stream: it does not wait for work queued on the context's stream.
+ * Synchronises that upload stream. The plan may be destroyed afterwards
+ * (the job keeps the host mesh it shares with the plan). */
+int ep_plan_create(const ep_mesh_desc *desc, const ep_params *params, ep_plan **out);
+int64_t ep_plan_bytes(const ep_plan *plan);
+int ep_plan_info(const ep_plan *plan, int64_t *n_cells, int64_t *n_nodes);
+int ep_plan_destroy(ep_plan *plan);
+int ep_job_create(ep_context *ctx, const ep_plan *plan, ep_job **out);
 
 /* Advance n_jobs jobs of one context by n_steps time steps each. All jobs are
  * advanced together: every step is one node-value launch and one fused

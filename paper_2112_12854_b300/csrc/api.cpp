@@ -53,6 +53,7 @@ struct ep_context {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;
+    cudaStream_t upload = nullptr;   // job creation uploads: never waits on queued steps
     ep_alloc_fn alloc = nullptr;
     ep_free_fn free_fn = nullptr;
     void *user = nullptr;
@@ -65,8 +66,10 @@ struct ep_context {
 
 struct ep_job {
     ep_context *ctx = nullptr;
-    HostMesh mesh;
-    Sell sell;
+    std::shared_ptr<HostMesh> mp;   // shared with the ep_plan it came from, if any
+    std::shared_ptr<Sell> sp;
+    const HostMesh &mesh() const { return *mp; }
+    const Sell &sell() const { return *sp; }
     bool has_params = false;
     ep_params params{};
     int precision = -1;
@@ -135,9 +138,9 @@ int upload(ep_context *ctx, const std::vector<T> &v, std::vector<DevBuf> *pool, 
     if (rc) return rc;
     pool->push_back(b);
     if (!v.empty()) {
-        cudaError_t e = cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream);
+        cudaError_t e = cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->upload);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
-        e = cudaStreamSynchronize(ctx->stream);
+        e = cudaStreamSynchronize(ctx->upload);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
     }
     *out = b.p;
@@ -180,10 +183,10 @@ void build_tiles(ep_job *j) {
     j->cell_tiles.clear();
     j->node_tiles.clear();
     for (int m = 0; m < EP_N_MODELS; ++m)
-        for (int64_t s = j->mesh.model_off[m]; s < j->mesh.model_off[m + 1]; s += kCellThreads)
-            j->cell_tiles.push_back(Tile{0, m, int(s), int(std::min<int64_t>(kCellThreads, j->mesh.model_off[m + 1] - s))});
-    for (int64_t s = 0; s < j->mesh.n_nodes; s += kNodeThreads)
-        j->node_tiles.push_back(Tile{0, 0, int(s), int(std::min<int64_t>(kNodeThreads, j->mesh.n_nodes - s))});
+        for (int64_t s = j->mesh().model_off[m]; s < j->mesh().model_off[m + 1]; s += kCellThreads)
+            j->cell_tiles.push_back(Tile{0, m, int(s), int(std::min<int64_t>(kCellThreads, j->mesh().model_off[m + 1] - s))});
+    for (int64_t s = 0; s < j->mesh().n_nodes; s += kNodeThreads)
+        j->node_tiles.push_back(Tile{0, 0, int(s), int(std::min<int64_t>(kNodeThreads, j->mesh().n_nodes - s))});
 }
 
 }  // namespace
@@ -200,6 +203,7 @@ int ep_context_create(ep_alloc_fn alloc, ep_free_fn free_fn, void *user, void *c
         cudaError_t e = cudaGetDevice(&ctx->device);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->upload, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
             g_create_error = std::string("ep_context_create: ") + cudaGetErrorString(e);
             delete ctx;
@@ -231,6 +235,7 @@ int ep_context_destroy(ep_context *ctx) {
     for (auto &p : ctx->plans) free_plan(ctx, p.get());
     ctx->plans.clear();
     if (ctx->capture) cudaStreamDestroy(ctx->capture);
+    if (ctx->upload) cudaStreamDestroy(ctx->upload);
     delete ctx;
     return EP_OK;
 }
@@ -257,61 +262,254 @@ int64_t ep_estimate_bytes(int64_t n_cells, int64_t n_nodes, int32_t precision) {
     return b + (1 << 20);
 }
 
+}  // extern "C"
+
+namespace {
+
+// Validate a parameter block and fold it into FP64 coefficients for a mesh,
+// with the explicit stability check dt * rho(L) < 2 (host only).
+int plan_params(const HostMesh &m, const ep_params *p, Coeffs *cf, std::string *err) {
+    if (!(p->dt > 0.0) || !std::isfinite(p->dt)) {
+        *err = "params: dt must be > 0";
+        return EP_EINVAL;
+    }
+    if (p->precision != EP_FP32_MIXED && p->precision != EP_FP64_PLAIN) {
+        *err = "params: unknown precision";
+        return EP_EINVAL;
+    }
+    if (p->n_sets < 1 || p->n_sets > EP_MAX_PARAM_SETS || p->n_stim < 0 || p->n_stim > EP_MAX_STIMULI) {
+        *err = "params: n_sets must be 1..16 and n_stim 0..8";
+        return EP_EINVAL;
+    }
+    for (int s = 0; s < p->n_sets; ++s) {
+        const ep_cell_params &c = p->sets[s];
+        if (!(c.D_l >= 0.0) || !(c.D_t >= 0.0) || !(c.K_o > 0.0) || c.variant < 0 || c.variant > 2) {
+            *err = "params: bad parameter set " + std::to_string(s);
+            return EP_EINVAL;
+        }
+    }
+    int rc = build_coeffs(m, p, cf, err);
+    if (rc) return rc;
+    double rho = cf->gershgorin;
+    if (p->dt * rho >= 1.9) rho = 1.05 * power_radius(m, *cf, 60);
+    if (p->dt * rho >= 2.0) {
+        *err = "params: dt = " + std::to_string(p->dt) + " ms exceeds the explicit stability bound " +
+               std::to_string(2.0 / rho) + " ms of the diffusion operator";
+        return EP_EUNSTABLE;
+    }
+    return EP_OK;
+}
+
+// Upload a job's precision-independent arrays (on the context's upload stream).
+int job_upload_topology(ep_context *ctx, ep_job *j) {
+    const HostMesh &m = j->mesh();
+    const int64_t N = m.n_cells;
+    std::vector<int4> na(N), nb(N), nc(N);
+    for (int64_t c = 0; c < N; ++c) {
+        const int32_t *t = &m.tet[4 * c];
+        na[c] = make_int4(t[0], t[1], t[2], t[3]);
+        int o[4], q[4];
+        for (int k = 0; k < 4; ++k) {
+            o[k] = m.opp[4 * c + k] >= 0 ? m.opp[4 * c + k] : t[0];
+            q[k] = m.nbr[4 * c + k] >= 0 ? m.nbr[4 * c + k] : int(c);
+        }
+        nb[c] = make_int4(o[0], o[1], o[2], o[3]);
+        nc[c] = make_int4(q[0], q[1], q[2], q[3]);
+    }
+    void *p;
+    int rc;
+    if ((rc = upload(ctx, na, &j->topo, &p))) return rc;
+    j->dj.nodes_a = static_cast<const int4 *>(p);
+    if ((rc = upload(ctx, nb, &j->topo, &p))) return rc;
+    j->dj.nodes_b = static_cast<const int4 *>(p);
+    if ((rc = upload(ctx, nc, &j->topo, &p))) return rc;
+    j->dj.nbr = static_cast<const int4 *>(p);
+    if ((rc = upload(ctx, m.pset, &j->topo, &p))) return rc;
+    j->dj.pset = static_cast<const uint8_t *>(p);
+    if ((rc = upload(ctx, m.smask, &j->topo, &p))) return rc;
+    j->dj.smask = static_cast<const uint8_t *>(p);
+    std::vector<long long> sp(j->sell().slice_ptr.begin(), j->sell().slice_ptr.end());
+    if ((rc = upload(ctx, sp, &j->topo, &p))) return rc;
+    j->dj.slice_ptr = static_cast<const long long *>(p);
+    if ((rc = upload(ctx, j->sell().col, &j->topo, &p))) return rc;
+    j->dj.ncol = static_cast<const int *>(p);
+    if ((rc = upload(ctx, m.cell_new2old, &j->topo, &p))) return rc;
+    j->perm_dev = static_cast<const int *>(p);
+    DevBuf b;
+    if ((rc = dalloc(ctx, sizeof(long long), &b))) return rc;
+    j->step_dev = b;
+    cudaError_t e = cudaMemsetAsync(b.p, 0, sizeof(long long), ctx->upload);
+    j->dj.step = static_cast<long long *>(b.p);
+    if ((rc = dalloc(ctx, sizeof(DevJob), &b))) return rc;
+    j->dj_dev = b;
+    j->dj.n_cells = N;
+    j->dj.n_nodes = m.n_nodes;
+    build_tiles(j);
+    for (auto &t : j->topo) j->device_bytes += t.bytes;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->upload);
+    return e == cudaSuccess ? EP_OK : cuda_fail(ctx, e, "job topology upload");
+}
+
+// Upload coefficients and parameters; on the first call (or a precision
+// change) allocate the state and set it to the models' resting states.
+int job_apply_params(ep_job *job, const ep_params *p, const Coeffs &cf) {
+    ep_context *ctx = job->ctx;
+    const bool fresh = !job->has_params || job->precision != p->precision;
+    if (job->has_params) {
+        cudaStreamSynchronize(ctx->stream);
+        drop_plans_with(ctx, job);
+    }
+    const HostMesh &m = job->mesh();
+    const Sell &sl = job->sell();
+    const int64_t N = m.n_cells;
+    std::vector<DevBuf> newprec;
+    DevJob dj = job->dj;
+    int rc;
+    auto put = [&](auto &vec, void **dst) { return upload(ctx, vec, &newprec, dst); };
+    auto coeff_upload = [&](const std::vector<double> &v, const void **dst) -> int {
+        void *q = nullptr;
+        int r;
+        if (p->precision == EP_FP64_PLAIN) {
+            r = put(v, &q);
+        } else {
+            std::vector<float> f(v.begin(), v.end());
+            r = put(f, &q);
+        }
+        *dst = q;
+        return r;
+    };
+    std::vector<double> nwd(sl.col.size());
+    for (size_t k = 0; k < nwd.size(); ++k) nwd[k] = sl.src[k] >= 0 ? cf.nw[sl.src[k]] : 0.0;
+    if ((rc = coeff_upload(cf.wa, &dj.wa)) || (rc = coeff_upload(cf.wb, &dj.wb)) || (rc = coeff_upload(cf.q, &dj.q)) ||
+        (rc = coeff_upload(nwd, &dj.nw))) {
+        for (auto &b : newprec) dfree(ctx, &b);
+        return rc;
+    }
+    if (fresh) {
+        const size_t r = p->precision == EP_FP64_PLAIN ? 8 : 4;
+        DevBuf b;
+        auto grab = [&](size_t bytes, void **dst) {
+            int r2 = dalloc(ctx, bytes, &b);
+            if (!r2) {
+                newprec.push_back(b);
+                *dst = b.p;
+            }
+            return r2;
+        };
+        rc = grab(N * r, &dj.V[0]);
+        if (!rc) rc = grab(N * r, &dj.V[1]);
+        if (!rc) rc = grab(N * r, &dj.act);
+        if (!rc) rc = grab(m.n_nodes * r, &dj.vn);
+        for (int md = 0; md < EP_N_MODELS && !rc; ++md) {
+            DevRegion &rg = dj.reg[md];
+            rg.off = m.model_off[md];
+            rg.n = m.model_off[md + 1] - m.model_off[md];
+            rg.stride = round_up(std::max<int64_t>(rg.n, 1), 64);
+            rg.r = nullptr;
+            rg.a = nullptr;
+            if (rg.n == 0) continue;
+            void *q = nullptr;
+            rc = grab(size_t(model_nr(md)) * rg.stride * r, &rg.r);
+            if (!rc) rc = grab(size_t(model_na(md)) * rg.stride * 8, &q);
+            rg.a = static_cast<double *>(q);
+        }
+        if (rc) {
+            for (auto &bb : newprec) dfree(ctx, &bb);
+            return rc;
+        }
+    }
+    for (int s = 0; s < EP_MAX_PARAM_SETS; ++s) {
+        const ep_cell_params &c = p->sets[s < p->n_sets ? s : 0];
+        const double sq = std::sqrt(c.K_o / 5.4);
+        dj.params[s] = DevParams{c.variant, 0, c.gks_scale, c.gkr_scale, c.K_o, sq,
+                                 float(c.gks_scale), float(c.gkr_scale), float(c.K_o), float(sq)};
+    }
+    dj.n_stim = p->n_stim;
+    for (int k = 0; k < p->n_stim; ++k) {
+        const ep_stimulus &s = p->stim[k];
+        dj.stim[k] = DevStim{s.amplitude, std::llround(s.t_on / p->dt), std::llround(s.duration / p->dt),
+                             std::llround(s.period / p->dt), float(s.amplitude), 0};
+    }
+    dj.precision = p->precision;
+    dj.dt = p->dt;
+    dj.threshold = p->threshold;
+    dj.dt_f = float(p->dt);
+    dj.threshold_f = float(p->threshold);
+    // coefficient arrays are always new (the first 4 entries of prec); state arrays only when fresh
+    if (fresh) {
+        free_job_arrays(job, &job->prec);
+        job->prec = newprec;
+    } else {
+        for (int k = 0; k < 4; ++k) dfree(ctx, &job->prec[k]);
+        for (int k = 0; k < 4; ++k) job->prec[k] = newprec[k];
+    }
+    job->dj = dj;
+    cudaError_t e = cudaMemcpyAsync(job->dj_dev.p, &job->dj, sizeof(DevJob), cudaMemcpyHostToDevice, ctx->upload);
+    if (e == cudaSuccess && fresh) {
+        e = cudaMemsetAsync(job->step_dev.p, 0, sizeof(long long), ctx->upload);
+        if (e == cudaSuccess) e = launch_init(p->precision, static_cast<const DevJob *>(job->dj_dev.p), N, ctx->upload);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->upload);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "params upload");
+    job->params = *p;
+    job->precision = p->precision;
+    job->has_params = true;
+    job->version++;
+    job->device_bytes = 0;
+    for (auto &t : job->topo) job->device_bytes += t.bytes;
+    for (auto &t : job->prec) job->device_bytes += t.bytes;
+    return EP_OK;
+}
+
+// Device bytes a job built from this mesh holds once parameters of the given
+// precision are set (the allocations of job_upload_topology + job_apply_params).
+int64_t job_bytes(const HostMesh &m, const Sell &sl, int precision) {
+    auto rnd = [](int64_t b) { return std::max<int64_t>(b, 256); };
+    const int64_t N = m.n_cells, r = precision == EP_FP64_PLAIN ? 8 : 4, E = int64_t(sl.col.size());
+    int64_t b = 3 * rnd(16 * N) + 2 * rnd(N) + rnd(8 * int64_t(sl.slice_ptr.size())) + rnd(4 * E) + rnd(4 * N) + 256 +
+                rnd(sizeof(DevJob));
+    b += 3 * rnd(4 * r * N) + rnd(r * E) + 3 * rnd(r * N) + rnd(r * m.n_nodes);
+    for (int md = 0; md < EP_N_MODELS; ++md) {
+        const int64_t n = m.model_off[md + 1] - m.model_off[md];
+        if (!n) continue;
+        const int64_t stride = round_up(n, 64);
+        b += rnd(model_nr(md) * stride * r) + rnd(model_na(md) * stride * 8);
+    }
+    return b;
+}
+
+}  // namespace
+
+struct ep_plan {
+    std::shared_ptr<HostMesh> mesh;
+    std::shared_ptr<Sell> sell;
+    bool has_params = false;
+    ep_params params{};
+    Coeffs cf;
+};
+
+extern "C" {
+
 int ep_mesh_create(ep_context *ctx, const ep_mesh_desc *desc, ep_job **out) {
     if (!ctx || !desc || !out) return fail(ctx, EP_EINVAL, "ep_mesh_create: NULL argument");
     DeviceGuard g(ctx->device);
     try {
         std::unique_ptr<ep_job> j(new ep_job());
         j->ctx = ctx;
+        auto mesh = std::make_shared<HostMesh>();
         std::string err;
-        int rc = build_mesh(desc, &j->mesh, &err);
+        int rc = build_mesh(desc, mesh.get(), &err);
         if (rc) return fail(ctx, rc, err);
-        build_sell(j->mesh, &j->sell);
-        const HostMesh &m = j->mesh;
-        const int64_t N = m.n_cells;
-        std::vector<int4> na(N), nb(N), nc(N);
-        for (int64_t c = 0; c < N; ++c) {
-            const int32_t *t = &m.tet[4 * c];
-            na[c] = make_int4(t[0], t[1], t[2], t[3]);
-            int o[4], q[4];
-            for (int k = 0; k < 4; ++k) {
-                o[k] = m.opp[4 * c + k] >= 0 ? m.opp[4 * c + k] : t[0];
-                q[k] = m.nbr[4 * c + k] >= 0 ? m.nbr[4 * c + k] : int(c);
-            }
-            nb[c] = make_int4(o[0], o[1], o[2], o[3]);
-            nc[c] = make_int4(q[0], q[1], q[2], q[3]);
+        auto sell = std::make_shared<Sell>();
+        build_sell(*mesh, sell.get());
+        j->mp = mesh;
+        j->sp = sell;
+        if ((rc = job_upload_topology(ctx, j.get()))) {
+            free_job_arrays(j.get(), &j->topo);
+            dfree(ctx, &j->dj_dev);
+            dfree(ctx, &j->step_dev);
+            return rc;
         }
-        void *p;
-        if ((rc = upload(ctx, na, &j->topo, &p))) return rc;
-        j->dj.nodes_a = static_cast<const int4 *>(p);
-        if ((rc = upload(ctx, nb, &j->topo, &p))) return rc;
-        j->dj.nodes_b = static_cast<const int4 *>(p);
-        if ((rc = upload(ctx, nc, &j->topo, &p))) return rc;
-        j->dj.nbr = static_cast<const int4 *>(p);
-        if ((rc = upload(ctx, m.pset, &j->topo, &p))) return rc;
-        j->dj.pset = static_cast<const uint8_t *>(p);
-        if ((rc = upload(ctx, m.smask, &j->topo, &p))) return rc;
-        j->dj.smask = static_cast<const uint8_t *>(p);
-        std::vector<long long> sp(j->sell.slice_ptr.begin(), j->sell.slice_ptr.end());
-        if ((rc = upload(ctx, sp, &j->topo, &p))) return rc;
-        j->dj.slice_ptr = static_cast<const long long *>(p);
-        if ((rc = upload(ctx, j->sell.col, &j->topo, &p))) return rc;
-        j->dj.ncol = static_cast<const int *>(p);
-        if ((rc = upload(ctx, m.cell_new2old, &j->topo, &p))) return rc;
-        j->perm_dev = static_cast<const int *>(p);
-        DevBuf b;
-        if ((rc = dalloc(ctx, sizeof(long long), &b))) return rc;
-        j->step_dev = b;
-        cudaMemsetAsync(b.p, 0, sizeof(long long), ctx->stream);
-        j->dj.step = static_cast<long long *>(b.p);
-        if ((rc = dalloc(ctx, sizeof(DevJob), &b))) return rc;
-        j->dj_dev = b;
-        j->dj.n_cells = N;
-        j->dj.n_nodes = m.n_nodes;
-        build_tiles(j.get());
-        for (auto &t : j->topo) j->device_bytes += t.bytes;
-        cudaError_t e = cudaStreamSynchronize(ctx->stream);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_mesh_create");
         ctx->jobs.insert(j.get());
         *out = j.release();
         return EP_OK;
@@ -323,140 +521,88 @@ int ep_mesh_create(ep_context *ctx, const ep_mesh_desc *desc, ep_job **out) {
 int ep_params_set(ep_job *job, const ep_params *p) {
     if (!job || !p) return EP_EINVAL;
     ep_context *ctx = job->ctx;
-    if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return fail(ctx, EP_EINVAL, "ep_params_set: dt must be > 0");
-    if (p->precision != EP_FP32_MIXED && p->precision != EP_FP64_PLAIN)
-        return fail(ctx, EP_EINVAL, "ep_params_set: unknown precision");
-    if (p->n_sets < 1 || p->n_sets > EP_MAX_PARAM_SETS || p->n_stim < 0 || p->n_stim > EP_MAX_STIMULI)
-        return fail(ctx, EP_EINVAL, "ep_params_set: n_sets must be 1..16 and n_stim 0..8");
-    for (int s = 0; s < p->n_sets; ++s) {
-        const ep_cell_params &c = p->sets[s];
-        if (!(c.D_l >= 0.0) || !(c.D_t >= 0.0) || !(c.K_o > 0.0) || c.variant < 0 || c.variant > 2)
-            return fail(ctx, EP_EINVAL, "ep_params_set: bad parameter set " + std::to_string(s));
-    }
     DeviceGuard g(ctx->device);
     try {
         std::string err;
         Coeffs cf;
-        int rc = build_coeffs(job->mesh, p, &cf, &err);
-        if (rc) return fail(ctx, rc, err);
-        // explicit stability of the diffusion part: dt * rho(L) < 2
-        double rho = cf.gershgorin;
-        if (p->dt * rho >= 1.9) rho = 1.05 * power_radius(job->mesh, cf, 60);
-        if (p->dt * rho >= 2.0)
-            return fail(ctx, EP_EUNSTABLE,
-                        "ep_params_set: dt = " + std::to_string(p->dt) + " ms exceeds the explicit stability bound " +
-                            std::to_string(2.0 / rho) + " ms of the diffusion operator");
-        const bool fresh = !job->has_params || job->precision != p->precision;
-        cudaStreamSynchronize(ctx->stream);
-        drop_plans_with(ctx, job);
-        const HostMesh &m = job->mesh;
-        const int64_t N = m.n_cells;
-        std::vector<DevBuf> newprec;
-        DevJob dj = job->dj;
-        auto put = [&](auto &vec, void **dst) { return upload(ctx, vec, &newprec, dst); };
-        auto coeff_upload = [&](const std::vector<double> &v, const void **dst) -> int {
-            void *q = nullptr;
-            int r;
-            if (p->precision == EP_FP64_PLAIN) {
-                r = put(v, &q);
-            } else {
-                std::vector<float> f(v.begin(), v.end());
-                r = put(f, &q);
-            }
-            *dst = q;
-            return r;
-        };
-        std::vector<double> nwd(job->sell.col.size());
-        for (size_t k = 0; k < nwd.size(); ++k) nwd[k] = job->sell.src[k] >= 0 ? cf.nw[job->sell.src[k]] : 0.0;
-        if ((rc = coeff_upload(cf.wa, &dj.wa)) || (rc = coeff_upload(cf.wb, &dj.wb)) || (rc = coeff_upload(cf.q, &dj.q)) ||
-            (rc = coeff_upload(nwd, &dj.nw))) {
-            for (auto &b : newprec) dfree(ctx, &b);
-            return rc;
-        }
-        std::vector<DevBuf> keep;
-        if (fresh) {
-            const size_t r = p->precision == EP_FP64_PLAIN ? 8 : 4;
-            DevBuf b;
-            auto grab = [&](size_t bytes, void **dst) {
-                int r2 = dalloc(ctx, bytes, &b);
-                if (!r2) {
-                    newprec.push_back(b);
-                    *dst = b.p;
-                }
-                return r2;
-            };
-            rc = grab(N * r, &dj.V[0]);
-            if (!rc) rc = grab(N * r, &dj.V[1]);
-            if (!rc) rc = grab(N * r, &dj.act);
-            if (!rc) rc = grab(m.n_nodes * r, &dj.vn);
-            for (int md = 0; md < EP_N_MODELS && !rc; ++md) {
-                DevRegion &rg = dj.reg[md];
-                rg.off = m.model_off[md];
-                rg.n = m.model_off[md + 1] - m.model_off[md];
-                rg.stride = round_up(std::max<int64_t>(rg.n, 1), 64);
-                rg.r = nullptr;
-                rg.a = nullptr;
-                if (rg.n == 0) continue;
-                void *q = nullptr;
-                rc = grab(size_t(model_nr(md)) * rg.stride * r, &rg.r);
-                if (!rc) rc = grab(size_t(model_na(md)) * rg.stride * 8, &q);
-                rg.a = static_cast<double *>(q);
-            }
-            if (rc) {
-                for (auto &bb : newprec) dfree(ctx, &bb);
-                return rc;
-            }
-        } else {
-            // keep the state arrays (V, act, vn, regions): they are the last entries of prec
-            // coefficient arrays of the previous call are replaced
-        }
-        // parameters and stimuli
-        for (int s = 0; s < EP_MAX_PARAM_SETS; ++s) {
-            const ep_cell_params &c = p->sets[s < p->n_sets ? s : 0];
-            const double sq = std::sqrt(c.K_o / 5.4);
-            dj.params[s] = DevParams{c.variant, 0, c.gks_scale, c.gkr_scale, c.K_o, sq,
-                                     float(c.gks_scale), float(c.gkr_scale), float(c.K_o), float(sq)};
-        }
-        dj.n_stim = p->n_stim;
-        for (int k = 0; k < p->n_stim; ++k) {
-            const ep_stimulus &s = p->stim[k];
-            dj.stim[k] = DevStim{s.amplitude, std::llround(s.t_on / p->dt), std::llround(s.duration / p->dt),
-                                 std::llround(s.period / p->dt), float(s.amplitude), 0};
-        }
-        dj.precision = p->precision;
-        dj.dt = p->dt;
-        dj.threshold = p->threshold;
-        dj.dt_f = float(p->dt);
-        dj.threshold_f = float(p->threshold);
-        // swap in: coefficient arrays always new; state arrays new only when fresh
-        if (fresh) {
-            free_job_arrays(job, &job->prec);
-            job->prec = newprec;
-        } else {
-            // replace the 4 coefficient buffers (first 4 of prec), keep state buffers
-            for (int k = 0; k < 4; ++k) dfree(ctx, &job->prec[k]);
-            for (int k = 0; k < 4; ++k) job->prec[k] = newprec[k];
-        }
-        job->dj = dj;
-        cudaError_t e = cudaMemcpyAsync(job->dj_dev.p, &job->dj, sizeof(DevJob), cudaMemcpyHostToDevice, ctx->stream);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_params_set");
-        if (fresh) {
-            cudaMemsetAsync(job->step_dev.p, 0, sizeof(long long), ctx->stream);
-            e = launch_init(p->precision, static_cast<const DevJob *>(job->dj_dev.p), N, ctx->stream);
-            if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_params_set: init");
-        }
-        e = cudaStreamSynchronize(ctx->stream);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_params_set");
-        job->params = *p;
-        job->precision = p->precision;
-        job->has_params = true;
-        job->version++;
-        job->device_bytes = 0;
-        for (auto &t : job->topo) job->device_bytes += t.bytes;
-        for (auto &t : job->prec) job->device_bytes += t.bytes;
-        return EP_OK;
+        int rc = plan_params(job->mesh(), p, &cf, &err);
+        if (rc) return fail(ctx, rc, "ep_params_set: " + err);
+        return job_apply_params(job, p, cf);
     } catch (const std::bad_alloc &) {
         return fail(ctx, EP_ENOMEM, "ep_params_set: out of host memory");
+    }
+}
+
+int ep_plan_create(const ep_mesh_desc *desc, const ep_params *params, ep_plan **out) {
+    if (!desc || !out) {
+        g_create_error = "ep_plan_create: NULL argument";
+        return EP_EINVAL;
+    }
+    try {
+        std::unique_ptr<ep_plan> pl(new ep_plan());
+        pl->mesh = std::make_shared<HostMesh>();
+        std::string err;
+        int rc = build_mesh(desc, pl->mesh.get(), &err);
+        if (!rc) {
+            pl->sell = std::make_shared<Sell>();
+            build_sell(*pl->mesh, pl->sell.get());
+            if (params) {
+                rc = plan_params(*pl->mesh, params, &pl->cf, &err);
+                pl->has_params = rc == EP_OK;
+                pl->params = *params;
+            }
+        }
+        if (rc) {
+            g_create_error = "ep_plan_create: " + err;
+            return rc;
+        }
+        *out = pl.release();
+        return EP_OK;
+    } catch (const std::bad_alloc &) {
+        g_create_error = "ep_plan_create: out of host memory";
+        return EP_ENOMEM;
+    }
+}
+
+int64_t ep_plan_bytes(const ep_plan *plan) {
+    if (!plan) return -1;
+    return job_bytes(*plan->mesh, *plan->sell, plan->has_params ? plan->params.precision : EP_FP32_MIXED);
+}
+
+int ep_plan_info(const ep_plan *plan, int64_t *n_cells, int64_t *n_nodes) {
+    if (!plan) return EP_EINVAL;
+    if (n_cells) *n_cells = plan->mesh->n_cells;
+    if (n_nodes) *n_nodes = plan->mesh->n_nodes;
+    return EP_OK;
+}
+
+int ep_plan_destroy(ep_plan *plan) {
+    delete plan;
+    return EP_OK;
+}
+
+int ep_job_create(ep_context *ctx, const ep_plan *plan, ep_job **out) {
+    if (!ctx || !plan || !out) return fail(ctx, EP_EINVAL, "ep_job_create: NULL argument");
+    DeviceGuard g(ctx->device);
+    try {
+        std::unique_ptr<ep_job> j(new ep_job());
+        j->ctx = ctx;
+        j->mp = plan->mesh;
+        j->sp = plan->sell;
+        int rc = job_upload_topology(ctx, j.get());
+        if (!rc && plan->has_params) rc = job_apply_params(j.get(), &plan->params, plan->cf);
+        if (rc) {
+            free_job_arrays(j.get(), &j->prec);
+            free_job_arrays(j.get(), &j->topo);
+            dfree(ctx, &j->dj_dev);
+            dfree(ctx, &j->step_dev);
+            return rc;
+        }
+        ctx->jobs.insert(j.get());
+        *out = j.release();
+        return EP_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(ctx, EP_ENOMEM, "ep_job_create: out of host memory");
     }
 }
 
@@ -487,7 +633,7 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
         if ((rc = upload(ctx, ct, &tmp, &p))) return rc;
         g.cell_tiles = tmp.back();
         if ((rc = dalloc(ctx, sizeof(unsigned), &g.done))) return rc;
-        cudaMemsetAsync(g.done.p, 0, sizeof(unsigned), ctx->stream);
+        cudaMemsetAsync(g.done.p, 0, sizeof(unsigned), ctx->upload);
         g.L.jobs = static_cast<const DevJob *>(g.jobtab.p);
         g.L.n_jobs = g.n_jobs;
         g.L.node_tiles = static_cast<const Tile *>(g.node_tiles.p);
@@ -501,7 +647,7 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
             std::max(1, std::min<int>(int(ct.size()), ctx->sm_count * cell_blocks_per_sm(prec, g.L.cell_variant)));
         pl->groups.push_back(g);
     }
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    cudaError_t e = cudaStreamSynchronize(ctx->upload);
     return e == cudaSuccess ? EP_OK : cuda_fail(ctx, e, "plan");
 }
 
@@ -548,6 +694,7 @@ static int get_plan(ep_context *ctx, ep_job *const *jobs, int32_t n_jobs, Plan *
         return rc;
     }
     if (ctx->plans.size() >= 8) {
+        cudaStreamSynchronize(ctx->stream);   // its tables may still be read by queued steps
         free_plan(ctx, ctx->plans.front().get());
         ctx->plans.erase(ctx->plans.begin());
     }
@@ -732,7 +879,7 @@ int ep_autotune(ep_job *const *jobs, int32_t n_jobs, int32_t steps_per_variant, 
 
 static int check_io(ep_job *job, int64_t n, const void *buf) {
     if (!job) return EP_EINVAL;
-    if (!buf || n != job->mesh.n_cells)
+    if (!buf || n != job->mesh().n_cells)
         return fail(job->ctx, EP_EINVAL, "buffer is NULL or its length differs from the number of cells");
     if (!job->has_params) return fail(job->ctx, EP_ESTATE, "job has no parameters (no state yet)");
     return EP_OK;
@@ -797,7 +944,7 @@ int ep_reset_activation(ep_job *job) {
     if (!job) return EP_EINVAL;
     if (!job->has_params) return fail(job->ctx, EP_ESTATE, "job has no parameters");
     DeviceGuard g(job->ctx->device);
-    cudaError_t e = launch_reset_act(job->precision, static_cast<const DevJob *>(job->dj_dev.p), job->mesh.n_cells,
+    cudaError_t e = launch_reset_act(job->precision, static_cast<const DevJob *>(job->dj_dev.p), job->mesh().n_cells,
                                      job->ctx->stream);
     return e == cudaSuccess ? EP_OK : cuda_fail(job->ctx, e, "ep_reset_activation");
 }
@@ -822,7 +969,7 @@ int ep_set_step_index(ep_job *job, int64_t n) {
     if (rc) return rc;
     cudaError_t e = cudaSuccess;
     if (job->has_params && ((cur ^ n) & 1)) {
-        const size_t bytes = job->mesh.n_cells * (job->precision == EP_FP64_PLAIN ? 8 : 4);
+        const size_t bytes = job->mesh().n_cells * (job->precision == EP_FP64_PLAIN ? 8 : 4);
         e = cudaMemcpyAsync(job->dj.V[n & 1], job->dj.V[cur & 1], bytes, cudaMemcpyDeviceToDevice, job->ctx->stream);
     }
     long long v = n;
@@ -842,7 +989,7 @@ int ep_check_finite(ep_job *job) {
     unsigned cnt = 0;
     cudaError_t e = cudaMemsetAsync(b.p, 0, sizeof(unsigned), ctx->stream);
     if (e == cudaSuccess)
-        e = launch_check_finite(job->precision, static_cast<const DevJob *>(job->dj_dev.p), job->mesh.n_cells,
+        e = launch_check_finite(job->precision, static_cast<const DevJob *>(job->dj_dev.p), job->mesh().n_cells,
                                 static_cast<unsigned *>(b.p), ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, b.p, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -855,9 +1002,9 @@ int ep_check_finite(ep_job *job) {
 int ep_job_info(const ep_job *job, int64_t *n_cells, int64_t *n_nodes, int64_t *n_interior_faces,
                 int64_t *device_bytes) {
     if (!job) return EP_EINVAL;
-    if (n_cells) *n_cells = job->mesh.n_cells;
-    if (n_nodes) *n_nodes = job->mesh.n_nodes;
-    if (n_interior_faces) *n_interior_faces = job->mesh.n_interior_faces;
+    if (n_cells) *n_cells = job->mesh().n_cells;
+    if (n_nodes) *n_nodes = job->mesh().n_nodes;
+    if (n_interior_faces) *n_interior_faces = job->mesh().n_interior_faces;
     if (device_bytes) *device_bytes = job->device_bytes;
     return EP_OK;
 }
@@ -929,14 +1076,14 @@ int ep_step_noalloc(ep_job *job, int64_t n_steps) {
     ep_context *ctx = job->ctx;
     if (n_steps < 0) return fail(ctx, EP_EINVAL, "ep_step_noalloc: n_steps < 0");
     if (!job->has_params) return fail(ctx, EP_ESTATE, "ep_step_noalloc: the job has no parameters");
-    if (job->mesh.n_nodes > EP_NOALLOC_MAX_NODES)
-        return fail(ctx, EP_EINVAL, "ep_step_noalloc: the mesh has " + std::to_string(job->mesh.n_nodes) +
+    if (job->mesh().n_nodes > EP_NOALLOC_MAX_NODES)
+        return fail(ctx, EP_EINVAL, "ep_step_noalloc: the mesh has " + std::to_string(job->mesh().n_nodes) +
                                         " nodes; at most " + std::to_string(EP_NOALLOC_MAX_NODES) +
                                         " fit the static node-value array");
     if (n_steps == 0) return EP_OK;
     DeviceGuard g(ctx->device);
-    cudaError_t e = launch_step_noalloc(job->precision, static_cast<const DevJob *>(job->dj_dev.p), job->mesh.n_nodes,
-                                        job->mesh.n_cells, n_steps, ctx->stream);
+    cudaError_t e = launch_step_noalloc(job->precision, static_cast<const DevJob *>(job->dj_dev.p), job->mesh().n_nodes,
+                                        job->mesh().n_cells, n_steps, ctx->stream);
     return e == cudaSuccess ? EP_OK : cuda_fail(ctx, e, "ep_step_noalloc");
 }
 

@@ -63,7 +63,8 @@ EXPORTS = ["ep_context_create", "ep_context_set_stream", "ep_context_destroy", "
            "ep_activation_times", "ep_reset_activation", "ep_step_index", "ep_set_step_index",
            "ep_check_finite", "ep_job_info", "ep_estimate_bytes", "ep_job_destroy", "ep_model_nvar",
            "ep_model_varname", "ep_plan_inspect", "ep_time_kernels",
-           "ep_step_noalloc", "ep_autotune", "ep_set_cell_variant"]
+           "ep_step_noalloc", "ep_autotune", "ep_set_cell_variant", "ep_plan_create", "ep_plan_bytes",
+           "ep_plan_info", "ep_plan_destroy", "ep_job_create"]
 
 _lib = None
 _P = ctypes.c_void_p
@@ -100,6 +101,11 @@ def load():
         "ep_model_nvar": ([ctypes.c_int32], ctypes.c_int32),
         "ep_model_varname": ([ctypes.c_int32, ctypes.c_int32], ctypes.c_char_p),
         "ep_step_noalloc": ([_P, _I64], ctypes.c_int),
+        "ep_plan_create": ([ctypes.POINTER(MeshDesc), ctypes.POINTER(Params), ctypes.POINTER(_P)], ctypes.c_int),
+        "ep_plan_bytes": ([_P], _I64),
+        "ep_plan_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
+        "ep_plan_destroy": ([_P], ctypes.c_int),
+        "ep_job_create": ([_P, _P, ctypes.POINTER(_P)], ctypes.c_int),
         "ep_autotune": ([ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32, _P, _P], ctypes.c_int),
         "ep_set_cell_variant": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
         "ep_time_kernels": ([ctypes.POINTER(_P), ctypes.c_int32, _I64, ctypes.POINTER(ctypes.c_double),
@@ -206,34 +212,69 @@ def make_params(dt, sets, stimuli=(), *, precision=EP_FP32_MIXED, threshold=-20.
     return p
 
 
+def _mesh_desc(xyz, tets, cell_model=None, param_set=None, stim_mask=None, fibre=None):
+    """ep_mesh_desc of numpy inputs; returns (desc, arrays to keep alive)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    n = tets.shape[0]
+    keep = [xyz, tets]
+    d = MeshDesc()
+    d.n_nodes, d.xyz, d.n_cells, d.tet = xyz.shape[0], _ptr(xyz), n, _ptr(tets)
+    for name, arr, dt, width in (("cell_model", cell_model, np.uint8, 1), ("param_set", param_set, np.uint8, 1),
+                                 ("stim_mask", stim_mask, np.uint8, 1), ("fibre", fibre, np.float64, 3)):
+        if arr is None:
+            setattr(d, name, None)
+            continue
+        a = np.ascontiguousarray(arr, dtype=dt)
+        if a.size != n * width:
+            raise ValueError(f"{name} must have {n * width} entries")
+        keep.append(a)
+        setattr(d, name, _ptr(a))
+    return d, keep
+
+
+class Plan:
+    """Host-only job preparation (ep_plan_create): no device, no context,
+    safe to build in worker threads while the GPU steps other jobs."""
+
+    def __init__(self, xyz, tets, params: Params | None = None, *, cell_model=None, param_set=None,
+                 stim_mask=None, fibre=None):
+        L = load()
+        d, keep = _mesh_desc(xyz, tets, cell_model, param_set, stim_mask, fibre)
+        h = _P()
+        rc = L.ep_plan_create(ctypes.byref(d), ctypes.byref(params) if params is not None else None,
+                              ctypes.byref(h))
+        if rc:
+            raise EPError(rc, L.ep_last_error(None).decode())
+        self._h = h
+        a, b = _I64(), _I64()
+        L.ep_plan_info(h, ctypes.byref(a), ctypes.byref(b))
+        self.n_cells, self.n_nodes = int(a.value), int(b.value)
+        self.device_bytes = int(L.ep_plan_bytes(h))
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            load().ep_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.destroy()
+
+
 class Job:
-    def __init__(self, ctx: Context, xyz, tets, *, cell_model=None, param_set=None, stim_mask=None, fibre=None):
+    def __init__(self, ctx: Context, xyz=None, tets=None, *, plan: Plan | None = None, cell_model=None,
+                 param_set=None, stim_mask=None, fibre=None):
         L = load()
         self.ctx = ctx
-        self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
-        self._tets = np.ascontiguousarray(tets, dtype=np.int32)
-        n = self._tets.shape[0]
-        self._arrays = {}
-        d = MeshDesc()
-        d.n_nodes = self._xyz.shape[0]
-        d.xyz = _ptr(self._xyz)
-        d.n_cells = n
-        d.tet = _ptr(self._tets)
-        for name, arr, dt, width in (("cell_model", cell_model, np.uint8, 1), ("param_set", param_set, np.uint8, 1),
-                                     ("stim_mask", stim_mask, np.uint8, 1), ("fibre", fibre, np.float64, 3)):
-            if arr is None:
-                setattr(d, name, None)
-                continue
-            a = np.ascontiguousarray(arr, dtype=dt)
-            if a.size != n * width:
-                raise ValueError(f"{name} must have {n * width} entries")
-            self._arrays[name] = a
-            setattr(d, name, _ptr(a))
         h = _P()
-        ctx.check(L.ep_mesh_create(ctx._h, ctypes.byref(d), ctypes.byref(h)))
+        if plan is not None:
+            ctx.check(L.ep_job_create(ctx._h, plan._h, ctypes.byref(h)))
+            self.n_cells = plan.n_cells
+        else:
+            d, keep = _mesh_desc(xyz, tets, cell_model, param_set, stim_mask, fibre)
+            ctx.check(L.ep_mesh_create(ctx._h, ctypes.byref(d), ctypes.byref(h)))
+            self.n_cells = int(d.n_cells)
         self._h = h
-        self.n_cells = n
-        self._arrays.clear()
         ctx.jobs.add(self)
 
     def set_params(self, params: Params):
@@ -340,11 +381,21 @@ def time_kernels(jobs, n_steps: int):
     return a.value, b.value
 
 
+def case_cell_model(case):
+    return np.array([case.param_sets[k].model for k in range(len(case.param_sets))], np.uint8)[case.param_set]
+
+
+def plan_from_case(case, *, precision=EP_FP32_MIXED) -> Plan:
+    """Host-only plan of a ``workloads.TissueCase`` (mesh + parameters)."""
+    params = make_params(case.dt, case.param_sets, case.stimuli, precision=precision, threshold=case.threshold)
+    return Plan(case.xyz, case.tets, params, cell_model=case_cell_model(case), param_set=case.param_set,
+                stim_mask=case.stim_mask, fibre=case.fibre)
+
+
 def job_from_case(ctx: Context, case, *, precision=EP_FP32_MIXED, cell_model=None) -> Job:
     """Create a job from a ``workloads.TissueCase`` and set its parameters."""
     if cell_model is None:
-        cell_model = np.array([case.param_sets[k].model for k in range(len(case.param_sets))],
-                              np.uint8)[case.param_set]
+        cell_model = case_cell_model(case)
     j = ctx.mesh(case.xyz, case.tets, cell_model=cell_model, param_set=case.param_set,
                  stim_mask=case.stim_mask, fibre=case.fibre)
     j.set_params(make_params(case.dt, case.param_sets, case.stimuli, precision=precision,

@@ -218,3 +218,127 @@ def slab_from_spec(spec, *, dt=0.02, n_steps=20000, threshold=-20.0) -> TissueCa
                       param_set=ps, stim_mask=stim, param_sets=sets,
                       stimuli=[Stimulus(-52.0, 0.0, 1.0)], dt=dt, n_steps=n_steps,
                       threshold=threshold)
+
+
+def kuhn_cubes(mask: np.ndarray, h: float, origin=(0.0, 0.0, 0.0)) -> tuple[np.ndarray, np.ndarray]:
+    """Kuhn 6-tet split of the cubes where ``mask`` (shape nx, ny, nz) is
+    True; cube (i, j, k) spans origin + h*[i, i+1] x ... . All cubes use the
+    same split, so the mesh is conforming; only used nodes are kept."""
+    nx, ny, nz = mask.shape
+    ci, cj, ck = np.nonzero(mask)
+
+    def nid(i, j, k):
+        return i + (nx + 1) * (j + (ny + 1) * k)
+
+    tets = np.empty((ci.size, 6, 4), dtype=np.int64)
+    for t, perm in enumerate(_KUHN_PERMS):
+        pos = [ci.copy(), cj.copy(), ck.copy()]
+        verts = [nid(*pos)]
+        for ax in perm:
+            pos[ax] = pos[ax] + 1
+            verts.append(nid(*pos))
+        parity = sum(1 for a in range(3) for b in range(a + 1, 3) if perm[a] > perm[b]) % 2
+        if parity:
+            verts[2], verts[3] = verts[3], verts[2]
+        tets[:, t, :] = np.stack(verts, axis=1)
+    tets = tets.reshape(-1, 4)
+    used, inv = np.unique(tets, return_inverse=True)
+    i = used % (nx + 1)
+    j = (used // (nx + 1)) % (ny + 1)
+    k = used // ((nx + 1) * (ny + 1))
+    xyz = np.stack([i, j, k], axis=1).astype(np.float64) * h + np.asarray(origin, dtype=np.float64)
+    return xyz, inv.reshape(-1, 4).astype(np.int32)
+
+
+# Synthetic four-chamber topology (mm): two truncated ventricular ellipsoid
+# shells (LV inside, RV wrapping its right side) below a base plane, and two
+# atrial ellipsoid shells above it, electrically separate in 3D.
+_LV_OUT, _LV_IN = (25.0, 25.0, 45.0), (17.0, 17.0, 37.0)
+_RV_C, _RV_OUT, _RV_IN = (-14.0, 0.0, 0.0), (33.0, 26.0, 40.0), (28.0, 21.0, 35.0)
+_BASE_Z = 20.0
+_LA_C, _RA_C = (10.0, 0.0, 46.0), (-24.0, 0.0, 44.0)
+_LA_OUT, _RA_OUT, _ATRIAL_WALL = (17.0, 16.0, 13.0), (18.0, 16.0, 13.0), 4.0
+
+
+def _ell(p, c, ax):
+    return np.sqrt(((p[..., 0] - c[0]) / ax[0]) ** 2 + ((p[..., 1] - c[1]) / ax[1]) ** 2
+                   + ((p[..., 2] - c[2]) / ax[2]) ** 2)
+
+
+def heart_regions(p):
+    """Region label of points p (..., 3): 0 none, 1 LV, 2 RV, 3 LA, 4 RA, and
+    the normalised transmural depth (0 endocardium, 1 epicardium)."""
+    lv_o, lv_i = _ell(p, (0, 0, 0), _LV_OUT), _ell(p, (0, 0, 0), _LV_IN)
+    rv_o, rv_i = _ell(p, _RV_C, _RV_OUT), _ell(p, _RV_C, _RV_IN)
+    below = p[..., 2] < _BASE_Z
+    lv = below & (lv_o <= 1.0) & (lv_i > 1.0)
+    rv = below & (rv_o <= 1.0) & (rv_i > 1.0) & (lv_o > 1.0)
+    la_o = _ell(p, _LA_C, _LA_OUT)
+    la_i = _ell(p, _LA_C, tuple(a - _ATRIAL_WALL for a in _LA_OUT))
+    ra_o = _ell(p, _RA_C, _RA_OUT)
+    ra_i = _ell(p, _RA_C, tuple(a - _ATRIAL_WALL for a in _RA_OUT))
+    la = (la_o <= 1.0) & (la_i > 1.0)
+    ra = (ra_o <= 1.0) & (ra_i > 1.0) & ~la
+    label = np.zeros(p.shape[:-1], np.uint8)
+    label[lv], label[rv], label[la], label[ra] = 1, 2, 3, 4
+    # depth from the inner to the outer surface along the ellipsoidal coordinate
+    d = np.zeros(p.shape[:-1])
+    d = np.where(lv, np.clip((lv_i - 1.0) / (lv_i - lv_o + 1e-9), 0, 1), d)
+    d = np.where(rv, np.clip((rv_i - 1.0) / (rv_i - rv_o + 1e-9), 0, 1), d)
+    d = np.where(la, np.clip((la_i - 1.0) / (la_i - la_o + 1e-9), 0, 1), d)
+    d = np.where(ra, np.clip((ra_i - 1.0) / (ra_i - ra_o + 1e-9), 0, 1), d)
+    return label, d
+
+
+def heart_case(h: float = 0.4, *, scale: float = 1.0, dt: float = 0.02, n_steps: int = 40000,
+               threshold: float = -20.0, av_delay: float = 100.0) -> TissueCase:
+    """Synthetic whole-heart topology: ventricles (TP06, endo/epi variants by
+    depth, fibres -60..+60 deg transmurally) and atria (Courtemanche,
+    circumferential fibres) voxelised at spacing h and Kuhn-split; the
+    geometry is scaled by ``scale``. Stimuli: a sinus-node sphere in the right
+    atrium for 2.5 ms (Eq. 4), and, standing in for the conduction system, a
+    sphere at the LV apex endocardium av_delay ms later."""
+    lo = np.array([-50.0, -30.0, -47.0]) * scale
+    hi = np.array([30.0, 30.0, 61.0]) * scale
+    n = np.ceil((hi - lo) / h).astype(int)
+    g = [lo[a] + h * (np.arange(n[a]) + 0.5) for a in range(3)]
+    P = np.stack(np.meshgrid(*g, indexing="ij"), axis=-1) / scale
+    label, dep = heart_regions(P)
+    mask = label > 0
+    xyz, tets = kuhn_cubes(mask, h, lo)
+    c = tet_centroids(xyz, tets) / scale
+    # every tet takes the region and depth of its voxel (6 tets per voxel, in voxel order)
+    lab = np.repeat(label[mask], 6)
+    depth = np.repeat(dep[mask], 6)
+    atrial = lab >= 3
+    ps = np.where(atrial, 2, np.where(depth < 0.5, 1, 0)).astype(np.uint8)
+    # fibres: circumferential around the chamber axis, rotated towards the long axis by alpha(depth)
+    ctr = np.where((lab == 2)[:, None], np.array(_RV_C), 0.0)
+    ctr = np.where((lab == 3)[:, None], np.array(_LA_C), ctr)
+    ctr = np.where((lab == 4)[:, None], np.array(_RA_C), ctr)
+    r = c - ctr
+    t = np.stack([-r[:, 1], r[:, 0], np.zeros(len(r))], axis=1)
+    t /= np.maximum(np.linalg.norm(t, axis=1, keepdims=True), 1e-9)
+    alpha = np.where(atrial, 0.0, np.deg2rad(-60.0 + 120.0 * depth))
+    fib = np.cos(alpha)[:, None] * t + np.sin(alpha)[:, None] * np.array([0.0, 0.0, 1.0])
+    sinus = np.linalg.norm(c - (np.array(_RA_C) + [0, 0, 11.0]), axis=1) < 3.0
+    apex = np.linalg.norm(c - np.array([0.0, 0.0, -38.0]), axis=1) < 4.0
+    smask = (sinus.astype(np.uint8) | (apex.astype(np.uint8) << 1))
+    sets = [ParamSet(model=0, variant=0), ParamSet(model=0, variant=2),
+            ParamSet(model=1, D_l=0.154 * 1.05, D_t=0.0385 * 1.05)]
+    return TissueCase(name="heart", xyz=xyz, tets=tets, fibre=fib, param_set=ps, stim_mask=smask,
+                      param_sets=sets, stimuli=[Stimulus(-52.0, 0.0, 2.5), Stimulus(-52.0, av_delay, 2.0)],
+                      dt=dt, n_steps=n_steps, threshold=threshold)
+
+
+def heart_h_for_cells(target_cells: int, scale: float = 1.0) -> float:
+    """Voxel spacing giving about target_cells tets for heart_case at this scale
+    (tissue volume measured once on a coarse grid)."""
+    hc = 1.0
+    lo = np.array([-50.0, -30.0, -47.0])
+    hi = np.array([30.0, 30.0, 61.0])
+    n = np.ceil((hi - lo) / hc).astype(int)
+    g = [lo[a] + hc * (np.arange(n[a]) + 0.5) for a in range(3)]
+    P = np.stack(np.meshgrid(*g, indexing="ij"), axis=-1)
+    vol = float((heart_regions(P)[0] > 0).sum()) * hc ** 3 * scale ** 3
+    return (6.0 * vol / max(target_cells, 1)) ** (1.0 / 3.0)
