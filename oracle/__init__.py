@@ -25,7 +25,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
-SOURCES = ["fv3d.c", "tp06.c", "crn.c", "stewart.c", "tissue.c"]
+SOURCES = ["fv3d.c", "tp06.c", "crn.c", "stewart.c", "tissue.c", "purkinje.c"]
 
 TP06, CRN, STEWART = 0, 1, 2
 MAXVAR = 24
@@ -51,6 +51,14 @@ class CellParams(ctypes.Structure):
                 ("D_l", ctypes.c_double), ("D_t", ctypes.c_double),
                 ("gks_scale", ctypes.c_double), ("gkr_scale", ctypes.c_double),
                 ("K_o", ctypes.c_double)]
+
+
+class GraphParams(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_double), ("g_graph", ctypes.c_double), ("g_cell", ctypes.c_double),
+                ("threshold", ctypes.c_double), ("delay_ortho", ctypes.c_double),
+                ("delay_anti", ctypes.c_double), ("amplitude", ctypes.c_double), ("duration", ctypes.c_double),
+                ("radius", ctypes.c_double), ("two_way", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("act_threshold", ctypes.c_double)]
 
 
 class Stim(ctypes.Structure):
@@ -104,6 +112,15 @@ def lib():
         L.orc_sim_set_var.argtypes = [_P, ctypes.c_int, _P]
         L.orc_sim_get_act.argtypes = [_P, _P]
         L.orc_sim_diffusion.argtypes = [_P, _P, _P]
+        L.orc_sim_attach_graph.restype = ctypes.c_int
+        L.orc_sim_attach_graph.argtypes = [_P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P, _P,
+                                           ctypes.c_int64, _P, _P, _P, ctypes.POINTER(GraphParams)]
+        L.orc_sim_graph_substeps.restype = ctypes.c_int
+        L.orc_sim_graph_substeps.argtypes = [_P]
+        for f in ("orc_sim_graph_get_var", "orc_sim_graph_set_var"):
+            getattr(L, f).argtypes = [_P, ctypes.c_int, _P]
+        L.orc_sim_graph_get_act.argtypes = [_P, _P]
+        L.orc_sim_graph_laplacian.argtypes = [_P, _P, _P]
         L.orc_stim_active.restype = ctypes.c_int
         L.orc_stim_active.argtypes = [ctypes.POINTER(Stim), ctypes.c_double, ctypes.c_int64]
         _lib = L
@@ -286,4 +303,50 @@ class Sim:
         v = np.ascontiguousarray(v, dtype=np.float64)
         out = np.zeros(self.n_cells)
         lib().orc_sim_diffusion(self._h, _ptr(v), _ptr(out))
+        return out
+
+    def attach_graph(self, graph):
+        """graph: an object with xyz, edges, edge_D (or None), param_set,
+        stim_mask, junction_node, junction_cell, junction_mode and params
+        (fields of GraphParams)."""
+        keep = [np.ascontiguousarray(graph.xyz, dtype=np.float64),
+                np.ascontiguousarray(graph.edges, dtype=np.int32),
+                None if graph.edge_D is None else np.ascontiguousarray(graph.edge_D, dtype=np.float64),
+                np.ascontiguousarray(graph.param_set, dtype=np.uint8),
+                np.ascontiguousarray(graph.stim_mask, dtype=np.uint8),
+                np.ascontiguousarray(graph.junction_node, dtype=np.int32),
+                np.ascontiguousarray(graph.junction_cell, dtype=np.int32),
+                np.ascontiguousarray(graph.junction_mode, dtype=np.uint8)]
+        gp = graph.params
+        p = GraphParams(gp.D, gp.g_graph, gp.g_cell, gp.threshold, gp.delay_ortho, gp.delay_anti,
+                        gp.amplitude, gp.duration, gp.radius, int(gp.two_way), 0, 0.0)
+        rc = lib().orc_sim_attach_graph(self._h, keep[0].shape[0], _ptr(keep[0]), keep[1].shape[0], _ptr(keep[1]),
+                                        None if keep[2] is None else _ptr(keep[2]), _ptr(keep[3]), _ptr(keep[4]),
+                                        keep[5].size, _ptr(keep[5]), _ptr(keep[6]), _ptr(keep[7]), ctypes.byref(p))
+        if rc:
+            raise ValueError(f"oracle graph rejected (code {rc})")
+        self.n_graph = keep[0].shape[0]
+
+    @property
+    def graph_substeps(self) -> int:
+        return int(lib().orc_sim_graph_substeps(self._h))
+
+    def graph_get(self, var: int) -> np.ndarray:
+        out = np.zeros(self.n_graph)
+        lib().orc_sim_graph_get_var(self._h, int(var), _ptr(out))
+        return out
+
+    def graph_set(self, var: int, values) -> None:
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        lib().orc_sim_graph_set_var(self._h, int(var), _ptr(v))
+
+    def graph_laplacian(self, W) -> np.ndarray:
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        out = np.zeros(self.n_graph)
+        lib().orc_sim_graph_laplacian(self._h, _ptr(W), _ptr(out))
+        return out
+
+    def graph_activation_times(self) -> np.ndarray:
+        out = np.zeros(self.n_graph)
+        lib().orc_sim_graph_get_act(self._h, _ptr(out))
         return out

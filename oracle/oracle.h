@@ -92,8 +92,46 @@ void orc_sim_diffusion(const orc_sim *s, const double *v, double *out);
 const orc_mesh *orc_sim_mesh(const orc_sim *s);
 int orc_stim_active(const orc_stim *st, double dt, int64_t n);
 
-/* ---- Purkinje graph (purkinje.c) ---- */
-typedef struct orc_purk orc_purk;
+/* ---- conduction graph and junctions (purkinje.c) ---- */
+enum { ORC_JUNC_RESISTIVE = 0, ORC_JUNC_TRIGGERED = 1 };
+typedef struct {
+    double D;                        /* default edge diffusivity, mm^2/ms */
+    double g_graph, g_cell;          /* resistive coupling rates, 1/ms */
+    double threshold;                /* triggered: crossing threshold, mV */
+    double delay_ortho, delay_anti;  /* ms */
+    double amplitude, duration;      /* triggered stimulus, uA/uF and ms */
+    double radius;                   /* triggered: target cells within this distance, mm */
+    int32_t two_way, pad;
+    double act_threshold;            /* activation threshold of graph nodes (set by the sim) */
+} orc_graph_params;
+typedef struct orc_graph orc_graph;
+orc_graph *orc_graph_build(int64_t n, const double *xyz, int64_t n_edges, const int32_t *edges,
+                           const double *edge_D, const uint8_t *pset, const uint8_t *smask,
+                           int n_sets, const orc_cellparams *sets, double dt,
+                           int64_t n_junc, const int32_t *jnode, const int32_t *jcell,
+                           const uint8_t *jmode, const orc_graph_params *p,
+                           int64_t n_cells, const double *cell_centroid, int *err);
+void orc_graph_free(orc_graph *g);
+int orc_graph_substeps(const orc_graph *g);
+int64_t orc_graph_n(const orc_graph *g);
+double *orc_graph_state(orc_graph *g);
+double *orc_graph_act(orc_graph *g);
+void orc_graph_cell_terms(const orc_graph *g, const double *V, double t, double *i_extra, double *s_extra);
+void orc_graph_step(orc_graph *g, const double *V3, double t, double dt, int64_t n_step,
+                    const orc_cellparams *sets, const orc_stim *stim, int n_stim);
+void orc_graph_triggers(orc_graph *g, const double *V3_old, const double *V3_new, const double *Vg_old,
+                        double t, double dt);
+
+int orc_sim_attach_graph(orc_sim *s, int64_t n, const double *xyz, int64_t n_edges, const int32_t *edges,
+                         const double *edge_D, const uint8_t *pset, const uint8_t *smask,
+                         int64_t n_junc, const int32_t *jnode, const int32_t *jcell, const uint8_t *jmode,
+                         const orc_graph_params *p);
+int orc_sim_graph_substeps(const orc_sim *s);
+void orc_graph_laplacian(const orc_graph *g, const double *W, double *out);
+void orc_sim_graph_laplacian(const orc_sim *s, const double *W, double *out);
+void orc_sim_graph_get_var(const orc_sim *s, int var, double *out);
+void orc_sim_graph_set_var(orc_sim *s, int var, const double *in);
+void orc_sim_graph_get_act(const orc_sim *s, double *out);
 
 #ifdef __cplusplus
 }

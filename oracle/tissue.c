@@ -10,6 +10,10 @@
  *   V^{n+1}  = V^n + dt (diff_c - I_ion(V^n, s^n) - I_s,c)
  *   activation time: at the first step with V^n < theta <= V^{n+1},
  *              t_act = t^n + dt (theta - V^n) / (V^{n+1} - V^n)
+ * With a conduction graph attached (purkinje.c), the junction terms at step
+ * n enter the cells' update (a resistive current beside the diffusion term,
+ * a triggered stimulus beside I_s), then the graph advances from its own
+ * (V^n, s^n) and the 3D V^n, then junction crossings are recorded.
  *
  * A stimulus protocol is on at step n when n >= n_on and
  * (n - n_on) mod n_period < n_dur (single pulse: n < n_on + n_dur), with
@@ -110,6 +114,8 @@ struct orc_sim {
     double *D;       /* [n_cells][9] */
     double *act;
     double *v, *diff;
+    orc_graph *g;              /* optional conduction graph */
+    double *i_extra, *s_extra, *vg_old, *v_new;
 };
 
 orc_sim *orc_sim_create(int64_t n_nodes, const double *xyz, int64_t n_cells,
@@ -158,6 +164,8 @@ orc_sim *orc_sim_create(int64_t n_nodes, const double *xyz, int64_t n_cells,
 void orc_sim_destroy(orc_sim *s) {
     if (!s) return;
     orc_mesh_destroy(s->m);
+    orc_graph_free(s->g);
+    free(s->i_extra); free(s->s_extra); free(s->vg_old); free(s->v_new);
     free(s->pset); free(s->smask); free(s->state); free(s->D); free(s->act);
     free(s->v); free(s->diff);
     free(s);
@@ -166,26 +174,85 @@ void orc_sim_destroy(orc_sim *s) {
 void orc_sim_run(orc_sim *s, int64_t n_steps) {
     for (int64_t it = 0; it < n_steps; ++it) {
         const int64_t n = s->step;
+        const double t = (double)n * s->dt;
         double amp[8];
         for (int k = 0; k < s->n_stim; ++k)
             amp[k] = orc_stim_active(&s->stim[k], s->dt, n) ? s->stim[k].amplitude : 0.0;
         for (int64_t c = 0; c < s->n_cells; ++c) s->v[c] = s->state[ORC_MAXVAR * c];
         orc_diffusion(s->m, s->D, s->v, s->diff);
+        if (s->g) {
+            memset(s->i_extra, 0, sizeof(double) * s->n_cells);
+            memset(s->s_extra, 0, sizeof(double) * s->n_cells);
+            orc_graph_cell_terms(s->g, s->v, t, s->i_extra, s->s_extra);
+        }
 #pragma omp parallel for schedule(static)
         for (int64_t c = 0; c < s->n_cells; ++c) {
             double *st = s->state + ORC_MAXVAR * c;
-            double is = 0.0;
+            double is = 0.0, ix = 0.0;
             for (int k = 0; k < s->n_stim; ++k)
                 if (s->smask[c] & (1u << k)) is += amp[k];
+            if (s->g) {
+                is += s->s_extra[c];
+                ix = s->i_extra[c];
+            }
             const double vn = st[0];
             const double iion = orc_model_step(st, s->dt, is, &s->sets[s->pset[c]]);
-            const double vnew = vn + s->dt * (s->diff[c] - iion - is);
+            const double vnew = vn + s->dt * (s->diff[c] - iion - is - ix);
             st[0] = vnew;
             if (isinf(s->act[c]) && vn < s->theta && vnew >= s->theta)
-                s->act[c] = (double)n * s->dt + s->dt * (s->theta - vn) / (vnew - vn);
+                s->act[c] = t + s->dt * (s->theta - vn) / (vnew - vn);
+        }
+        if (s->g) {
+            const int64_t ng = orc_graph_n(s->g);
+            double *gs = orc_graph_state(s->g);
+            for (int64_t i = 0; i < ng; ++i) s->vg_old[i] = gs[ORC_MAXVAR * i];
+            orc_graph_step(s->g, s->v, t, s->dt, n, s->sets, s->stim, s->n_stim);
+            for (int64_t c = 0; c < s->n_cells; ++c) s->v_new[c] = s->state[ORC_MAXVAR * c];
+            orc_graph_triggers(s->g, s->v, s->v_new, s->vg_old, t, s->dt);
         }
         s->step = n + 1;
     }
+}
+
+int orc_sim_attach_graph(orc_sim *s, int64_t n, const double *xyz, int64_t n_edges, const int32_t *edges,
+                         const double *edge_D, const uint8_t *pset, const uint8_t *smask,
+                         int64_t n_junc, const int32_t *jnode, const int32_t *jcell, const uint8_t *jmode,
+                         const orc_graph_params *p) {
+    orc_graph_params q = *p;
+    q.act_threshold = s->theta;
+    double *cen = (double *)malloc(sizeof(double) * 3 * s->n_cells);
+    orc_mesh_cell_info(s->m, cen, NULL, NULL);
+    int err = 0;
+    orc_graph *g = orc_graph_build(n, xyz, n_edges, edges, edge_D, pset, smask, s->n_sets, s->sets, s->dt,
+                                   n_junc, jnode, jcell, jmode, &q, s->n_cells, cen, &err);
+    free(cen);
+    if (!g) return err;
+    orc_graph_free(s->g);
+    s->g = g;
+    free(s->i_extra); free(s->s_extra); free(s->vg_old); free(s->v_new);
+    s->i_extra = (double *)calloc(s->n_cells, sizeof(double));
+    s->s_extra = (double *)calloc(s->n_cells, sizeof(double));
+    s->v_new = (double *)calloc(s->n_cells, sizeof(double));
+    s->vg_old = (double *)calloc(n ? n : 1, sizeof(double));
+    return 0;
+}
+
+void orc_sim_graph_laplacian(const orc_sim *s, const double *W, double *out) { orc_graph_laplacian(s->g, W, out); }
+
+int orc_sim_graph_substeps(const orc_sim *s) { return s->g ? orc_graph_substeps(s->g) : 0; }
+
+void orc_sim_graph_get_var(const orc_sim *s, int var, double *out) {
+    const double *gs = orc_graph_state(s->g);
+    for (int64_t i = 0; i < orc_graph_n(s->g); ++i) out[i] = gs[ORC_MAXVAR * i + var];
+}
+
+void orc_sim_graph_set_var(orc_sim *s, int var, const double *in) {
+    double *gs = orc_graph_state(s->g);
+    for (int64_t i = 0; i < orc_graph_n(s->g); ++i) gs[ORC_MAXVAR * i + var] = in[i];
+}
+
+void orc_sim_graph_get_act(const orc_sim *s, double *out) {
+    memcpy(out, orc_graph_act(s->g), sizeof(double) * orc_graph_n(s->g));
 }
 
 int64_t orc_sim_step_index(const orc_sim *s) { return s->step; }

@@ -342,3 +342,53 @@ def heart_h_for_cells(target_cells: int, scale: float = 1.0) -> float:
     P = np.stack(np.meshgrid(*g, indexing="ij"), axis=-1)
     vol = float((heart_regions(P)[0] > 0).sum()) * hc ** 3 * scale ** 3
     return (6.0 * vol / max(target_cells, 1)) ** (1.0 / 3.0)
+
+
+@dataclass
+class GraphParams:
+    """Coupling parameters of a conduction graph (units mm, ms, mV, uA/uF)."""
+    D: float = 2.82                 # Purkinje: 3.95 mS/mm / (chi C_m) (Table 2)
+    g_graph: float = 0.5            # resistive junction rates, 1/ms
+    g_cell: float = 0.05
+    threshold: float = 0.0          # triggered: V crossing threshold (Sec. 3.3: 0 mV)
+    delay_ortho: float = 5.0        # Purkinje -> muscle delay (Sec. 3.3)
+    delay_anti: float = 3.0         # muscle -> Purkinje delay (Sec. 1: 2-3 ms)
+    amplitude: float = -52.0
+    duration: float = 0.5           # S_d of a communication-node stimulus (Sec. 3.3)
+    radius: float = 0.1             # R_S (Sec. 3.3: 0.1 mm Purkinje, 1 mm atria)
+    two_way: int = 0
+    substeps: int = 0               # 0 = chosen from the stability bound
+
+
+JUNC_RESISTIVE, JUNC_TRIGGERED = 0, 1
+
+
+@dataclass
+class Graph:
+    xyz: np.ndarray
+    edges: np.ndarray
+    param_set: np.ndarray
+    stim_mask: np.ndarray
+    junction_node: np.ndarray
+    junction_cell: np.ndarray
+    junction_mode: np.ndarray
+    params: GraphParams
+    edge_D: np.ndarray | None = None
+
+    @property
+    def n_nodes(self):
+        return int(self.xyz.shape[0])
+
+
+def chain_graph(n, ds, start=(0.0, 0.0, 0.0), direction=(1.0, 0.0, 0.0), *, param_set=0, stim_nodes=0,
+                params=None):
+    """A straight cable of n nodes spaced ds mm; the first stim_nodes nodes
+    carry stimulus protocol 0."""
+    d = np.asarray(direction, float)
+    d /= np.linalg.norm(d)
+    xyz = np.asarray(start, float) + ds * np.arange(n)[:, None] * d
+    edges = np.stack([np.arange(n - 1), np.arange(1, n)], axis=1).astype(np.int32)
+    sm = np.zeros(n, np.uint8)
+    sm[:stim_nodes] = 1
+    return Graph(xyz, edges, np.full(n, param_set, np.uint8), sm, np.zeros(0, np.int32), np.zeros(0, np.int32),
+                 np.zeros(0, np.uint8), params or GraphParams())
