@@ -179,6 +179,34 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_heart(ctx, args, stream, torch):
+    """Synthetic whole heart with its conduction system at full scale: about
+    9.3M tets (ventricles TP06, atria Courtemanche) and a 50k-node graph
+    (atrial bundle, AV delay line, two Purkinje trees with 2000 resistive
+    PMJs, triggered atrial communication nodes); FP32 mixed, dt 0.02 ms."""
+    from paper_2112_12854_b300 import ep
+    case, g = w.whole_heart(h=0.4, scale=1.0, n_tree=50_000)
+    node_model = np.array([ps.model for ps in case.param_sets], np.uint8)[g.param_set]
+    job = ep.job_from_case(ctx, case)
+    job.attach_graph(g, node_model=node_model)
+    gi = job.graph_info()
+    ep.autotune([job], 2)
+    job.step(5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    job.step(args.heart_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.heart_steps
+    node_graph_ms, cell_ms = ep.time_kernels([job], 20)
+    job.destroy()
+    return {"cells": case.n_cells, "graph_nodes": gi["n_nodes"], "junctions": gi["n_junctions"],
+            "graph_substeps": gi["substeps"], "steps": args.heart_steps, "ms_per_step": ms,
+            "cell_updates_per_s": case.n_cells / (ms * 1e-3),
+            "node_and_graph_kernels_ms": node_graph_ms, "cell_kernel_ms": cell_ms}
+
+
 def run_serving(ctx, args, capacity_cups, rank, world, dist):
     """Two serving runs of the job-stream workload (sizes log-uniform 20k-4M
     cells, 100-800 ms simulated, 70 % slabs / 30 % whole-heart topology at
@@ -230,6 +258,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="debug: 1/8-volume crop instead of the full wedge")
+    ap.add_argument("--heart-steps", type=int, default=200, help="timed steps of the whole-heart leg (0 = skip)")
     ap.add_argument("--serve-window", type=float, default=40.0,
                     help="seconds of Poisson arrivals in each serving run (0 = no serving leg)")
     ap.add_argument("--serve-load", type=float, default=0.7, help="offered load of the first serving run, "
@@ -353,6 +382,10 @@ def main():
             "steps": args.fp64_steps, "cell_variant": int(chosen64[1])}
     job64.destroy()
 
+    heart = None
+    if args.heart_steps > 0:
+        heart = run_heart(ctx, args, stream, torch)
+
     serving = None
     if args.serve_window > 0:
         serving = run_serving(ctx, args, value / world, rank, world, dist)
@@ -378,7 +411,7 @@ def main():
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": 2 * args.steps, "fp64_plain": fp64,
                "speedup_vs_fp64_plain": value / world / fp64["value"], "state_finite": finite,
-               "serving": serving}
+               "whole_heart": heart, "serving": serving}
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist is not None:

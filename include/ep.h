@@ -311,6 +311,69 @@ int ep_plan_inspect(const ep_mesh_desc *desc, const ep_params *params, int64_t *
 #define EP_NOALLOC_MAX_NODES 2097152
 int ep_step_noalloc(ep_job *job, int64_t n_steps);
 
+/* ---- conduction graph (Purkinje network, 1D bundles) and junctions ---- */
+
+/* A 1D conduction graph attached to a job (Sec. 3.2: vertex-based FV on a
+ * graph, several branches allowed at a node). Node i obeys
+ *   dV_i/dt = (2 / sum_j L_ij) sum_j D_ij (V_j - V_i) / L_ij - I_ion - I_s - I_junction
+ * with L_ij the edge length and D_ij its diffusivity (mm^2/ms). Every node
+ * carries the cell model of its parameter set's model (node_model) with the
+ * job's parameter sets. The diffusion is subcycled within each step (the
+ * reaction frozen at step n) with k = max(1, ceil(dt rho / 1.8)) substeps,
+ * rho = max_i 2 sum_j c_ij, c_ij = 2 D_ij / (L_ij sum_k L_ik).
+ * Junctions (Sec. 3.3) pair graph node junction_node[j] with myocardial cell
+ * junction_cell[j] (caller numbering):
+ *   EP_PMJ_RESISTIVE: g_graph (V_p - V_m) leaves the node and g_cell (V_m - V_p)
+ *     leaves the cell, at step n (rates in 1/ms);
+ *   EP_PMJ_TRIGGERED: each upward crossing of `threshold` by V_p (time t_p,
+ *     interpolated) stimulates every cell within `radius` mm of the junction
+ *     cell with `amplitude` over [t_p + delay_ortho, t_p + delay_ortho +
+ *     duration); with two_way, crossings by V_m at t_m stimulate the node over
+ *     [t_m + delay_anti, ... + duration).
+ * xyz: 3 n_nodes doubles; edges: 2 n_edges node indices; edge_D: per-edge
+ * diffusivity or NULL (then params->D); node_model / node_param_set /
+ * node_stim_mask: per node or NULL (Stewart / 0 / none); junction_mode: per
+ * junction or NULL (all params->default_mode). */
+typedef struct {
+    int64_t n_nodes;
+    const double *xyz;
+    int64_t n_edges;
+    const int32_t *edges;
+    const double *edge_D;
+    const uint8_t *node_model;
+    const uint8_t *node_param_set;
+    const uint8_t *node_stim_mask;
+    int64_t n_junctions;
+    const int32_t *junction_node;
+    const int32_t *junction_cell;
+    const uint8_t *junction_mode;
+} ep_graph_desc;
+
+typedef struct {
+    double D;                         /* default edge diffusivity, mm^2/ms */
+    double g_graph, g_cell;           /* resistive junction rates, 1/ms */
+    double threshold;                 /* triggered junction threshold, mV (Sec. 3.3: 0 mV) */
+    double delay_ortho, delay_anti;   /* ms (Sec. 3.3: 5 ms orthodromic; Sec. 1: 2-3 ms antidromic) */
+    double amplitude, duration;       /* triggered stimulus: uA/uF and ms (Sec. 3.3: S_d = 0.5 ms) */
+    double radius;                    /* R_S, mm (Sec. 3.3: 0.1 mm Purkinje, 1 mm atria) */
+    int32_t two_way;                  /* 1: muscle -> graph triggering too */
+    int32_t default_mode;             /* EP_PMJ_RESISTIVE or EP_PMJ_TRIGGERED */
+} ep_graph_params;
+
+/* Attach (or replace) the job's conduction graph. The job must have
+ * parameters. Graph nodes start at their models' resting states; the graph
+ * is rebuilt for a later ep_params_set. Synchronises. Errors: EP_EINVAL
+ * (bad index, parameter set, or mode), EP_ESTATE (no parameters). */
+int ep_graph_attach(ep_job *job, const ep_graph_desc *desc, const ep_graph_params *params);
+
+/* Graph node state / activation times in the caller's node order (as
+ * ep_read_state / ep_write_state / ep_activation_times), and the graph's
+ * node count and diffusion substeps per time step. Synchronise. */
+int ep_graph_read_state(ep_job *job, int32_t model, int32_t var, double *host_out, int64_t n);
+int ep_graph_write_state(ep_job *job, int32_t model, int32_t var, const double *host_in, int64_t n);
+int ep_graph_activation_times(ep_job *job, double *host_out, int64_t n);
+int ep_graph_info(const ep_job *job, int64_t *n_nodes, int32_t *substeps, int64_t *n_junctions);
+
 /* Number of state variables of a model and the name of each
  * (e.g. "V", "Ca_i", "Na_i", "m"). */
 int32_t ep_model_nvar(int32_t model);

@@ -15,6 +15,7 @@
 
 #include "../../include/ep.h"
 #include "devtypes.h"
+#include "graph_plan.h"
 #include "kernels.h"
 #include "planner.h"
 #include "varmap.h"
@@ -39,7 +40,7 @@ struct Plan {
     struct Group {
         int precision;
         int n_jobs;
-        DevBuf jobtab, node_tiles, cell_tiles, done;
+        DevBuf jobtab, node_tiles, cell_tiles, done, graph_tiles;
         StepLaunch L;
     };
     std::vector<Group> groups;
@@ -82,6 +83,12 @@ struct ep_job {
     std::vector<DevBuf> prec;     // precision-dependent device arrays
     std::vector<Tile> cell_tiles, node_tiles;
     int64_t device_bytes = 0;
+    // conduction graph (ep_graph_attach)
+    std::unique_ptr<GraphPlan> gp;
+    std::vector<DevBuf> gbufs;
+    std::vector<Tile> graph_tiles;
+    const int *gperm_dev = nullptr;
+    DevBuf graph_view;               // DevJob whose V/act/regions are the graph's (init, I/O)
 };
 
 namespace {
@@ -155,6 +162,7 @@ void free_plan(ep_context *ctx, Plan *p) {
         dfree(ctx, &g.node_tiles);
         dfree(ctx, &g.cell_tiles);
         dfree(ctx, &g.done);
+        dfree(ctx, &g.graph_tiles);
     }
 }
 
@@ -265,6 +273,8 @@ int64_t ep_estimate_bytes(int64_t n_cells, int64_t n_nodes, int32_t precision) {
 }  // extern "C"
 
 namespace {
+
+int graph_apply(ep_job *job);
 
 // Validate a parameter block and fold it into FP64 coefficients for a mesh,
 // with the explicit stability check dt * rho(L) < 2 (host only).
@@ -458,6 +468,7 @@ int job_apply_params(ep_job *job, const ep_params *p, const Coeffs &cf) {
     job->device_bytes = 0;
     for (auto &t : job->topo) job->device_bytes += t.bytes;
     for (auto &t : job->prec) job->device_bytes += t.bytes;
+    if (job->gp) return graph_apply(job);
     return EP_OK;
 }
 
@@ -476,6 +487,123 @@ int64_t job_bytes(const HostMesh &m, const Sell &sl, int precision) {
         b += rnd(model_nr(md) * stride * r) + rnd(model_na(md) * stride * 8);
     }
     return b;
+}
+
+// Upload (or rebuild) the job's conduction graph for its current
+// parameters: state arrays at rest, FV coefficients, junction tables, and
+// the junction flags in the cells' parameter-set bytes.
+int graph_apply(ep_job *job) {
+    ep_context *ctx = job->ctx;
+    GraphPlan &g = *job->gp;
+    const HostMesh &m = job->mesh();
+    const int prec = job->precision;
+    const size_t r = prec == EP_FP64_PLAIN ? 8 : 4;
+    cudaStreamSynchronize(ctx->stream);
+    drop_plans_with(ctx, job);
+    for (auto &b : job->gbufs) dfree(ctx, &b);
+    job->gbufs.clear();
+    dfree(ctx, &job->graph_view);
+    DevGraph G{};
+    const int64_t n = g.n;
+    int rc = EP_OK;
+    void *q = nullptr;
+    auto grab = [&](size_t bytes, void **dst) {
+        DevBuf b;
+        int r2 = dalloc(ctx, bytes, &b);
+        if (!r2) {
+            job->gbufs.push_back(b);
+            *dst = b.p;
+        }
+        return r2;
+    };
+    auto put = [&](auto &vec, void **dst) { return upload(ctx, vec, &job->gbufs, dst); };
+    G.n_nodes = n;
+    for (int k = 0; k < 2 && !rc; ++k) rc = grab(std::max<int64_t>(n, 1) * r, &G.V[k]);
+    for (int k = 0; k < 2 && !rc; ++k) rc = grab(std::max<int64_t>(n, 1) * r, &G.W[k]);
+    if (!rc) rc = grab(std::max<int64_t>(n, 1) * r, &G.itot);
+    if (!rc) rc = grab(std::max<int64_t>(n, 1) * r, &G.act);
+    if (!rc) rc = put(g.row, &q), G.row = static_cast<const int *>(q);
+    if (!rc) rc = put(g.col, &q), G.col = static_cast<const int *>(q);
+    if (!rc) {
+        if (prec == EP_FP64_PLAIN) rc = put(g.coef, &q);
+        else {
+            std::vector<float> f(g.coef.begin(), g.coef.end());
+            rc = put(f, &q);
+        }
+        G.coef = q;
+    }
+    if (!rc) rc = put(g.pset, &q), G.pset = static_cast<const uint8_t *>(q);
+    if (!rc) rc = put(g.smask, &q), G.smask = static_cast<const uint8_t *>(q);
+    for (int md = 0; md < EP_N_MODELS && !rc; ++md) {
+        DevRegion &rg = G.reg[md];
+        rg.off = g.model_off[md];
+        rg.n = g.model_off[md + 1] - g.model_off[md];
+        rg.stride = round_up(std::max<int64_t>(rg.n, 1), 64);
+        rg.r = nullptr;
+        rg.a = nullptr;
+        if (rg.n == 0) continue;
+        rc = grab(size_t(model_nr(md)) * rg.stride * r, &rg.r);
+        if (!rc) rc = grab(size_t(model_na(md)) * rg.stride * 8, &q), rg.a = static_cast<double *>(q);
+    }
+    const int64_t nj = int64_t(g.jnode.size());
+    G.n_junc = int(nj);
+    if (!rc) rc = put(g.jnode, &q), G.jnode = static_cast<const int *>(q);
+    if (!rc) rc = put(g.jcell, &q), G.jcell = static_cast<const int *>(q);
+    if (!rc) rc = put(g.jmode, &q), G.jmode = static_cast<const uint8_t *>(q);
+    std::vector<double> neg(std::max<int64_t>(nj, 1), -INFINITY);
+    if (!rc) rc = put(neg, &q), G.t_graph = static_cast<double *>(q);
+    if (!rc) rc = put(neg, &q), G.t_cell = static_cast<double *>(q);
+    if (!rc) rc = put(g.node_junc_ptr, &q), G.node_junc_ptr = static_cast<const int *>(q);
+    if (!rc) rc = put(g.node_junc, &q), G.node_junc = static_cast<const int *>(q);
+    if (!rc) rc = put(g.tgt_cell, &q), G.tgt_cell = static_cast<const int *>(q);
+    if (!rc) rc = put(g.tgt_junc, &q), G.tgt_junc = static_cast<const int *>(q);
+    if (!rc) rc = put(g.new2old, &q), job->gperm_dev = static_cast<const int *>(q);
+    if (rc) return rc;
+    G.n_tgt = int(g.tgt_cell.size());
+    G.two_way = g.p.two_way;
+    G.substeps = g.substeps = std::max(1, int(std::ceil(job->params.dt * g.rho / 1.8)));
+    G.g_graph = g.p.g_graph;
+    G.g_cell = g.p.g_cell;
+    G.threshold = g.p.threshold;
+    G.delay_ortho = g.p.delay_ortho;
+    G.delay_anti = g.p.delay_anti;
+    G.amplitude = g.p.amplitude;
+    G.duration = g.p.duration;
+    G.h = job->params.dt / g.substeps;
+    G.g_graph_f = float(G.g_graph);
+    G.g_cell_f = float(G.g_cell);
+    G.amplitude_f = float(G.amplitude);
+    G.h_f = float(G.h);
+    job->dj.g = G;
+    // junction flags in the cells' parameter-set bytes
+    std::vector<uint8_t> ps(m.pset);
+    for (int32_t c : g.tgt_cell) ps[c] |= uint8_t(kJunctionFlag);
+    cudaError_t e = cudaMemcpyAsync(const_cast<uint8_t *>(job->dj.pset), ps.data(), ps.size(), cudaMemcpyHostToDevice,
+                                    ctx->upload);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(job->dj_dev.p, &job->dj, sizeof(DevJob), cudaMemcpyHostToDevice, ctx->upload);
+    // the graph view: a DevJob whose cells are the graph nodes, for init and state transfer
+    DevJob view = job->dj;
+    view.V[0] = G.V[0];
+    view.V[1] = G.V[1];
+    view.act = G.act;
+    view.n_cells = n;
+    for (int md = 0; md < EP_N_MODELS; ++md) view.reg[md] = G.reg[md];
+    view.pset = G.pset;
+    if (e == cudaSuccess && (rc = dalloc(ctx, sizeof(DevJob), &job->graph_view))) return rc;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(job->graph_view.p, &view, sizeof(DevJob), cudaMemcpyHostToDevice, ctx->upload);
+    if (e == cudaSuccess && n > 0)
+        e = launch_init(prec, static_cast<const DevJob *>(job->graph_view.p), n, ctx->upload);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->upload);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph upload");
+    job->graph_tiles.clear();
+    for (int md = 0; md < EP_N_MODELS; ++md)
+        for (int64_t s = g.model_off[md]; s < g.model_off[md + 1]; s += kGraphThreads)
+            job->graph_tiles.push_back(
+                Tile{0, md, int(s), int(std::min<int64_t>(kGraphThreads, g.model_off[md + 1] - s))});
+    job->version++;
+    for (auto &b : job->gbufs) job->device_bytes += b.bytes;
+    return EP_OK;
 }
 
 }  // namespace
@@ -611,13 +739,18 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
     for (int i = 0; i < n; ++i) pl->versions.push_back(jobs[i]->version);
     for (int prec : {EP_FP32_MIXED, EP_FP64_PLAIN}) {
         std::vector<DevJob> tab;
-        std::vector<Tile> nt, ct;
+        std::vector<Tile> nt, ct, gt;
+        int max_sub = 0;
         for (int i = 0; i < n; ++i) {
             if (jobs[i]->precision != prec) continue;
             const int jid = int(tab.size());
             tab.push_back(jobs[i]->dj);
             for (Tile t : jobs[i]->node_tiles) nt.push_back(Tile{jid, t.model, t.start, t.count});
             for (Tile t : jobs[i]->cell_tiles) ct.push_back(Tile{jid, t.model, t.start, t.count});
+            if (jobs[i]->gp) {
+                for (Tile t : jobs[i]->graph_tiles) gt.push_back(Tile{jid, t.model, t.start, t.count});
+                max_sub = std::max(max_sub, jobs[i]->gp->substeps);
+            }
         }
         if (tab.empty()) continue;
         Plan::Group g{};
@@ -641,6 +774,18 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
         g.L.cell_tiles = static_cast<const Tile *>(g.cell_tiles.p);
         g.L.n_cell_tiles = int(ct.size());
         g.L.done = static_cast<unsigned *>(g.done.p);
+        g.L.graph_tiles = nullptr;
+        g.L.n_graph_tiles = 0;
+        g.L.graph_substeps = 0;
+        g.L.graph_grid = 1;
+        if (!gt.empty()) {
+            if ((rc = upload(ctx, gt, &tmp, &p))) return rc;
+            g.graph_tiles = tmp.back();
+            g.L.graph_tiles = static_cast<const Tile *>(g.graph_tiles.p);
+            g.L.n_graph_tiles = int(gt.size());
+            g.L.graph_substeps = max_sub;
+            g.L.graph_grid = std::max(1, std::min<int>(int(gt.size()), ctx->sm_count * 4));
+        }
         g.L.node_grid = std::max(1, std::min<int>(int(nt.size()), ctx->sm_count * node_blocks_per_sm(prec)));
         g.L.cell_variant = ctx->cell_variant[prec];
         g.L.cell_grid =
@@ -759,6 +904,7 @@ int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double
             for (auto &gr : pl->groups) {
                 e = cudaEventRecord(ev[k++], ctx->stream);
                 if (e == cudaSuccess) e = launch_node(gr.precision, gr.L, ctx->stream);
+                if (e == cudaSuccess) e = launch_graph(gr.precision, gr.L, ctx->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(ev[k++], ctx->stream);
                 if (e == cudaSuccess) e = launch_cell(gr.precision, gr.L, ctx->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(ev[k++], ctx->stream);
@@ -845,6 +991,7 @@ int ep_autotune(ep_job *const *jobs, int32_t n_jobs, int32_t steps_per_variant, 
                     for (auto &other : pl->groups) {
                         if (&other == &gr) {
                             e = launch_node(gr.precision, gr.L, ctx->stream);
+                            if (e == cudaSuccess) e = launch_graph(gr.precision, gr.L, ctx->stream);
                             if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
                             if (e == cudaSuccess) e = launch_cell(gr.precision, gr.L, ctx->stream);
                             if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
@@ -969,8 +1116,12 @@ int ep_set_step_index(ep_job *job, int64_t n) {
     if (rc) return rc;
     cudaError_t e = cudaSuccess;
     if (job->has_params && ((cur ^ n) & 1)) {
-        const size_t bytes = job->mesh().n_cells * (job->precision == EP_FP64_PLAIN ? 8 : 4);
-        e = cudaMemcpyAsync(job->dj.V[n & 1], job->dj.V[cur & 1], bytes, cudaMemcpyDeviceToDevice, job->ctx->stream);
+        const size_t r = job->precision == EP_FP64_PLAIN ? 8 : 4;
+        e = cudaMemcpyAsync(job->dj.V[n & 1], job->dj.V[cur & 1], job->mesh().n_cells * r, cudaMemcpyDeviceToDevice,
+                            job->ctx->stream);
+        if (e == cudaSuccess && job->gp && job->gp->n > 0)
+            e = cudaMemcpyAsync(job->dj.g.V[n & 1], job->dj.g.V[cur & 1], job->gp->n * r, cudaMemcpyDeviceToDevice,
+                                job->ctx->stream);
     }
     long long v = n;
     if (e == cudaSuccess) e = cudaMemcpyAsync(job->step_dev.p, &v, sizeof(v), cudaMemcpyHostToDevice, job->ctx->stream);
@@ -1017,6 +1168,8 @@ int ep_job_destroy(ep_job *job) {
     drop_plans_with(ctx, job);
     free_job_arrays(job, &job->prec);
     free_job_arrays(job, &job->topo);
+    free_job_arrays(job, &job->gbufs);
+    dfree(ctx, &job->graph_view);
     dfree(ctx, &job->dj_dev);
     dfree(ctx, &job->step_dev);
     ctx->jobs.erase(job);
@@ -1076,6 +1229,7 @@ int ep_step_noalloc(ep_job *job, int64_t n_steps) {
     ep_context *ctx = job->ctx;
     if (n_steps < 0) return fail(ctx, EP_EINVAL, "ep_step_noalloc: n_steps < 0");
     if (!job->has_params) return fail(ctx, EP_ESTATE, "ep_step_noalloc: the job has no parameters");
+    if (job->gp) return fail(ctx, EP_EINVAL, "ep_step_noalloc: jobs with a conduction graph need ep_step");
     if (job->mesh().n_nodes > EP_NOALLOC_MAX_NODES)
         return fail(ctx, EP_EINVAL, "ep_step_noalloc: the mesh has " + std::to_string(job->mesh().n_nodes) +
                                         " nodes; at most " + std::to_string(EP_NOALLOC_MAX_NODES) +
@@ -1085,6 +1239,77 @@ int ep_step_noalloc(ep_job *job, int64_t n_steps) {
     cudaError_t e = launch_step_noalloc(job->precision, static_cast<const DevJob *>(job->dj_dev.p), job->mesh().n_nodes,
                                         job->mesh().n_cells, n_steps, ctx->stream);
     return e == cudaSuccess ? EP_OK : cuda_fail(ctx, e, "ep_step_noalloc");
+}
+
+int ep_graph_attach(ep_job *job, const ep_graph_desc *desc, const ep_graph_params *params) {
+    if (!job || !desc || !params) return EP_EINVAL;
+    ep_context *ctx = job->ctx;
+    if (!job->has_params) return fail(ctx, EP_ESTATE, "ep_graph_attach: set the job's parameters first");
+    DeviceGuard g(ctx->device);
+    try {
+        std::unique_ptr<GraphPlan> gp(new GraphPlan());
+        std::string err;
+        int rc = build_graph(job->mesh(), desc, params, &job->params, gp.get(), &err);
+        if (rc) return fail(ctx, rc, "ep_graph_attach: " + err);
+        job->gp = std::move(gp);
+        rc = graph_apply(job);
+        if (rc) {
+            for (auto &b : job->gbufs) dfree(ctx, &b);
+            job->gbufs.clear();
+            job->gp.reset();
+        }
+        return rc;
+    } catch (const std::bad_alloc &) {
+        return fail(ctx, EP_ENOMEM, "ep_graph_attach: out of host memory");
+    }
+}
+
+static int graph_io(ep_job *job, int32_t model, int32_t var, double *host, int64_t n, int kind) {
+    if (!job) return EP_EINVAL;
+    ep_context *ctx = job->ctx;
+    if (!job->gp) return fail(ctx, EP_ESTATE, "no conduction graph attached");
+    if (!host || n != job->gp->n) return fail(ctx, EP_EINVAL, "buffer length differs from the number of graph nodes");
+    if (kind != 2 && (model < 0 || model >= EP_N_MODELS || var < 0 || var >= model_nvar(model)))
+        return fail(ctx, EP_EINVAL, "unknown model or variable id");
+    if (n == 0) return EP_OK;
+    DeviceGuard g(ctx->device);
+    DevBuf b;
+    int rc = dalloc(ctx, n * sizeof(double), &b);
+    if (rc) return rc;
+    const DevJob *view = static_cast<const DevJob *>(job->graph_view.p);
+    double *buf = static_cast<double *>(b.p);
+    cudaError_t e = cudaSuccess;
+    if (kind == 1) {
+        e = cudaMemcpyAsync(buf, host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = launch_scatter(job->precision, view, job->gperm_dev, n, model, var, buf, ctx->stream);
+    } else {
+        e = kind == 0 ? launch_gather(job->precision, view, job->gperm_dev, n, model, var, buf, ctx->stream)
+                      : launch_gather_act(job->precision, view, job->gperm_dev, n, buf, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host, buf, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, &b);
+    return e == cudaSuccess ? EP_OK : cuda_fail(ctx, e, "graph state transfer");
+}
+
+int ep_graph_read_state(ep_job *job, int32_t model, int32_t var, double *host_out, int64_t n) {
+    return graph_io(job, model, var, host_out, n, 0);
+}
+
+int ep_graph_write_state(ep_job *job, int32_t model, int32_t var, const double *host_in, int64_t n) {
+    return graph_io(job, model, var, const_cast<double *>(host_in), n, 1);
+}
+
+int ep_graph_activation_times(ep_job *job, double *host_out, int64_t n) {
+    return graph_io(job, 0, 0, host_out, n, 2);
+}
+
+int ep_graph_info(const ep_job *job, int64_t *n_nodes, int32_t *substeps, int64_t *n_junctions) {
+    if (!job) return EP_EINVAL;
+    if (n_nodes) *n_nodes = job->gp ? job->gp->n : 0;
+    if (substeps) *substeps = job->gp ? job->gp->substeps : 0;
+    if (n_junctions) *n_junctions = job->gp ? int64_t(job->gp->jnode.size()) : 0;
+    return EP_OK;
 }
 
 }  // extern "C"

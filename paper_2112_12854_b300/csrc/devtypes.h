@@ -39,6 +39,31 @@ struct DevRegion {
     long long n;
 };
 
+// Conduction graph of a job (n_nodes == 0: none). Node potentials are
+// double-buffered by the job's step parity like the cells' V.
+struct DevGraph {
+    long long n_nodes;
+    void *V[2];
+    void *W[2];                 // substep buffers
+    void *itot;                 // reaction current frozen over the step's substeps
+    void *act;
+    const int *row, *col;       // neighbours (CSR)
+    const void *coef;           // c_ij
+    const uint8_t *pset, *smask;
+    DevRegion reg[EP_N_MODELS];
+    int substeps;
+    int n_junc;
+    const int *jnode, *jcell;
+    const uint8_t *jmode;
+    double *t_graph, *t_cell;   // last upward threshold crossing of each junction's two sides
+    const int *node_junc_ptr, *node_junc;
+    const int *tgt_cell, *tgt_junc;
+    int n_tgt;
+    int two_way;
+    double g_graph, g_cell, threshold, delay_ortho, delay_anti, amplitude, duration, h;
+    float g_graph_f, g_cell_f, amplitude_f, h_f;
+};
+
 struct DevJob {
     const int4 *nodes_a;      // the cell's 4 vertices
     const int4 *nodes_b;      // vertex of the neighbour opposite each face (own vertex 0 on the boundary)
@@ -61,6 +86,7 @@ struct DevJob {
     double dt, threshold;
     float dt_f, threshold_f;
     long long *step;          // steps taken (device counter)
+    DevGraph g;
 };
 
 // A tile is a run of consecutive cells (or nodes) of one job and one model.
@@ -72,6 +98,8 @@ struct Tile {
 };
 
 constexpr int kCellThreads = 256;
+constexpr int kGraphThreads = 256;
+constexpr unsigned kJunctionFlag = 0x80;   // set in a cell's parameter-set byte when a junction touches it
 constexpr int kNodeThreads = 256;
 
 }  // namespace ep

@@ -62,6 +62,48 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const DevJob *__rest
     }
 }
 
+__device__ __forceinline__ bool window_on(double t_trig, double delay, double dur, double t) {
+    return t_trig > -INFINITY && t >= t_trig + delay && t < t_trig + delay + dur;
+}
+
+// Junction terms of a cell touched by the conduction graph (Sec. 3.3): the
+// resistive current g_cell (V_m - V_p) and the triggered stimulus. The
+// cell's (cell, junction) entries are found by binary search.
+template <class R>
+__device__ void junction_cell_terms(const DevJob &J, long long c, long long n, R Vc, R &is, R &ix, int &first,
+                                    int &last) {
+    const DevGraph &G = J.g;
+    int lo = 0, hi = G.n_tgt;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (G.tgt_cell[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    first = lo;
+    const R *Vg = static_cast<const R *>(G.V[n & 1]);
+    const double t = double(n) * J.dt;
+    int k = lo;
+    for (; k < G.n_tgt && G.tgt_cell[k] == c; ++k) {
+        const int j = G.tgt_junc[k];
+        if (G.jmode[j] == EP_PMJ_RESISTIVE) ix += pick<R>(G.g_cell, G.g_cell_f) * (Vc - Vg[G.jnode[j]]);
+        else if (window_on(G.t_graph[j], G.delay_ortho, G.duration, t)) is += pick<R>(G.amplitude, G.amplitude_f);
+    }
+    last = k;
+}
+
+// Muscle-side threshold crossing of two-way triggered junctions.
+template <class R>
+__device__ void junction_cell_crossing(const DevJob &J, long long c, long long n, R v0, R v1, int first, int last) {
+    const DevGraph &G = J.g;
+    const double th = G.threshold;
+    if (!(double(v0) < th && double(v1) >= th)) return;
+    for (int k = first; k < last; ++k) {
+        const int j = G.tgt_junc[k];
+        if (G.jmode[j] == EP_PMJ_TRIGGERED && G.jcell[j] == c)
+            G.t_cell[j] = double(n) * J.dt + J.dt * (th - double(v0)) / (double(v1) - double(v0));
+    }
+}
+
 template <class R>
 __device__ __forceinline__ void cell_update(const DevJob &J, int model, long long c) {
     using R4 = typename Vec4T<R>::type;
@@ -80,8 +122,12 @@ __device__ __forceinline__ void cell_update(const DevJob &J, int model, long lon
     diff += q.x * (V[nc.x] - Vc) + q.y * (V[nc.y] - Vc) + q.z * (V[nc.z] - Vc) + q.w * (V[nc.w] - Vc);
 
     const unsigned mask = J.smask[c];
-    const R is = mask ? stimulus<R>(J, mask, n) : R(0);
-    const DevParams &P = J.params[J.pset[c]];
+    R is = mask ? stimulus<R>(J, mask, n) : R(0);
+    const unsigned ps = J.pset[c];
+    R ix = R(0);
+    int jfirst = 0, jlast = 0;
+    if (ps & kJunctionFlag) junction_cell_terms<R>(J, c, n, Vc, is, ix, jfirst, jlast);
+    const DevParams &P = J.params[ps & (EP_MAX_PARAM_SETS - 1)];
     const R dt = pick<R>(J.dt, J.dt_f);
     const DevRegion &rg = J.reg[model];
     const long long li = c - rg.off;
@@ -89,12 +135,97 @@ __device__ __forceinline__ void cell_update(const DevJob &J, int model, long lon
     if (model == EP_TP06) iion = tt_step<R, false>(rg, li, P, Vc, dt, is);
     else if (model == EP_STEWART) iion = tt_step<R, true>(rg, li, P, Vc, dt, is);
     else iion = crn_step<R>(rg, li, P, Vc, dt);
-    const R Vn = Vc + dt * (diff - iion - is);
+    const R Vn = Vc + dt * (diff - iion - is - ix);
     Vnext[c] = Vn;
+    if ((ps & kJunctionFlag) && J.g.two_way) junction_cell_crossing<R>(J, c, n, Vc, Vn, jfirst, jlast);
     const R th = pick<R>(J.threshold, J.threshold_f);
     if (Vc < th && Vn >= th) {
         R *act = static_cast<R *>(J.act);
         if (isinf(act[c])) act[c] = R(double(n) * J.dt) + dt * (th - Vc) / (Vn - Vc);
+    }
+}
+
+// Conduction graph, part 1 (Sec. 3.2 / 3.3): the reaction of every graph node
+// at (V^n, s^n) -- cell model, stimulus protocols, antidromic triggered
+// stimulus and resistive junction current -- frozen for the step's substeps.
+template <class R>
+__global__ void __launch_bounds__(kGraphThreads) graph_ionic_kernel(const DevJob *__restrict__ jobs,
+                                                                    const Tile *__restrict__ tiles, int n_tiles) {
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        const DevJob &J = jobs[tl.job];
+        const DevGraph &G = J.g;
+        for (int i = threadIdx.x; i < tl.count; i += blockDim.x) {
+            const long long node = (long long)tl.start + i;
+            const long long n = *J.step;
+            const double tn = double(n) * J.dt;
+            const R Vg = static_cast<const R *>(G.V[n & 1])[node];
+            const R *V3 = static_cast<const R *>(J.V[n & 1]);
+            const unsigned mask = G.smask[node];
+            R is = mask ? stimulus<R>(J, mask, n) : R(0);
+            R ix = R(0);
+            for (int k = G.node_junc_ptr[node]; k < G.node_junc_ptr[node + 1]; ++k) {
+                const int j = G.node_junc[k];
+                if (G.jmode[j] == EP_PMJ_RESISTIVE) ix += pick<R>(G.g_graph, G.g_graph_f) * (Vg - V3[G.jcell[j]]);
+                else if (G.two_way && window_on(G.t_cell[j], G.delay_anti, G.duration, tn))
+                    is += pick<R>(G.amplitude, G.amplitude_f);
+            }
+            const DevParams &P = J.params[G.pset[node]];
+            const R dt = pick<R>(J.dt, J.dt_f);
+            const DevRegion &rg = G.reg[tl.model];
+            const long long li = node - rg.off;
+            R iion;
+            if (tl.model == EP_TP06) iion = tt_step<R, false>(rg, li, P, Vg, dt, is);
+            else if (tl.model == EP_STEWART) iion = tt_step<R, true>(rg, li, P, Vg, dt, is);
+            else iion = crn_step<R>(rg, li, P, Vg, dt);
+            static_cast<R *>(G.itot)[node] = iion + is + ix;
+        }
+    }
+}
+
+// Conduction graph, part 2: diffusion substep s of each job's k substeps of
+// h = dt / k (a job with fewer substeps than the batch's largest copies its
+// values through). The last substep writes V^{n+1}, the activation times and
+// the graph-side junction crossings.
+template <class R>
+__global__ void __launch_bounds__(kGraphThreads) graph_diffuse_kernel(const DevJob *__restrict__ jobs,
+                                                                      const Tile *__restrict__ tiles, int n_tiles,
+                                                                      int s, int last) {
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        const DevJob &J = jobs[tl.job];
+        const DevGraph &G = J.g;
+        const long long n = *J.step;
+        const R *Win = static_cast<const R *>(s == 0 ? G.V[n & 1] : G.W[s & 1]);
+        const R *cf = static_cast<const R *>(G.coef);
+        for (int i = threadIdx.x; i < tl.count; i += blockDim.x) {
+            const long long node = (long long)tl.start + i;
+            const R w = Win[node];
+            R out = w;
+            if (s < G.substeps) {
+                R lap = R(0);
+                for (int e = G.row[node]; e < G.row[node + 1]; ++e) lap += cf[e] * (Win[G.col[e]] - w);
+                out = w + pick<R>(G.h, G.h_f) * (lap - static_cast<const R *>(G.itot)[node]);
+            }
+            if (!last) {
+                static_cast<R *>(G.W[(s + 1) & 1])[node] = out;
+                continue;
+            }
+            static_cast<R *>(G.V[(n & 1) ^ 1])[node] = out;
+            const R v0 = static_cast<const R *>(G.V[n & 1])[node];
+            const R th = pick<R>(J.threshold, J.threshold_f);
+            if (v0 < th && out >= th) {
+                R *act = static_cast<R *>(G.act);
+                if (isinf(act[node])) act[node] = R(double(n) * J.dt) + pick<R>(J.dt, J.dt_f) * (th - v0) / (out - v0);
+            }
+            const double gth = G.threshold;
+            if (double(v0) < gth && double(out) >= gth)
+                for (int k = G.node_junc_ptr[node]; k < G.node_junc_ptr[node + 1]; ++k) {
+                    const int j = G.node_junc[k];
+                    if (G.jmode[j] == EP_PMJ_TRIGGERED)
+                        G.t_graph[j] = double(n) * J.dt + J.dt * (gth - double(v0)) / (double(out) - double(v0));
+                }
+        }
     }
 }
 
@@ -217,8 +348,24 @@ static int grid_for(long long n, int threads) {
 }
 
 template <class R>
+static cudaError_t graph_impl(const StepLaunch &L, cudaStream_t s) {
+    if (L.n_graph_tiles > 0) {
+        graph_ionic_kernel<R><<<L.graph_grid, kGraphThreads, 0, s>>>(L.jobs, L.graph_tiles, L.n_graph_tiles);
+        for (int k = 0; k < L.graph_substeps; ++k)
+            graph_diffuse_kernel<R><<<L.graph_grid, kGraphThreads, 0, s>>>(L.jobs, L.graph_tiles, L.n_graph_tiles, k,
+                                                                           k == L.graph_substeps - 1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_graph(int precision, const StepLaunch &L, cudaStream_t s) {
+    return precision == EP_FP64_PLAIN ? graph_impl<double>(L, s) : graph_impl<float>(L, s);
+}
+
+template <class R>
 static cudaError_t step_impl(const StepLaunch &L, cudaStream_t s) {
     node_kernel<R><<<L.node_grid, kNodeThreads, 0, s>>>(L.jobs, L.node_tiles, L.n_node_tiles);
+    graph_impl<R>(L, s);
     return launch_cell(sizeof(R) == 8 ? EP_FP64_PLAIN : EP_FP32_MIXED, L, s);
 }
 

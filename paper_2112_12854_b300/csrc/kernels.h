@@ -16,6 +16,10 @@ struct StepLaunch {
     unsigned *done;            // device counter used to advance the step counters
     int node_grid, cell_grid;  // persistent grid sizes
     int cell_variant;          // launch shape of the cell kernel (EP_CELL_VARIANTS)
+    const Tile *graph_tiles;   // conduction-graph nodes of all jobs (none: n_graph_tiles = 0)
+    int n_graph_tiles;
+    int graph_grid;
+    int graph_substeps;        // largest substep count of the jobs' graphs
 };
 
 // Launch shapes of the cell kernel: (index, threads per block, minimum
@@ -30,16 +34,19 @@ struct StepLaunch {
 constexpr int kNumCellVariants = 6;
 int cell_variant_threads(int variant);
 
-// One time step of every job in the table: node values, then the fused
-// diffusion + cell-model + activation update.
+// One time step of every job in the table: node values, the conduction
+// graphs (reaction, then the diffusion substeps), then the fused diffusion +
+// cell-model + activation update.
 cudaError_t launch_step(int precision, const StepLaunch &L, cudaStream_t s);
 
 // Set the state of every cell to its model's resting state, activation
 // times to +inf (job given by a device pointer to its DevJob).
 cudaError_t launch_init(int precision, const DevJob *job, long long n_cells, cudaStream_t s);
 
-// The two launches of launch_step, separately (for timing).
+// The parts of launch_step, separately (for timing): node values, the
+// conduction graphs (no launch when no job has one), the cell update.
 cudaError_t launch_node(int precision, const StepLaunch &L, cudaStream_t s);
+cudaError_t launch_graph(int precision, const StepLaunch &L, cudaStream_t s);
 cudaError_t launch_cell(int precision, const StepLaunch &L, cudaStream_t s);
 
 // Copy variable `var` of `model` (all cells for var 0 = V) into out[n_cells]

@@ -52,6 +52,21 @@ class Params(ctypes.Structure):
                 ("stim", Stimulus * MAX_STIM), ("threshold", ctypes.c_double)]
 
 
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("xyz", ctypes.c_void_p), ("n_edges", ctypes.c_int64),
+                ("edges", ctypes.c_void_p), ("edge_D", ctypes.c_void_p), ("node_model", ctypes.c_void_p),
+                ("node_param_set", ctypes.c_void_p), ("node_stim_mask", ctypes.c_void_p),
+                ("n_junctions", ctypes.c_int64), ("junction_node", ctypes.c_void_p),
+                ("junction_cell", ctypes.c_void_p), ("junction_mode", ctypes.c_void_p)]
+
+
+class GraphParamsC(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_double), ("g_graph", ctypes.c_double), ("g_cell", ctypes.c_double),
+                ("threshold", ctypes.c_double), ("delay_ortho", ctypes.c_double), ("delay_anti", ctypes.c_double),
+                ("amplitude", ctypes.c_double), ("duration", ctypes.c_double), ("radius", ctypes.c_double),
+                ("two_way", ctypes.c_int32), ("default_mode", ctypes.c_int32)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 
@@ -64,7 +79,8 @@ EXPORTS = ["ep_context_create", "ep_context_set_stream", "ep_context_destroy", "
            "ep_check_finite", "ep_job_info", "ep_estimate_bytes", "ep_job_destroy", "ep_model_nvar",
            "ep_model_varname", "ep_plan_inspect", "ep_time_kernels",
            "ep_step_noalloc", "ep_autotune", "ep_set_cell_variant", "ep_plan_create", "ep_plan_bytes",
-           "ep_plan_info", "ep_plan_destroy", "ep_job_create"]
+           "ep_plan_info", "ep_plan_destroy", "ep_job_create", "ep_graph_attach", "ep_graph_read_state",
+           "ep_graph_write_state", "ep_graph_activation_times", "ep_graph_info"]
 
 _lib = None
 _P = ctypes.c_void_p
@@ -101,6 +117,12 @@ def load():
         "ep_model_nvar": ([ctypes.c_int32], ctypes.c_int32),
         "ep_model_varname": ([ctypes.c_int32, ctypes.c_int32], ctypes.c_char_p),
         "ep_step_noalloc": ([_P, _I64], ctypes.c_int),
+        "ep_graph_attach": ([_P, ctypes.POINTER(GraphDesc), ctypes.POINTER(GraphParamsC)], ctypes.c_int),
+        "ep_graph_read_state": ([_P, ctypes.c_int32, ctypes.c_int32, _P, _I64], ctypes.c_int),
+        "ep_graph_write_state": ([_P, ctypes.c_int32, ctypes.c_int32, _P, _I64], ctypes.c_int),
+        "ep_graph_activation_times": ([_P, _P, _I64], ctypes.c_int),
+        "ep_graph_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_I64)],
+                          ctypes.c_int),
         "ep_plan_create": ([ctypes.POINTER(MeshDesc), ctypes.POINTER(Params), ctypes.POINTER(_P)], ctypes.c_int),
         "ep_plan_bytes": ([_P], _I64),
         "ep_plan_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
@@ -334,6 +356,60 @@ class Job:
         self.ctx.check(load().ep_job_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                           ctypes.byref(d)))
         return dict(n_cells=a.value, n_nodes=b.value, n_interior_faces=c.value, device_bytes=d.value)
+
+    def attach_graph(self, graph, *, node_model=None):
+        """Attach a conduction graph (an object like ``workloads.Graph``:
+        xyz, edges, edge_D, param_set, stim_mask, junction_node/cell/mode,
+        params). node_model defaults to the models of the graph's parameter
+        sets when ``model_of_set`` is given on the graph, else Stewart."""
+        L = load()
+        keep = []
+
+        def arr(a, dt):
+            if a is None:
+                return None
+            b = np.ascontiguousarray(a, dtype=dt)
+            keep.append(b)
+            return _ptr(b)
+        d = GraphDesc()
+        d.n_nodes = int(np.asarray(graph.xyz).shape[0])
+        d.xyz = arr(graph.xyz, np.float64)
+        d.n_edges = int(np.asarray(graph.edges).reshape(-1, 2).shape[0])
+        d.edges = arr(np.asarray(graph.edges).reshape(-1, 2), np.int32)
+        d.edge_D = arr(graph.edge_D, np.float64)
+        d.node_model = arr(node_model, np.uint8)
+        d.node_param_set = arr(graph.param_set, np.uint8)
+        d.node_stim_mask = arr(graph.stim_mask, np.uint8)
+        d.n_junctions = int(np.asarray(graph.junction_node).size)
+        d.junction_node = arr(graph.junction_node, np.int32)
+        d.junction_cell = arr(graph.junction_cell, np.int32)
+        d.junction_mode = arr(graph.junction_mode, np.uint8)
+        gp = graph.params
+        p = GraphParamsC(gp.D, gp.g_graph, gp.g_cell, gp.threshold, gp.delay_ortho, gp.delay_anti, gp.amplitude,
+                         gp.duration, gp.radius, int(gp.two_way), 0)
+        self.ctx.check(L.ep_graph_attach(self._h, ctypes.byref(d), ctypes.byref(p)))
+        self.n_graph = d.n_nodes
+
+    def graph_read(self, var, model: int = EP_STEWART, out=None) -> np.ndarray:
+        if isinstance(var, str):
+            var = model_varnames(model).index(var)
+        out = np.empty(self.n_graph, np.float64) if out is None else out
+        self.ctx.check(load().ep_graph_read_state(self._h, model, var, _ptr(out), self.n_graph))
+        return out
+
+    def graph_write(self, var, values, model: int = EP_STEWART):
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        self.ctx.check(load().ep_graph_write_state(self._h, model, int(var), _ptr(v), self.n_graph))
+
+    def graph_activation_times(self) -> np.ndarray:
+        out = np.empty(self.n_graph, np.float64)
+        self.ctx.check(load().ep_graph_activation_times(self._h, _ptr(out), self.n_graph))
+        return out
+
+    def graph_info(self) -> dict:
+        a, b, c = _I64(), ctypes.c_int32(), _I64()
+        self.ctx.check(load().ep_graph_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return dict(n_nodes=a.value, substeps=b.value, n_junctions=c.value)
 
     def destroy(self):
         if getattr(self, "_h", None):

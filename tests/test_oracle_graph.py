@@ -166,3 +166,23 @@ def test_triggered_junction_equals_delayed_stimulus(orc):
     assert np.array_equal(np.isfinite(a), np.isfinite(b)) and np.all(np.isfinite(a[near]))
     assert np.allclose(a[np.isfinite(a)], b[np.isfinite(b)], atol=1e-9)
     assert np.all(a[near] > tp + gp.delay_ortho)
+
+
+def test_atrial_bundle_velocity_matches_table2(orc):
+    """A Courtemanche cable with D = m / (chi C_m) for Table 2's 1D bundle
+    conductivity conducts at the 1.54 m/s Table 2 states (within 10 %)."""
+    gd = _golden("table2_bundle.txt")
+    D = gd["m_bundle"] / (gd["chi"] * gd["C_m"])
+    ds, dt, n = 0.2, 0.02, 61
+    case = _tet_case(dt)
+    case.param_sets = case.param_sets + [w.ParamSet(model=1)]
+    g = w.chain_graph(n, ds, param_set=2, stim_nodes=10, params=w.GraphParams(D=D))
+    s = orc.Sim(case)
+    s.attach_graph(g)
+    s.run(int(round(30 / dt)))
+    a = s.graph_activation_times()
+    x = np.arange(n) * ds
+    sel = (x > 3) & (x < 11)
+    assert np.all(np.isfinite(a[sel]))
+    cv = np.polyfit(a[sel], x[sel], 1)[0]
+    assert abs(cv - gd["velocity_mm_per_ms"]) < 0.1 * gd["velocity_mm_per_ms"]

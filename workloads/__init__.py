@@ -392,3 +392,173 @@ def chain_graph(n, ds, start=(0.0, 0.0, 0.0), direction=(1.0, 0.0, 0.0), *, para
     sm[:stim_nodes] = 1
     return Graph(xyz, edges, np.full(n, param_set, np.uint8), sm, np.zeros(0, np.int32), np.zeros(0, np.int32),
                  np.zeros(0, np.uint8), params or GraphParams())
+
+
+def _project(q, c, ax):
+    """Radial projection of q onto the ellipsoid (centre c, semi-axes ax)."""
+    r = _ell(q[None], c, ax)[0]
+    return np.asarray(c) + (q - np.asarray(c)) / r
+
+
+def _normal(q, c, ax):
+    g = 2.0 * (q - np.asarray(c)) / np.asarray(ax) ** 2
+    return g / np.linalg.norm(g)
+
+
+def _rotate(v, axis, th):
+    """Rodrigues rotation of v about a unit axis by th radians."""
+    return (v * np.cos(th) + np.cross(axis, v) * np.sin(th) + axis * np.dot(axis, v) * (1 - np.cos(th)))
+
+
+def grow_tree(rng, start, centre, axes, n_target, ds=0.2, seg_len=(1.0, 3.0), angle_deg=(30.0, 60.0),
+              z_max=18.0, first_dir=(0.0, 0.0, -1.0)):
+    """Seeded fractal tree on an ellipsoidal surface: straight segments of
+    length U[seg_len] sampled every ds, each ending in a bifurcation whose
+    children turn by +/- U[angle_deg] about the surface normal; nodes are
+    projected onto the surface; branches stop above z_max (the base).
+    Returns (xyz, edges, parent-order node list); node 0 is `start`."""
+    start = _project(np.asarray(start, float), centre, axes)
+    xyz, edges = [start], []
+    d0 = np.asarray(first_dir, float)
+    n0 = _normal(start, centre, axes)
+    d0 = d0 - np.dot(d0, n0) * n0
+    active = [(0, d0 / np.linalg.norm(d0))]
+    while active and len(xyz) < n_target:
+        i, d = active.pop(0)
+        p, prev = xyz[i], i
+        m = max(1, int(round(rng.uniform(*seg_len) / ds)))
+        ok = True
+        for _ in range(m):
+            q = _project(p + ds * d, centre, axes)
+            if q[2] > z_max:
+                ok = False
+                break
+            xyz.append(q)
+            edges.append((prev, len(xyz) - 1))
+            d = (q - p) / np.linalg.norm(q - p)
+            p, prev = q, len(xyz) - 1
+            if len(xyz) >= n_target:
+                break
+        if not ok or prev == i:
+            continue
+        nrm = _normal(p, centre, axes)
+        for sign in (1.0, -1.0):
+            th = np.deg2rad(rng.uniform(*angle_deg))
+            d2 = _rotate(d, nrm, sign * th)
+            d2 -= np.dot(d2, nrm) * nrm
+            active.append((prev, d2 / np.linalg.norm(d2)))
+    return np.array(xyz), np.array(edges, np.int32).reshape(-1, 2)
+
+
+def whole_heart(h: float = 0.4, *, scale: float = 1.0, n_tree: int = 50_000, n_pmj: int = 2000,
+                ds: float = 0.2, dt: float = 0.02, n_steps: int = 40_000, seed: int = 3,
+                g_graph: float = 0.3, g_cell: float = 4.0):
+    """Synthetic whole-heart topology with its conduction system:
+    ventricles (TP06) and atria (Courtemanche) from heart_case; an atrial
+    bundle (Courtemanche, Table 2 1D conductivity) from the sinus node over
+    the right atrium to the AV node, with a branch to the left atrium; a low
+    diffusivity AV delay line to the His root; and two seeded fractal Stewart
+    trees (left and right bundle branches, Table 2 Purkinje conductivity)
+    grown on the ventricular endocardia until n_tree nodes in all. Up to
+    n_pmj tree terminals are paired with their nearest ventricular cell
+    through resistive junctions (PMJs); every 5th bundle node is a
+    communication node that triggers the nearest atrial cells (R_S = 1 mm,
+    Sec. 3.3). A sinus stimulus (S_d = 2.5 ms, Eq. 4) excites the sinus
+    node in 3D and the first bundle nodes. Geometry scaled by `scale`.
+    Returns (TissueCase, Graph)."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(MASTER_SEED + 3 + seed)
+    case = heart_case(h=h, scale=scale, dt=dt, n_steps=n_steps, av_delay=1e9)
+    case.param_sets.append(ParamSet(model=2))                 # set 3: Stewart (Purkinje)
+    ds_s = ds / scale                                          # node spacing in unscaled units
+    # atrial bundle over the right-atrial endocardium, sinus node -> AV node, with a branch to the LA
+    ra_ax = tuple(a - _ATRIAL_WALL + 0.5 for a in _RA_OUT)
+    la_ax = tuple(a - _ATRIAL_WALL + 0.5 for a in _LA_OUT)
+    sinus = np.array(_RA_C) + [0.0, 0.0, 11.0]
+    avn = np.array(_RA_C) + [12.0, 0.0, -9.0]
+
+    def surface_path(a, b, c, ax):
+        # project a dense chord onto the surface, then resample at equal arc length ds
+        dense = np.array([_project(a + (b - a) * t, c, ax) for t in np.linspace(0, 1, 2001)])
+        s_arc = np.concatenate([[0.0], np.cumsum(np.linalg.norm(np.diff(dense, axis=0), axis=1))])
+        m = max(2, int(np.ceil(s_arc[-1] / ds_s)))
+        t = np.linspace(0, s_arc[-1], m + 1)
+        return np.stack([np.interp(t, s_arc, dense[:, k]) for k in range(3)], axis=1)
+    ra_path = surface_path(sinus, avn, _RA_C, ra_ax)
+    mid = ra_path[len(ra_path) // 3]
+    bach = surface_path(mid, np.array(_LA_C) + [-6.0, 0.0, 8.0], _LA_C, la_ax)
+    his = np.array([-8.0, 0.0, 17.0])
+    av_line = np.array([avn + (his - avn) * t
+                        for t in np.linspace(0, 1, int(np.ceil(np.linalg.norm(his - avn) / ds_s)) + 1)])
+    xyz = [ra_path, bach[1:], av_line[1:]]
+    edges = [np.stack([np.arange(len(ra_path) - 1), np.arange(1, len(ra_path))], 1)]
+    o = len(ra_path)
+    imid = len(ra_path) // 3
+    eb = [(imid, o)] + [(o + k, o + k + 1) for k in range(len(bach) - 2)]
+    edges.append(np.array(eb))
+    o2 = o + len(bach) - 1
+    ea = [(len(ra_path) - 1, o2)] + [(o2 + k, o2 + k + 1) for k in range(len(av_line) - 2)]
+    edges.append(np.array(ea))
+    n_bundle = o2                                             # bundle nodes (Courtemanche, fast)
+    av_end = o2 + len(av_line) - 2
+    # the AV delay line's diffusivity slows conduction to about 0.18 mm/ms, i.e. ~100 ms over
+    # its 18 mm at full scale (delays shrink with the geometry when scale < 1)
+    D_bundle, D_av, D_purk = 1.29 / 1.4, 0.038, 3.95 / 1.4
+    edge_D = [np.full(len(ra_path) - 1, D_bundle), np.full(len(eb), D_bundle), np.full(len(ea), D_av)]
+    # His bundle: a short Stewart segment whose diffusivity rises geometrically from the AV line's
+    # to the Purkinje value, so that the slow line can drive the two fast branches
+    n_his = 15
+    his_seg = np.array([his + [0.0, 0.0, -ds_s * (k + 1)] for k in range(n_his)])
+    xyz.append(his_seg)
+    o3 = av_end + 1
+    edges.append(np.array([(av_end, o3)] + [(o3 + k, o3 + k + 1) for k in range(n_his - 1)]))
+    edge_D.append(D_av * (D_purk / D_av) ** (np.arange(1, n_his + 1) / n_his))
+    his_idx = o3 + n_his - 1
+    his = his_seg[-1]
+    # left and right bundle branches on the endocardia
+    base = his_idx + 1
+    node_off = base
+    tree_nodes = []
+    lv_ax = tuple(a + 0.6 for a in _LV_IN)
+    rv_ax = tuple(a + 0.6 for a in _RV_IN)
+    # each branch starts on its chamber's septal endocardium below the base and grows downwards
+    for c, ax, share, sdir in (((0.0, 0.0, 0.0), lv_ax, 0.55, (-1.0, 0.0, 0.35)),
+                               (_RV_C, rv_ax, 0.45, (1.0, 0.0, 0.35))):
+        start = np.asarray(c) + 10.0 * np.asarray(sdir)
+        txyz, tedges = grow_tree(rng, start, c, ax, int(n_tree * share), ds=ds_s, z_max=_BASE_Z - 2.0)
+        xyz.append(txyz)
+        edges.append(tedges + node_off)
+        edges.append(np.array([[his_idx, node_off]]))
+        edge_D += [np.full(len(tedges), D_purk), np.array([D_purk])]
+        tree_nodes.append((node_off, len(txyz), tedges))
+        node_off += len(txyz)
+    gxyz = np.concatenate(xyz) * scale
+    gedges = np.concatenate(edges).astype(np.int32)
+    gD = np.concatenate(edge_D)
+    n = gxyz.shape[0]
+    pset = np.full(n, 3, np.uint8)
+    pset[:av_end + 1] = 2                                     # bundle and AV line: Courtemanche
+    smask = np.zeros(n, np.uint8)
+    smask[:max(5, int(round(2.0 / ds)))] = 1                  # sinus stimulus on the first 2 mm of bundle
+    cen = tet_centroids(case.xyz, case.tets)
+    vent = case.param_set <= 1
+    atr = case.param_set == 2
+    kv = cKDTree(cen[vent])
+    ka = cKDTree(cen[atr])
+    vid, aid = np.flatnonzero(vent), np.flatnonzero(atr)
+    deg = np.bincount(gedges.ravel(), minlength=n)
+    leaves = np.array([i for i in range(base, n) if deg[i] == 1])
+    if len(leaves) > n_pmj:
+        leaves = leaves[np.linspace(0, len(leaves) - 1, n_pmj).astype(int)]
+    _, pm = kv.query(gxyz[leaves])
+    cn = np.arange(0, n_bundle, 5)
+    _, ac = ka.query(gxyz[cn])
+    jn = np.concatenate([leaves, cn]).astype(np.int32)
+    jc = np.concatenate([vid[pm], aid[ac]]).astype(np.int32)
+    jm = np.concatenate([np.full(len(leaves), JUNC_RESISTIVE), np.full(len(cn), JUNC_TRIGGERED)]).astype(np.uint8)
+    gp = GraphParams(D=D_purk, g_graph=g_graph, g_cell=g_cell, threshold=0.0, delay_ortho=5.0, delay_anti=3.0,
+                     amplitude=-52.0, duration=0.5, radius=1.0 * scale)
+    case.stimuli[0] = Stimulus(-100.0, 0.0, 2.5)
+    graph = Graph(gxyz, gedges, pset, smask, jn, jc, jm, gp, edge_D=gD)
+    graph.n_bundle, graph.his = n_bundle, his_idx
+    return case, graph
