@@ -179,6 +179,69 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_sweep(ctx, args, stream, torch):
+    """Batched parametric sweep: args.sweep_jobs slab jobs drawn from the
+    configured distribution (sizes log-uniform 50k-2M tets, G_Ks / G_Kr
+    scalings U[0.5, 1.5], p = 0.5 ischemic sphere with [K]o = 8 mM), all
+    advanced together -- one node launch + one cell launch per step for the
+    whole batch, captured-graph replay -- against the same jobs stepped one
+    job at a time."""
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2112_12854_b300 import ep
+    specs = w.sweep_jobs(n_jobs=256)[:args.sweep_jobs]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=8) as pool:
+        plans = list(pool.map(lambda sp: ep.plan_from_case(w.slab_from_spec(sp)), specs))
+    jobs = [ep.Job(ctx, plan=p) for p in plans]
+    for p in plans:
+        p.destroy()
+    build_s = time.perf_counter() - t0
+    cells = sum(j.n_cells for j in jobs)
+    chosen, _ = ep.autotune(jobs, 2)
+    ep.step(jobs, 5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ep.step(jobs, args.sweep_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / args.sweep_steps
+    for j in jobs:                       # build each job's own plan and graph outside the timing
+        j.step(64)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for j in jobs:
+        j.step(args.sweep_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_u = e0.elapsed_time(e1) / args.sweep_steps
+    small = [j for j in jobs if j.n_cells < 200_000]
+    out = {"jobs": len(jobs), "configured_jobs": 256, "cells": cells, "steps": args.sweep_steps,
+           "batched_ms_per_step": ms_b, "batched_cell_updates_per_s": cells / (ms_b * 1e-3),
+           "one_job_at_a_time_ms_per_step": ms_u, "one_job_at_a_time_cell_updates_per_s": cells / (ms_u * 1e-3),
+           "cell_variant": int(chosen[0]), "host_build_s": build_s}
+    if small:
+        sc = sum(j.n_cells for j in small)
+        ep.step(small, 64)                # the small batch's own plan and graph, outside the timing
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ep.step(small, args.sweep_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msb = e0.elapsed_time(e1) / args.sweep_steps
+        e0.record(stream)
+        for j in small:
+            j.step(args.sweep_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msu = e0.elapsed_time(e1) / args.sweep_steps
+        out["small_jobs"] = {"jobs": len(small), "cells": sc, "batched_cell_updates_per_s": sc / (msb * 1e-3),
+                             "one_job_at_a_time_cell_updates_per_s": sc / (msu * 1e-3)}
+    for j in jobs:
+        j.destroy()
+    return out
+
+
 def run_heart(ctx, args, stream, torch):
     """Synthetic whole heart with its conduction system at full scale: about
     9.3M tets (ventricles TP06, atria Courtemanche) and a 50k-node graph
@@ -259,6 +322,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="debug: 1/8-volume crop instead of the full wedge")
     ap.add_argument("--heart-steps", type=int, default=200, help="timed steps of the whole-heart leg (0 = skip)")
+    ap.add_argument("--sweep-jobs", type=int, default=64, help="jobs of the batched parametric sweep (0 = skip; "
+                    "the configured sweep has 256)")
+    ap.add_argument("--sweep-steps", type=int, default=200)
     ap.add_argument("--serve-window", type=float, default=40.0,
                     help="seconds of Poisson arrivals in each serving run (0 = no serving leg)")
     ap.add_argument("--serve-load", type=float, default=0.7, help="offered load of the first serving run, "
@@ -382,6 +448,10 @@ def main():
             "steps": args.fp64_steps, "cell_variant": int(chosen64[1])}
     job64.destroy()
 
+    sweep = None
+    if args.sweep_jobs > 0:
+        sweep = run_sweep(ctx, args, stream, torch)
+
     heart = None
     if args.heart_steps > 0:
         heart = run_heart(ctx, args, stream, torch)
@@ -411,7 +481,7 @@ def main():
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": 2 * args.steps, "fp64_plain": fp64,
                "speedup_vs_fp64_plain": value / world / fp64["value"], "state_finite": finite,
-               "whole_heart": heart, "serving": serving}
+               "batched_sweep": sweep, "whole_heart": heart, "serving": serving}
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist is not None:

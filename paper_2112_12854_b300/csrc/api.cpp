@@ -32,6 +32,7 @@ struct DevBuf {
 };
 
 constexpr int kGraphSteps = 32;       // steps per captured graph
+constexpr size_t kMaxPlans = 512;     // cached batch plans per context (job tables, tiles, graphs)
 constexpr int kGraphMinSteps = 64;    // below this, launch directly
 
 struct Plan {
@@ -838,7 +839,7 @@ static int get_plan(ep_context *ctx, ep_job *const *jobs, int32_t n_jobs, Plan *
         free_plan(ctx, np.get());
         return rc;
     }
-    if (ctx->plans.size() >= 8) {
+    if (ctx->plans.size() >= kMaxPlans) {
         cudaStreamSynchronize(ctx->stream);   // its tables may still be read by queued steps
         free_plan(ctx, ctx->plans.front().get());
         ctx->plans.erase(ctx->plans.begin());

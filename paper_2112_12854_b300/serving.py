@@ -105,6 +105,9 @@ class LibBackend:
     def wait(self, mark):
         mark.synchronize()
 
+    def healthy(self, job) -> bool:
+        return job.check_finite()
+
     def finish(self, job, keep: bool):
         V = job.V if keep else None
         act = job.activation_times() if keep else None
@@ -126,6 +129,12 @@ class Server:
         self.clock, self.sleep = clock, sleep
         self.rank, self.world = rank, world
         self.log: list[dict] = []
+        self.cancelled: set[int] = set()
+
+    def cancel(self, rid: int):
+        """Cancel a request: dropped if not yet admitted, released (no
+        result) at the next iteration boundary if resident."""
+        self.cancelled.add(rid)
 
     def run(self, requests: list[Request], *, time_limit: float | None = None) -> list[Result]:
         """Serve the requests (those with rid % world == rank); returns the
@@ -147,6 +156,21 @@ class Server:
                     break
                 while pending and pending[-1].arrival <= now:
                     queue.append(pending.pop())
+                if self.cancelled:
+                    for r in [r for r in queue if r.rid in self.cancelled] + \
+                             [r for r, _ in ready if r.rid in self.cancelled]:
+                        results.append(Result(r.rid, r.arrival, now, now, r.n_cells, r.n_steps, error="cancelled"))
+                    queue = [r for r in queue if r.rid not in self.cancelled]
+                    ready = [(r, t) for r, t in ready if r.rid not in self.cancelled]
+                    keep = []
+                    for x in resident:
+                        if x[0].rid in self.cancelled:
+                            self.b.finish(x[1], False)
+                            results.append(Result(x[0].rid, x[0].arrival, x[3], now, x[0].n_cells, x[0].n_steps,
+                                                  error="cancelled"))
+                        else:
+                            keep.append(x)
+                    resident = keep
                 while queue and len(preparing) + len(ready) < self.max_prepared:
                     r = queue.pop(0)
                     preparing.append((r, pool.submit(r.prepare)))
@@ -190,9 +214,10 @@ class Server:
                 if done:
                     resident = [x for x in resident if x[2] > 0]
                     for r, job, _, adm in done:
-                        V, act = self.b.finish(job, r.keep_result)
+                        err = None if self.b.healthy(job) else "non-finite state"
+                        V, act = self.b.finish(job, r.keep_result and err is None)
                         results.append(Result(r.rid, r.arrival, adm, self.clock() - t0, r.n_cells, r.n_steps,
-                                              V=V, act=act))
+                                              V=V, act=act, error=err))
                     inflight.clear()               # finish() synchronised the stream
         finally:
             pool.shutdown(wait=True, cancel_futures=True)

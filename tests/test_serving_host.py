@@ -59,9 +59,12 @@ class FakeBackend:
     def wait(self, m):
         pass
 
+    def healthy(self, job):
+        return not job.tok.get("nan", False)
+
     def finish(self, job, keep):
         self.used -= job.tok["bytes"]
-        return np.full(3, float(job.steps)), None
+        return (np.full(3, float(job.steps)) if keep else None), None
 
 
 def _requests(n, rng, arrival_scale=0.01):
@@ -158,3 +161,16 @@ def test_jobs_shard_across_ranks_gloo():
     a, b = set(got[0]), set(got[1])
     assert not (a & b) and a | b == set(range(23))
     assert all(x % 2 == 0 for x in a) and all(x % 2 == 1 for x in b)
+
+
+def test_cancel_and_nonfinite_jobs_fail_alone():
+    clk = FakeClock()
+    be = FakeBackend(clk, budget=10 ** 9)
+    reqs = _requests(12, np.random.default_rng(3))
+    reqs[4].prepare = (lambda tok={"rid": 4, "bytes": 1000, "cells": 1000, "nan": True}: tok)
+    srv = Server(be, steps_per_iter=50, clock=clk, sleep=clk.sleep)
+    srv.cancel(7)
+    res = {r.rid: r for r in srv.run(reqs)}
+    assert res[7].error == "cancelled" and res[4].error == "non-finite state"
+    assert all(res[k].error is None for k in res if k not in (4, 7))
+    assert be.used == 0
