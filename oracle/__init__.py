@@ -122,9 +122,22 @@ def lib():
         L.orc_sim_graph_get_act.argtypes = [_P, _P]
         L.orc_sim_graph_laplacian.argtypes = [_P, _P, _P]
         L.orc_stim_active.restype = ctypes.c_int
+        L.orc_sim_set_bidomain.restype = ctypes.c_int
+        L.orc_sim_set_bidomain.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int64]
+        for f in ("orc_sim_get_ve", "orc_sim_set_ve", "orc_sim_bidomain_stats"):
+            getattr(L, f).argtypes = [_P, _P]
+        L.orc_sim_bidomain_operator.argtypes = [_P, _P, _P]
+        L.orc_set_threads.restype = ctypes.c_int
+        L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_stim_active.argtypes = [ctypes.POINTER(Stim), ctypes.c_double, ctypes.c_int64]
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Thread count of the oracle's OpenMP loops for later calls from this
+    thread (n <= 0 leaves it); returns the previous count."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def conductivity(fibre, D_l, D_t) -> np.ndarray:
@@ -297,6 +310,41 @@ class Sim:
     def activation_times(self) -> np.ndarray:
         out = np.zeros(self.n_cells)
         lib().orc_sim_get_act(self._h, _ptr(out))
+        return out
+
+    def set_bidomain(self, De_l, De_t, tol=1e-10, restart=20, max_iter=200000):
+        """Bidomain model: the parameter sets' (D_l, D_t) become the
+        intracellular diffusivities; De_l, De_t (scalars or one per set) the
+        extracellular ones. v_e is solved at once from the current V."""
+        k = len(self.case.param_sets)
+        el = np.ascontiguousarray(np.broadcast_to(np.asarray(De_l, np.float64), (k,)))
+        et = np.ascontiguousarray(np.broadcast_to(np.asarray(De_t, np.float64), (k,)))
+        rc = lib().orc_sim_set_bidomain(self._h, _ptr(el), _ptr(et), float(tol), int(restart), int(max_iter))
+        if rc:
+            raise ValueError(f"oracle bidomain rejected (code {rc})")
+
+    @property
+    def ve(self) -> np.ndarray:
+        out = np.zeros(self.n_cells)
+        lib().orc_sim_get_ve(self._h, _ptr(out))
+        return out
+
+    @ve.setter
+    def ve(self, values):
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        assert v.size == self.n_cells
+        lib().orc_sim_set_ve(self._h, _ptr(v))
+
+    def bidomain_stats(self) -> dict:
+        st = np.zeros(4)
+        lib().orc_sim_bidomain_stats(self._h, _ptr(st))
+        return {"last_iters": int(st[0]), "total_iters": int(st[1]), "last_rel_res": float(st[2]),
+                "failed": bool(st[3])}
+
+    def bidomain_operator(self, x) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        out = np.zeros(self.n_cells)
+        lib().orc_sim_bidomain_operator(self._h, _ptr(x), _ptr(out))
         return out
 
     def diffusion(self, v) -> np.ndarray:

@@ -20,7 +20,9 @@
  *     everything else, all evaluated at (V^n, s^n) (Sec. 3.2);
  *   - the stimulus of Eq. 4 and the activation time (first upward crossing of
  *     a threshold, Sec. 4);
- *   - the 1D vertex-based FV Purkinje graph and its junctions (Sec. 3.2, 3.3).
+ *   - the 1D vertex-based FV Purkinje graph and its junctions (Sec. 3.2, 3.3);
+ *   - the bidomain model (Eqs. 1, 5-6): the extracellular potential from the
+ *     elliptic equation by restarted GMRES warm-started from the last step.
  *
  * Units: V in mV, t in ms, D in mm^2/ms, currents in uA/uF.
  */
@@ -82,6 +84,7 @@ orc_sim *orc_sim_create(int64_t n_nodes, const double *xyz, int64_t n_cells,
                         int n_stim, const orc_stim *stim,
                         double dt, double threshold, int *err);
 void orc_sim_destroy(orc_sim *s);
+int orc_set_threads(int n);
 void orc_sim_run(orc_sim *s, int64_t n_steps);
 int64_t orc_sim_step_index(const orc_sim *s);
 void orc_sim_get_var(const orc_sim *s, int var, double *out);
@@ -90,6 +93,14 @@ void orc_sim_get_act(const orc_sim *s, double *out);
 void orc_sim_set_step_index(orc_sim *s, int64_t n);
 void orc_sim_diffusion(const orc_sim *s, const double *v, double *out);
 const orc_mesh *orc_sim_mesh(const orc_sim *s);
+/* bidomain (tissue.c): extracellular diffusivities per parameter set, the
+ * GMRES stopping rule; v_e state, solver statistics, the elliptic operator */
+int orc_sim_set_bidomain(orc_sim *s, const double *De_l, const double *De_t, double tol, int restart,
+                         int64_t max_iter);
+void orc_sim_get_ve(const orc_sim *s, double *out);
+void orc_sim_set_ve(orc_sim *s, const double *in);
+void orc_sim_bidomain_stats(const orc_sim *s, double *stats);
+void orc_sim_bidomain_operator(const orc_sim *s, const double *x, double *out);
 int orc_stim_active(const orc_stim *st, double dt, int64_t n);
 
 /* ---- conduction graph and junctions (purkinje.c) ---- */

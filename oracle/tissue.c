@@ -23,7 +23,23 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include "oracle.h"
+
+/* Thread count of the OpenMP loops of later calls from this thread (n <= 0
+ * leaves it); returns the count in effect before. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    const int prev = omp_get_max_threads();
+    if (n > 0) omp_set_num_threads(n);
+    return prev;
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 int orc_tp06_nvar(void);
 const char *orc_tp06_varname(int v);
@@ -116,7 +132,17 @@ struct orc_sim {
     double *v, *diff;
     orc_graph *g;              /* optional conduction graph */
     double *i_extra, *s_extra, *vg_old, *v_new;
+    double *fibre;             /* [n_cells][3] */
+    /* bidomain (NULL ve: monodomain) */
+    double *ve, *Die, *u, *rhs;
+    double gm_tol;
+    int gm_restart;
+    int64_t gm_max_iter, gm_last_iter, gm_total_iter;
+    double gm_last_res;
+    int gm_failed;
 };
+
+static void bidomain_solve(orc_sim *s);
 
 orc_sim *orc_sim_create(int64_t n_nodes, const double *xyz, int64_t n_cells,
                         const int32_t *tet, const double *fibre,
@@ -149,11 +175,13 @@ orc_sim *orc_sim_create(int64_t n_nodes, const double *xyz, int64_t n_cells,
     s->act = (double *)malloc(sizeof(double) * n_cells);
     s->v = (double *)malloc(sizeof(double) * n_cells);
     s->diff = (double *)malloc(sizeof(double) * n_cells);
+    s->fibre = (double *)malloc(sizeof(double) * 3 * n_cells);
     for (int64_t c = 0; c < n_cells; ++c) {
         const orc_cellparams *p = &s->sets[s->pset[c]];
         orc_model_init(p, s->state + ORC_MAXVAR * c);
         double f[3] = {1.0, 0.0, 0.0};
         if (fibre) { f[0] = fibre[3 * c]; f[1] = fibre[3 * c + 1]; f[2] = fibre[3 * c + 2]; }
+        memcpy(s->fibre + 3 * c, f, sizeof(f));
         orc_conductivity(f, p->D_l, p->D_t, s->D + 9 * c);
         s->act[c] = INFINITY;
     }
@@ -167,7 +195,8 @@ void orc_sim_destroy(orc_sim *s) {
     orc_graph_free(s->g);
     free(s->i_extra); free(s->s_extra); free(s->vg_old); free(s->v_new);
     free(s->pset); free(s->smask); free(s->state); free(s->D); free(s->act);
-    free(s->v); free(s->diff);
+    free(s->v); free(s->diff); free(s->fibre);
+    free(s->ve); free(s->Die); free(s->u); free(s->rhs);
     free(s);
 }
 
@@ -179,7 +208,13 @@ void orc_sim_run(orc_sim *s, int64_t n_steps) {
         for (int k = 0; k < s->n_stim; ++k)
             amp[k] = orc_stim_active(&s->stim[k], s->dt, n) ? s->stim[k].amplitude : 0.0;
         for (int64_t c = 0; c < s->n_cells; ++c) s->v[c] = s->state[ORC_MAXVAR * c];
-        orc_diffusion(s->m, s->D, s->v, s->diff);
+        if (s->ve) {
+            /* bidomain: intracellular flux of V + v_e (first line of Eq. 6) */
+            for (int64_t c = 0; c < s->n_cells; ++c) s->u[c] = s->v[c] + s->ve[c];
+            orc_diffusion(s->m, s->D, s->u, s->diff);
+        } else {
+            orc_diffusion(s->m, s->D, s->v, s->diff);
+        }
         if (s->g) {
             memset(s->i_extra, 0, sizeof(double) * s->n_cells);
             memset(s->s_extra, 0, sizeof(double) * s->n_cells);
@@ -210,6 +245,7 @@ void orc_sim_run(orc_sim *s, int64_t n_steps) {
             for (int64_t c = 0; c < s->n_cells; ++c) s->v_new[c] = s->state[ORC_MAXVAR * c];
             orc_graph_triggers(s->g, s->v, s->v_new, s->vg_old, t, s->dt);
         }
+        if (s->ve) bidomain_solve(s);
         s->step = n + 1;
     }
 }
@@ -275,3 +311,174 @@ void orc_sim_diffusion(const orc_sim *s, const double *v, double *out) {
 }
 
 const orc_mesh *orc_sim_mesh(const orc_sim *s) { return s->m; }
+
+/* ---- bidomain (Eq. 1, Eqs. 5-6) -------------------------------------------
+ * With the extracellular potential v_e as a second unknown, a step is
+ *   V^{n+1} = V^n + dt (L_i(V^n + v_e^n) - I_ion - I_s)
+ * followed by the second line of Eq. 6 for v_e^{n+1}:
+ *   L_ie(v_e^{n+1}) = -L_i(V^{n+1}),
+ * L_i and L_ie being the diffusion operator of fv3d.c with the intracellular
+ * tensor D_i and with D_i + D_e. As in Sec. 3.2 the linear system is solved
+ * by restarted GMRES started from v_e^n; this is the textbook method
+ * (Arnoldi with modified Gram-Schmidt, Givens rotations on the Hessenberg
+ * matrix), stopped when the true residual satisfies ||b - A x|| <= tol ||b||.
+ * v_e is defined up to a constant (zero-flux boundaries everywhere); it is
+ * fixed to zero volume-weighted mean after each solve.
+ */
+
+static double dot(const double *a, const double *b, int64_t n) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* Restarted GMRES on L(D) x = b; returns the iterations (matrix-vector
+ * products inside the Arnoldi cycles) and the final relative residual. */
+static int64_t gmres(const orc_mesh *m, const double *D, const double *b, double *x, int64_t n, double tol,
+                     int restart, int64_t max_iter, double *rel_res, int *failed) {
+    const int k = restart;
+    double *Vb = (double *)malloc(sizeof(double) * (size_t)(k + 1) * (size_t)n);
+    double *H = (double *)calloc((size_t)(k + 1) * k, sizeof(double));   /* H[i * k + j] */
+    double *cs = (double *)malloc(sizeof(double) * k), *sn = (double *)malloc(sizeof(double) * k);
+    double *g = (double *)malloc(sizeof(double) * (k + 1)), *y = (double *)malloc(sizeof(double) * k);
+    double *w = (double *)malloc(sizeof(double) * n);
+    const double bnorm = sqrt(dot(b, b, n));
+    int64_t it = 0;
+    *failed = 0;
+    *rel_res = 0.0;
+    if (bnorm == 0.0) {
+        memset(x, 0, sizeof(double) * n);
+    } else {
+        for (;;) {
+            /* true residual r = b - A x, into the first basis vector */
+            double *v0 = Vb;
+            orc_diffusion(m, D, x, v0);
+            for (int64_t i = 0; i < n; ++i) v0[i] = b[i] - v0[i];
+            const double beta = sqrt(dot(v0, v0, n));
+            *rel_res = beta / bnorm;
+            if (beta <= tol * bnorm) break;
+            if (it >= max_iter) {
+                *failed = 1;
+                break;
+            }
+            for (int64_t i = 0; i < n; ++i) v0[i] /= beta;
+            for (int i = 0; i <= k; ++i) g[i] = 0.0;
+            g[0] = beta;
+            int j = 0;
+            while (j < k && it < max_iter) {
+                double *vj = Vb + (size_t)j * n, *vn = Vb + (size_t)(j + 1) * n;
+                orc_diffusion(m, D, vj, w);
+                ++it;
+                for (int i = 0; i <= j; ++i) {          /* modified Gram-Schmidt */
+                    const double *vi = Vb + (size_t)i * n;
+                    const double h = dot(w, vi, n);
+                    H[i * k + j] = h;
+                    for (int64_t r = 0; r < n; ++r) w[r] -= h * vi[r];
+                }
+                const double hn = sqrt(dot(w, w, n));
+                H[(j + 1) * k + j] = hn;
+                for (int64_t r = 0; r < n; ++r) vn[r] = hn > 0.0 ? w[r] / hn : 0.0;
+                for (int i = 0; i < j; ++i) {           /* earlier rotations on column j */
+                    const double a = H[i * k + j], c = H[(i + 1) * k + j];
+                    H[i * k + j] = cs[i] * a + sn[i] * c;
+                    H[(i + 1) * k + j] = -sn[i] * a + cs[i] * c;
+                }
+                const double a = H[j * k + j], c = H[(j + 1) * k + j];
+                const double rr = sqrt(a * a + c * c);
+                cs[j] = rr > 0.0 ? a / rr : 1.0;
+                sn[j] = rr > 0.0 ? c / rr : 0.0;
+                H[j * k + j] = rr;
+                H[(j + 1) * k + j] = 0.0;
+                g[j + 1] = -sn[j] * g[j];
+                g[j] = cs[j] * g[j];
+                ++j;
+                if (fabs(g[j]) <= tol * bnorm || hn == 0.0) break;
+            }
+            /* x += V_j y, H_j y = g (upper triangular) */
+            for (int i = j - 1; i >= 0; --i) {
+                double sacc = g[i];
+                for (int l = i + 1; l < j; ++l) sacc -= H[i * k + l] * y[l];
+                y[i] = H[i * k + i] != 0.0 ? sacc / H[i * k + i] : 0.0;
+            }
+            for (int i = 0; i < j; ++i) {
+                const double *vi = Vb + (size_t)i * n;
+                for (int64_t r = 0; r < n; ++r) x[r] += y[i] * vi[r];
+            }
+        }
+    }
+    free(Vb); free(H); free(cs); free(sn); free(g); free(y); free(w);
+    return it;
+}
+
+static void bidomain_solve(orc_sim *s) {
+    const int64_t n = s->n_cells;
+    for (int64_t c = 0; c < n; ++c) s->v[c] = s->state[ORC_MAXVAR * c];
+    orc_diffusion(s->m, s->D, s->v, s->rhs);
+    for (int64_t c = 0; c < n; ++c) s->rhs[c] = -s->rhs[c];
+    int failed = 0;
+    s->gm_last_iter = gmres(s->m, s->Die, s->rhs, s->ve, n, s->gm_tol, s->gm_restart, s->gm_max_iter,
+                            &s->gm_last_res, &failed);
+    s->gm_total_iter += s->gm_last_iter;
+    s->gm_failed |= failed;
+    /* gauge: zero volume-weighted mean */
+    double sv = 0.0, sw = 0.0;
+    double *vol = s->u;   /* scratch */
+    orc_mesh_cell_info(s->m, NULL, vol, NULL);
+    for (int64_t c = 0; c < n; ++c) {
+        sv += vol[c] * s->ve[c];
+        sw += vol[c];
+    }
+    for (int64_t c = 0; c < n; ++c) s->ve[c] -= sv / sw;
+}
+
+/* Switch the simulation to the bidomain model: the parameter sets' (D_l,
+ * D_t) become the intracellular diffusivities, De_l[k], De_t[k] are the
+ * extracellular ones of set k (mm^2/ms, both tensors in the cell's fibre
+ * frame, Eqs. 2-3). v_e is solved at once from the current V (from x = 0).
+ * tol, restart, max_iter: the GMRES stopping rule, Krylov dimension and
+ * iteration cap per solve. */
+int orc_sim_set_bidomain(orc_sim *s, const double *De_l, const double *De_t, double tol, int restart,
+                         int64_t max_iter) {
+    if (!(tol > 0.0) || restart < 1 || max_iter < 1) return 20;
+    const int64_t n = s->n_cells;
+    free(s->ve); free(s->Die); free(s->u); free(s->rhs);
+    s->ve = (double *)calloc(n, sizeof(double));
+    s->Die = (double *)malloc(sizeof(double) * 9 * n);
+    s->u = (double *)malloc(sizeof(double) * n);
+    s->rhs = (double *)malloc(sizeof(double) * n);
+    for (int64_t c = 0; c < n; ++c) {
+        const orc_cellparams *p = &s->sets[s->pset[c]];
+        const int k = s->pset[c];
+        orc_conductivity(s->fibre + 3 * c, p->D_l + De_l[k], p->D_t + De_t[k], s->Die + 9 * c);
+    }
+    s->gm_tol = tol;
+    s->gm_restart = restart;
+    s->gm_max_iter = max_iter;
+    s->gm_total_iter = 0;
+    s->gm_failed = 0;
+    bidomain_solve(s);
+    return 0;
+}
+
+void orc_sim_get_ve(const orc_sim *s, double *out) {
+    if (s->ve) memcpy(out, s->ve, sizeof(double) * s->n_cells);
+    else memset(out, 0, sizeof(double) * s->n_cells);
+}
+
+void orc_sim_set_ve(orc_sim *s, const double *in) {
+    if (s->ve) memcpy(s->ve, in, sizeof(double) * s->n_cells);
+}
+
+/* stats[0] iterations of the last solve, [1] all iterations, [2] the last
+ * relative residual, [3] 1 if a solve hit its iteration cap. */
+void orc_sim_bidomain_stats(const orc_sim *s, double *stats) {
+    stats[0] = (double)s->gm_last_iter;
+    stats[1] = (double)s->gm_total_iter;
+    stats[2] = s->gm_last_res;
+    stats[3] = (double)s->gm_failed;
+}
+
+/* The elliptic operator alone: out = L_ie(x) (a check of the solve). */
+void orc_sim_bidomain_operator(const orc_sim *s, const double *x, double *out) {
+    orc_diffusion(s->m, s->Die, x, out);
+}
