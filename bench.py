@@ -66,18 +66,24 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(n_cells):
-    """DRAM bytes per cell of the cell kernel from the committed ncu summary,
+def profile_value(fname, key):
+    """A per-cell figure recorded in a committed ncu summary under profiles/,
     if it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "cell_kernel_wedge.md")
+    path = os.path.join(ROOT, "profiles", fname)
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
-    m_b = re.search(r"dram_bytes_per_cell:\s*([0-9.]+)", txt)
-    if not m_hash or not m_b or m_hash.group(1) != kernel_source_hash():
+    m_v = re.search(key + r":\s*([0-9.eE+]+)", txt)
+    if not m_hash or not m_v or m_hash.group(1) != kernel_source_hash():
         return None
-    return float(m_b.group(1)) * n_cells
+    return float(m_v.group(1))
+
+
+def traffic_from_profile(n_cells):
+    """DRAM bytes of one cell-kernel launch (FP32) from the ncu summary."""
+    b = profile_value("cell_kernel_wedge.md", "dram_bytes_per_cell")
+    return None if b is None else b * n_cells
 
 
 class Clocks:
@@ -148,7 +154,7 @@ def oracle_throughput(dims, budget_s, max_steps=None):
         el = time.perf_counter() - t0
         if el >= budget_s or (max_steps and steps >= max_steps):
             break
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.set_threads(0)     # the OpenMP thread count the oracle ran with
     return case.n_cells * steps / el, steps, case.n_cells, cores
 
 
@@ -165,7 +171,7 @@ def run_reference(args):
     for _ in range(args.steps):
         s.run(1)
     el = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.set_threads(0)
     val = case.n_cells * args.steps / el
     sample = (f"oracle (FP64 C, OpenMP) on a crop of the wedge workload: {CROP['nx']}x{CROP['ny']}x{CROP['nz']} "
               f"cubes x 6 = {case.n_cells} cells, one time step per bench step")
@@ -355,6 +361,7 @@ def main():
     case = wedge_case(dims)
     N = case.n_cells
     ctx = ep.Context()
+    alu = ep.alu_peaks(ctx)
     job = ep.job_from_case(ctx, case, precision=ep.EP_FP32_MIXED)
     info = job.info()
     stream = torch.cuda.current_stream()
@@ -444,9 +451,20 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     ms64 = e0.elapsed_time(e1)
-    fp64 = {"value": N * args.fp64_steps / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps,
-            "steps": args.fp64_steps, "cell_variant": int(chosen64[1])}
+    node64_ms, cell64_ms = ep.time_kernels([job64], 2)
     job64.destroy()
+    # the plain FP64 cell kernel runs on the FP64 pipe: its roof is the measured FP64 FMA rate;
+    # its FP64 flops per cell (2 per DFMA, 1 per DADD / DMUL) come from the ncu summary
+    f64_per_cell = profile_value("cell_kernel_fp64_crop.md", "fp64_flops_per_cell")
+    f64_peak = alu["fp64_fma_flops"] / 1e12
+    f64_ach = None if f64_per_cell is None else f64_per_cell * N / (cell64_ms * 1e-3) / 1e12
+    fp64 = {"value": N * args.fp64_steps / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps,
+            "steps": args.fp64_steps, "cell_variant": int(chosen64[1]),
+            "roofline": {"bound": "alu", "kernel": "cell_kernel<double>", "achieved": f64_ach, "peak": f64_peak,
+                         "unit": "TFLOP/s", "frac": None if f64_ach is None else f64_ach / f64_peak,
+                         "peak_source": "measured FP64 FMA issue rate (ep_alu_peaks)",
+                         "fp64_flops_per_cell": f64_per_cell, "cell_kernel_ms": cell64_ms,
+                         "node_kernel_ms": node64_ms}}
 
     sweep = None
     if args.sweep_jobs > 0:
@@ -463,9 +481,14 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, st, cells, cores = oracle_throughput(CROP, args.cpu_budget)
+        import oracle
+        prev = oracle.set_threads(1)
+        val1, st1, _, _ = oracle_throughput(CROP, args.cpu_budget / 3)
+        oracle.set_threads(prev)
         cpu = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"oracle on a {CROP['nx']}x{CROP['ny']}x{CROP['nz']}-cube crop of the wedge "
-                         f"({cells} cells), {st} steps"}
+                         f"({cells} cells), {st} steps",
+               "value_1core": val1, "sample_1core": f"the same crop on one thread, {st1} steps"}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -474,12 +497,16 @@ def main():
                "config": {"workload": f"ventricular wedge slab {dims['nx']}x{dims['ny']}x{dims['nz']} cubes "
                                       f"of {dims['h']} mm x 6 tets, TP06 endo/M/epi, fibres -60..+60 deg",
                           "cells": N, "nodes": info["n_nodes"], "dt_ms": case.dt,
-                          "precision": "FP32 with FP64 [Na]i/[K]i/[Ca]SR accumulation",
+                          "precision": "FP32 with two-float compensated [Na]i/[K]i/[Ca]SR accumulation",
                           "l2": f"inputs larger than L2 ({info['device_bytes'] / 1e9:.2f} GB resident, "
                                 f"~{(CELL_BYTES * N + node_bytes) / 1e9:.2f} GB moved per step > 126 MB)",
                           "parallelism": f"replicas x{world}", "graph_replay": True},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": 2 * args.steps, "fp64_plain": fp64,
+               "alu_peaks": {"fp32_fma_tflops": alu["fp32_fma_flops"] / 1e12,
+                             "mufu_ex2_tops": alu["mufu_ex2_ops"] / 1e12,
+                             "fp64_fma_tflops": alu["fp64_fma_flops"] / 1e12,
+                             "source": "ep_alu_peaks: independent FMA / ex2 chains on every SM, CUDA events"},
                "speedup_vs_fp64_plain": value / world / fp64["value"], "state_finite": finite,
                "batched_sweep": sweep, "whole_heart": heart, "serving": serving}
         print(json.dumps(out), flush=True)

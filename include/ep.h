@@ -267,6 +267,17 @@ int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double
 int ep_autotune(ep_job *const *jobs, int32_t n_jobs, int32_t steps_per_variant, int32_t *chosen,
                 double *variant_ms);
 
+/* Measured issue rates of the arithmetic pipes the cell step runs on, for
+ * the ALU roofs of the cell kernels (the FP64 plain step is bound by the
+ * FP64 pipe, the FP32 step by HBM). Each probe fills every SM with
+ * independent dependency chains and is timed with CUDA events on the
+ * context's stream (best of five, after a warm-up launch). out[3] receives
+ * operations per second: out[0] FP32 FMA flops (an FMA counts two),
+ * out[1] MUFU ex2 results, out[2] FP64 FMA flops. Takes a few
+ * milliseconds, allocates 256 bytes through the context's allocator and
+ * synchronises. */
+int ep_alu_peaks(ep_context *ctx, double *out);
+
 /* Force the cell kernel's launch-shape variant (0..5) for one precision. */
 int ep_set_cell_variant(ep_context *ctx, int32_t precision, int32_t variant);
 

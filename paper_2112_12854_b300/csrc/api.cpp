@@ -952,6 +952,40 @@ static void apply_cell_variant(ep_context *ctx, int precision, int variant) {
     }
 }
 
+int ep_alu_peaks(ep_context *ctx, double *out) {
+    if (!ctx || !out) return EP_EINVAL;
+    DeviceGuard g(ctx->device);
+    DevBuf sink;
+    int rc = dalloc(ctx, 16, &sink);
+    if (rc) return rc;
+    // iterations per kind: about a millisecond per launch on a full B300
+    const int iters[3] = {16384, 2048, 512};
+    const int blocks = ctx->sm_count * (2048 / alu_probe_threads());
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int kind = 0; kind < 3 && e == cudaSuccess; ++kind) {
+        double ops = 0.0, best = 0.0;
+        e = launch_alu_probe(kind, blocks, iters[kind], static_cast<double *>(sink.p), ctx->stream, &ops);  // warm-up
+        for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep) {
+            e = cudaEventRecord(e0, ctx->stream);
+            if (e == cudaSuccess) e = launch_alu_probe(kind, blocks, iters[kind], static_cast<double *>(sink.p), ctx->stream, &ops);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms > 0.f) best = std::max(best, ops / (1e-3 * double(ms)));
+        }
+        out[kind] = best;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, &sink);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_alu_peaks");
+    return EP_OK;
+}
+
 int ep_set_cell_variant(ep_context *ctx, int32_t precision, int32_t variant) {
     if (!ctx) return EP_EINVAL;
     if ((precision != EP_FP32_MIXED && precision != EP_FP64_PLAIN) || variant < 0 || variant >= kNumCellVariants)

@@ -66,6 +66,11 @@ cudaError_t launch_check_finite(int precision, const DevJob *job, long long n_ce
 
 // Step one job n_steps times with its node values in a static device array
 // instead of job memory (no allocation; at most EP_NOALLOC_MAX_NODES nodes).
+// Pipe issue-rate probe (peaks.cu): kind 0 FP32 FMA, 1 MUFU ex2, 2 FP64
+// FMA. *ops receives the operations (flops for FMA kinds) of the launch.
+cudaError_t launch_alu_probe(int kind, int blocks, int iters, double *sink, cudaStream_t s, double *ops);
+int alu_probe_threads();
+
 cudaError_t launch_step_noalloc(int precision, const DevJob *job, long long n_nodes, long long n_cells,
                                 long long n_steps, cudaStream_t s);
 

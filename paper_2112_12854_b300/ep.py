@@ -80,7 +80,7 @@ EXPORTS = ["ep_context_create", "ep_context_set_stream", "ep_context_destroy", "
            "ep_model_varname", "ep_plan_inspect", "ep_time_kernels",
            "ep_step_noalloc", "ep_autotune", "ep_set_cell_variant", "ep_plan_create", "ep_plan_bytes",
            "ep_plan_info", "ep_plan_destroy", "ep_job_create", "ep_graph_attach", "ep_graph_read_state",
-           "ep_graph_write_state", "ep_graph_activation_times", "ep_graph_info"]
+           "ep_graph_write_state", "ep_graph_activation_times", "ep_graph_info", "ep_alu_peaks"]
 
 _lib = None
 _P = ctypes.c_void_p
@@ -130,6 +130,7 @@ def load():
         "ep_job_create": ([_P, _P, ctypes.POINTER(_P)], ctypes.c_int),
         "ep_autotune": ([ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32, _P, _P], ctypes.c_int),
         "ep_set_cell_variant": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+        "ep_alu_peaks": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "ep_time_kernels": ([ctypes.POINTER(_P), ctypes.c_int32, _I64, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "ep_plan_inspect": ([ctypes.POINTER(MeshDesc), ctypes.POINTER(Params)] + [_P] * 10
@@ -455,6 +456,14 @@ def time_kernels(jobs, n_steps: int):
     a, b = ctypes.c_double(), ctypes.c_double()
     jobs[0].ctx.check(load().ep_time_kernels(arr, len(jobs), int(n_steps), ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def alu_peaks(ctx) -> dict:
+    """Measured issue rates of the FP32 FMA, MUFU ex2 and FP64 FMA pipes
+    (operations per second; an FMA counts two flops)."""
+    out = (ctypes.c_double * 3)()
+    ctx.check(load().ep_alu_peaks(ctx._h, out))
+    return {"fp32_fma_flops": out[0], "mufu_ex2_ops": out[1], "fp64_fma_flops": out[2]}
 
 
 def case_cell_model(case):
