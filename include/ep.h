@@ -252,6 +252,7 @@ int ep_job_destroy(ep_job *job);
  * graph), recording CUDA events on the context's stream around each launch,
  * and return the mean device time per step of the node-value kernel and of
  * the fused cell kernel (ms, summed over the jobs' precision groups).
+ * The elliptic solves of bidomain jobs run after each step, untimed.
  * Synchronises. The results equal those of ep_step. */
 int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double *node_ms, double *cell_ms);
 
@@ -384,6 +385,50 @@ int ep_graph_read_state(ep_job *job, int32_t model, int32_t var, double *host_ou
 int ep_graph_write_state(ep_job *job, int32_t model, int32_t var, const double *host_in, int64_t n);
 int ep_graph_activation_times(ep_job *job, double *host_out, int64_t n);
 int ep_graph_info(const ep_job *job, int64_t *n_nodes, int32_t *substeps, int64_t *n_junctions);
+
+/* ---- bidomain (Eq. 1, Eqs. 5-6) -------------------------------------------
+ * Switch a job to the bidomain model. The parameter sets' (D_l, D_t) become
+ * the intracellular diffusivities D_i; De_l[k], De_t[k] (mm^2/ms, k <
+ * n_sets = the job's parameter-set count) are the extracellular ones of set
+ * k, in the same fibre frame (Eqs. 2-3). Each ep_step then
+ *   1. updates V with the intracellular flux of V^n + v_e^n (first line of
+ *      Eq. 6), everything else as in the monodomain step;
+ *   2. solves the second line of Eq. 6, L_ie(v_e^{n+1}) = -L_i(V^{n+1}), by
+ *      restarted GMRES (Sec. 3.2) started from v_e^n, with L_ie the same
+ *      finite-volume operator for D_i + D_e, stopping at
+ *      ||b - L_ie v_e|| <= max(tol ||b||, atol sqrt(n_cells)) (2-norms over
+ *      cells, b in mV/ms per cell) or after max_iter Arnoldi steps, with a
+ *      restart every `restart` steps (1..30);
+ *   3. fixes v_e to zero volume-weighted mean (the equation leaves a
+ *      constant free under zero-flux boundaries).
+ * v_e is solved once from the current V before returning. Calling it again
+ * replaces the settings; ep_params_set keeps them (and rebuilds the
+ * operator). The solve is one cooperative launch per job and step on the
+ * context's stream; steps of batches that hold bidomain jobs are not
+ * captured in CUDA graphs. Device memory: (restart + 5) values per cell plus
+ * the L_ie coefficients. Synchronises. Errors: EP_EINVAL (bad sizes or
+ * settings), EP_ESTATE (no parameters), EP_ENOMEM; on error the job is left
+ * monodomain. */
+int ep_bidomain_enable(ep_job *job, const double *De_l, const double *De_t, int32_t n_sets, double tol, double atol,
+                       int32_t restart, int64_t max_iter);
+
+/* Back to the monodomain model (frees the bidomain state). */
+int ep_bidomain_disable(ep_job *job);
+
+/* v_e (mV) in the caller's cell order, read or written through host
+ * buffers of n = n_cells doubles. A write also recomputes L_i(v_e) for the
+ * next step. Synchronise. Errors: EP_EINVAL (length), EP_ESTATE (not
+ * bidomain). */
+int ep_bidomain_read_ve(ep_job *job, double *host_out, int64_t n);
+int ep_bidomain_write_ve(ep_job *job, const double *host_in, int64_t n);
+
+/* Solver counters: Arnoldi steps of the last solve and in total, solves,
+ * the last solve's final residual norm and right-hand-side norm, and
+ * whether any solve stopped at max_iter unconverged (any pointer may be
+ * NULL). Synchronises. Returns EP_ETIMEOUT if a grid barrier of the solve
+ * kernel gave up waiting (2 s limit; v_e may then be partly updated). */
+int ep_bidomain_stats(ep_job *job, int64_t *last_iters, int64_t *total_iters, int64_t *solves, double *last_res,
+                      double *last_bnorm, int32_t *failed);
 
 /* Number of state variables of a model and the name of each
  * (e.g. "V", "Ca_i", "Na_i", "m"). */

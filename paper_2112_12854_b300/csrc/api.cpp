@@ -16,6 +16,7 @@
 #include "../../include/ep.h"
 #include "devtypes.h"
 #include "graph_plan.h"
+#include "bidomain.h"
 #include "kernels.h"
 #include "planner.h"
 #include "varmap.h"
@@ -45,8 +46,20 @@ struct Plan {
         StepLaunch L;
     };
     std::vector<Group> groups;
+    std::vector<ep_job *> bido;   // jobs whose step ends with the elliptic solve
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
+};
+
+// Bidomain state of a job (ep_bidomain_enable).
+struct BidoHost {
+    std::vector<double> De_l, De_t;   // extracellular diffusivities per parameter set
+    double tol = 1e-6, atol = 0.0;
+    int restart = 20;
+    int64_t max_iter = 1000;
+    std::vector<DevBuf> bufs;
+    BidoArgs args{};
+    int grid = 1;
 };
 
 }  // namespace
@@ -90,6 +103,8 @@ struct ep_job {
     std::vector<Tile> graph_tiles;
     const int *gperm_dev = nullptr;
     DevBuf graph_view;               // DevJob whose V/act/regions are the graph's (init, I/O)
+    // bidomain (ep_bidomain_enable)
+    std::unique_ptr<BidoHost> bido;
 };
 
 namespace {
@@ -276,6 +291,8 @@ int64_t ep_estimate_bytes(int64_t n_cells, int64_t n_nodes, int32_t precision) {
 namespace {
 
 int graph_apply(ep_job *job);
+int bido_apply(ep_job *job);
+void bido_drop(ep_job *job);
 
 // Validate a parameter block and fold it into FP64 coefficients for a mesh,
 // with the explicit stability check dt * rho(L) < 2 (host only).
@@ -469,7 +486,11 @@ int job_apply_params(ep_job *job, const ep_params *p, const Coeffs &cf) {
     job->device_bytes = 0;
     for (auto &t : job->topo) job->device_bytes += t.bytes;
     for (auto &t : job->prec) job->device_bytes += t.bytes;
-    if (job->gp) return graph_apply(job);
+    if (job->gp && (rc = graph_apply(job))) return rc;
+    if (job->bido && (rc = bido_apply(job))) {
+        bido_drop(job);
+        return rc;
+    }
     return EP_OK;
 }
 
@@ -607,6 +628,133 @@ int graph_apply(ep_job *job) {
     return EP_OK;
 }
 
+// Upload (or rebuild) the bidomain state of a job for its current
+// parameters and precision: the operator of D_i + D_e folded like the job's
+// own, the gauge weights, v_e = 0 and the solver buffers; then solve v_e from
+// the current V. The cell update adds L_i(v_e) from the next step on.
+int bido_apply(ep_job *job) {
+    ep_context *ctx = job->ctx;
+    BidoHost &B = *job->bido;
+    const HostMesh &m = job->mesh();
+    const int prec = job->precision;
+    const size_t r = prec == EP_FP64_PLAIN ? 8 : 4;
+    const int64_t N = m.n_cells;
+    cudaStreamSynchronize(ctx->stream);
+    drop_plans_with(ctx, job);
+    free_job_arrays(job, &B.bufs);
+    ep_params p2 = job->params;
+    for (int k = 0; k < p2.n_sets; ++k) {
+        p2.sets[k].D_l += B.De_l[k];
+        p2.sets[k].D_t += B.De_t[k];
+    }
+    Coeffs cf;
+    std::string err;
+    int rc = build_coeffs(m, &p2, &cf, &err);
+    if (rc) return fail(ctx, rc, "ep_bidomain_enable: " + err);
+    // gauge weights V_c / sum V
+    std::vector<double> wv(N);
+    double tot = 0.0;
+    for (int64_t c = 0; c < N; ++c) {
+        const double *x0 = &m.xyz[3 * int64_t(m.tet[4 * c])];
+        double d[3][3];
+        for (int k = 1; k < 4; ++k)
+            for (int a = 0; a < 3; ++a) d[k - 1][a] = m.xyz[3 * int64_t(m.tet[4 * c + k]) + a] - x0[a];
+        const double det = d[0][0] * (d[1][1] * d[2][2] - d[1][2] * d[2][1]) -
+                           d[0][1] * (d[1][0] * d[2][2] - d[1][2] * d[2][0]) +
+                           d[0][2] * (d[1][0] * d[2][1] - d[1][1] * d[2][0]);
+        wv[c] = std::fabs(det) / 6.0;
+        tot += wv[c];
+    }
+    for (auto &x : wv) x /= tot;
+    auto put_r = [&](const std::vector<double> &v, const void **dst) -> int {
+        void *q = nullptr;
+        int r2;
+        if (prec == EP_FP64_PLAIN) {
+            r2 = upload(ctx, v, &B.bufs, &q);
+        } else {
+            std::vector<float> f(v.begin(), v.end());
+            r2 = upload(ctx, f, &B.bufs, &q);
+        }
+        *dst = q;
+        return r2;
+    };
+    auto grab = [&](size_t bytes, void **dst) {
+        DevBuf b;
+        int r2 = dalloc(ctx, bytes, &b);
+        if (!r2) {
+            B.bufs.push_back(b);
+            *dst = b.p;
+        }
+        return r2;
+    };
+    BidoArgs a{};
+    B.grid = bido_grid(prec, ctx->sm_count, N);
+    a.ld = round_up(std::max<int64_t>(N, 1), 64);
+    void *ve = nullptr, *xd = nullptr, *bb = nullptr, *w = nullptr, *basis = nullptr, *part = nullptr, *st = nullptr,
+         *sy = nullptr;
+    if (!rc) rc = put_r(cf.wa, &a.wa);
+    if (!rc) rc = put_r(cf.wb, &a.wb);
+    if (!rc) rc = put_r(cf.q, &a.q);
+    if (!rc) rc = put_r(wv, &a.wvol);
+    if (!rc) rc = grab(N * r, &ve);
+    if (!rc) rc = grab(N * r, &xd);
+    if (!rc) rc = grab(N * r, &bb);
+    if (!rc) rc = grab(N * r, &w);
+    if (!rc) rc = grab(size_t(B.restart + 1) * a.ld * r, &basis);
+    if (!rc) rc = grab(2 * size_t(kBidoMaxRestart + 1) * B.grid * sizeof(double), &part);
+    if (!rc) rc = grab(sizeof(BidoStats), &st);
+    if (!rc) rc = grab(sizeof(BidoSync), &sy);
+    if (rc) {
+        free_job_arrays(job, &B.bufs);
+        return rc;
+    }
+    a.job = static_cast<const DevJob *>(job->dj_dev.p);
+    a.ve = ve;
+    a.xdiv = xd;
+    a.b = bb;
+    a.w = w;
+    a.basis = basis;
+    a.part = static_cast<double *>(part);
+    a.stats = static_cast<BidoStats *>(st);
+    a.sync = static_cast<BidoSync *>(sy);
+    a.tol = B.tol;
+    a.atol = B.atol;
+    a.max_iter = B.max_iter;
+    a.restart = B.restart;
+    a.mode = 0;
+    B.args = a;
+    job->dj.xdiv = xd;
+    cudaError_t e = cudaMemsetAsync(ve, 0, N * r, ctx->upload);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(BidoStats), ctx->upload);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sy, 0, sizeof(BidoSync), ctx->upload);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(job->dj_dev.p, &job->dj, sizeof(DevJob), cudaMemcpyHostToDevice, ctx->upload);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->upload);
+    if (e == cudaSuccess) e = launch_bido(prec, a, B.grid, ctx->stream);   // v_e from the current V
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bidomain upload");
+    job->version++;
+    job->device_bytes = 0;
+    for (auto *pool : {&job->topo, &job->prec, &job->gbufs, &B.bufs})
+        for (auto &b : *pool) job->device_bytes += b.bytes;
+    return EP_OK;
+}
+
+// Back to the monodomain model (also the cleanup of a failed bido_apply).
+void bido_drop(ep_job *job) {
+    ep_context *ctx = job->ctx;
+    if (!job->bido) return;
+    cudaStreamSynchronize(ctx->stream);
+    drop_plans_with(ctx, job);
+    for (auto &b : job->bido->bufs) job->device_bytes -= b.bytes;
+    free_job_arrays(job, &job->bido->bufs);
+    job->bido.reset();
+    job->dj.xdiv = nullptr;
+    cudaMemcpyAsync(job->dj_dev.p, &job->dj, sizeof(DevJob), cudaMemcpyHostToDevice, ctx->upload);
+    cudaStreamSynchronize(ctx->upload);
+    job->version++;
+}
+
 }  // namespace
 
 struct ep_plan {
@@ -741,13 +889,17 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
     for (int prec : {EP_FP32_MIXED, EP_FP64_PLAIN}) {
         std::vector<DevJob> tab;
         std::vector<Tile> nt, ct, gt;
-        int max_sub = 0;
+        int max_sub = 0, any_bido = 0;
         for (int i = 0; i < n; ++i) {
             if (jobs[i]->precision != prec) continue;
             const int jid = int(tab.size());
             tab.push_back(jobs[i]->dj);
             for (Tile t : jobs[i]->node_tiles) nt.push_back(Tile{jid, t.model, t.start, t.count});
             for (Tile t : jobs[i]->cell_tiles) ct.push_back(Tile{jid, t.model, t.start, t.count});
+            if (jobs[i]->bido) {
+                any_bido = 1;
+                pl->bido.push_back(jobs[i]);
+            }
             if (jobs[i]->gp) {
                 for (Tile t : jobs[i]->graph_tiles) gt.push_back(Tile{jid, t.model, t.start, t.count});
                 max_sub = std::max(max_sub, jobs[i]->gp->substeps);
@@ -779,6 +931,7 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
         g.L.n_graph_tiles = 0;
         g.L.graph_substeps = 0;
         g.L.graph_grid = 1;
+        g.L.bido = any_bido;
         if (!gt.empty()) {
             if ((rc = upload(ctx, gt, &tmp, &p))) return rc;
             g.graph_tiles = tmp.back();
@@ -798,11 +951,16 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
 }
 
 static cudaError_t enqueue_steps(Plan *pl, int64_t steps, cudaStream_t s) {
-    for (int64_t it = 0; it < steps; ++it)
+    for (int64_t it = 0; it < steps; ++it) {
         for (auto &g : pl->groups) {
             cudaError_t e = launch_step(g.precision, g.L, s);
             if (e != cudaSuccess) return e;
         }
+        for (ep_job *j : pl->bido) {   // second line of Eq. 6 for v_e^{n+1}
+            cudaError_t e = launch_bido(j->precision, j->bido->args, j->bido->grid, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
     return cudaSuccess;
 }
 
@@ -860,7 +1018,7 @@ int ep_step(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps) {
         Plan *pl = nullptr;
         if ((rc = get_plan(ctx, jobs, n_jobs, &pl))) return rc;
         int64_t left = n_steps;
-        if (n_steps >= kGraphMinSteps) {
+        if (n_steps >= kGraphMinSteps && pl->bido.empty()) {   // cooperative solves launch directly
             if (!pl->exec) {
                 cudaError_t e = cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal);
                 if (e == cudaSuccess) {
@@ -910,6 +1068,8 @@ int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double
                 if (e == cudaSuccess) e = launch_cell(gr.precision, gr.L, ctx->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(ev[k++], ctx->stream);
             }
+            for (ep_job *j : pl->bido)   // untimed: the elliptic solves of bidomain jobs
+                if (e == cudaSuccess) e = launch_bido(j->precision, j->bido->args, j->bido->grid, ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         double tn = 0.0, tc = 0.0;
         for (size_t i = 0; i + 2 < k + 1 && e == cudaSuccess; i += 3) {
@@ -1038,6 +1198,8 @@ int ep_autotune(ep_job *const *jobs, int32_t n_jobs, int32_t steps_per_variant, 
                             e = launch_step(other.precision, other.L, ctx->stream);
                         }
                     }
+                    for (ep_job *j : pl->bido)
+                        if (e == cudaSuccess) e = launch_bido(j->precision, j->bido->args, j->bido->grid, ctx->stream);
                 }
                 const double mean = tot / steps_per_variant;
                 if (variant_ms) variant_ms[gr.precision * kNumCellVariants + v] = mean;
@@ -1204,6 +1366,7 @@ int ep_job_destroy(ep_job *job) {
     free_job_arrays(job, &job->prec);
     free_job_arrays(job, &job->topo);
     free_job_arrays(job, &job->gbufs);
+    if (job->bido) free_job_arrays(job, &job->bido->bufs);
     dfree(ctx, &job->graph_view);
     dfree(ctx, &job->dj_dev);
     dfree(ctx, &job->step_dev);
@@ -1265,6 +1428,7 @@ int ep_step_noalloc(ep_job *job, int64_t n_steps) {
     if (n_steps < 0) return fail(ctx, EP_EINVAL, "ep_step_noalloc: n_steps < 0");
     if (!job->has_params) return fail(ctx, EP_ESTATE, "ep_step_noalloc: the job has no parameters");
     if (job->gp) return fail(ctx, EP_EINVAL, "ep_step_noalloc: jobs with a conduction graph need ep_step");
+    if (job->bido) return fail(ctx, EP_EINVAL, "ep_step_noalloc: bidomain jobs need ep_step");
     if (job->mesh().n_nodes > EP_NOALLOC_MAX_NODES)
         return fail(ctx, EP_EINVAL, "ep_step_noalloc: the mesh has " + std::to_string(job->mesh().n_nodes) +
                                         " nodes; at most " + std::to_string(EP_NOALLOC_MAX_NODES) +
@@ -1344,6 +1508,107 @@ int ep_graph_info(const ep_job *job, int64_t *n_nodes, int32_t *substeps, int64_
     if (n_nodes) *n_nodes = job->gp ? job->gp->n : 0;
     if (substeps) *substeps = job->gp ? job->gp->substeps : 0;
     if (n_junctions) *n_junctions = job->gp ? int64_t(job->gp->jnode.size()) : 0;
+    return EP_OK;
+}
+
+int ep_bidomain_enable(ep_job *job, const double *De_l, const double *De_t, int32_t n_sets, double tol, double atol,
+                       int32_t restart, int64_t max_iter) {
+    if (!job) return EP_EINVAL;
+    ep_context *ctx = job->ctx;
+    if (!job->has_params) return fail(ctx, EP_ESTATE, "ep_bidomain_enable: job has no parameters");
+    if (!De_l || !De_t || n_sets != job->params.n_sets)
+        return fail(ctx, EP_EINVAL, "ep_bidomain_enable: need one extracellular (D_l, D_t) per parameter set");
+    if (!(tol > 0.0) || !(atol >= 0.0) || restart < 1 || restart > kBidoMaxRestart || max_iter < 1)
+        return fail(ctx, EP_EINVAL, "ep_bidomain_enable: tol > 0, atol >= 0, restart 1..30, max_iter >= 1");
+    for (int k = 0; k < n_sets; ++k)
+        if (!(De_l[k] >= 0.0) || !(De_t[k] >= 0.0))
+            return fail(ctx, EP_EINVAL, "ep_bidomain_enable: negative extracellular diffusivity");
+    DeviceGuard g(ctx->device);
+    try {
+        if (!job->bido) job->bido.reset(new BidoHost());
+        BidoHost &B = *job->bido;
+        B.De_l.assign(De_l, De_l + n_sets);
+        B.De_t.assign(De_t, De_t + n_sets);
+        B.tol = tol;
+        B.atol = atol;
+        B.restart = restart;
+        B.max_iter = max_iter;
+        int rc = bido_apply(job);
+        if (rc) bido_drop(job);
+        return rc;
+    } catch (const std::bad_alloc &) {
+        bido_drop(job);
+        return fail(ctx, EP_ENOMEM, "ep_bidomain_enable: out of host memory");
+    }
+}
+
+int ep_bidomain_disable(ep_job *job) {
+    if (!job) return EP_EINVAL;
+    DeviceGuard g(job->ctx->device);
+    bido_drop(job);
+    return EP_OK;
+}
+
+static int transfer_ve(ep_job *job, double *host, int64_t n, bool write) {
+    int rc = check_io(job, n, host);
+    if (rc) return rc;
+    ep_context *ctx = job->ctx;
+    if (!job->bido) return fail(ctx, EP_ESTATE, "job is not bidomain (ep_bidomain_enable)");
+    DeviceGuard g(ctx->device);
+    DevBuf b;
+    if ((rc = dalloc(ctx, n * sizeof(double), &b))) return rc;
+    double *buf = static_cast<double *>(b.p);
+    cudaError_t e;
+    if (write) {
+        BidoArgs a = job->bido->args;
+        a.mode = 1;   // refresh L_i(v_e) for the next step
+        e = cudaMemcpyAsync(buf, host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = launch_field_scatter(job->precision, buf, job->perm_dev, n, a.ve, ctx->stream);
+        if (e == cudaSuccess) e = launch_bido(job->precision, a, job->bido->grid, ctx->stream);
+    } else {
+        e = launch_field_gather(job->precision, job->bido->args.ve, job->perm_dev, n, buf, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host, buf, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, &b);
+    return e == cudaSuccess ? EP_OK : cuda_fail(ctx, e, write ? "ep_bidomain_write_ve" : "ep_bidomain_read_ve");
+}
+
+int ep_bidomain_read_ve(ep_job *job, double *host_out, int64_t n) {
+    try {
+        return transfer_ve(job, host_out, n, false);
+    } catch (const std::bad_alloc &) {
+        return fail(job->ctx, EP_ENOMEM, "ep_bidomain_read_ve: out of host memory");
+    }
+}
+
+int ep_bidomain_write_ve(ep_job *job, const double *host_in, int64_t n) {
+    try {
+        return transfer_ve(job, const_cast<double *>(host_in), n, true);
+    } catch (const std::bad_alloc &) {
+        return fail(job->ctx, EP_ENOMEM, "ep_bidomain_write_ve: out of host memory");
+    }
+}
+
+int ep_bidomain_stats(ep_job *job, int64_t *last_iters, int64_t *total_iters, int64_t *solves, double *last_res,
+                      double *last_bnorm, int32_t *failed) {
+    if (!job) return EP_EINVAL;
+    ep_context *ctx = job->ctx;
+    if (!job->bido) return fail(ctx, EP_ESTATE, "job is not bidomain (ep_bidomain_enable)");
+    DeviceGuard g(ctx->device);
+    BidoStats st{};
+    BidoSync sy{};
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&st, job->bido->args.stats, sizeof(st), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&sy, job->bido->args.sync, sizeof(sy), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_bidomain_stats");
+    if (last_iters) *last_iters = st.last_iters;
+    if (total_iters) *total_iters = st.total_iters;
+    if (solves) *solves = st.solves;
+    if (last_res) *last_res = st.last_res;
+    if (last_bnorm) *last_bnorm = st.last_bnorm;
+    if (failed) *failed = st.failed;
+    if (sy.err) return fail(ctx, EP_ETIMEOUT, "bidomain solve: a grid barrier wait hit its time limit");
     return EP_OK;
 }
 

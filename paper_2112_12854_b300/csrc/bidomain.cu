@@ -1,0 +1,422 @@
+// Bidomain solve kernel (see bidomain.h): one cooperative, persistent launch
+// per job and step runs the whole restarted GMRES solve of the elliptic
+// equation -- node values, fluxes, Gram-Schmidt passes, reductions and the
+// Givens least-squares update -- with grid barriers between the phases, so
+// no host round trip decides the iteration count.
+//
+// GMRES (Sec. 3.2; textbook restarted GMRES): Arnoldi with classical
+// Gram-Schmidt applied twice (CGS2; the two passes cost two streaming reads
+// of the basis instead of the j dependent reductions of modified
+// Gram-Schmidt), Givens rotations on the Hessenberg column, restart after
+// `restart` steps from the true residual. The basis is stored unnormalised
+// with a scale per vector, so normalisation needs no extra pass. Dot
+// products are summed per thread in the compute type, per block and across
+// blocks in FP64, in a fixed order: the result depends only on the job and
+// the device, not on the batch.
+#include <algorithm>
+#include <cmath>
+
+#include "bidomain.h"
+
+namespace ep {
+
+namespace {
+
+template <class R> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = double4_32a; };
+
+constexpr int kWarps = kBidoThreads / 32;
+constexpr int KP = kBidoMaxRestart + 1;
+constexpr unsigned long long kBarrierLimitNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier of a cooperative launch (all blocks co-resident). The wait is
+// bounded: past the limit the block sets the error flag and every block
+// leaves the kernel at its next barrier. Returns false on error.
+__device__ bool grid_sync(BidoSync *s, int *flag_sh) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &s->gen;
+        volatile int *verr = &s->err;
+        const unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(&s->count, 1u) == gridDim.x - 1) {
+            atomicExch(&s->count, 0u);
+            __threadfence();
+            atomicAdd(&s->gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*vgen == g && *verr == 0) {
+                if (global_ns() - t0 > kBarrierLimitNs) {
+                    atomicExch(&s->err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *flag_sh = *verr;
+    }
+    __syncthreads();
+    return *flag_sh == 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block partial sums of acc[0..count) into part[i * gridDim.x + blockIdx.x].
+template <class R>
+__device__ void block_partials(const R (&acc)[KP], int count, double *part, double *red_sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < KP; ++i) {
+        if (i < count) {
+            const double v = warp_sum(double(acc[i]));
+            if (lane == 0) red_sh[warp * KP + i] = v;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < kWarps; ++w) s += red_sh[w * KP + i];
+        part[size_t(i) * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// Grid totals of the partials (after a barrier), computed by every block in
+// the same order: tot_sh[i] for i < count.
+__device__ void grid_totals(const double *part, int count, double *tot_sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < count; i += kWarps) {
+        double s = 0.0;
+        for (int b = lane; b < int(gridDim.x); b += 32) s += part[size_t(i) * gridDim.x + b];
+        s = warp_sum(s);
+        if (lane == 0) tot_sh[i] = s;
+    }
+    __syncthreads();
+}
+
+// S1 on a field x (times `scale`): inverse-distance node values into vn.
+template <class R>
+__device__ void node_pass(const DevJob &J, const R *__restrict__ x, R scale, R *__restrict__ vn, long long gtid,
+                          long long gsz) {
+    const R *__restrict__ w = static_cast<const R *>(J.nw);
+    for (long long node = gtid; node < J.n_nodes; node += gsz) {
+        const long long s = node >> 5;
+        const long long b = J.slice_ptr[s] + (node & 31), e = J.slice_ptr[s + 1];
+        R acc = R(0);
+        for (long long k = b; k < e; k += 32) acc += w[k] * x[J.ncol[k]];
+        vn[node] = acc * scale;
+    }
+}
+
+// Folded diffusion term (Eqs. 7-8) of cell c for the field x * scale whose
+// node values are vn, with coefficient set (wa, wb, q).
+template <class R>
+__device__ __forceinline__ R flux(const DevJob &J, const void *wa_, const void *wb_, const void *q_,
+                                  const R *__restrict__ vn, const R *__restrict__ x, R scale, long long c) {
+    using R4 = typename V4<R>::type;
+    const int4 na = J.nodes_a[c], nb = J.nodes_b[c], nc = J.nbr[c];
+    const R4 wa = static_cast<const R4 *>(wa_)[c];
+    const R4 wb = static_cast<const R4 *>(wb_)[c];
+    const R4 q = static_cast<const R4 *>(q_)[c];
+    const R xc = x[c];
+    R d = wa.x * vn[na.x] + wa.y * vn[na.y] + wa.z * vn[na.z] + wa.w * vn[na.w];
+    d += wb.x * vn[nb.x] + wb.y * vn[nb.y] + wb.z * vn[nb.z] + wb.w * vn[nb.w];
+    d += scale * (q.x * (x[nc.x] - xc) + q.y * (x[nc.y] - xc) + q.z * (x[nc.z] - xc) + q.w * (x[nc.w] - xc));
+    return d;
+}
+
+}  // namespace
+
+template <class R>
+__global__ void __launch_bounds__(kBidoThreads) bido_kernel(BidoArgs A) {
+    __shared__ double red_sh[kWarps * KP];
+    __shared__ double tot[KP];
+    __shared__ double H[KP * kBidoMaxRestart];   // H[i * kBidoMaxRestart + j]
+    __shared__ double cs[kBidoMaxRestart], sn[kBidoMaxRestart], g[KP], y[KP];
+    __shared__ double sc[KP];                     // basis vector i = basis_i * sc[i]
+    __shared__ R coef[KP];                        // per-pass multipliers of the basis vectors
+    __shared__ int flag_sh;
+
+    const DevJob &J = *A.job;
+    const long long n = J.n_cells;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gsz = (long long)gridDim.x * blockDim.x;
+    const long long step = *J.step;
+    const R *__restrict__ V = static_cast<const R *>(J.V[step & 1]);
+    R *__restrict__ vn = static_cast<R *>(J.vn);
+    R *__restrict__ x = static_cast<R *>(A.ve);
+    R *__restrict__ b = static_cast<R *>(A.b);
+    R *__restrict__ wv = static_cast<R *>(A.w);
+    R *__restrict__ basis = static_cast<R *>(A.basis);
+    const long long ld = A.ld;
+    const int m = A.restart;
+    R acc[KP];
+    // Two partial-sum buffers used in turn: a block may write the next
+    // reduction's partials while another still reads the previous totals, but
+    // never before every block has passed the barrier that follows.
+    int red = 0;
+    auto part_w = [&]() { return A.part + size_t(red & 1) * KP * gridDim.x; };
+#define BIDO_SYNC()                              \
+    do {                                         \
+        if (!grid_sync(A.sync, &flag_sh)) return; \
+    } while (0)
+
+    long long iters = 0;
+    int failed = 0;
+    double res = 0.0, bnorm = 0.0;
+    if (A.mode == 0) {
+        // right-hand side b = -L_i(V^{n+1}) and its norm
+        node_pass<R>(J, V, R(1), vn, gtid, gsz);
+        BIDO_SYNC();
+        acc[0] = R(0);
+        for (long long c = gtid; c < n; c += gsz) {
+            const R bc = -flux<R>(J, J.wa, J.wb, J.q, vn, V, R(1), c);
+            b[c] = bc;
+            acc[0] += bc * bc;
+        }
+        block_partials<R>(acc, 1, part_w(), red_sh);
+        BIDO_SYNC();
+        grid_totals(part_w(), 1, tot);
+        ++red;
+        bnorm = sqrt(tot[0]);
+        const double thr = fmax(A.tol * bnorm, A.atol * sqrt(double(n)));
+        for (;;) {
+            // true residual r = b - L_ie x into basis vector 0
+            node_pass<R>(J, x, R(1), vn, gtid, gsz);
+            BIDO_SYNC();
+            acc[0] = R(0);
+            for (long long c = gtid; c < n; c += gsz) {
+                const R r = b[c] - flux<R>(J, A.wa, A.wb, A.q, vn, x, R(1), c);
+                basis[c] = r;
+                acc[0] += r * r;
+            }
+            block_partials<R>(acc, 1, part_w(), red_sh);
+            BIDO_SYNC();
+            grid_totals(part_w(), 1, tot);
+            ++red;
+            const double beta = sqrt(tot[0]);
+            res = beta;
+            if (beta <= thr) break;
+            if (iters >= A.max_iter) {
+                failed = 1;
+                break;
+            }
+            if (threadIdx.x == 0) {
+                sc[0] = 1.0 / beta;
+                for (int i = 0; i < KP; ++i) g[i] = 0.0;
+                g[0] = beta;
+            }
+            __syncthreads();
+            int j = 0;
+            while (j < m && iters < A.max_iter) {
+                const R *__restrict__ vj = basis + j * ld;
+                const R sj = R(sc[j]);
+                // w = L_ie v_j, and the first Gram-Schmidt dots <v_i, w>
+                node_pass<R>(J, vj, sj, vn, gtid, gsz);
+                BIDO_SYNC();
+#pragma unroll
+                for (int i = 0; i < KP; ++i) acc[i] = R(0);
+                for (long long c = gtid; c < n; c += gsz) {
+                    const R w = flux<R>(J, A.wa, A.wb, A.q, vn, vj, sj, c);
+                    wv[c] = w;
+#pragma unroll
+                    for (int i = 0; i < KP; ++i)
+                        if (i <= j) acc[i] += basis[i * ld + c] * w;
+                }
+                block_partials<R>(acc, j + 1, part_w(), red_sh);
+                BIDO_SYNC();
+                grid_totals(part_w(), j + 1, tot);
+                ++red;
+                if (threadIdx.x <= j) {
+                    const double h = tot[threadIdx.x] * sc[threadIdx.x];
+                    H[threadIdx.x * kBidoMaxRestart + j] = h;
+                    coef[threadIdx.x] = R(h * sc[threadIdx.x]);
+                }
+                __syncthreads();
+                // second pass: w' = w - V h, and the re-orthogonalisation dots
+#pragma unroll
+                for (int i = 0; i < KP; ++i) acc[i] = R(0);
+                for (long long c = gtid; c < n; c += gsz) {
+                    R w = wv[c];
+#pragma unroll
+                    for (int i = 0; i < KP; ++i)
+                        if (i <= j) w -= coef[i] * basis[i * ld + c];
+                    wv[c] = w;
+#pragma unroll
+                    for (int i = 0; i < KP; ++i)
+                        if (i <= j) acc[i] += basis[i * ld + c] * w;
+                }
+                block_partials<R>(acc, j + 1, part_w(), red_sh);
+                BIDO_SYNC();
+                grid_totals(part_w(), j + 1, tot);
+                ++red;
+                if (threadIdx.x <= j) {
+                    const double h2 = tot[threadIdx.x] * sc[threadIdx.x];
+                    H[threadIdx.x * kBidoMaxRestart + j] += h2;
+                    coef[threadIdx.x] = R(h2 * sc[threadIdx.x]);
+                }
+                __syncthreads();
+                // third pass: v_{j+1} (unnormalised) = w' - V h2, and its norm
+                R *__restrict__ vnext = basis + (j + 1) * ld;
+                acc[0] = R(0);
+                for (long long c = gtid; c < n; c += gsz) {
+                    R w = wv[c];
+#pragma unroll
+                    for (int i = 0; i < KP; ++i)
+                        if (i <= j) w -= coef[i] * basis[i * ld + c];
+                    vnext[c] = w;
+                    acc[0] += w * w;
+                }
+                block_partials<R>(acc, 1, part_w(), red_sh);
+                BIDO_SYNC();
+                grid_totals(part_w(), 1, tot);
+                ++red;
+                const double hn = sqrt(tot[0]);
+                if (threadIdx.x == 0) {
+                    sc[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+                    double *Hc = H + j;   // column j, row stride kBidoMaxRestart
+                    for (int i = 0; i < j; ++i) {
+                        const double a = Hc[i * kBidoMaxRestart], c2 = Hc[(i + 1) * kBidoMaxRestart];
+                        Hc[i * kBidoMaxRestart] = cs[i] * a + sn[i] * c2;
+                        Hc[(i + 1) * kBidoMaxRestart] = -sn[i] * a + cs[i] * c2;
+                    }
+                    const double a = Hc[j * kBidoMaxRestart];
+                    const double rr = sqrt(a * a + hn * hn);
+                    cs[j] = rr > 0.0 ? a / rr : 1.0;
+                    sn[j] = rr > 0.0 ? hn / rr : 0.0;
+                    Hc[j * kBidoMaxRestart] = rr;
+                    g[j + 1] = -sn[j] * g[j];
+                    g[j] = cs[j] * g[j];
+                }
+                __syncthreads();
+                ++j;
+                ++iters;
+                if (fabs(g[j]) <= thr || hn == 0.0) break;
+            }
+            // x += V_j y with H_j y = g (upper triangular, every block the same)
+            if (threadIdx.x == 0) {
+                for (int i = j - 1; i >= 0; --i) {
+                    double s = g[i];
+                    for (int l = i + 1; l < j; ++l) s -= H[i * kBidoMaxRestart + l] * y[l];
+                    const double d = H[i * kBidoMaxRestart + i];
+                    y[i] = d != 0.0 ? s / d : 0.0;
+                }
+                for (int i = 0; i < j; ++i) coef[i] = R(y[i] * sc[i]);
+            }
+            __syncthreads();
+            for (long long c = gtid; c < n; c += gsz) {
+                R xc = x[c];
+#pragma unroll
+                for (int i = 0; i < KP; ++i)
+                    if (i < j) xc += coef[i] * basis[i * ld + c];
+                x[c] = xc;
+            }
+            BIDO_SYNC();
+        }
+        // gauge: zero volume-weighted mean
+        const R *__restrict__ wvol = static_cast<const R *>(A.wvol);
+        acc[0] = R(0);
+        for (long long c = gtid; c < n; c += gsz) acc[0] += wvol[c] * x[c];
+        block_partials<R>(acc, 1, part_w(), red_sh);
+        BIDO_SYNC();
+        grid_totals(part_w(), 1, tot);
+        ++red;
+        const R mean = R(tot[0]);
+        for (long long c = gtid; c < n; c += gsz) x[c] -= mean;
+        BIDO_SYNC();
+    }
+    // intracellular flux of v_e for the next step's V update
+    node_pass<R>(J, x, R(1), vn, gtid, gsz);
+    BIDO_SYNC();
+    R *__restrict__ xd = static_cast<R *>(A.xdiv);
+    for (long long c = gtid; c < n; c += gsz) xd[c] = flux<R>(J, J.wa, J.wb, J.q, vn, x, R(1), c);
+    if (A.mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+        BidoStats *st = A.stats;
+        st->last_iters = iters;
+        st->total_iters += iters;
+        st->solves += 1;
+        st->last_res = res;
+        st->last_bnorm = bnorm;
+        st->failed |= failed;
+    }
+#undef BIDO_SYNC
+}
+
+namespace {
+
+template <class R>
+__global__ void field_gather_kernel(const R *__restrict__ src, const int *__restrict__ perm, long long n,
+                                    double *__restrict__ out) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) out[perm[c]] = double(src[c]);
+}
+
+template <class R>
+__global__ void field_scatter_kernel(const double *__restrict__ in, const int *__restrict__ perm, long long n,
+                                     R *__restrict__ dst) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) dst[c] = R(in[perm[c]]);
+}
+
+template <class R>
+int grid_of(int sm_count) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bido_kernel<R>, kBidoThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return sm_count * std::max(1, std::min(nb, 2));
+}
+
+}  // namespace
+
+int bido_grid(int precision, int sm_count, long long n_cells) {
+    const int co = precision == EP_FP64_PLAIN ? grid_of<double>(sm_count) : grid_of<float>(sm_count);
+    const long long want = (n_cells + 4 * kBidoThreads - 1) / (4 * kBidoThreads);
+    return int(std::max(1LL, std::min<long long>(co, want)));
+}
+
+cudaError_t launch_bido(int precision, const BidoArgs &a, int grid, cudaStream_t s) {
+    BidoArgs arg = a;
+    void *args[] = {&arg};
+    if (precision == EP_FP64_PLAIN)
+        return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(bido_kernel<double>), dim3(grid),
+                                           dim3(kBidoThreads), args, 0, s);
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(bido_kernel<float>), dim3(grid),
+                                       dim3(kBidoThreads), args, 0, s);
+}
+
+cudaError_t launch_field_gather(int precision, const void *src, const int *perm, long long n, double *out,
+                                cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const unsigned blocks = unsigned((n + 255) / 256);
+    if (precision == EP_FP64_PLAIN)
+        field_gather_kernel<double><<<blocks, 256, 0, s>>>(static_cast<const double *>(src), perm, n, out);
+    else
+        field_gather_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(src), perm, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_scatter(int precision, const double *in, const int *perm, long long n, void *dst,
+                                 cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const unsigned blocks = unsigned((n + 255) / 256);
+    if (precision == EP_FP64_PLAIN)
+        field_scatter_kernel<double><<<blocks, 256, 0, s>>>(in, perm, n, static_cast<double *>(dst));
+    else
+        field_scatter_kernel<float><<<blocks, 256, 0, s>>>(in, perm, n, static_cast<float *>(dst));
+    return cudaGetLastError();
+}
+
+}  // namespace ep

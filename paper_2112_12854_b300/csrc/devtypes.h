@@ -87,6 +87,7 @@ struct DevJob {
     float dt_f, threshold_f;
     long long *step;          // steps taken (device counter)
     DevGraph g;
+    const void *xdiv;         // bidomain: intracellular flux of v_e, added to the diffusion term (else NULL)
 };
 
 // A tile is a run of consecutive cells (or nodes) of one job and one model.

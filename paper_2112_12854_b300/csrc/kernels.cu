@@ -104,7 +104,9 @@ __device__ void junction_cell_crossing(const DevJob &J, long long c, long long n
     }
 }
 
-template <class R>
+// XD: the batch holds bidomain jobs, whose cells add L_i(v_e^n) (first line
+// of Eq. 6) to the diffusion term; monodomain-only batches compile without it.
+template <class R, bool XD = false>
 __device__ __forceinline__ void cell_update(const DevJob &J, int model, long long c) {
     using R4 = typename Vec4T<R>::type;
     const long long n = *J.step;
@@ -120,6 +122,7 @@ __device__ __forceinline__ void cell_update(const DevJob &J, int model, long lon
     R diff = wa.x * vn[na.x] + wa.y * vn[na.y] + wa.z * vn[na.z] + wa.w * vn[na.w];
     diff += wb.x * vn[nb.x] + wb.y * vn[nb.y] + wb.z * vn[nb.z] + wb.w * vn[nb.w];
     diff += q.x * (V[nc.x] - Vc) + q.y * (V[nc.y] - Vc) + q.z * (V[nc.z] - Vc) + q.w * (V[nc.w] - Vc);
+    if (XD && J.xdiv) diff += static_cast<const R *>(J.xdiv)[c];
 
     const unsigned mask = J.smask[c];
     R is = mask ? stimulus<R>(J, mask, n) : R(0);
@@ -234,13 +237,14 @@ __global__ void __launch_bounds__(kGraphThreads) graph_diffuse_kernel(const DevJ
 // the register allocator. All variants run the same per-cell arithmetic, so
 // their results are bitwise identical. Tiles hold kCellThreads cells; a
 // block narrower than a tile walks it in strides of its width.
-template <class R, int T, int MINB>
+template <class R, int T, int MINB, bool XD>
 __global__ void __launch_bounds__(T, MINB) cell_kernel(const DevJob *__restrict__ jobs,
                                                         const Tile *__restrict__ tiles, int n_tiles,
                                                         unsigned *done, int n_jobs) {
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const Tile tl = tiles[t];
-        for (int i = threadIdx.x; i < tl.count; i += T) cell_update<R>(jobs[tl.job], tl.model, (long long)tl.start + i);
+        for (int i = threadIdx.x; i < tl.count; i += T)
+            cell_update<R, XD>(jobs[tl.job], tl.model, (long long)tl.start + i);
     }
     // Every block has read the step counters; the last one to finish advances them.
     __syncthreads();
@@ -426,7 +430,12 @@ static cudaError_t cell_launch_variant(const StepLaunch &L, cudaStream_t s) {
     switch (L.cell_variant) {
 #define EP_CELL_CASE(k, T, B)                                                                                  \
     case k:                                                                                                    \
-        cell_kernel<R, T, B><<<L.cell_grid, T, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done, L.n_jobs); \
+        if (L.bido)                                                                                            \
+            cell_kernel<R, T, B, true><<<L.cell_grid, T, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done,  \
+                                                                 L.n_jobs);                                    \
+        else                                                                                                   \
+            cell_kernel<R, T, B, false><<<L.cell_grid, T, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done, \
+                                                                  L.n_jobs);                                   \
         break;
         EP_CELL_VARIANTS(EP_CELL_CASE)
 #undef EP_CELL_CASE
@@ -446,7 +455,7 @@ static int cell_blocks_variant(int variant) {
     switch (variant) {
 #define EP_CELL_CASE(k, T, B)                                                                 \
     case k:                                                                                   \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_kernel<R, T, B>, T, 0);       \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_kernel<R, T, B, false>, T, 0); \
         break;
         EP_CELL_VARIANTS(EP_CELL_CASE)
 #undef EP_CELL_CASE

@@ -20,6 +20,7 @@ struct StepLaunch {
     int n_graph_tiles;
     int graph_grid;
     int graph_substeps;        // largest substep count of the jobs' graphs
+    int bido;                  // some job is bidomain (cell kernel adds DevJob::xdiv)
 };
 
 // Launch shapes of the cell kernel: (index, threads per block, minimum

@@ -80,7 +80,9 @@ EXPORTS = ["ep_context_create", "ep_context_set_stream", "ep_context_destroy", "
            "ep_model_varname", "ep_plan_inspect", "ep_time_kernels",
            "ep_step_noalloc", "ep_autotune", "ep_set_cell_variant", "ep_plan_create", "ep_plan_bytes",
            "ep_plan_info", "ep_plan_destroy", "ep_job_create", "ep_graph_attach", "ep_graph_read_state",
-           "ep_graph_write_state", "ep_graph_activation_times", "ep_graph_info", "ep_alu_peaks"]
+           "ep_graph_write_state", "ep_graph_activation_times", "ep_graph_info", "ep_alu_peaks",
+           "ep_bidomain_enable", "ep_bidomain_disable", "ep_bidomain_read_ve", "ep_bidomain_write_ve",
+           "ep_bidomain_stats"]
 
 _lib = None
 _P = ctypes.c_void_p
@@ -131,6 +133,13 @@ def load():
         "ep_autotune": ([ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32, _P, _P], ctypes.c_int),
         "ep_set_cell_variant": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
         "ep_alu_peaks": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "ep_bidomain_enable": ([_P, _P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32, _I64],
+                               ctypes.c_int),
+        "ep_bidomain_disable": ([_P], ctypes.c_int),
+        "ep_bidomain_read_ve": ([_P, _P, _I64], ctypes.c_int),
+        "ep_bidomain_write_ve": ([_P, _P, _I64], ctypes.c_int),
+        "ep_bidomain_stats": ([_P] + [ctypes.POINTER(_I64)] * 3 + [ctypes.POINTER(ctypes.c_double)] * 2
+                              + [ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "ep_time_kernels": ([ctypes.POINTER(_P), ctypes.c_int32, _I64, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "ep_plan_inspect": ([ctypes.POINTER(MeshDesc), ctypes.POINTER(Params)] + [_P] * 10
@@ -270,6 +279,7 @@ class Plan:
         if rc:
             raise EPError(rc, L.ep_last_error(None).decode())
         self._h = h
+        self.params = params
         a, b = _I64(), _I64()
         L.ep_plan_info(h, ctypes.byref(a), ctypes.byref(b))
         self.n_cells, self.n_nodes = int(a.value), int(b.value)
@@ -293,6 +303,8 @@ class Job:
         if plan is not None:
             ctx.check(L.ep_job_create(ctx._h, plan._h, ctypes.byref(h)))
             self.n_cells = plan.n_cells
+            if plan.params is not None:
+                self.params = plan.params
         else:
             d, keep = _mesh_desc(xyz, tets, cell_model, param_set, stim_mask, fibre)
             ctx.check(L.ep_mesh_create(ctx._h, ctypes.byref(d), ctypes.byref(h)))
@@ -302,6 +314,7 @@ class Job:
 
     def set_params(self, params: Params):
         self.ctx.check(load().ep_params_set(self._h, ctypes.byref(params)))
+        self.params = params
 
     def step(self, n_steps: int):
         step([self], n_steps)
@@ -411,6 +424,49 @@ class Job:
         a, b, c = _I64(), ctypes.c_int32(), _I64()
         self.ctx.check(load().ep_graph_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return dict(n_nodes=a.value, substeps=b.value, n_junctions=c.value)
+
+    def enable_bidomain(self, De_l, De_t, *, tol=None, atol=None, restart=20, max_iter=2000, n_sets=None):
+        """Bidomain model (ep_bidomain_enable): De_l, De_t are the
+        extracellular diffusivities, scalars or one per parameter set; the
+        parameter sets' own (D_l, D_t) become the intracellular ones. Default
+        stopping rule: tol 1e-5, atol 1e-3 mV/ms (FP32 mixed: about the
+        rounding floor of an FP32 residual); tol 1e-11, atol 0 (FP64 plain)."""
+        params = getattr(self, "params", None)
+        if n_sets is None:
+            n_sets = params.n_sets if params is not None else np.size(De_l)
+        plain = params is not None and params.precision == EP_FP64_PLAIN
+        if tol is None:
+            tol = 1e-11 if plain else 1e-5
+        if atol is None:
+            atol = 0.0 if plain else 1e-3
+        el = np.ascontiguousarray(np.broadcast_to(np.asarray(De_l, np.float64), (n_sets,)))
+        et = np.ascontiguousarray(np.broadcast_to(np.asarray(De_t, np.float64), (n_sets,)))
+        self.ctx.check(load().ep_bidomain_enable(self._h, _ptr(el), _ptr(et), int(n_sets), float(tol), float(atol),
+                                                 int(restart), int(max_iter)))
+
+    def disable_bidomain(self):
+        self.ctx.check(load().ep_bidomain_disable(self._h))
+
+    @property
+    def ve(self) -> np.ndarray:
+        out = np.empty(self.n_cells, np.float64)
+        self.ctx.check(load().ep_bidomain_read_ve(self._h, _ptr(out), self.n_cells))
+        return out
+
+    @ve.setter
+    def ve(self, values):
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        assert v.size == self.n_cells
+        self.ctx.check(load().ep_bidomain_write_ve(self._h, _ptr(v), self.n_cells))
+
+    def bidomain_stats(self) -> dict:
+        a, b, c = _I64(), _I64(), _I64()
+        r, bn = ctypes.c_double(), ctypes.c_double()
+        f = ctypes.c_int32()
+        self.ctx.check(load().ep_bidomain_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                                ctypes.byref(r), ctypes.byref(bn), ctypes.byref(f)))
+        return {"last_iters": a.value, "total_iters": b.value, "solves": c.value, "last_res": r.value,
+                "last_bnorm": bn.value, "failed": bool(f.value)}
 
     def destroy(self):
         if getattr(self, "_h", None):
