@@ -276,6 +276,49 @@ def run_heart(ctx, args, stream, torch):
             "node_and_graph_kernels_ms": node_graph_ms, "cell_kernel_ms": cell_ms}
 
 
+def run_bidomain(ctx, args, dims, stream, torch, peak):
+    """Bidomain on the benchmark wedge (Eq. 1, Eqs. 5-6): the ventricular
+    conductivities of Table 2 (intracellular 0.17 / 0.019, extracellular
+    0.62 / 0.24 mS/mm over chi C_m = 1.4 uF/mm^3), FP32 mixed, the
+    library's default solver (restarted GMRES(12), stopping rule). Timed after
+    args.bido_warmup steps, once the stimulated front is moving; the
+    elliptic-solve kernel is placed against HBM with its own algorithmic
+    byte count."""
+    from paper_2112_12854_b300 import ep
+    case = wedge_case(dims)
+    for ps in case.param_sets:
+        ps.D_l, ps.D_t = 0.17 / 1.4, 0.019 / 1.4
+    job = ep.job_from_case(ctx, case)
+    job.enable_bidomain(0.62 / 1.4, 0.24 / 1.4)
+    job.step(args.bido_warmup)
+    torch.cuda.synchronize()
+    st0 = job.bidomain_stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    job.step(args.bido_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.bido_steps
+    st1 = job.bidomain_stats()
+    node_ms, cell_ms = ep.time_kernels([job], 3)
+    job.destroy()
+    solve_ms = ms - node_ms - cell_ms
+    iters = (st1["total_iters"] - st0["total_iters"]) / args.bido_steps
+    gbs = (st1["alg_bytes"] - st0["alg_bytes"]) / args.bido_steps / (solve_ms * 1e-3) / 1e9
+    return {"cells": case.n_cells, "steps": args.bido_steps, "warmup_steps": args.bido_warmup,
+            "ms_per_step": ms, "cell_updates_per_s": case.n_cells / (ms * 1e-3),
+            "arnoldi_steps_per_step": iters, "solve_ms_per_step": solve_ms,
+            "node_kernel_ms": node_ms, "cell_kernel_ms": cell_ms,
+            "solve_phase_ms_per_step": {k: (b - a) / args.bido_steps for k, a, b in
+                                        zip(("node_values", "fluxes_and_dots", "gs_pass2", "gs_pass3", "updates"),
+                                            st0["phase_ms"], st1["phase_ms"])},
+            "solver": "restarted GMRES(12), classical Gram-Schmidt, tol 1e-5 relative / 1e-3 mV/ms per cell absolute",
+            "solve_roofline": {"bound": "hbm", "kernel": "bido_kernel<float>", "achieved": gbs, "peak": peak,
+                               "unit": "GB/s", "frac": gbs / peak,
+                               "alg_bytes_per_step": (st1["alg_bytes"] - st0["alg_bytes"]) / args.bido_steps},
+            "last_rel_res": st1["last_res"] / max(st1["last_bnorm"], 1e-300), "failed": st1["failed"]}
+
+
 def run_serving(ctx, args, capacity_cups, rank, world, dist):
     """Two serving runs of the job-stream workload (sizes log-uniform 20k-4M
     cells, 100-800 ms simulated, 70 % slabs / 30 % whole-heart topology at
@@ -331,6 +374,8 @@ def main():
     ap.add_argument("--sweep-jobs", type=int, default=64, help="jobs of the batched parametric sweep (0 = skip; "
                     "the configured sweep has 256)")
     ap.add_argument("--sweep-steps", type=int, default=200)
+    ap.add_argument("--bido-steps", type=int, default=100, help="timed steps of the bidomain leg (0 = skip)")
+    ap.add_argument("--bido-warmup", type=int, default=100)
     ap.add_argument("--serve-window", type=float, default=40.0,
                     help="seconds of Poisson arrivals in each serving run (0 = no serving leg)")
     ap.add_argument("--serve-load", type=float, default=0.7, help="offered load of the first serving run, "
@@ -470,6 +515,10 @@ def main():
     if args.sweep_jobs > 0:
         sweep = run_sweep(ctx, args, stream, torch)
 
+    bido = None
+    if args.bido_steps > 0:
+        bido = run_bidomain(ctx, args, dims, stream, torch, peak)
+
     heart = None
     if args.heart_steps > 0:
         heart = run_heart(ctx, args, stream, torch)
@@ -508,7 +557,7 @@ def main():
                              "fp64_fma_tflops": alu["fp64_fma_flops"] / 1e12,
                              "source": "ep_alu_peaks: independent FMA / ex2 chains on every SM, CUDA events"},
                "speedup_vs_fp64_plain": value / world / fp64["value"], "state_finite": finite,
-               "batched_sweep": sweep, "whole_heart": heart, "serving": serving}
+               "batched_sweep": sweep, "bidomain": bido, "whole_heart": heart, "serving": serving}
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist is not None:

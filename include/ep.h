@@ -387,20 +387,32 @@ int ep_graph_activation_times(ep_job *job, double *host_out, int64_t n);
 int ep_graph_info(const ep_job *job, int64_t *n_nodes, int32_t *substeps, int64_t *n_junctions);
 
 /* ---- bidomain (Eq. 1, Eqs. 5-6) -------------------------------------------
- * Switch a job to the bidomain model. The parameter sets' (D_l, D_t) become
+ * Settings of the elliptic solve (restarted GMRES, Sec. 3.2). A solve stops
+ * when ||b - L_ie v_e|| <= max(tol ||b||, atol sqrt(n_cells)) (2-norms over
+ * cells, b in mV/ms per cell) or after max_iter Arnoldi steps; the Krylov
+ * basis restarts every `restart` steps (1..30) from the true residual;
+ * reorth = 1 applies classical Gram-Schmidt twice (CGS2), 0 once (CGS). */
+typedef struct {
+    double tol, atol;
+    int32_t restart;
+    int32_t reorth;
+    int64_t max_iter;
+} ep_bidomain_solver;
+
+/* Switch a job to the bidomain model. The parameter sets' (D_l, D_t) become
  * the intracellular diffusivities D_i; De_l[k], De_t[k] (mm^2/ms, k <
  * n_sets = the job's parameter-set count) are the extracellular ones of set
  * k, in the same fibre frame (Eqs. 2-3). Each ep_step then
  *   1. updates V with the intracellular flux of V^n + v_e^n (first line of
  *      Eq. 6), everything else as in the monodomain step;
  *   2. solves the second line of Eq. 6, L_ie(v_e^{n+1}) = -L_i(V^{n+1}), by
- *      restarted GMRES (Sec. 3.2) started from v_e^n, with L_ie the same
- *      finite-volume operator for D_i + D_e, stopping at
- *      ||b - L_ie v_e|| <= max(tol ||b||, atol sqrt(n_cells)) (2-norms over
- *      cells, b in mV/ms per cell) or after max_iter Arnoldi steps, with a
- *      restart every `restart` steps (1..30);
+ *      restarted GMRES started from v_e^n, L_ie being the same
+ *      finite-volume operator for D_i + D_e;
  *   3. fixes v_e to zero volume-weighted mean (the equation leaves a
  *      constant free under zero-flux boundaries).
+ * solver NULL takes the defaults: restart 12, CGS, max_iter 2000, and
+ * tol 1e-5, atol 1e-3 mV/ms (FP32 mixed: about the rounding floor of an FP32
+ * residual) or tol 1e-11, atol 0 (FP64 plain).
  * v_e is solved once from the current V before returning. Calling it again
  * replaces the settings; ep_params_set keeps them (and rebuilds the
  * operator). The solve is one cooperative launch per job and step on the
@@ -409,8 +421,8 @@ int ep_graph_info(const ep_job *job, int64_t *n_nodes, int32_t *substeps, int64_
  * the L_ie coefficients. Synchronises. Errors: EP_EINVAL (bad sizes or
  * settings), EP_ESTATE (no parameters), EP_ENOMEM; on error the job is left
  * monodomain. */
-int ep_bidomain_enable(ep_job *job, const double *De_l, const double *De_t, int32_t n_sets, double tol, double atol,
-                       int32_t restart, int64_t max_iter);
+int ep_bidomain_enable(ep_job *job, const double *De_l, const double *De_t, int32_t n_sets,
+                       const ep_bidomain_solver *solver);
 
 /* Back to the monodomain model (frees the bidomain state). */
 int ep_bidomain_disable(ep_job *job);
@@ -422,13 +434,25 @@ int ep_bidomain_disable(ep_job *job);
 int ep_bidomain_read_ve(ep_job *job, double *host_out, int64_t n);
 int ep_bidomain_write_ve(ep_job *job, const double *host_in, int64_t n);
 
-/* Solver counters: Arnoldi steps of the last solve and in total, solves,
- * the last solve's final residual norm and right-hand-side norm, and
- * whether any solve stopped at max_iter unconverged (any pointer may be
- * NULL). Synchronises. Returns EP_ETIMEOUT if a grid barrier of the solve
- * kernel gave up waiting (2 s limit; v_e may then be partly updated). */
-int ep_bidomain_stats(ep_job *job, int64_t *last_iters, int64_t *total_iters, int64_t *solves, double *last_res,
-                      double *last_bnorm, int32_t *failed);
+/* Solver counters of a bidomain job. */
+typedef struct {
+    int64_t last_iters;    /* Arnoldi steps (products with L_ie) of the last solve */
+    int64_t total_iters;   /* ... of all solves */
+    int64_t solves;
+    double last_res;       /* ||b - L_ie v_e|| at the end of the last solve */
+    double last_bnorm;     /* ||b|| of the last solve */
+    double alg_bytes;      /* algorithmic device bytes of all solves: each array a phase of
+                              the solve touches, counted once per phase */
+    double phase_ms[5];    /* device time of all solves by phase: node values, fluxes (with
+                              the first Gram-Schmidt dots), second and third Gram-Schmidt
+                              passes, updates of v_e and the gauge */
+    int32_t failed;        /* some solve stopped at max_iter unconverged */
+    int32_t pad;
+} ep_bidomain_stats_t;
+
+/* Fill *out. Synchronises. Returns EP_ETIMEOUT if a grid barrier of the
+ * solve kernel gave up waiting (2 s limit; v_e may then be partly updated). */
+int ep_bidomain_stats(ep_job *job, ep_bidomain_stats_t *out);
 
 /* Number of state variables of a model and the name of each
  * (e.g. "V", "Ca_i", "Na_i", "m"). */

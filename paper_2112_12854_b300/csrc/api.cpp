@@ -55,8 +55,9 @@ struct Plan {
 struct BidoHost {
     std::vector<double> De_l, De_t;   // extracellular diffusivities per parameter set
     double tol = 1e-6, atol = 0.0;
-    int restart = 20;
-    int64_t max_iter = 1000;
+    int restart = 12;
+    int reorth = 0;
+    int64_t max_iter = 2000;
     std::vector<DevBuf> bufs;
     BidoArgs args{};
     int grid = 1;
@@ -696,10 +697,10 @@ int bido_apply(ep_job *job) {
     if (!rc) rc = put_r(cf.wb, &a.wb);
     if (!rc) rc = put_r(cf.q, &a.q);
     if (!rc) rc = put_r(wv, &a.wvol);
-    if (!rc) rc = grab(N * r, &ve);
+    if (!rc) rc = grab(a.ld * r, &ve);
     if (!rc) rc = grab(N * r, &xd);
     if (!rc) rc = grab(N * r, &bb);
-    if (!rc) rc = grab(N * r, &w);
+    if (!rc) rc = grab(a.ld * r, &w);
     if (!rc) rc = grab(size_t(B.restart + 1) * a.ld * r, &basis);
     if (!rc) rc = grab(2 * size_t(kBidoMaxRestart + 1) * B.grid * sizeof(double), &part);
     if (!rc) rc = grab(sizeof(BidoStats), &st);
@@ -722,9 +723,13 @@ int bido_apply(ep_job *job) {
     a.max_iter = B.max_iter;
     a.restart = B.restart;
     a.mode = 0;
+    a.reorth = B.reorth;
     B.args = a;
     job->dj.xdiv = xd;
-    cudaError_t e = cudaMemsetAsync(ve, 0, N * r, ctx->upload);
+    // v_e = 0; the vector pads past n_cells must stay zero for the basis passes
+    cudaError_t e = cudaMemsetAsync(ve, 0, a.ld * r, ctx->upload);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w, 0, a.ld * r, ctx->upload);
+    if (e == cudaSuccess) e = cudaMemsetAsync(basis, 0, size_t(B.restart + 1) * a.ld * r, ctx->upload);
     if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(BidoStats), ctx->upload);
     if (e == cudaSuccess) e = cudaMemsetAsync(sy, 0, sizeof(BidoSync), ctx->upload);
     if (e == cudaSuccess)
@@ -1511,15 +1516,23 @@ int ep_graph_info(const ep_job *job, int64_t *n_nodes, int32_t *substeps, int64_
     return EP_OK;
 }
 
-int ep_bidomain_enable(ep_job *job, const double *De_l, const double *De_t, int32_t n_sets, double tol, double atol,
-                       int32_t restart, int64_t max_iter) {
+int ep_bidomain_enable(ep_job *job, const double *De_l, const double *De_t, int32_t n_sets,
+                       const ep_bidomain_solver *solver) {
     if (!job) return EP_EINVAL;
     ep_context *ctx = job->ctx;
     if (!job->has_params) return fail(ctx, EP_ESTATE, "ep_bidomain_enable: job has no parameters");
     if (!De_l || !De_t || n_sets != job->params.n_sets)
         return fail(ctx, EP_EINVAL, "ep_bidomain_enable: need one extracellular (D_l, D_t) per parameter set");
-    if (!(tol > 0.0) || !(atol >= 0.0) || restart < 1 || restart > kBidoMaxRestart || max_iter < 1)
-        return fail(ctx, EP_EINVAL, "ep_bidomain_enable: tol > 0, atol >= 0, restart 1..30, max_iter >= 1");
+    ep_bidomain_solver sv;
+    if (solver) {
+        sv = *solver;
+    } else {
+        const bool plain = job->precision == EP_FP64_PLAIN;
+        sv = ep_bidomain_solver{plain ? 1e-11 : 1e-5, plain ? 0.0 : 1e-3, 12, 0, 2000};
+    }
+    if (!(sv.tol > 0.0) || !(sv.atol >= 0.0) || sv.restart < 1 || sv.restart > kBidoMaxRestart || sv.max_iter < 1 ||
+        (sv.reorth != 0 && sv.reorth != 1))
+        return fail(ctx, EP_EINVAL, "ep_bidomain_enable: tol > 0, atol >= 0, restart 1..30, reorth 0/1, max_iter >= 1");
     for (int k = 0; k < n_sets; ++k)
         if (!(De_l[k] >= 0.0) || !(De_t[k] >= 0.0))
             return fail(ctx, EP_EINVAL, "ep_bidomain_enable: negative extracellular diffusivity");
@@ -1529,10 +1542,11 @@ int ep_bidomain_enable(ep_job *job, const double *De_l, const double *De_t, int3
         BidoHost &B = *job->bido;
         B.De_l.assign(De_l, De_l + n_sets);
         B.De_t.assign(De_t, De_t + n_sets);
-        B.tol = tol;
-        B.atol = atol;
-        B.restart = restart;
-        B.max_iter = max_iter;
+        B.tol = sv.tol;
+        B.atol = sv.atol;
+        B.restart = sv.restart;
+        B.reorth = sv.reorth;
+        B.max_iter = sv.max_iter;
         int rc = bido_apply(job);
         if (rc) bido_drop(job);
         return rc;
@@ -1590,9 +1604,8 @@ int ep_bidomain_write_ve(ep_job *job, const double *host_in, int64_t n) {
     }
 }
 
-int ep_bidomain_stats(ep_job *job, int64_t *last_iters, int64_t *total_iters, int64_t *solves, double *last_res,
-                      double *last_bnorm, int32_t *failed) {
-    if (!job) return EP_EINVAL;
+int ep_bidomain_stats(ep_job *job, ep_bidomain_stats_t *out) {
+    if (!job || !out) return EP_EINVAL;
     ep_context *ctx = job->ctx;
     if (!job->bido) return fail(ctx, EP_ESTATE, "job is not bidomain (ep_bidomain_enable)");
     DeviceGuard g(ctx->device);
@@ -1602,12 +1615,15 @@ int ep_bidomain_stats(ep_job *job, int64_t *last_iters, int64_t *total_iters, in
     if (e == cudaSuccess) e = cudaMemcpy(&st, job->bido->args.stats, sizeof(st), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(&sy, job->bido->args.sync, sizeof(sy), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_bidomain_stats");
-    if (last_iters) *last_iters = st.last_iters;
-    if (total_iters) *total_iters = st.total_iters;
-    if (solves) *solves = st.solves;
-    if (last_res) *last_res = st.last_res;
-    if (last_bnorm) *last_bnorm = st.last_bnorm;
-    if (failed) *failed = st.failed;
+    *out = ep_bidomain_stats_t{};
+    out->last_iters = st.last_iters;
+    out->total_iters = st.total_iters;
+    out->solves = st.solves;
+    out->last_res = st.last_res;
+    out->last_bnorm = st.last_bnorm;
+    out->alg_bytes = st.alg_bytes;
+    for (int k = 0; k < 5; ++k) out->phase_ms[k] = st.phase_ms[k];
+    out->failed = st.failed;
     if (sy.err) return fail(ctx, EP_ETIMEOUT, "bidomain solve: a grid barrier wait hit its time limit");
     return EP_OK;
 }

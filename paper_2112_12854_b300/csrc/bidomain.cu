@@ -5,14 +5,15 @@
 // no host round trip decides the iteration count.
 //
 // GMRES (Sec. 3.2; textbook restarted GMRES): Arnoldi with classical
-// Gram-Schmidt applied twice (CGS2; the two passes cost two streaming reads
-// of the basis instead of the j dependent reductions of modified
-// Gram-Schmidt), Givens rotations on the Hessenberg column, restart after
-// `restart` steps from the true residual. The basis is stored unnormalised
-// with a scale per vector, so normalisation needs no extra pass. Dot
-// products are summed per thread in the compute type, per block and across
-// blocks in FP64, in a fixed order: the result depends only on the job and
-// the device, not on the batch.
+// Gram-Schmidt, once (CGS) or twice (CGS2) -- one or two streaming passes
+// over the basis and one reduction each, instead of the j dependent
+// reductions of modified Gram-Schmidt -- Givens rotations on the Hessenberg
+// column, and a restart after `restart` steps from the true residual, which
+// also decides convergence. The basis is stored unnormalised with a scale
+// per vector, so normalisation needs no extra pass, and is streamed in
+// 16-byte vectors. Dot products are summed per thread in the compute type,
+// per block and across blocks in FP64, in a fixed order: the result depends
+// only on the job and the device, not on the batch.
 #include <algorithm>
 #include <cmath>
 
@@ -25,6 +26,11 @@ namespace {
 template <class R> struct V4;
 template <> struct V4<float> { using type = float4; };
 template <> struct V4<double> { using type = double4_32a; };
+
+// 16-byte vectors for the streaming passes over the Krylov basis.
+template <class R> struct VW;
+template <> struct VW<float> { using type = float4; static constexpr int n = 4; };
+template <> struct VW<double> { using type = double2; static constexpr int n = 2; };
 
 constexpr int kWarps = kBidoThreads / 32;
 constexpr int KP = kBidoMaxRestart + 1;
@@ -138,8 +144,14 @@ __device__ __forceinline__ R flux(const DevJob &J, const void *wa_, const void *
 
 }  // namespace
 
+// Resident blocks per SM the register budget is cut for: three for FP32
+// (80 registers, 24 warps per SM to keep the gathers of the flux passes in
+// flight), one for FP64.
+template <class R> struct BidoMinBlocks { static constexpr int value = 1; };
+template <> struct BidoMinBlocks<float> { static constexpr int value = 3; };
+
 template <class R>
-__global__ void __launch_bounds__(kBidoThreads) bido_kernel(BidoArgs A) {
+__global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_kernel(BidoArgs A) {
     __shared__ double red_sh[kWarps * KP];
     __shared__ double tot[KP];
     __shared__ double H[KP * kBidoMaxRestart];   // H[i * kBidoMaxRestart + j]
@@ -160,6 +172,12 @@ __global__ void __launch_bounds__(kBidoThreads) bido_kernel(BidoArgs A) {
     R *__restrict__ wv = static_cast<R *>(A.w);
     R *__restrict__ basis = static_cast<R *>(A.basis);
     const long long ld = A.ld;
+    // vector views (ld is a multiple of 64; the pads past n_cells stay zero)
+    using VT = typename VW<R>::type;
+    constexpr int NW = VW<R>::n;
+    const long long lq = ld / NW;
+    const VT *__restrict__ bq = reinterpret_cast<const VT *>(basis);
+    VT *__restrict__ wq = reinterpret_cast<VT *>(wv);
     const int m = A.restart;
     R acc[KP];
     // Two partial-sum buffers used in turn: a block may write the next
@@ -167,18 +185,37 @@ __global__ void __launch_bounds__(kBidoThreads) bido_kernel(BidoArgs A) {
     // never before every block has passed the barrier that follows.
     int red = 0;
     auto part_w = [&]() { return A.part + size_t(red & 1) * KP * gridDim.x; };
-#define BIDO_SYNC()                              \
-    do {                                         \
-        if (!grid_sync(A.sync, &flag_sh)) return; \
+    // device time between barriers, by phase (block 0's clock): 0 node values,
+    // 1 fluxes (+ first dots), 2 second Gram-Schmidt pass, 3 third pass,
+    // 4 updates of x and the gauge
+    __shared__ unsigned long long ph_sh[5], t_last_sh;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int k = 0; k < 5; ++k) ph_sh[k] = 0ull;
+        t_last_sh = global_ns();
+    }
+#define BIDO_SYNC(ph)                                          \
+    do {                                                       \
+        if (!grid_sync(A.sync, &flag_sh)) return;              \
+        if (blockIdx.x == 0 && threadIdx.x == 0) {             \
+            const unsigned long long t_ = global_ns();         \
+            ph_sh[ph] += t_ - t_last_sh;                       \
+            t_last_sh = t_;                                    \
+        }                                                      \
     } while (0)
 
     long long iters = 0;
     int failed = 0;
     double res = 0.0, bnorm = 0.0;
+    // algorithmic bytes of each phase: every array it touches counted once
+    // (the node table as stored, coefficients, indices, fields, basis vectors)
+    const double RB = double(sizeof(R)), dn = double(n), dnn = double(J.n_nodes);
+    const double node_b = double(J.slice_ptr[(J.n_nodes + 31) >> 5]) * (4.0 + RB) + dn * RB + dnn * RB;
+    const double flux_b = dn * (48.0 + 12.0 * RB) + dnn * RB + 2.0 * dn * RB;
+    double bytes = 0.0;
     if (A.mode == 0) {
         // right-hand side b = -L_i(V^{n+1}) and its norm
         node_pass<R>(J, V, R(1), vn, gtid, gsz);
-        BIDO_SYNC();
+        BIDO_SYNC(0);
         acc[0] = R(0);
         for (long long c = gtid; c < n; c += gsz) {
             const R bc = -flux<R>(J, J.wa, J.wb, J.q, vn, V, R(1), c);
@@ -186,15 +223,16 @@ __global__ void __launch_bounds__(kBidoThreads) bido_kernel(BidoArgs A) {
             acc[0] += bc * bc;
         }
         block_partials<R>(acc, 1, part_w(), red_sh);
-        BIDO_SYNC();
+        BIDO_SYNC(1);
         grid_totals(part_w(), 1, tot);
         ++red;
         bnorm = sqrt(tot[0]);
+        bytes += node_b + flux_b;
         const double thr = fmax(A.tol * bnorm, A.atol * sqrt(double(n)));
         for (;;) {
             // true residual r = b - L_ie x into basis vector 0
             node_pass<R>(J, x, R(1), vn, gtid, gsz);
-            BIDO_SYNC();
+            BIDO_SYNC(0);
             acc[0] = R(0);
             for (long long c = gtid; c < n; c += gsz) {
                 const R r = b[c] - flux<R>(J, A.wa, A.wb, A.q, vn, x, R(1), c);
@@ -202,11 +240,12 @@ __global__ void __launch_bounds__(kBidoThreads) bido_kernel(BidoArgs A) {
                 acc[0] += r * r;
             }
             block_partials<R>(acc, 1, part_w(), red_sh);
-            BIDO_SYNC();
+            BIDO_SYNC(1);
             grid_totals(part_w(), 1, tot);
             ++red;
             const double beta = sqrt(tot[0]);
             res = beta;
+            bytes += node_b + flux_b + dn * RB;
             if (beta <= thr) break;
             if (iters >= A.max_iter) {
                 failed = 1;
@@ -224,7 +263,7 @@ __global__ void __launch_bounds__(kBidoThreads) bido_kernel(BidoArgs A) {
                 const R sj = R(sc[j]);
                 // w = L_ie v_j, and the first Gram-Schmidt dots <v_i, w>
                 node_pass<R>(J, vj, sj, vn, gtid, gsz);
-                BIDO_SYNC();
+                BIDO_SYNC(0);
 #pragma unroll
                 for (int i = 0; i < KP; ++i) acc[i] = R(0);
                 for (long long c = gtid; c < n; c += gsz) {
@@ -235,7 +274,7 @@ __global__ void __launch_bounds__(kBidoThreads) bido_kernel(BidoArgs A) {
                         if (i <= j) acc[i] += basis[i * ld + c] * w;
                 }
                 block_partials<R>(acc, j + 1, part_w(), red_sh);
-                BIDO_SYNC();
+                BIDO_SYNC(1);
                 grid_totals(part_w(), j + 1, tot);
                 ++red;
                 if (threadIdx.x <= j) {
@@ -244,45 +283,71 @@ __global__ void __launch_bounds__(kBidoThreads) bido_kernel(BidoArgs A) {
                     coef[threadIdx.x] = R(h * sc[threadIdx.x]);
                 }
                 __syncthreads();
-                // second pass: w' = w - V h, and the re-orthogonalisation dots
+                if (A.reorth) {
+                    // second pass: w' = w - V h, and the re-orthogonalisation dots
 #pragma unroll
-                for (int i = 0; i < KP; ++i) acc[i] = R(0);
-                for (long long c = gtid; c < n; c += gsz) {
-                    R w = wv[c];
+                    for (int i = 0; i < KP; ++i) acc[i] = R(0);
+                    for (long long qi = gtid; qi < lq; qi += gsz) {
+                        VT w = wq[qi];
+                        R *wp = reinterpret_cast<R *>(&w);
 #pragma unroll
-                    for (int i = 0; i < KP; ++i)
-                        if (i <= j) w -= coef[i] * basis[i * ld + c];
-                    wv[c] = w;
+                        for (int i = 0; i < KP; ++i)
+                            if (i <= j) {
+                                const VT b4 = bq[i * lq + qi];
+                                const R *bp = reinterpret_cast<const R *>(&b4);
+                                const R ci = coef[i];
 #pragma unroll
-                    for (int i = 0; i < KP; ++i)
-                        if (i <= j) acc[i] += basis[i * ld + c] * w;
+                                for (int k = 0; k < NW; ++k) wp[k] -= ci * bp[k];
+                            }
+                        wq[qi] = w;
+#pragma unroll
+                        for (int i = 0; i < KP; ++i)
+                            if (i <= j) {
+                                const VT b4 = bq[i * lq + qi];
+                                const R *bp = reinterpret_cast<const R *>(&b4);
+                                R d = R(0);
+#pragma unroll
+                                for (int k = 0; k < NW; ++k) d += bp[k] * wp[k];
+                                acc[i] += d;
+                            }
+                    }
+                    block_partials<R>(acc, j + 1, part_w(), red_sh);
+                    BIDO_SYNC(2);
+                    grid_totals(part_w(), j + 1, tot);
+                    ++red;
+                    if (threadIdx.x <= j) {
+                        const double h2 = tot[threadIdx.x] * sc[threadIdx.x];
+                        H[threadIdx.x * kBidoMaxRestart + j] += h2;
+                        coef[threadIdx.x] = R(h2 * sc[threadIdx.x]);
+                    }
+                    __syncthreads();
                 }
-                block_partials<R>(acc, j + 1, part_w(), red_sh);
-                BIDO_SYNC();
-                grid_totals(part_w(), j + 1, tot);
-                ++red;
-                if (threadIdx.x <= j) {
-                    const double h2 = tot[threadIdx.x] * sc[threadIdx.x];
-                    H[threadIdx.x * kBidoMaxRestart + j] += h2;
-                    coef[threadIdx.x] = R(h2 * sc[threadIdx.x]);
-                }
-                __syncthreads();
-                // third pass: v_{j+1} (unnormalised) = w' - V h2, and its norm
-                R *__restrict__ vnext = basis + (j + 1) * ld;
+                // last pass: v_{j+1} (unnormalised) = w - V (coefficients of the last
+                // projection), and its norm
+                VT *__restrict__ vq = reinterpret_cast<VT *>(basis + (j + 1) * ld);
                 acc[0] = R(0);
-                for (long long c = gtid; c < n; c += gsz) {
-                    R w = wv[c];
+                for (long long qi = gtid; qi < lq; qi += gsz) {
+                    VT w = wq[qi];
+                    R *wp = reinterpret_cast<R *>(&w);
 #pragma unroll
                     for (int i = 0; i < KP; ++i)
-                        if (i <= j) w -= coef[i] * basis[i * ld + c];
-                    vnext[c] = w;
-                    acc[0] += w * w;
+                        if (i <= j) {
+                            const VT b4 = bq[i * lq + qi];
+                            const R *bp = reinterpret_cast<const R *>(&b4);
+                            const R ci = coef[i];
+#pragma unroll
+                            for (int k = 0; k < NW; ++k) wp[k] -= ci * bp[k];
+                        }
+                    vq[qi] = w;
+#pragma unroll
+                    for (int k = 0; k < NW; ++k) acc[0] += wp[k] * wp[k];
                 }
                 block_partials<R>(acc, 1, part_w(), red_sh);
-                BIDO_SYNC();
+                BIDO_SYNC(3);
                 grid_totals(part_w(), 1, tot);
                 ++red;
                 const double hn = sqrt(tot[0]);
+                bytes += node_b + flux_b + (A.reorth ? double(3 * (j + 1) + 4) : double(2 * (j + 1) + 2)) * dn * RB;
                 if (threadIdx.x == 0) {
                     sc[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
                     double *Hc = H + j;   // column j, row stride kBidoMaxRestart
@@ -315,30 +380,40 @@ __global__ void __launch_bounds__(kBidoThreads) bido_kernel(BidoArgs A) {
                 for (int i = 0; i < j; ++i) coef[i] = R(y[i] * sc[i]);
             }
             __syncthreads();
-            for (long long c = gtid; c < n; c += gsz) {
-                R xc = x[c];
+            bytes += double(2 + j) * dn * RB;
+            VT *__restrict__ xq = reinterpret_cast<VT *>(x);
+            for (long long qi = gtid; qi < lq; qi += gsz) {
+                VT xv = xq[qi];
+                R *xp = reinterpret_cast<R *>(&xv);
 #pragma unroll
                 for (int i = 0; i < KP; ++i)
-                    if (i < j) xc += coef[i] * basis[i * ld + c];
-                x[c] = xc;
+                    if (i < j) {
+                        const VT b4 = bq[i * lq + qi];
+                        const R *bp = reinterpret_cast<const R *>(&b4);
+                        const R ci = coef[i];
+#pragma unroll
+                        for (int k = 0; k < NW; ++k) xp[k] += ci * bp[k];
+                    }
+                xq[qi] = xv;
             }
-            BIDO_SYNC();
+            BIDO_SYNC(4);
         }
         // gauge: zero volume-weighted mean
         const R *__restrict__ wvol = static_cast<const R *>(A.wvol);
         acc[0] = R(0);
         for (long long c = gtid; c < n; c += gsz) acc[0] += wvol[c] * x[c];
         block_partials<R>(acc, 1, part_w(), red_sh);
-        BIDO_SYNC();
+        BIDO_SYNC(4);
         grid_totals(part_w(), 1, tot);
         ++red;
         const R mean = R(tot[0]);
+        bytes += 4.0 * dn * RB;
         for (long long c = gtid; c < n; c += gsz) x[c] -= mean;
-        BIDO_SYNC();
+        BIDO_SYNC(4);
     }
     // intracellular flux of v_e for the next step's V update
     node_pass<R>(J, x, R(1), vn, gtid, gsz);
-    BIDO_SYNC();
+    BIDO_SYNC(0);
     R *__restrict__ xd = static_cast<R *>(A.xdiv);
     for (long long c = gtid; c < n; c += gsz) xd[c] = flux<R>(J, J.wa, J.wb, J.q, vn, x, R(1), c);
     if (A.mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -349,6 +424,9 @@ __global__ void __launch_bounds__(kBidoThreads) bido_kernel(BidoArgs A) {
         st->last_res = res;
         st->last_bnorm = bnorm;
         st->failed |= failed;
+        st->alg_bytes += bytes + node_b + flux_b;
+        ph_sh[1] += global_ns() - t_last_sh;
+        for (int k = 0; k < 5; ++k) st->phase_ms[k] += 1e-6 * double(ph_sh[k]);
     }
 #undef BIDO_SYNC
 }
@@ -376,7 +454,7 @@ int grid_of(int sm_count) {
         cudaGetLastError();
         nb = 1;
     }
-    return sm_count * std::max(1, std::min(nb, 2));
+    return sm_count * std::max(1, std::min(nb, 4));
 }
 
 }  // namespace

@@ -23,6 +23,8 @@ struct BidoStats {
     long long solves;
     double last_res;         // ||b - L_ie x|| at the end of the last solve
     double last_bnorm;       // ||b|| of the last solve
+    double alg_bytes;        // algorithmic bytes of all solves (every array a phase touches, once)
+    double phase_ms[5];      // device time by phase: node values, fluxes, GS pass 2, GS pass 3, updates
     int failed;              // some solve stopped at max_iter without converging
     int timeout;             // a grid barrier gave up (error flag)
 };
@@ -39,8 +41,9 @@ struct BidoArgs {
     const DevJob *job;           // device job: topology, L_i coefficients, V, node scratch, step
     const void *wa, *wb, *q;     // L_ie coefficients (layout of DevJob::wa/wb/q)
     const void *wvol;            // V_c / sum V (gauge weights)
-    void *ve, *xdiv, *b, *w;     // [n_cells] each
-    void *basis;                 // [(restart + 1) * ld]
+    void *ve, *w;                // [ld] each, zero past n_cells
+    void *xdiv, *b;              // [n_cells] each
+    void *basis;                 // [(restart + 1) * ld], zero past n_cells
     long long ld;
     double *part;                // [(kBidoMaxRestart + 1) * grid] block partials
     BidoStats *stats;
@@ -49,6 +52,8 @@ struct BidoArgs {
     long long max_iter;          // Arnoldi steps per solve
     int restart;
     int mode;                    // 0: solve, then L_i(v_e); 1: only L_i(v_e) from the current v_e
+    int reorth;                  // 1: Gram-Schmidt twice (CGS2); 0: once (CGS)
+    int pad;
 };
 
 // Grid of the cooperative solve kernel for a job of n_cells: co-resident on

@@ -52,6 +52,17 @@ class Params(ctypes.Structure):
                 ("stim", Stimulus * MAX_STIM), ("threshold", ctypes.c_double)]
 
 
+class BidoSolver(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("atol", ctypes.c_double), ("restart", ctypes.c_int32),
+                ("reorth", ctypes.c_int32), ("max_iter", ctypes.c_int64)]
+
+
+class BidoStats(ctypes.Structure):
+    _fields_ = [("last_iters", ctypes.c_int64), ("total_iters", ctypes.c_int64), ("solves", ctypes.c_int64),
+                ("last_res", ctypes.c_double), ("last_bnorm", ctypes.c_double), ("alg_bytes", ctypes.c_double),
+                ("phase_ms", ctypes.c_double * 5), ("failed", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
 class GraphDesc(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("xyz", ctypes.c_void_p), ("n_edges", ctypes.c_int64),
                 ("edges", ctypes.c_void_p), ("edge_D", ctypes.c_void_p), ("node_model", ctypes.c_void_p),
@@ -133,13 +144,11 @@ def load():
         "ep_autotune": ([ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32, _P, _P], ctypes.c_int),
         "ep_set_cell_variant": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
         "ep_alu_peaks": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
-        "ep_bidomain_enable": ([_P, _P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32, _I64],
-                               ctypes.c_int),
+        "ep_bidomain_enable": ([_P, _P, _P, ctypes.c_int32, ctypes.POINTER(BidoSolver)], ctypes.c_int),
         "ep_bidomain_disable": ([_P], ctypes.c_int),
         "ep_bidomain_read_ve": ([_P, _P, _I64], ctypes.c_int),
         "ep_bidomain_write_ve": ([_P, _P, _I64], ctypes.c_int),
-        "ep_bidomain_stats": ([_P] + [ctypes.POINTER(_I64)] * 3 + [ctypes.POINTER(ctypes.c_double)] * 2
-                              + [ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "ep_bidomain_stats": ([_P, ctypes.POINTER(BidoStats)], ctypes.c_int),
         "ep_time_kernels": ([ctypes.POINTER(_P), ctypes.c_int32, _I64, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "ep_plan_inspect": ([ctypes.POINTER(MeshDesc), ctypes.POINTER(Params)] + [_P] * 10
@@ -425,24 +434,25 @@ class Job:
         self.ctx.check(load().ep_graph_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return dict(n_nodes=a.value, substeps=b.value, n_junctions=c.value)
 
-    def enable_bidomain(self, De_l, De_t, *, tol=None, atol=None, restart=20, max_iter=2000, n_sets=None):
+    def enable_bidomain(self, De_l, De_t, *, tol=None, atol=None, restart=12, reorth=0, max_iter=2000,
+                        n_sets=None):
         """Bidomain model (ep_bidomain_enable): De_l, De_t are the
         extracellular diffusivities, scalars or one per parameter set; the
-        parameter sets' own (D_l, D_t) become the intracellular ones. Default
-        stopping rule: tol 1e-5, atol 1e-3 mV/ms (FP32 mixed: about the
-        rounding floor of an FP32 residual); tol 1e-11, atol 0 (FP64 plain)."""
+        parameter sets' own (D_l, D_t) become the intracellular ones. tol /
+        atol None take the library's defaults for the job's precision."""
         params = getattr(self, "params", None)
         if n_sets is None:
             n_sets = params.n_sets if params is not None else np.size(De_l)
-        plain = params is not None and params.precision == EP_FP64_PLAIN
-        if tol is None:
-            tol = 1e-11 if plain else 1e-5
-        if atol is None:
-            atol = 0.0 if plain else 1e-3
         el = np.ascontiguousarray(np.broadcast_to(np.asarray(De_l, np.float64), (n_sets,)))
         et = np.ascontiguousarray(np.broadcast_to(np.asarray(De_t, np.float64), (n_sets,)))
-        self.ctx.check(load().ep_bidomain_enable(self._h, _ptr(el), _ptr(et), int(n_sets), float(tol), float(atol),
-                                                 int(restart), int(max_iter)))
+        sv = None
+        if tol is not None or atol is not None or restart != 12 or reorth != 0 or max_iter != 2000:
+            plain = params is not None and params.precision == EP_FP64_PLAIN
+            sv = BidoSolver(float(tol if tol is not None else (1e-11 if plain else 1e-5)),
+                            float(atol if atol is not None else (0.0 if plain else 1e-3)),
+                            int(restart), int(reorth), int(max_iter))
+        self.ctx.check(load().ep_bidomain_enable(self._h, _ptr(el), _ptr(et), int(n_sets),
+                                                 ctypes.byref(sv) if sv is not None else None))
 
     def disable_bidomain(self):
         self.ctx.check(load().ep_bidomain_disable(self._h))
@@ -460,13 +470,11 @@ class Job:
         self.ctx.check(load().ep_bidomain_write_ve(self._h, _ptr(v), self.n_cells))
 
     def bidomain_stats(self) -> dict:
-        a, b, c = _I64(), _I64(), _I64()
-        r, bn = ctypes.c_double(), ctypes.c_double()
-        f = ctypes.c_int32()
-        self.ctx.check(load().ep_bidomain_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
-                                                ctypes.byref(r), ctypes.byref(bn), ctypes.byref(f)))
-        return {"last_iters": a.value, "total_iters": b.value, "solves": c.value, "last_res": r.value,
-                "last_bnorm": bn.value, "failed": bool(f.value)}
+        st = BidoStats()
+        self.ctx.check(load().ep_bidomain_stats(self._h, ctypes.byref(st)))
+        return {"last_iters": st.last_iters, "total_iters": st.total_iters, "solves": st.solves,
+                "last_res": st.last_res, "last_bnorm": st.last_bnorm, "alg_bytes": st.alg_bytes,
+                "phase_ms": list(st.phase_ms), "failed": bool(st.failed)}
 
     def destroy(self):
         if getattr(self, "_h", None):

@@ -43,11 +43,12 @@ def _slab(cubes=(12, 8, 3), h=0.25, D=(DIL, DIT), models=(0,), fibre_rot=True):
                         sets, [w.Stimulus(-80.0, 0.0, 1.0)], 0.02, 0, -20.0)
 
 
-@pytest.mark.parametrize("pname", ["mixed", "plain"])
-def test_bidomain_parity(ctx, pname):
+@pytest.mark.parametrize("pname,reorth", [("mixed", 0), ("plain", 0), ("mixed", 1)])
+def test_bidomain_parity(ctx, pname, reorth):
     """Mixed TP06 / Courtemanche / Stewart slab with rotating fibres and
     unequal anisotropy ratios; V, v_e and activation times against the
-    oracle at three output times (1728 cells: several tiles, ragged tail)."""
+    oracle at three output times (1728 cells: several tiles, ragged tail),
+    with Gram-Schmidt once (default) and twice."""
     import oracle
     from paper_2112_12854_b300 import ep
     prec = _prec(pname)
@@ -56,7 +57,7 @@ def test_bidomain_parity(ctx, pname):
     o = oracle.Sim(case)
     o.set_bidomain(DEL, DET, tol=1e-11)
     j = ep.job_from_case(ctx, case, precision=prec)
-    j.enable_bidomain(DEL, DET)
+    j.enable_bidomain(DEL, DET, reorth=reorth)
     assert np.abs(j.ve - o.ve).max() <= TOL_VE[pname]
     done = 0
     for n in (100, 250, 500):
