@@ -57,12 +57,17 @@ def wedge_case(dims):
     return w.wedge_case(nx=dims["nx"], ny=dims["ny"], nz=dims["nz"], h=dims["h"], n_steps=20000)
 
 
+# Sources the node and cell kernels are compiled from (the profiles under
+# profiles/ record the hash of these files at capture time).
+STEP_KERNEL_SOURCES = ("kernels.cu", "kernels.h", "devtypes.h", "cellmath.cuh", "ttcells.cuh", "crncell.cuh",
+                       "varmap.h")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2112_12854_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in STEP_KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
