@@ -186,3 +186,29 @@ def test_atrial_bundle_velocity_matches_table2(orc):
     assert np.all(np.isfinite(a[sel]))
     cv = np.polyfit(a[sel], x[sel], 1)[0]
     assert abs(cv - gd["velocity_mm_per_ms"]) < 0.1 * gd["velocity_mm_per_ms"]
+
+
+def test_branch_block_by_conductivity(orc):
+    """Bundle-branch block (Sec. 5): a segment of a Purkinje cable with its
+    conductivity scaled by f. Cable theory gives a speed proportional to
+    sqrt(f) inside the segment, so the transit time through it grows by about
+    1/sqrt(f) (the segment's ends load it, hence a band); f = 0 (null
+    conductivity) blocks conduction completely."""
+    ds, dt, n = 0.2, 0.01, 101
+    seg = (np.arange(n - 1) >= 40) & (np.arange(n - 1) < 70)      # edges of the 6 mm segment
+    transit = {}
+    for f in (1.0, 0.25, 0.0):
+        g = w.chain_graph(n, ds, param_set=1, stim_nodes=10, params=w.GraphParams(D=2.82))
+        g.edge_D = np.where(seg, 2.82 * f, 2.82)
+        s = orc.Sim(_tet_case(dt))
+        s.attach_graph(g)
+        s.run(int(round(25 / dt)))
+        a = s.graph_activation_times()
+        assert np.all(np.isfinite(a[:41]))
+        if f == 0.0:
+            assert not np.any(np.isfinite(a[71:]))               # nothing beyond the block
+        else:
+            assert np.all(np.isfinite(a))
+            transit[f] = a[70] - a[40]
+    ratio = transit[0.25] / transit[1.0]
+    assert 1.6 < ratio < 2.6, ratio

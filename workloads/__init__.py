@@ -17,7 +17,7 @@ from __future__ import annotations
 
 import itertools
 import math
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 
 import numpy as np
 
@@ -522,6 +522,8 @@ def whole_heart(h: float = 0.4, *, scale: float = 1.0, n_tree: int = 50_000, n_p
     lv_ax = tuple(a + 0.6 for a in _LV_IN)
     rv_ax = tuple(a + 0.6 for a in _RV_IN)
     # each branch starts on its chamber's septal endocardium below the base and grows downwards
+    n_edges_before = sum(len(e) for e in edges)
+    branch_edges = []
     for c, ax, share, sdir in (((0.0, 0.0, 0.0), lv_ax, 0.55, (-1.0, 0.0, 0.35)),
                                (_RV_C, rv_ax, 0.45, (1.0, 0.0, 0.35))):
         start = np.asarray(c) + 10.0 * np.asarray(sdir)
@@ -531,6 +533,8 @@ def whole_heart(h: float = 0.4, *, scale: float = 1.0, n_tree: int = 50_000, n_p
         edges.append(np.array([[his_idx, node_off]]))
         edge_D += [np.full(len(tedges), D_purk), np.array([D_purk])]
         tree_nodes.append((node_off, len(txyz), tedges))
+        branch_edges.append(np.arange(n_edges_before, n_edges_before + len(tedges) + 1))
+        n_edges_before += len(tedges) + 1
         node_off += len(txyz)
     gxyz = np.concatenate(xyz) * scale
     gedges = np.concatenate(edges).astype(np.int32)
@@ -561,4 +565,74 @@ def whole_heart(h: float = 0.4, *, scale: float = 1.0, n_tree: int = 50_000, n_p
     case.stimuli[0] = Stimulus(-100.0, 0.0, 2.5)
     graph = Graph(gxyz, gedges, pset, smask, jn, jc, jm, gp, edge_D=gD)
     graph.n_bundle, graph.his = n_bundle, his_idx
+    # edge and node sets of the parts, for pathology scenarios (heart_scenario)
+    graph.av_edges = np.arange(len(ra_path) - 1 + len(eb), len(ra_path) - 1 + len(eb) + len(ea))
+    graph.lv_edges, graph.rv_edges = branch_edges
+    graph.lv_nodes = np.arange(tree_nodes[0][0], tree_nodes[0][0] + tree_nodes[0][1])
+    graph.rv_nodes = np.arange(tree_nodes[1][0], tree_nodes[1][0] + tree_nodes[1][1])
+    graph.scale = scale
     return case, graph
+
+
+def heart_lead_site(case: TissueCase, graph: Graph, site: str) -> np.ndarray:
+    """Lead sites of Sec. 5 on the synthetic heart (case coordinates): the
+    right-ventricular apex ("rv_apex": the lowest right-ventricular cell) or
+    the right-atrial appendage ("ra_appendage": the most lateral right-atrial
+    cell)."""
+    cen = tet_centroids(case.xyz, case.tets)
+    lab, _ = heart_regions(cen / graph.scale)
+    if site == "rv_apex":
+        k = np.flatnonzero(lab == 2)
+        return cen[k[np.argmin(cen[k, 2])]]
+    if site == "ra_appendage":
+        k = np.flatnonzero(lab == 4)
+        return cen[k[np.argmin(cen[k, 0])]]
+    raise ValueError(site)
+
+
+def heart_scenario(case: TissueCase, graph: Graph, *, block: str | None = None, severity: float = 1.0,
+                   av_block: bool = False, sinus: bool = True, lead=None, lead_radius: float = 2.0,
+                   lead_onset: float = 0.0, lead_period: float = 0.0, lead_amp: float = -100.0,
+                   lead_dur: float = 2.0, two_way: bool | None = None, cn_amplitude: float | None = None,
+                   cn_duration: float | None = None):
+    """Pathology and pacing variants of a whole-heart case (Sec. 5), as inputs only:
+    - block "left" / "right": bundle-branch block, the branch's conductivity
+      scaled by (1 - severity) (severity 1: null conductivity, complete block);
+    - av_block: null conductivity along the AV delay line;
+    - sinus False: no sinus-node stimulus;
+    - two_way: the communication nodes also let the myocardium excite the
+      graph (Sec. 3.3: pathological cases), else as built; cn_amplitude /
+      cn_duration replace the communication-node stimulus (a single 1D node
+      is tightly coupled to its cable neighbours, so exciting it takes a
+      larger current than exciting a patch of myocardium);
+    - lead (a site name of heart_lead_site or a point): a pacing lead, a
+      stimulus protocol (lead_amp uA/uF for lead_dur ms from lead_onset,
+      every lead_period ms; 0 = once) on the myocardial cells within
+      lead_radius mm of the point.
+    Returns new (case, graph); the inputs are not modified."""
+    import copy
+    c2, g2 = copy.deepcopy(case), copy.deepcopy(graph)
+    D = np.array(g2.edge_D, dtype=np.float64)
+    if block is not None:
+        D[g2.lv_edges if block == "left" else g2.rv_edges] *= (1.0 - severity)
+    if av_block:
+        D[g2.av_edges] = 0.0
+    g2.edge_D = D
+    if two_way is not None:
+        g2.params = replace(g2.params, two_way=int(two_way))
+    if cn_amplitude is not None:
+        g2.params = replace(g2.params, amplitude=float(cn_amplitude))
+    if cn_duration is not None:
+        g2.params = replace(g2.params, duration=float(cn_duration))
+    if not sinus:   # protocol 0 drives the sinus node: the first bundle nodes and the RA sphere
+        g2.stim_mask = np.zeros_like(g2.stim_mask)
+        c2.stim_mask = c2.stim_mask & np.uint8(0xFE)
+    if lead is not None:
+        cen = tet_centroids(c2.xyz, c2.tets)
+        p = heart_lead_site(c2, g2, lead) if isinstance(lead, str) else np.asarray(lead, float)
+        d = np.linalg.norm(cen - p, axis=1)
+        sel = d <= lead_radius
+        k = len(c2.stimuli)
+        c2.stimuli = list(c2.stimuli) + [Stimulus(lead_amp, lead_onset, lead_dur, lead_period)]
+        c2.stim_mask = c2.stim_mask | (sel.astype(np.uint8) << k)
+    return c2, g2
