@@ -96,9 +96,11 @@ def lib():
         L.orc_model_varname.argtypes = [ctypes.c_int, ctypes.c_int]
         L.orc_model_init.argtypes = [ctypes.POINTER(CellParams), _P]
         L.orc_model_step.restype = ctypes.c_double
-        L.orc_model_step.argtypes = [_P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(CellParams)]
+        L.orc_model_step.argtypes = [_P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(CellParams), _P]
+        L.orc_sim_set_integrator.restype = ctypes.c_int
+        L.orc_sim_set_integrator.argtypes = [_P, ctypes.c_int]
         L.orc_cell_run.argtypes = [ctypes.POINTER(CellParams), ctypes.c_double, ctypes.c_int64,
-                                   ctypes.POINTER(Stim), ctypes.c_int64, _P, _P]
+                                   ctypes.POINTER(Stim), ctypes.c_int64, _P, _P, ctypes.c_int]
         L.orc_sim_create.restype = _P
         L.orc_sim_create.argtypes = [ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P, _P,
                                      ctypes.c_int, _P, ctypes.c_int, _P,
@@ -235,18 +237,19 @@ def model_step(state, dt, i_stim, params) -> float:
     """One RL/FE update of every variable but V; returns I_ion(V^n, s^n)."""
     assert state.dtype == np.float64 and state.size >= MAXVAR
     return float(lib().orc_model_step(_ptr(state), float(dt), float(i_stim),
-                                      ctypes.byref(_cellparams(params))))
+                                      ctypes.byref(_cellparams(params)), None))
 
 
-def cell_run(params, dt, n_steps, stim=None, record_every=1, state=None):
-    """Single-cell run; returns (V every record_every steps, final state)."""
+def cell_run(params, dt, n_steps, stim=None, record_every=1, state=None, integrator=0):
+    """Single-cell run; returns (V every record_every steps, final state).
+    integrator 1: AB2 for the non-gating variables."""
     st = model_init(params) if state is None else np.array(state, dtype=np.float64)
     nrec = n_steps // record_every if record_every > 0 else 0
     v = np.zeros(max(nrec, 1))
     sp = _stim(stim)
     lib().orc_cell_run(ctypes.byref(_cellparams(params)), float(dt), int(n_steps),
                        ctypes.byref(sp) if sp is not None else None, int(record_every),
-                       _ptr(v), _ptr(st))
+                       _ptr(v), _ptr(st), int(integrator))
     return v[:nrec], st
 
 
@@ -284,6 +287,11 @@ class Sim:
 
     def run(self, n_steps):
         lib().orc_sim_run(self._h, int(n_steps))
+
+    def set_integrator(self, integrator: int) -> None:
+        """0 forward Euler, 1 AB2 for the non-gating variables (from now on)."""
+        if lib().orc_sim_set_integrator(self._h, int(integrator)):
+            raise ValueError("unknown integrator")
 
     @property
     def step_index(self) -> int:

@@ -54,7 +54,7 @@ static double x_over_expm1(double x, double k) {
     return (y == 0.0) ? k : k * y / expm1(y);
 }
 
-double orc_crn_step(double *s, double dt, double i_stim, const orc_cellparams *p) {
+double orc_crn_step(double *s, double dt, double i_stim, const orc_cellparams *p, orc_ab2 *ab) {
     (void)i_stim;
     const double V = s[V_], Nai = s[NAI], Ki = s[KI], Cai = s[CAI];
     const double Caup = s[CAUP], Carel = s[CAREL];
@@ -169,11 +169,11 @@ double orc_crn_step(double *s, double dt, double i_stim, const orc_cellparams *p
         ns[W_] = rush_larsen(s[W_], 1.0 - 1.0 / (1.0 + exp(-(V - 40.0) / 17.0)), tau, dt);
     }
 
-    ns[NAI] = Nai + dt * dNai;
-    ns[KI] = Ki + dt * dKi;
-    ns[CAI] = Cai + dt * dCai;
-    ns[CAUP] = Caup + dt * dCaup;
-    ns[CAREL] = Carel + dt * dCarel;
+    ns[NAI] = Nai + dt * orc_rate(ab, 1, dNai);
+    ns[KI] = Ki + dt * orc_rate(ab, 2, dKi);
+    ns[CAI] = Cai + dt * orc_rate(ab, 3, dCai);
+    ns[CAUP] = Caup + dt * orc_rate(ab, 4, dCaup);
+    ns[CAREL] = Carel + dt * orc_rate(ab, 5, dCarel);
     for (int k = 1; k < NVAR; ++k) s[k] = ns[k];
     return Iion;
 }

@@ -69,11 +69,31 @@ void orc_conductivity(const double *fibre, double D_l, double D_t, double *D);
 int orc_model_nvar(int model);
 const char *orc_model_varname(int model, int var);
 void orc_model_init(const orc_cellparams *p, double *s);
-double orc_model_step(double *s, double dt, double i_stim, const orc_cellparams *p);
+/* Second-order Adams-Bashforth for the non-gating variables (Sec. 4: the
+ * alternative to forward Euler the paper tests). h holds ORC_NHIST rates of
+ * the previous step: slot 0 the V equation (tissue.c), 1..5 the model's
+ * non-gating variables; `on` is 0 on the first step after a (re)start,
+ * which is forward Euler and only records the rates. */
+#define ORC_NHIST 6
+typedef struct {
+    double *h;
+    int on;
+} orc_ab2;
+
+/* The rate a non-gating variable advances with over the step: f (forward
+ * Euler, ab NULL or off) or 3/2 f - 1/2 f_prev (AB2); slot k then holds f. */
+static inline double orc_rate(orc_ab2 *ab, int k, double f) {
+    if (!ab) return f;
+    const double g = ab->on ? 1.5 * f - 0.5 * ab->h[k] : f;
+    ab->h[k] = f;
+    return g;
+}
+
+double orc_model_step(double *s, double dt, double i_stim, const orc_cellparams *p, orc_ab2 *ab);
 /* single-cell run: V recorded every record_every steps (n_steps/record_every values) */
 void orc_cell_run(const orc_cellparams *p, double dt, int64_t n_steps,
                   const orc_stim *stim, int64_t record_every, double *v_out,
-                  double *state_inout);
+                  double *state_inout, int ab2);
 
 /* ---- tissue simulation (tissue.c) ---- */
 typedef struct orc_sim orc_sim;
@@ -91,6 +111,7 @@ void orc_sim_get_var(const orc_sim *s, int var, double *out);
 void orc_sim_set_var(orc_sim *s, int var, const double *in);
 void orc_sim_get_act(const orc_sim *s, double *out);
 void orc_sim_set_step_index(orc_sim *s, int64_t n);
+int orc_sim_set_integrator(orc_sim *s, int integrator);
 void orc_sim_diffusion(const orc_sim *s, const double *v, double *out);
 const orc_mesh *orc_sim_mesh(const orc_sim *s);
 /* bidomain (tissue.c): extracellular diffusivities per parameter set, the

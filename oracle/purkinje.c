@@ -195,7 +195,7 @@ void orc_graph_step(orc_graph *g, const double *V3, double t, double dt, int64_t
             if ((g->smask[i] >> k) & 1u)
                 if (orc_stim_active(&stim[k], dt, n_step)) is += stim[k].amplitude;
         W[i] = st[0];
-        const double iion = orc_model_step(st, dt, is, &sets[g->pset[i]]);
+        const double iion = orc_model_step(st, dt, is, &sets[g->pset[i]], NULL);
         itot[i] += iion + is;
     }
     const double h = dt / g->substeps;

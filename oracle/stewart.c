@@ -53,7 +53,7 @@ static double rush_larsen(double y, double yinf, double tau, double dt) {
     return yinf + (y - yinf) * exp(-dt / tau);
 }
 
-double orc_stewart_step(double *s, double dt, double i_stim, const orc_cellparams *p) {
+double orc_stewart_step(double *s, double dt, double i_stim, const orc_cellparams *p, orc_ab2 *ab) {
     const double V = s[V_], Cai = s[CAI], Casr = s[CASR], Cass = s[CASS];
     const double Nai = s[NAI], Ki = s[KI];
     const double RTF = Rgas * Temp / Fara;
@@ -169,11 +169,11 @@ double orc_stewart_step(double *s, double dt, double i_stim, const orc_cellparam
     tau = 4000.0 / (exp(-2.9 - 0.04 * V) + exp(3.6 + 0.11 * V));
     ns[Y_] = rush_larsen(s[Y_], yinf, tau, dt);
 
-    ns[NAI] = Nai + dt * dNai;
-    ns[KI] = Ki + dt * dKi;
-    ns[CAI] = buffered_free(buffered_total(Cai, Bufc, Kbufc) + dt * dCai_tot, Bufc, Kbufc);
-    ns[CASR] = buffered_free(buffered_total(Casr, Bufsr, Kbufsr) + dt * dCasr_tot, Bufsr, Kbufsr);
-    ns[CASS] = buffered_free(buffered_total(Cass, Bufss, Kbufss) + dt * dCass_tot, Bufss, Kbufss);
+    ns[NAI] = Nai + dt * orc_rate(ab, 1, dNai);
+    ns[KI] = Ki + dt * orc_rate(ab, 2, dKi);
+    ns[CAI] = buffered_free(buffered_total(Cai, Bufc, Kbufc) + dt * orc_rate(ab, 3, dCai_tot), Bufc, Kbufc);
+    ns[CASR] = buffered_free(buffered_total(Casr, Bufsr, Kbufsr) + dt * orc_rate(ab, 4, dCasr_tot), Bufsr, Kbufsr);
+    ns[CASS] = buffered_free(buffered_total(Cass, Bufss, Kbufss) + dt * orc_rate(ab, 5, dCass_tot), Bufss, Kbufss);
     for (int k = 1; k < NVAR; ++k) s[k] = ns[k];
     return Iion;
 }

@@ -44,15 +44,15 @@ int orc_set_threads(int n) {
 int orc_tp06_nvar(void);
 const char *orc_tp06_varname(int v);
 void orc_tp06_init(int variant, double *s);
-double orc_tp06_step(double *s, double dt, double i_stim, const orc_cellparams *p);
+double orc_tp06_step(double *s, double dt, double i_stim, const orc_cellparams *p, orc_ab2 *ab);
 int orc_crn_nvar(void);
 const char *orc_crn_varname(int v);
 void orc_crn_init(double *s);
-double orc_crn_step(double *s, double dt, double i_stim, const orc_cellparams *p);
+double orc_crn_step(double *s, double dt, double i_stim, const orc_cellparams *p, orc_ab2 *ab);
 int orc_stewart_nvar(void);
 const char *orc_stewart_varname(int v);
 void orc_stewart_init(double *s);
-double orc_stewart_step(double *s, double dt, double i_stim, const orc_cellparams *p);
+double orc_stewart_step(double *s, double dt, double i_stim, const orc_cellparams *p, orc_ab2 *ab);
 
 int orc_model_nvar(int model) {
     switch (model) {
@@ -82,11 +82,11 @@ void orc_model_init(const orc_cellparams *p, double *s) {
 }
 
 /* Advances every state variable except V (index 0); returns I_ion(V^n, s^n). */
-double orc_model_step(double *s, double dt, double i_stim, const orc_cellparams *p) {
+double orc_model_step(double *s, double dt, double i_stim, const orc_cellparams *p, orc_ab2 *ab) {
     switch (p->model) {
-    case ORC_TP06: return orc_tp06_step(s, dt, i_stim, p);
-    case ORC_CRN: return orc_crn_step(s, dt, i_stim, p);
-    case ORC_STEWART: return orc_stewart_step(s, dt, i_stim, p);
+    case ORC_TP06: return orc_tp06_step(s, dt, i_stim, p, ab);
+    case ORC_CRN: return orc_crn_step(s, dt, i_stim, p, ab);
+    case ORC_STEWART: return orc_stewart_step(s, dt, i_stim, p, ab);
     }
     return 0.0;
 }
@@ -102,15 +102,17 @@ int orc_stim_active(const orc_stim *st, double dt, int64_t n) {
 
 void orc_cell_run(const orc_cellparams *p, double dt, int64_t n_steps,
                   const orc_stim *stim, int64_t record_every, double *v_out,
-                  double *state_inout) {
-    double s[ORC_MAXVAR];
+                  double *state_inout, int ab2) {
+    double s[ORC_MAXVAR], h[ORC_NHIST] = {0};
+    orc_ab2 ab = {h, 0};
     memcpy(s, state_inout, sizeof(s));
     int64_t r = 0;
     for (int64_t n = 0; n < n_steps; ++n) {
         double is = (stim && orc_stim_active(stim, dt, n)) ? stim->amplitude : 0.0;
         double vn = s[0];
-        double iion = orc_model_step(s, dt, is, p);
-        s[0] = vn + dt * (-iion - is);
+        ab.on = n > 0;
+        double iion = orc_model_step(s, dt, is, p, ab2 ? &ab : NULL);
+        s[0] = vn + dt * orc_rate(ab2 ? &ab : NULL, 0, -iion - is);
         if (record_every > 0 && (n + 1) % record_every == 0) v_out[r++] = s[0];
     }
     memcpy(state_inout, s, sizeof(s));
@@ -133,6 +135,9 @@ struct orc_sim {
     orc_graph *g;              /* optional conduction graph */
     double *i_extra, *s_extra, *vg_old, *v_new;
     double *fibre;             /* [n_cells][3] */
+    int integrator;            /* 0 forward Euler, 1 AB2 for the non-gating variables */
+    int64_t ab2_from;          /* step whose rates start the AB2 history (forward Euler there) */
+    double *hist;              /* [n_cells][ORC_NHIST] */
     /* bidomain (NULL ve: monodomain) */
     double *ve, *Die, *u, *rhs;
     double gm_tol;
@@ -196,7 +201,7 @@ void orc_sim_destroy(orc_sim *s) {
     free(s->i_extra); free(s->s_extra); free(s->vg_old); free(s->v_new);
     free(s->pset); free(s->smask); free(s->state); free(s->D); free(s->act);
     free(s->v); free(s->diff); free(s->fibre);
-    free(s->ve); free(s->Die); free(s->u); free(s->rhs);
+    free(s->ve); free(s->Die); free(s->u); free(s->rhs); free(s->hist);
     free(s);
 }
 
@@ -231,8 +236,10 @@ void orc_sim_run(orc_sim *s, int64_t n_steps) {
                 ix = s->i_extra[c];
             }
             const double vn = st[0];
-            const double iion = orc_model_step(st, s->dt, is, &s->sets[s->pset[c]]);
-            const double vnew = vn + s->dt * (s->diff[c] - iion - is - ix);
+            orc_ab2 ab = {s->hist ? s->hist + (size_t)ORC_NHIST * c : NULL, n > s->ab2_from};
+            orc_ab2 *abp = s->integrator ? &ab : NULL;
+            const double iion = orc_model_step(st, s->dt, is, &s->sets[s->pset[c]], abp);
+            const double vnew = vn + s->dt * orc_rate(abp, 0, s->diff[c] - iion - is - ix);
             st[0] = vnew;
             if (isinf(s->act[c]) && vn < s->theta && vnew >= s->theta)
                 s->act[c] = t + s->dt * (s->theta - vn) / (vnew - vn);
@@ -292,7 +299,22 @@ void orc_sim_graph_get_act(const orc_sim *s, double *out) {
 }
 
 int64_t orc_sim_step_index(const orc_sim *s) { return s->step; }
-void orc_sim_set_step_index(orc_sim *s, int64_t n) { s->step = n; }
+void orc_sim_set_step_index(orc_sim *s, int64_t n) {
+    s->step = n;
+    s->ab2_from = n;   /* the AB2 history restarts */
+}
+
+/* Time integration of the non-gating variables (V and the concentrations):
+ * 0 forward Euler (Sec. 3.2), 1 second-order Adams-Bashforth (Sec. 4). The
+ * conduction graph's nodes stay forward Euler. AB2 starts from the current
+ * step with one forward-Euler step. */
+int orc_sim_set_integrator(orc_sim *s, int integrator) {
+    if (integrator != 0 && integrator != 1) return 30;
+    s->integrator = integrator;
+    s->ab2_from = s->step;
+    if (integrator && !s->hist) s->hist = (double *)calloc((size_t)ORC_NHIST * s->n_cells, sizeof(double));
+    return 0;
+}
 
 void orc_sim_get_var(const orc_sim *s, int var, double *out) {
     for (int64_t c = 0; c < s->n_cells; ++c) out[c] = s->state[ORC_MAXVAR * c + var];
@@ -300,6 +322,7 @@ void orc_sim_get_var(const orc_sim *s, int var, double *out) {
 
 void orc_sim_set_var(orc_sim *s, int var, const double *in) {
     for (int64_t c = 0; c < s->n_cells; ++c) s->state[ORC_MAXVAR * c + var] = in[c];
+    s->ab2_from = s->step;   /* the AB2 history restarts */
 }
 
 void orc_sim_get_act(const orc_sim *s, double *out) {
