@@ -70,8 +70,16 @@ enum {
 /* ---- arithmetic of a job ---- */
 enum {
     EP_FP32_MIXED = 0,  /* FP32 gates, currents, V and diffusion; [Na]i, [K]i and the
-                           SR calcium accumulated in FP64 */
+                           SR calcium accumulated as two-float compensated sums */
     EP_FP64_PLAIN = 1   /* everything in FP64 */
+};
+
+/* ---- time integration of the non-gating variables (V, concentrations) ---- */
+enum {
+    EP_INTEGRATOR_FE = 0,  /* forward Euler (Sec. 3.2) */
+    EP_INTEGRATOR_AB2 = 1  /* second-order Adams-Bashforth (Sec. 4); the first step after
+                              ep_params_set, ep_write_state or ep_set_step_index is forward
+                              Euler. The conduction graph's nodes stay forward Euler. */
 };
 
 /* ---- Purkinje-muscle junction coupling (Sec. 3.3) ---- */
@@ -141,7 +149,8 @@ typedef struct {
     int32_t n_sets;                     /* 1..EP_MAX_PARAM_SETS */
     ep_cell_params sets[EP_MAX_PARAM_SETS];
     int32_t n_stim;                     /* 0..EP_MAX_STIMULI */
-    int32_t reserved;
+    int32_t integrator;                 /* non-gating variables: EP_INTEGRATOR_FE (Sec. 3.2) or
+                                           EP_INTEGRATOR_AB2 (Sec. 4); gates are always Rush-Larsen */
     ep_stimulus stim[EP_MAX_STIMULI];
     double threshold;                   /* activation threshold, mV (Sec. 4 uses 0 mV) */
 } ep_params;

@@ -294,6 +294,7 @@ namespace {
 int graph_apply(ep_job *job);
 int bido_apply(ep_job *job);
 void bido_drop(ep_job *job);
+int restart_ab2(ep_job *job);
 
 // Validate a parameter block and fold it into FP64 coefficients for a mesh,
 // with the explicit stability check dt * rho(L) < 2 (host only).
@@ -310,6 +311,10 @@ int plan_params(const HostMesh &m, const ep_params *p, Coeffs *cf, std::string *
         *err = "params: n_sets must be 1..16 and n_stim 0..8";
         return EP_EINVAL;
     }
+    if (p->integrator != EP_INTEGRATOR_FE && p->integrator != EP_INTEGRATOR_AB2) {
+        *err = "params: unknown integrator";
+        return EP_EINVAL;
+    }
     for (int s = 0; s < p->n_sets; ++s) {
         const ep_cell_params &c = p->sets[s];
         if (!(c.D_l >= 0.0) || !(c.D_t >= 0.0) || !(c.K_o > 0.0) || c.variant < 0 || c.variant > 2) {
@@ -319,11 +324,15 @@ int plan_params(const HostMesh &m, const ep_params *p, Coeffs *cf, std::string *
     }
     int rc = build_coeffs(m, p, cf, err);
     if (rc) return rc;
+    // explicit stability on the diffusion operator's spectrum (real, in [-rho, 0]):
+    // forward Euler needs dt rho < 2, AB2 (stability interval [-1, 0]) dt rho < 1
+    const double lim = p->integrator == EP_INTEGRATOR_AB2 ? 1.0 : 2.0;
     double rho = cf->gershgorin;
-    if (p->dt * rho >= 1.9) rho = 1.05 * power_radius(m, *cf, 60);
-    if (p->dt * rho >= 2.0) {
+    if (p->dt * rho >= 0.95 * lim) rho = 1.05 * power_radius(m, *cf, 60);
+    if (p->dt * rho >= lim) {
         *err = "params: dt = " + std::to_string(p->dt) + " ms exceeds the explicit stability bound " +
-               std::to_string(2.0 / rho) + " ms of the diffusion operator";
+               std::to_string(lim / rho) + " ms of the diffusion operator" +
+               (p->integrator == EP_INTEGRATOR_AB2 ? " under AB2" : "");
         return EP_EUNSTABLE;
     }
     return EP_OK;
@@ -383,7 +392,8 @@ int job_upload_topology(ep_context *ctx, ep_job *j) {
 // change) allocate the state and set it to the models' resting states.
 int job_apply_params(ep_job *job, const ep_params *p, const Coeffs &cf) {
     ep_context *ctx = job->ctx;
-    const bool fresh = !job->has_params || job->precision != p->precision;
+    const bool fresh = !job->has_params || job->precision != p->precision ||
+                       job->params.integrator != p->integrator;
     if (job->has_params) {
         cudaStreamSynchronize(ctx->stream);
         drop_plans_with(ctx, job);
@@ -441,6 +451,8 @@ int job_apply_params(ep_job *job, const ep_params *p, const Coeffs &cf) {
             rc = grab(size_t(model_nr(md)) * rg.stride * r, &rg.r);
             if (!rc) rc = grab(size_t(model_na(md)) * rg.stride * 8, &q);
             rg.a = static_cast<double *>(q);
+            rg.h = nullptr;
+            if (!rc && p->integrator == EP_INTEGRATOR_AB2) rc = grab(size_t(kHistSlots) * rg.stride * r, &rg.h);
         }
         if (rc) {
             for (auto &bb : newprec) dfree(ctx, &bb);
@@ -460,6 +472,12 @@ int job_apply_params(ep_job *job, const ep_params *p, const Coeffs &cf) {
                              std::llround(s.period / p->dt), float(s.amplitude), 0};
     }
     dj.precision = p->precision;
+    dj.integrator = p->integrator;
+    dj.ab2_from = 0;
+    if (!fresh && p->integrator == EP_INTEGRATOR_AB2) {   // the AB2 history restarts at the current step
+        long long cur = 0;
+        if (cudaMemcpy(&cur, job->step_dev.p, sizeof(cur), cudaMemcpyDeviceToHost) == cudaSuccess) dj.ab2_from = cur;
+    }
     dj.dt = p->dt;
     dj.threshold = p->threshold;
     dj.dt_f = float(p->dt);
@@ -497,7 +515,7 @@ int job_apply_params(ep_job *job, const ep_params *p, const Coeffs &cf) {
 
 // Device bytes a job built from this mesh holds once parameters of the given
 // precision are set (the allocations of job_upload_topology + job_apply_params).
-int64_t job_bytes(const HostMesh &m, const Sell &sl, int precision) {
+int64_t job_bytes(const HostMesh &m, const Sell &sl, int precision, int integrator = EP_INTEGRATOR_FE) {
     auto rnd = [](int64_t b) { return std::max<int64_t>(b, 256); };
     const int64_t N = m.n_cells, r = precision == EP_FP64_PLAIN ? 8 : 4, E = int64_t(sl.col.size());
     int64_t b = 3 * rnd(16 * N) + 2 * rnd(N) + rnd(8 * int64_t(sl.slice_ptr.size())) + rnd(4 * E) + rnd(4 * N) + 256 +
@@ -508,6 +526,7 @@ int64_t job_bytes(const HostMesh &m, const Sell &sl, int precision) {
         if (!n) continue;
         const int64_t stride = round_up(n, 64);
         b += rnd(model_nr(md) * stride * r) + rnd(model_na(md) * stride * 8);
+        if (integrator == EP_INTEGRATOR_AB2) b += rnd(kHistSlots * stride * r);
     }
     return b;
 }
@@ -745,6 +764,21 @@ int bido_apply(ep_job *job) {
     return EP_OK;
 }
 
+// AB2 keeps the previous step's rates; after the state or the step index is
+// set from outside they are stale, so the next step is forward Euler again.
+int restart_ab2(ep_job *job) {
+    if (!job->has_params || job->params.integrator != EP_INTEGRATOR_AB2) return EP_OK;
+    ep_context *ctx = job->ctx;
+    long long cur = 0;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&cur, job->step_dev.p, sizeof(cur), cudaMemcpyDeviceToHost);
+    job->dj.ab2_from = cur;
+    if (e == cudaSuccess) e = cudaMemcpy(job->dj_dev.p, &job->dj, sizeof(DevJob), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "AB2 restart");
+    job->version++;   // the plans' copies of the job descriptor are rebuilt
+    return EP_OK;
+}
+
 // Back to the monodomain model (also the cleanup of a failed bido_apply).
 void bido_drop(ep_job *job) {
     ep_context *ctx = job->ctx;
@@ -848,7 +882,8 @@ int ep_plan_create(const ep_mesh_desc *desc, const ep_params *params, ep_plan **
 
 int64_t ep_plan_bytes(const ep_plan *plan) {
     if (!plan) return -1;
-    return job_bytes(*plan->mesh, *plan->sell, plan->has_params ? plan->params.precision : EP_FP32_MIXED);
+    return job_bytes(*plan->mesh, *plan->sell, plan->has_params ? plan->params.precision : EP_FP32_MIXED,
+                     plan->has_params ? plan->params.integrator : EP_INTEGRATOR_FE);
 }
 
 int ep_plan_info(const ep_plan *plan, int64_t *n_cells, int64_t *n_nodes) {
@@ -894,13 +929,14 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
     for (int prec : {EP_FP32_MIXED, EP_FP64_PLAIN}) {
         std::vector<DevJob> tab;
         std::vector<Tile> nt, ct, gt;
-        int max_sub = 0, any_bido = 0;
+        int max_sub = 0, any_bido = 0, any_ab2 = 0;
         for (int i = 0; i < n; ++i) {
             if (jobs[i]->precision != prec) continue;
             const int jid = int(tab.size());
             tab.push_back(jobs[i]->dj);
             for (Tile t : jobs[i]->node_tiles) nt.push_back(Tile{jid, t.model, t.start, t.count});
             for (Tile t : jobs[i]->cell_tiles) ct.push_back(Tile{jid, t.model, t.start, t.count});
+            if (jobs[i]->params.integrator == EP_INTEGRATOR_AB2) any_ab2 = 1;
             if (jobs[i]->bido) {
                 any_bido = 1;
                 pl->bido.push_back(jobs[i]);
@@ -937,6 +973,7 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
         g.L.graph_substeps = 0;
         g.L.graph_grid = 1;
         g.L.bido = any_bido;
+        g.L.ab2 = any_ab2;
         if (!gt.empty()) {
             if ((rc = upload(ctx, gt, &tmp, &p))) return rc;
             g.graph_tiles = tmp.back();
@@ -1255,7 +1292,8 @@ static int transfer_state(ep_job *job, int32_t model, int32_t var, double *host,
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     dfree(ctx, &b);
-    return e == cudaSuccess ? EP_OK : cuda_fail(ctx, e, write ? "ep_write_state" : "ep_read_state");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, write ? "ep_write_state" : "ep_read_state");
+    return write ? restart_ab2(job) : EP_OK;
 }
 
 int ep_read_state(ep_job *job, int32_t model, int32_t var, double *host_out, int64_t n) {
@@ -1328,7 +1366,8 @@ int ep_set_step_index(ep_job *job, int64_t n) {
     long long v = n;
     if (e == cudaSuccess) e = cudaMemcpyAsync(job->step_dev.p, &v, sizeof(v), cudaMemcpyHostToDevice, job->ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(job->ctx->stream);
-    return e == cudaSuccess ? EP_OK : cuda_fail(job->ctx, e, "ep_set_step_index");
+    if (e != cudaSuccess) return cuda_fail(job->ctx, e, "ep_set_step_index");
+    return restart_ab2(job);
 }
 
 int ep_check_finite(ep_job *job) {
@@ -1434,6 +1473,8 @@ int ep_step_noalloc(ep_job *job, int64_t n_steps) {
     if (!job->has_params) return fail(ctx, EP_ESTATE, "ep_step_noalloc: the job has no parameters");
     if (job->gp) return fail(ctx, EP_EINVAL, "ep_step_noalloc: jobs with a conduction graph need ep_step");
     if (job->bido) return fail(ctx, EP_EINVAL, "ep_step_noalloc: bidomain jobs need ep_step");
+    if (job->params.integrator != EP_INTEGRATOR_FE)
+        return fail(ctx, EP_EINVAL, "ep_step_noalloc: AB2 jobs need ep_step");
     if (job->mesh().n_nodes > EP_NOALLOC_MAX_NODES)
         return fail(ctx, EP_EINVAL, "ep_step_noalloc: the mesh has " + std::to_string(job->mesh().n_nodes) +
                                         " nodes; at most " + std::to_string(EP_NOALLOC_MAX_NODES) +

@@ -71,6 +71,27 @@ __device__ __forceinline__ float2 twofloat_add(float2 a, float d) {
 // Slowly drifting concentrations ([Na]i, [K]i, SR calcium) live in 8-byte
 // slots: an FP64 value in the plain path, a two-float compensated sum in the
 // mixed path, so that FP32 increments accumulate without FP64 arithmetic.
+// Rate a non-gating variable advances with over a step (V and the
+// concentrations): forward Euler, f^n; or, with AB2 (second-order
+// Adams-Bashforth, Sec. 4), 3/2 f^n - 1/2 f^{n-1} once the history exists.
+// Slot k of the cell's history (h[k * st]) keeps f^n for the next step.
+// Slots: 0 V, 1..5 the model's non-gating variables.
+template <class R, bool AB2>
+struct Rates {
+    R *h = nullptr;        // NULL: this cell's job integrates by forward Euler
+    long long st = 0;
+    bool on = false;
+    __device__ __forceinline__ R operator()(int k, R f) const {
+        if constexpr (!AB2) {
+            return f;
+        } else {
+            if (!h) return f;
+            const R g = on ? R(1.5) * f - R(0.5) * h[k * st] : f;
+            h[k * st] = f;
+            return g;
+        }
+    }
+};
 template <class R> struct Accum;
 template <> struct Accum<double> {
     double v;

@@ -28,8 +28,9 @@ __device__ __forceinline__ R lin_over_expm1(R x, R k) {
     return y == R(0) ? k : k * y / fexpm1(y);
 }
 
-template <class R>
-__device__ __forceinline__ R crn_step(const DevRegion &rg, long long i, const DevParams &P, R V, R dt) {
+template <class R, bool AB2 = false>
+__device__ __forceinline__ R crn_step(const DevRegion &rg, long long i, const DevParams &P, R V, R dt,
+                                      const Rates<R, AB2> &rt = Rates<R, AB2>{}) {
     R *x = static_cast<R *>(rg.r) + i;
     double *a = rg.a + i;
     const long long st = rg.stride;
@@ -146,11 +147,11 @@ __device__ __forceinline__ R crn_step(const DevRegion &rg, long long i, const De
     }
 
     // ---- concentrations ----
-    x[0] = Cai + dt * (B1 / B2);
-    Nai_a.store_add(a, dt * dNai);
-    Ki_a.store_add(a + st, dt * dKi);
-    Caup_a.store_add(a + 2 * st, dt * dCaup);
-    Carel_a.store_add(a + 3 * st, dt * dCarel);
+    x[0] = Cai + dt * rt(3, B1 / B2);
+    Nai_a.store_add(a, dt * rt(1, dNai));
+    Ki_a.store_add(a + st, dt * rt(2, dKi));
+    Caup_a.store_add(a + 2 * st, dt * rt(4, dCaup));
+    Carel_a.store_add(a + 3 * st, dt * rt(5, dCarel));
     return Iion;
 }
 

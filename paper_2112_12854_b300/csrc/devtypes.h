@@ -34,6 +34,7 @@ struct DevParams {
 struct DevRegion {
     void *r;
     double *a;
+    void *h;              // AB2 rate history, kHistSlots arrays of the compute type (NULL: forward Euler)
     long long stride;
     long long off;   // first cell of the region in the job's numbering
     long long n;
@@ -88,6 +89,9 @@ struct DevJob {
     long long *step;          // steps taken (device counter)
     DevGraph g;
     const void *xdiv;         // bidomain: intracellular flux of v_e, added to the diffusion term (else NULL)
+    int integrator;           // EP_INTEGRATOR_FE or EP_INTEGRATOR_AB2 (non-gating variables)
+    int pad2;
+    long long ab2_from;       // AB2: steps n > ab2_from use the history (the step ab2_from is forward Euler)
 };
 
 // A tile is a run of consecutive cells (or nodes) of one job and one model.
@@ -99,6 +103,7 @@ struct Tile {
 };
 
 constexpr int kCellThreads = 256;
+constexpr int kHistSlots = 6;              // AB2 rate history per cell: V and five non-gating variables
 constexpr int kGraphThreads = 256;
 constexpr unsigned kJunctionFlag = 0x80;   // set in a cell's parameter-set byte when a junction touches it
 constexpr int kNodeThreads = 256;

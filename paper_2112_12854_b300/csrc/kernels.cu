@@ -105,8 +105,10 @@ __device__ void junction_cell_crossing(const DevJob &J, long long c, long long n
 }
 
 // XD: the batch holds bidomain jobs, whose cells add L_i(v_e^n) (first line
-// of Eq. 6) to the diffusion term; monodomain-only batches compile without it.
-template <class R, bool XD = false>
+// of Eq. 6) to the diffusion term; AB2: the batch holds jobs that advance the
+// non-gating variables by second-order Adams-Bashforth. Batches without them
+// compile without the code.
+template <class R, bool XD = false, bool AB2 = false>
 __device__ __forceinline__ void cell_update(const DevJob &J, int model, long long c) {
     using R4 = typename Vec4T<R>::type;
     const long long n = *J.step;
@@ -135,10 +137,18 @@ __device__ __forceinline__ void cell_update(const DevJob &J, int model, long lon
     const DevRegion &rg = J.reg[model];
     const long long li = c - rg.off;
     R iion;
-    if (model == EP_TP06) iion = tt_step<R, false>(rg, li, P, Vc, dt, is);
-    else if (model == EP_STEWART) iion = tt_step<R, true>(rg, li, P, Vc, dt, is);
-    else iion = crn_step<R>(rg, li, P, Vc, dt);
-    const R Vn = Vc + dt * (diff - iion - is - ix);
+    Rates<R, AB2> rt;
+    if constexpr (AB2) {
+        if (J.integrator == EP_INTEGRATOR_AB2) {
+            rt.h = static_cast<R *>(rg.h) + li;
+            rt.st = rg.stride;
+            rt.on = n > J.ab2_from;
+        }
+    }
+    if (model == EP_TP06) iion = tt_step<R, false, AB2>(rg, li, P, Vc, dt, is, rt);
+    else if (model == EP_STEWART) iion = tt_step<R, true, AB2>(rg, li, P, Vc, dt, is, rt);
+    else iion = crn_step<R, AB2>(rg, li, P, Vc, dt, rt);
+    const R Vn = Vc + dt * rt(0, diff - iion - is - ix);
     Vnext[c] = Vn;
     if ((ps & kJunctionFlag) && J.g.two_way) junction_cell_crossing<R>(J, c, n, Vc, Vn, jfirst, jlast);
     const R th = pick<R>(J.threshold, J.threshold_f);
@@ -237,14 +247,14 @@ __global__ void __launch_bounds__(kGraphThreads) graph_diffuse_kernel(const DevJ
 // the register allocator. All variants run the same per-cell arithmetic, so
 // their results are bitwise identical. Tiles hold kCellThreads cells; a
 // block narrower than a tile walks it in strides of its width.
-template <class R, int T, int MINB, bool XD>
+template <class R, int T, int MINB, bool XD, bool AB2>
 __global__ void __launch_bounds__(T, MINB) cell_kernel(const DevJob *__restrict__ jobs,
                                                         const Tile *__restrict__ tiles, int n_tiles,
                                                         unsigned *done, int n_jobs) {
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const Tile tl = tiles[t];
         for (int i = threadIdx.x; i < tl.count; i += T)
-            cell_update<R, XD>(jobs[tl.job], tl.model, (long long)tl.start + i);
+            cell_update<R, XD, AB2>(jobs[tl.job], tl.model, (long long)tl.start + i);
     }
     // Every block has read the step counters; the last one to finish advances them.
     __syncthreads();
@@ -425,17 +435,19 @@ cudaError_t launch_node(int precision, const StepLaunch &L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <class R, int T, int B>
+static void launch_cell_kernel(const StepLaunch &L, cudaStream_t s) {
+    auto *k = L.bido ? (L.ab2 ? cell_kernel<R, T, B, true, true> : cell_kernel<R, T, B, true, false>)
+                     : (L.ab2 ? cell_kernel<R, T, B, false, true> : cell_kernel<R, T, B, false, false>);
+    k<<<L.cell_grid, T, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done, L.n_jobs);
+}
+
 template <class R>
 static cudaError_t cell_launch_variant(const StepLaunch &L, cudaStream_t s) {
     switch (L.cell_variant) {
 #define EP_CELL_CASE(k, T, B)                                                                                  \
     case k:                                                                                                    \
-        if (L.bido)                                                                                            \
-            cell_kernel<R, T, B, true><<<L.cell_grid, T, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done,  \
-                                                                 L.n_jobs);                                    \
-        else                                                                                                   \
-            cell_kernel<R, T, B, false><<<L.cell_grid, T, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done, \
-                                                                  L.n_jobs);                                   \
+        launch_cell_kernel<R, T, B>(L, s);                                                                     \
         break;
         EP_CELL_VARIANTS(EP_CELL_CASE)
 #undef EP_CELL_CASE
@@ -455,7 +467,7 @@ static int cell_blocks_variant(int variant) {
     switch (variant) {
 #define EP_CELL_CASE(k, T, B)                                                                 \
     case k:                                                                                   \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_kernel<R, T, B, false>, T, 0); \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_kernel<R, T, B, false, false>, T, 0); \
         break;
         EP_CELL_VARIANTS(EP_CELL_CASE)
 #undef EP_CELL_CASE

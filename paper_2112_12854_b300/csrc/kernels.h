@@ -21,6 +21,7 @@ struct StepLaunch {
     int graph_grid;
     int graph_substeps;        // largest substep count of the jobs' graphs
     int bido;                  // some job is bidomain (cell kernel adds DevJob::xdiv)
+    int ab2;                   // some job integrates by AB2 (cell kernel keeps rate histories)
 };
 
 // Launch shapes of the cell kernel: (index, threads per block, minimum

@@ -4,7 +4,7 @@
 //   - Stewart et al. 2009 human Purkinje cell, which adds I_f and I_sus to the
 //     same scaffold and changes I_Na, I_K1, I_to, I_Kr and I_Ks.
 // One step: currents and rates at (V^n, s^n); gates and Rbar by Rush-Larsen;
-// [Na]i, [K]i by forward Euler, accumulated in FP64 (plain path) or as a
+// [Na]i, [K]i by forward Euler (or AB2, see Rates), accumulated in FP64 (plain path) or as a
 // two-float compensated sum (mixed path); the three calcium
 // compartments by forward Euler on the buffered total, applied as an
 // increment of the free concentration (Sec. 3.2).
@@ -22,9 +22,9 @@ namespace ep {
 constexpr int kTTnr = 15, kSTWnr = 16, kTTna = 3;
 
 // Returns I_ion(V^n, s^n) in uA/uF and writes s^{n+1} (all but V).
-template <class R, bool PURKINJE>
+template <class R, bool PURKINJE, bool AB2 = false>
 __device__ __forceinline__ R tt_step(const DevRegion &rg, long long i, const DevParams &P, R V, R dt,
-                                     R i_stim) {
+                                     R i_stim, const Rates<R, AB2> &rt = Rates<R, AB2>{}) {
     R *x = static_cast<R *>(rg.r) + i;
     double *a = rg.a + i;
     const long long st = rg.stride;
@@ -198,11 +198,11 @@ __device__ __forceinline__ R tt_step(const DevRegion &rg, long long i, const Dev
     }
 
     // ---- concentrations ----
-    x[0] = Cai + buffered_increment(Cai, dt * dCai_tot, R(0.2), R(0.001));
-    x[st] = Cass + buffered_increment(Cass, dt * dCass_tot, R(0.4), R(0.00025));
-    Nai_a.store_add(a, dt * dNai);
-    Ki_a.store_add(a + st, dt * dKi);
-    Casr_a.store_add(a + 2 * st, buffered_increment(Casr, dt * dCasr_tot, R(10), R(0.3)));
+    x[0] = Cai + buffered_increment(Cai, dt * rt(3, dCai_tot), R(0.2), R(0.001));
+    x[st] = Cass + buffered_increment(Cass, dt * rt(5, dCass_tot), R(0.4), R(0.00025));
+    Nai_a.store_add(a, dt * rt(1, dNai));
+    Ki_a.store_add(a + st, dt * rt(2, dKi));
+    Casr_a.store_add(a + 2 * st, buffered_increment(Casr, dt * rt(4, dCasr_tot), R(10), R(0.3)));
     return Iion;
 }
 

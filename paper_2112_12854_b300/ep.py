@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libep.so")
 EP_OK, EP_EINVAL, EP_ENOMEM, EP_EMESH, EP_EUNSTABLE, EP_ENONFINITE, EP_ETIMEOUT, EP_ECUDA, EP_ESTATE = range(9)
 EP_TP06, EP_CRN, EP_STEWART = 0, 1, 2
 EP_FP32_MIXED, EP_FP64_PLAIN = 0, 1
+EP_INTEGRATOR_FE, EP_INTEGRATOR_AB2 = 0, 1
 MAX_SETS, MAX_STIM = 16, 8
 _STATUS = {1: "EINVAL", 2: "ENOMEM", 3: "EMESH", 4: "EUNSTABLE", 5: "ENONFINITE", 6: "ETIMEOUT",
            7: "ECUDA", 8: "ESTATE"}
@@ -48,7 +49,7 @@ class Stimulus(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("precision", ctypes.c_int32), ("n_sets", ctypes.c_int32),
-                ("sets", CellParams * MAX_SETS), ("n_stim", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("sets", CellParams * MAX_SETS), ("n_stim", ctypes.c_int32), ("integrator", ctypes.c_int32),
                 ("stim", Stimulus * MAX_STIM), ("threshold", ctypes.c_double)]
 
 
@@ -233,12 +234,15 @@ class Context:
                    fibre=fibre)
 
 
-def make_params(dt, sets, stimuli=(), *, precision=EP_FP32_MIXED, threshold=-20.0) -> Params:
+def make_params(dt, sets, stimuli=(), *, precision=EP_FP32_MIXED, threshold=-20.0,
+                integrator=0) -> Params:
     """sets: objects with variant, D_l, D_t, gks_scale, gkr_scale, K_o;
-    stimuli: objects with amplitude, t_on, duration, period."""
+    stimuli: objects with amplitude, t_on, duration, period; integrator
+    EP_INTEGRATOR_FE (0) or EP_INTEGRATOR_AB2 (1) for the non-gating variables."""
     p = Params()
     p.dt = float(dt)
     p.precision = int(precision)
+    p.integrator = int(integrator)
     p.n_sets = len(sets)
     if not 1 <= len(sets) <= MAX_SETS or len(stimuli) > MAX_STIM:
         raise ValueError("1..16 parameter sets and at most 8 stimuli")
@@ -534,21 +538,22 @@ def case_cell_model(case):
     return np.array([case.param_sets[k].model for k in range(len(case.param_sets))], np.uint8)[case.param_set]
 
 
-def plan_from_case(case, *, precision=EP_FP32_MIXED) -> Plan:
+def plan_from_case(case, *, precision=EP_FP32_MIXED, integrator=0) -> Plan:
     """Host-only plan of a ``workloads.TissueCase`` (mesh + parameters)."""
-    params = make_params(case.dt, case.param_sets, case.stimuli, precision=precision, threshold=case.threshold)
+    params = make_params(case.dt, case.param_sets, case.stimuli, precision=precision, threshold=case.threshold,
+                         integrator=integrator)
     return Plan(case.xyz, case.tets, params, cell_model=case_cell_model(case), param_set=case.param_set,
                 stim_mask=case.stim_mask, fibre=case.fibre)
 
 
-def job_from_case(ctx: Context, case, *, precision=EP_FP32_MIXED, cell_model=None) -> Job:
+def job_from_case(ctx: Context, case, *, precision=EP_FP32_MIXED, cell_model=None, integrator=0) -> Job:
     """Create a job from a ``workloads.TissueCase`` and set its parameters."""
     if cell_model is None:
         cell_model = case_cell_model(case)
     j = ctx.mesh(case.xyz, case.tets, cell_model=cell_model, param_set=case.param_set,
                  stim_mask=case.stim_mask, fibre=case.fibre)
     j.set_params(make_params(case.dt, case.param_sets, case.stimuli, precision=precision,
-                             threshold=case.threshold))
+                             threshold=case.threshold, integrator=integrator))
     return j
 
 

@@ -161,3 +161,20 @@ def test_library_has_no_unresolved_internal_symbols():
     out = subprocess.run(["nm", "-D", "--undefined-only", ep.LIB_PATH], capture_output=True, text=True).stdout
     bad = [l for l in out.splitlines() if "_ZN2ep" in l]
     assert not bad, bad
+
+
+def test_ab2_halves_the_explicit_stability_bound():
+    """AB2's stability interval on the negative real axis is [-1, 0], half
+    forward Euler's [-2, 0]: a dt that forward Euler accepts on this mesh is
+    rejected for AB2 (EP_EUNSTABLE) until it is halved (host-only planner)."""
+    xyz, tets = w.kuhn_box(12, 8, 3, 0.25)
+    n = tets.shape[0]
+    for dt, integ, ok in ((0.02, 0, True), (0.02, 1, False), (0.01, 1, True)):
+        case = w.TissueCase("slab", xyz, tets, w.fibres_uniform(n), np.zeros(n, np.uint8), np.zeros(n, np.uint8),
+                            [w.ParamSet()], [], dt, 0, -20.0)
+        if ok:
+            ep.plan_from_case(case, integrator=integ).destroy()
+        else:
+            with pytest.raises(ep.EPError) as e:
+                ep.plan_from_case(case, integrator=integ)
+            assert e.value.code == ep.EP_EUNSTABLE
