@@ -242,8 +242,10 @@ int ep_reset_activation(ep_job *job);
 int ep_step_index(ep_job *job, int64_t *out);
 int ep_set_step_index(ep_job *job, int64_t n);
 
-/* Scan the job's state for NaN/Inf on the device. Returns EP_OK or
- * EP_ENONFINITE. Synchronises. */
+/* Scan the job's state for NaN/Inf on the device. Returns EP_OK,
+ * EP_ENONFINITE, or EP_ETIMEOUT if a step kernel of the context gave up a
+ * bounded wait (the staged cell kernel waits at most 1 s for the bulk copies
+ * of a tile; the state is then not valid). Synchronises. */
 int ep_check_finite(ep_job *job);
 
 /* Job information: cells, nodes, interior faces, device bytes held. */
@@ -265,15 +267,21 @@ int ep_job_destroy(ep_job *job);
  * Synchronises. The results equal those of ep_step. */
 int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double *node_ms, double *cell_ms);
 
-/* Autotuner of the cell kernel's launch shape (threads per block and
- * resident blocks per SM, six variants). Advances the jobs by
- * 6 * steps_per_variant real time steps, timing the cell launch of each
+/* Autotuner of the cell kernel's launch shape. Variants 0-5: threads per
+ * block and resident blocks per SM of the plain kernel; variants 6 and 7:
+ * the staged FP32 kernel, whose streamed inputs are brought into shared
+ * memory by bulk asynchronous copies, double-buffered (6: all of them, two
+ * blocks per SM; 7: indices, coefficients, V and bytes, three blocks per
+ * SM); FP64 and AB2 batches run variant 0 for them. Advances the jobs by
+ * 8 * steps_per_variant real time steps, timing the cell launch of each
  * variant with CUDA events, and keeps the fastest variant per precision for
- * every later ep_step of the context. All variants compute bitwise identical
- * results. chosen[2] (may be NULL) receives the variant picked for
- * EP_FP32_MIXED and EP_FP64_PLAIN (-1 if no job of that precision);
- * variant_ms[2 * 6] (may be NULL) the mean cell-kernel time per variant.
- * Synchronises. */
+ * every later ep_step of the context. The variants compute the same
+ * arithmetic; TP06 and Stewart cells agree bitwise across all of them,
+ * Courtemanche cells can differ in the last bits between the
+ * register-limited shapes and the others. chosen[2] (may be NULL) receives
+ * the variant picked for EP_FP32_MIXED and EP_FP64_PLAIN (-1 if no job of
+ * that precision); variant_ms[2 * 8] (may be NULL) the mean cell-kernel time
+ * per variant. Synchronises. */
 int ep_autotune(ep_job *const *jobs, int32_t n_jobs, int32_t steps_per_variant, int32_t *chosen,
                 double *variant_ms);
 
@@ -288,7 +296,7 @@ int ep_autotune(ep_job *const *jobs, int32_t n_jobs, int32_t steps_per_variant, 
  * synchronises. */
 int ep_alu_peaks(ep_context *ctx, double *out);
 
-/* Force the cell kernel's launch-shape variant (0..5) for one precision. */
+/* Force the cell kernel's launch-shape variant (0..7) for one precision. */
 int ep_set_cell_variant(ep_context *ctx, int32_t precision, int32_t variant);
 
 /* Host-only inspection of the planner (no device work, no GPU needed): run

@@ -78,6 +78,7 @@ struct ep_context {
     std::vector<std::unique_ptr<Plan>> plans;
     int sm_count = 148;
     int cell_variant[2] = {0, 0};   // launch shape of the cell kernel per precision (ep_autotune)
+    DevBuf err_word;                 // device word: a bounded wait in a step kernel gave up
 };
 
 struct ep_job {
@@ -238,6 +239,15 @@ int ep_context_create(ep_alloc_fn alloc, ep_free_fn free_fn, void *user, void *c
         ctx->free_fn = free_fn;
         ctx->user = user;
         ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+        if (dalloc(ctx, sizeof(unsigned), &ctx->err_word) ||
+            cudaMemset(ctx->err_word.p, 0, sizeof(unsigned)) != cudaSuccess) {
+            g_create_error = "ep_context_create: device allocation failed";
+            if (ctx->err_word.p) dfree(ctx, &ctx->err_word);
+            cudaStreamDestroy(ctx->capture);
+            cudaStreamDestroy(ctx->upload);
+            delete ctx;
+            return EP_ENOMEM;
+        }
         *out = ctx;
         return EP_OK;
     } catch (...) {
@@ -259,6 +269,7 @@ int ep_context_destroy(ep_context *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto &p : ctx->plans) free_plan(ctx, p.get());
     ctx->plans.clear();
+    dfree(ctx, &ctx->err_word);
     if (ctx->capture) cudaStreamDestroy(ctx->capture);
     if (ctx->upload) cudaStreamDestroy(ctx->upload);
     delete ctx;
@@ -974,6 +985,7 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
         g.L.graph_grid = 1;
         g.L.bido = any_bido;
         g.L.ab2 = any_ab2;
+        g.L.err = static_cast<unsigned *>(ctx->err_word.p);
         if (!gt.empty()) {
             if ((rc = upload(ctx, gt, &tmp, &p))) return rc;
             g.graph_tiles = tmp.back();
@@ -1383,10 +1395,13 @@ int ep_check_finite(ep_job *job) {
     if (e == cudaSuccess)
         e = launch_check_finite(job->precision, static_cast<const DevJob *>(job->dj_dev.p), job->mesh().n_cells,
                                 static_cast<unsigned *>(b.p), ctx->stream);
+    unsigned werr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, b.p, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&werr, ctx->err_word.p, sizeof(werr), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     dfree(ctx, &b);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_check_finite");
+    if (werr) return fail(ctx, EP_ETIMEOUT, "a step kernel's wait for its staged copies hit its time limit");
     if (cnt) return fail(ctx, EP_ENONFINITE, std::to_string(cnt) + " non-finite state values");
     return EP_OK;
 }

@@ -92,6 +92,19 @@ struct Rates {
         }
     }
 };
+// Where a cell model reads its state s^n and writes s^{n+1}: variable k at
+// xi[k * si] / xo[k * so], 8-byte accumulator k at ai[k * si] / ao[k * so].
+// In place (xi == xo) in global memory, or read from a shared-memory stage.
+template <class R>
+struct CellIO {
+    const R *xi;
+    const double *ai;
+    long long si;
+    R *xo;
+    double *ao;
+    long long so;
+};
+
 template <class R> struct Accum;
 template <> struct Accum<double> {
     double v;

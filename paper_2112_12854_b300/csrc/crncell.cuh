@@ -29,16 +29,19 @@ __device__ __forceinline__ R lin_over_expm1(R x, R k) {
 }
 
 template <class R, bool AB2 = false>
-__device__ __forceinline__ R crn_step(const DevRegion &rg, long long i, const DevParams &P, R V, R dt,
+__device__ __forceinline__ R crn_step(const CellIO<R> &io, const DevParams &P, R V, R dt,
                                       const Rates<R, AB2> &rt = Rates<R, AB2>{}) {
-    R *x = static_cast<R *>(rg.r) + i;
-    double *a = rg.a + i;
-    const long long st = rg.stride;
-    const R Cai = x[0], m = x[st], h = x[2 * st], jj = x[3 * st], oa = x[4 * st], oi = x[5 * st];
-    const R ua = x[6 * st], ui = x[7 * st], xr = x[8 * st], xs = x[9 * st], d = x[10 * st];
-    const R f = x[11 * st], fCa = x[12 * st], u = x[13 * st], vv = x[14 * st], w = x[15 * st];
-    const Accum<R> Nai_a = Accum<R>::load(a), Ki_a = Accum<R>::load(a + st);
-    const Accum<R> Caup_a = Accum<R>::load(a + 2 * st), Carel_a = Accum<R>::load(a + 3 * st);
+    const R *xi = io.xi;
+    const double *ai = io.ai;
+    const long long si = io.si;
+    R *xo = io.xo;
+    double *ao = io.ao;
+    const long long so = io.so;
+    const R Cai = xi[0], m = xi[si], h = xi[2 * si], jj = xi[3 * si], oa = xi[4 * si], oi = xi[5 * si];
+    const R ua = xi[6 * si], ui = xi[7 * si], xr = xi[8 * si], xs = xi[9 * si], d = xi[10 * si];
+    const R f = xi[11 * si], fCa = xi[12 * si], u = xi[13 * si], vv = xi[14 * si], w = xi[15 * si];
+    const Accum<R> Nai_a = Accum<R>::load(ai), Ki_a = Accum<R>::load(ai + si);
+    const Accum<R> Caup_a = Accum<R>::load(ai + 2 * si), Carel_a = Accum<R>::load(ai + 3 * si);
     const R Nai = Nai_a.value(), Ki = Ki_a.value(), Caup = Caup_a.value(), Carel = Carel_a.value();
 
     const R Fc = R(96.4867);
@@ -87,7 +90,7 @@ __device__ __forceinline__ R crn_step(const DevRegion &rg, long long i, const De
     R al, be;
     al = R(0.32) * lin_over_1mexp(V + R(47.13), R(10));
     be = R(0.08) * fexp(-V * R(1.0 / 11.0));
-    x[st] = rush_larsen(m, al / (al + be), R(1) / (al + be), dt);
+    xo[so] = rush_larsen(m, al / (al + be), R(1) / (al + be), dt);
     if (V >= R(-40)) {
         al = R(0);
         be = R(1) / (R(0.13) * (R(1) + fexp(-(V + R(10.66)) * R(1.0 / 11.1))));
@@ -95,7 +98,7 @@ __device__ __forceinline__ R crn_step(const DevRegion &rg, long long i, const De
         al = R(0.135) * fexp(-(V + R(80)) * R(1.0 / 6.8));
         be = R(3.56) * fexp(R(0.079) * V) + R(3.1e5) * fexp(R(0.35) * V);
     }
-    x[2 * st] = rush_larsen(h, al / (al + be), R(1) / (al + be), dt);
+    xo[2 * so] = rush_larsen(h, al / (al + be), R(1) / (al + be), dt);
     if (V >= R(-40)) {
         al = R(0);
         be = R(0.3) * fexp(R(-2.535e-7) * V) * logistic(R(-0.1) * (V + R(32)));
@@ -104,54 +107,54 @@ __device__ __forceinline__ R crn_step(const DevRegion &rg, long long i, const De
              logistic(R(0.311) * (V + R(79.23)));
         be = R(0.1212) * fexp(R(-0.01052) * V) * logistic(R(-0.1378) * (V + R(40.14)));
     }
-    x[3 * st] = rush_larsen(jj, al / (al + be), R(1) / (al + be), dt);
+    xo[3 * so] = rush_larsen(jj, al / (al + be), R(1) / (al + be), dt);
     // oa and ua share their rate functions
     al = R(0.65) / (fexp(-(V + R(10)) * R(1.0 / 8.5)) + fexp(-(V - R(30)) * R(1.0 / 59.0)));
     be = R(0.65) / (R(2.5) + fexp((V + R(82)) * R(1.0 / 17.0)));
     const R tau_a = R(1) / ((al + be) * R(3));
-    x[4 * st] = rush_larsen(oa, logistic(-(V + R(20.47)) * R(1.0 / 17.54)), tau_a, dt);
-    x[6 * st] = rush_larsen(ua, logistic(-(V + R(30.3)) * R(1.0 / 9.6)), tau_a, dt);
+    xo[4 * so] = rush_larsen(oa, logistic(-(V + R(20.47)) * R(1.0 / 17.54)), tau_a, dt);
+    xo[6 * so] = rush_larsen(ua, logistic(-(V + R(30.3)) * R(1.0 / 9.6)), tau_a, dt);
     al = R(1) / (R(18.53) + fexp((V + R(113.7)) * R(1.0 / 10.95)));
     be = R(1) / (R(35.56) + fexp(-(V + R(1.26)) * R(1.0 / 7.44)));
-    x[5 * st] = rush_larsen(oi, logistic((V + R(43.1)) * R(1.0 / 5.3)), R(1) / ((al + be) * R(3)), dt);
+    xo[5 * so] = rush_larsen(oi, logistic((V + R(43.1)) * R(1.0 / 5.3)), R(1) / ((al + be) * R(3)), dt);
     al = R(1) / (R(21) + fexp(-(V - R(185)) * R(1.0 / 28.0)));
     be = fexp((V - R(158)) * R(1.0 / 16.0));
-    x[7 * st] = rush_larsen(ui, logistic((V - R(99.45)) * R(1.0 / 27.48)), R(1) / ((al + be) * R(3)), dt);
+    xo[7 * so] = rush_larsen(ui, logistic((V - R(99.45)) * R(1.0 / 27.48)), R(1) / ((al + be) * R(3)), dt);
     al = R(0.0003) * lin_over_1mexp(V + R(14.1), R(5));
     be = R(7.3898e-5) * lin_over_expm1(V - R(3.3328), R(5.1237));
-    x[8 * st] = rush_larsen(xr, logistic(-(V + R(14.1)) * R(1.0 / 6.5)), R(1) / (al + be), dt);
+    xo[8 * so] = rush_larsen(xr, logistic(-(V + R(14.1)) * R(1.0 / 6.5)), R(1) / (al + be), dt);
     al = R(4e-5) * lin_over_1mexp(V - R(19.9), R(17));
     be = R(3.5e-5) * lin_over_expm1(V - R(19.9), R(9));
-    x[9 * st] = rush_larsen(xs, R(1) / fsqrt(R(1) + fexp(-(V - R(19.9)) * R(1.0 / 12.7))), R(0.5) / (al + be), dt);
+    xo[9 * so] = rush_larsen(xs, R(1) / fsqrt(R(1) + fexp(-(V - R(19.9)) * R(1.0 / 12.7))), R(0.5) / (al + be), dt);
     {
         const R yv = (V + R(10)) * R(1.0 / 6.24);
         const R g = yv == R(0) ? R(1) : -fexpm1(-yv) / yv;
         const R tau = g / (R(6.24 * 0.035) * (R(1) + fexp(-yv)));
-        x[10 * st] = rush_larsen(d, logistic(-(V + R(10)) * R(0.125)), tau, dt);
+        xo[10 * so] = rush_larsen(d, logistic(-(V + R(10)) * R(0.125)), tau, dt);
     }
     {
         const R tau = R(9) / (R(0.0197) * fexp(R(-0.0337 * 0.0337) * (V + R(10)) * (V + R(10))) + R(0.02));
-        x[11 * st] = rush_larsen(f, logistic((V + R(28)) * R(1.0 / 6.9)), tau, dt);
+        xo[11 * so] = rush_larsen(f, logistic((V + R(28)) * R(1.0 / 6.9)), tau, dt);
     }
-    x[12 * st] = rush_larsen(fCa, R(1) / (R(1) + Cai * R(1.0 / 0.00035)), R(2), dt);
+    xo[12 * so] = rush_larsen(fCa, R(1) / (R(1) + Cai * R(1.0 / 0.00035)), R(2), dt);
     {
         const R Fn = R(1e-12) * Vrel * Irel - R(5e-13) / Fc * (R(0.5) * ICaL - R(0.2) * INaCa) * Cm;
         const R su = logistic(-(Fn - R(3.4175e-13)) * R(1.0 / 13.67e-16));
-        x[13 * st] = rush_larsen(u, su, R(8), dt);
+        xo[13 * so] = rush_larsen(u, su, R(8), dt);
         const R vinf = R(1) - logistic(-(Fn - R(6.835e-14)) * R(1.0 / 13.67e-16));
-        x[14 * st] = rush_larsen(vv, vinf, R(1.91) + R(2.09) * su, dt);
+        xo[14 * so] = rush_larsen(vv, vinf, R(1.91) + R(2.09) * su, dt);
         const R yw = (V - R(7.9)) * R(0.2);
         const R g = yw == R(0) ? R(1) : -fexpm1(-yw) / yw;
         const R tau = R(6) * g / (R(5) * (R(1) + R(0.3) * fexp(-yw)));
-        x[15 * st] = rush_larsen(w, R(1) - logistic(-(V - R(40)) * R(1.0 / 17.0)), tau, dt);
+        xo[15 * so] = rush_larsen(w, R(1) - logistic(-(V - R(40)) * R(1.0 / 17.0)), tau, dt);
     }
 
     // ---- concentrations ----
-    x[0] = Cai + dt * rt(3, B1 / B2);
-    Nai_a.store_add(a, dt * rt(1, dNai));
-    Ki_a.store_add(a + st, dt * rt(2, dKi));
-    Caup_a.store_add(a + 2 * st, dt * rt(4, dCaup));
-    Carel_a.store_add(a + 3 * st, dt * rt(5, dCarel));
+    xo[0] = Cai + dt * rt(3, B1 / B2);
+    Nai_a.store_add(ao, dt * rt(1, dNai));
+    Ki_a.store_add(ao + so, dt * rt(2, dKi));
+    Caup_a.store_add(ao + 2 * so, dt * rt(4, dCaup));
+    Carel_a.store_add(ao + 3 * so, dt * rt(5, dCarel));
     return Iion;
 }
 

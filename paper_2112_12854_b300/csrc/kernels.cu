@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "crncell.cuh"
 #include "kernels.h"
@@ -22,6 +23,14 @@
 #include "varmap.h"
 
 namespace ep {
+
+// In-place state access of local cell i of a region.
+template <class R>
+__device__ __forceinline__ CellIO<R> region_io(const DevRegion &rg, long long i) {
+    R *x = static_cast<R *>(rg.r) + i;
+    double *a = rg.a + i;
+    return CellIO<R>{x, a, rg.stride, x, a, rg.stride};
+}
 
 template <class R> struct Vec4T;
 template <> struct Vec4T<float> { using type = float4; };
@@ -104,50 +113,71 @@ __device__ void junction_cell_crossing(const DevJob &J, long long c, long long n
     }
 }
 
+// Where a cell's streamed step inputs are read: straight from the job's
+// arrays in global memory, or from a shared-memory stage filled by bulk
+// copies (cell_kernel_staged). The gathered inputs (node values, neighbour
+// potentials) are always read from global memory.
+template <class R>
+struct CellSrc {
+    const int4 *na, *nb, *nc;
+    const typename Vec4T<R>::type *wa, *wb, *q;
+    const R *Vc;
+    const uint8_t *smask, *pset;
+    CellIO<R> io;
+};
+
+template <class R>
+__device__ __forceinline__ CellSrc<R> global_src(const DevJob &J, int model, long long c, const R *V) {
+    using R4 = typename Vec4T<R>::type;
+    const DevRegion &rg = J.reg[model];
+    return CellSrc<R>{J.nodes_a + c, J.nodes_b + c, J.nbr + c,
+                      static_cast<const R4 *>(J.wa) + c, static_cast<const R4 *>(J.wb) + c,
+                      static_cast<const R4 *>(J.q) + c, V + c, J.smask + c, J.pset + c,
+                      region_io<R>(rg, c - rg.off)};
+}
+
 // XD: the batch holds bidomain jobs, whose cells add L_i(v_e^n) (first line
 // of Eq. 6) to the diffusion term; AB2: the batch holds jobs that advance the
 // non-gating variables by second-order Adams-Bashforth. Batches without them
 // compile without the code.
 template <class R, bool XD = false, bool AB2 = false>
-__device__ __forceinline__ void cell_update(const DevJob &J, int model, long long c) {
+__device__ __forceinline__ void cell_update_from(const DevJob &J, int model, long long c, long long n, const R *V,
+                                                 const CellSrc<R> &src) {
     using R4 = typename Vec4T<R>::type;
-    const long long n = *J.step;
-    const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
     R *__restrict__ Vnext = static_cast<R *>(J.V[(n & 1) ^ 1]);
     const R *__restrict__ vn = static_cast<const R *>(J.vn);
-    const int4 na = J.nodes_a[c], nb = J.nodes_b[c], nc = J.nbr[c];
-    const R4 wa = static_cast<const R4 *>(J.wa)[c];
-    const R4 wb = static_cast<const R4 *>(J.wb)[c];
-    const R4 q = static_cast<const R4 *>(J.q)[c];
-    const R Vc = V[c];
+    const int4 na = *src.na, nb = *src.nb, nc = *src.nc;
+    const R4 wa = *src.wa;
+    const R4 wb = *src.wb;
+    const R4 q = *src.q;
+    const R Vc = *src.Vc;
     // diffusion term of Eq. 7 (S2 + S3 folded): eight node values, four neighbours
     R diff = wa.x * vn[na.x] + wa.y * vn[na.y] + wa.z * vn[na.z] + wa.w * vn[na.w];
     diff += wb.x * vn[nb.x] + wb.y * vn[nb.y] + wb.z * vn[nb.z] + wb.w * vn[nb.w];
     diff += q.x * (V[nc.x] - Vc) + q.y * (V[nc.y] - Vc) + q.z * (V[nc.z] - Vc) + q.w * (V[nc.w] - Vc);
     if (XD && J.xdiv) diff += static_cast<const R *>(J.xdiv)[c];
 
-    const unsigned mask = J.smask[c];
+    const unsigned mask = *src.smask;
     R is = mask ? stimulus<R>(J, mask, n) : R(0);
-    const unsigned ps = J.pset[c];
+    const unsigned ps = *src.pset;
     R ix = R(0);
     int jfirst = 0, jlast = 0;
     if (ps & kJunctionFlag) junction_cell_terms<R>(J, c, n, Vc, is, ix, jfirst, jlast);
     const DevParams &P = J.params[ps & (EP_MAX_PARAM_SETS - 1)];
     const R dt = pick<R>(J.dt, J.dt_f);
-    const DevRegion &rg = J.reg[model];
-    const long long li = c - rg.off;
     R iion;
     Rates<R, AB2> rt;
     if constexpr (AB2) {
         if (J.integrator == EP_INTEGRATOR_AB2) {
-            rt.h = static_cast<R *>(rg.h) + li;
+            const DevRegion &rg = J.reg[model];
+            rt.h = static_cast<R *>(rg.h) + (c - rg.off);
             rt.st = rg.stride;
             rt.on = n > J.ab2_from;
         }
     }
-    if (model == EP_TP06) iion = tt_step<R, false, AB2>(rg, li, P, Vc, dt, is, rt);
-    else if (model == EP_STEWART) iion = tt_step<R, true, AB2>(rg, li, P, Vc, dt, is, rt);
-    else iion = crn_step<R, AB2>(rg, li, P, Vc, dt, rt);
+    if (model == EP_TP06) iion = tt_step<R, false, AB2>(src.io, P, Vc, dt, is, rt);
+    else if (model == EP_STEWART) iion = tt_step<R, true, AB2>(src.io, P, Vc, dt, is, rt);
+    else iion = crn_step<R, AB2>(src.io, P, Vc, dt, rt);
     const R Vn = Vc + dt * rt(0, diff - iion - is - ix);
     Vnext[c] = Vn;
     if ((ps & kJunctionFlag) && J.g.two_way) junction_cell_crossing<R>(J, c, n, Vc, Vn, jfirst, jlast);
@@ -156,6 +186,13 @@ __device__ __forceinline__ void cell_update(const DevJob &J, int model, long lon
         R *act = static_cast<R *>(J.act);
         if (isinf(act[c])) act[c] = R(double(n) * J.dt) + dt * (th - Vc) / (Vn - Vc);
     }
+}
+
+template <class R, bool XD = false, bool AB2 = false>
+__device__ __forceinline__ void cell_update(const DevJob &J, int model, long long c) {
+    const long long n = *J.step;
+    const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
+    cell_update_from<R, XD, AB2>(J, model, c, n, V, global_src<R>(J, model, c, V));
 }
 
 // Conduction graph, part 1 (Sec. 3.2 / 3.3): the reaction of every graph node
@@ -188,9 +225,10 @@ __global__ void __launch_bounds__(kGraphThreads) graph_ionic_kernel(const DevJob
             const DevRegion &rg = G.reg[tl.model];
             const long long li = node - rg.off;
             R iion;
-            if (tl.model == EP_TP06) iion = tt_step<R, false>(rg, li, P, Vg, dt, is);
-            else if (tl.model == EP_STEWART) iion = tt_step<R, true>(rg, li, P, Vg, dt, is);
-            else iion = crn_step<R>(rg, li, P, Vg, dt);
+            const CellIO<R> io = region_io<R>(rg, li);
+            if (tl.model == EP_TP06) iion = tt_step<R, false>(io, P, Vg, dt, is);
+            else if (tl.model == EP_STEWART) iion = tt_step<R, true>(io, P, Vg, dt, is);
+            else iion = crn_step<R>(io, P, Vg, dt);
             static_cast<R *>(G.itot)[node] = iion + is + ix;
         }
     }
@@ -259,6 +297,213 @@ __global__ void __launch_bounds__(T, MINB) cell_kernel(const DevJob *__restrict_
     // Every block has read the step counters; the last one to finish advances them.
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(done, 1u);
+        if (prev == gridDim.x - 1) {
+            for (int j = 0; j < n_jobs; ++j) *jobs[j].step += 1;
+            *done = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Staged cell kernel (FP32, forward Euler). The streamed inputs of a tile --
+// its cells' vertex / opposite-vertex / neighbour indices, folded
+// coefficients, state arrays, accumulators, V and the stimulus / parameter
+// bytes, all contiguous runs -- are brought into shared memory by bulk
+// asynchronous copies (cp.async.bulk, the TMA engine) issued by one thread,
+// double-buffered: while the block computes tile k from one stage, the copies
+// of tile k+1 land in the other, so the cell updates do not wait on HBM
+// latency for their own data. Gathers (node values, neighbour potentials)
+// still go through L2. Arithmetic and results are those of cell_kernel.
+namespace staged {
+
+constexpr int kCells = kCellThreads;   // one tile: up to 256 consecutive cells of one model
+constexpr int kMaxR = 16, kMaxA = 4;   // state arrays of the largest model
+
+// STATE: the tile's state arrays and accumulators are staged too (the full
+// stage, two blocks per SM), or only its indices, coefficients, V and bytes
+// (a third of the size, three blocks per SM), the state being read directly.
+template <bool STATE> struct StageState;
+template <> struct StageState<true> {
+    float r[kMaxR][kCells];
+    double a[kMaxA][kCells];
+};
+template <> struct StageState<false> {};
+template <bool STATE>
+struct Stage : StageState<STATE> {
+    int4 na[kCells], nb[kCells], nc[kCells];
+    float4 wa[kCells], wb[kCells], q[kCells];
+    float V[kCells];
+    uint8_t smask[kCells], pset[kCells];
+};
+template <bool STATE>
+struct Shared {
+    Stage<STATE> st[2];
+    unsigned long long bar[2];
+    int flags[2];   // bit 0: V staged, bit 1: stimulus / parameter bytes staged
+};
+template <bool STATE> constexpr size_t smem_bytes() { return sizeof(Shared<STATE>); }
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s
+
+__device__ __forceinline__ unsigned s_addr(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void bar_init(unsigned long long *b) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(b)) : "memory");
+}
+__device__ __forceinline__ void bar_expect(unsigned long long *b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_try(unsigned long long *b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(s_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bytes: a multiple of 16; both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes, unsigned long long *b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(s_addr(dst)), "l"(src), "r"(bytes), "r"(s_addr(b))
+                 : "memory");
+}
+// Bounded wait on a stage's barrier; false (and the error flag set) past the limit.
+__device__ __forceinline__ bool bar_wait(unsigned long long *b, unsigned parity, unsigned *err) {
+    if (bar_try(b, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    while (!bar_try(b, parity)) {
+        if (now_ns() - t0 > kWaitLimitNs) {
+            atomicOr(err, 1u);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ unsigned r16(unsigned b) { return (b + 15u) & ~15u; }
+
+// Issue the copies of tile tl into stage s (one thread). The region arrays are
+// padded to a multiple of 64 cells and a tile starts at a multiple of 256
+// cells inside its region, so rounding their sizes up to 16 bytes stays in
+// bounds; V and the byte arrays are staged only when their runs are aligned.
+template <bool STATE>
+__device__ void issue(const DevJob &J, const Tile &tl, Stage<STATE> &S, unsigned long long *bar, int *flags, int nr,
+                      int nA) {
+    const long long c0 = tl.start;
+    const unsigned cnt = unsigned(tl.count);
+    const DevRegion &rg = J.reg[tl.model];
+    const long long i0 = c0 - rg.off;
+    const long long step = *J.step;
+    const float *V = static_cast<const float *>(J.V[step & 1]);
+    const bool sv = (c0 % 4 == 0) && (cnt % 4 == 0);
+    const bool sb = (c0 % 16 == 0) && (cnt % 16 == 0);
+    *flags = (sv ? 1 : 0) | (sb ? 2 : 0);
+    unsigned total = 6u * cnt * 16u;
+    if constexpr (STATE) total += unsigned(nr) * r16(cnt * 4u) + unsigned(nA) * r16(cnt * 8u);
+    if (sv) total += cnt * 4u;
+    if (sb) total += 2u * cnt;
+    bar_expect(bar, total);
+    bulk_copy(S.na, J.nodes_a + c0, cnt * 16u, bar);
+    bulk_copy(S.nb, J.nodes_b + c0, cnt * 16u, bar);
+    bulk_copy(S.nc, J.nbr + c0, cnt * 16u, bar);
+    bulk_copy(S.wa, static_cast<const float4 *>(J.wa) + c0, cnt * 16u, bar);
+    bulk_copy(S.wb, static_cast<const float4 *>(J.wb) + c0, cnt * 16u, bar);
+    bulk_copy(S.q, static_cast<const float4 *>(J.q) + c0, cnt * 16u, bar);
+    if constexpr (STATE) {
+        const float *r = static_cast<const float *>(rg.r) + i0;
+        for (int v = 0; v < nr; ++v) bulk_copy(S.r[v], r + v * rg.stride, r16(cnt * 4u), bar);
+        const double *a = rg.a + i0;
+        for (int k = 0; k < nA; ++k) bulk_copy(S.a[k], a + k * rg.stride, r16(cnt * 8u), bar);
+    }
+    if (sv) bulk_copy(S.V, V + c0, cnt * 4u, bar);
+    if (sb) {
+        bulk_copy(S.smask, J.smask + c0, cnt, bar);
+        bulk_copy(S.pset, J.pset + c0, cnt, bar);
+    }
+}
+
+}  // namespace staged
+
+template <bool XD, bool STATE>
+__global__ void __launch_bounds__(kCellThreads, STATE ? 2 : 3)
+    cell_kernel_staged(const DevJob *__restrict__ jobs, const Tile *__restrict__ tiles, int n_tiles, unsigned *done,
+                       int n_jobs, unsigned *err) {
+    using namespace staged;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Shared<STATE> &sh = *reinterpret_cast<Shared<STATE> *>(smem_raw);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        bar_init(&sh.bar[0]);
+        bar_init(&sh.bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int k = 0;
+    int t = blockIdx.x;
+    if (tid == 0 && t < n_tiles) {
+        const Tile tl = tiles[t];
+        issue(jobs[tl.job], tl, sh.st[0], &sh.bar[0], &sh.flags[0], model_nr(tl.model), model_na(tl.model));
+    }
+    bool ok = true;
+    for (; t < n_tiles; t += gridDim.x, ++k) {
+        const int s = k & 1;
+        // prefetch the next tile into the other stage (its readers finished at the last barrier)
+        const int tn = t + gridDim.x;
+        if (tid == 0 && tn < n_tiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const Tile tl = tiles[tn];
+            issue(jobs[tl.job], tl, sh.st[s ^ 1], &sh.bar[s ^ 1], &sh.flags[s ^ 1], model_nr(tl.model),
+                  model_na(tl.model));
+        }
+        // every thread waits (acquiring the copied data); the block then agrees on the outcome
+        const bool arrived = bar_wait(&sh.bar[s], unsigned((k >> 1) & 1), err);
+        if (!__syncthreads_and(arrived)) {
+            ok = false;
+            break;
+        }
+        const Tile tl = tiles[t];
+        const DevJob &J = jobs[tl.job];
+        const Stage<STATE> &S = sh.st[s];
+        const int fl = sh.flags[s];
+        if (tid < tl.count) {
+            const long long c = (long long)tl.start + tid;
+            const long long n = *J.step;
+            const float *V = static_cast<const float *>(J.V[n & 1]);
+            const DevRegion &rg = J.reg[tl.model];
+            const long long li = c - rg.off;
+            CellIO<float> io = region_io<float>(rg, li);
+            if constexpr (STATE) {
+                io.xi = &S.r[0][tid];
+                io.ai = &S.a[0][tid];
+                io.si = kCells;
+            }
+            CellSrc<float> src{S.na + tid, S.nb + tid, S.nc + tid, S.wa + tid, S.wb + tid, S.q + tid,
+                               (fl & 1) ? S.V + tid : V + c, (fl & 2) ? S.smask + tid : J.smask + c,
+                               (fl & 2) ? S.pset + tid : J.pset + c, io};
+            cell_update_from<float, XD, false>(J, tl.model, c, n, V, src);
+        }
+        __syncthreads();
+    }
+    if (!ok && tid == 0) {
+        // a copy did not complete in time: wait (bounded) for the copies still in flight --
+        // tile k's and, if issued, tile k+1's -- before the block's shared memory is released
+        bar_wait(&sh.bar[k & 1], unsigned((k >> 1) & 1), err);
+        if (t + int(gridDim.x) < n_tiles) bar_wait(&sh.bar[(k + 1) & 1], unsigned(((k + 1) >> 1) & 1), err);
+    }
+    // Every block has read the step counters; the last one to finish advances them.
+    __syncthreads();
+    if (tid == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(done, 1u);
         if (prev == gridDim.x - 1) {
@@ -442,8 +687,48 @@ static void launch_cell_kernel(const StepLaunch &L, cudaStream_t s) {
     k<<<L.cell_grid, T, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done, L.n_jobs);
 }
 
+// The staged kernel needs more than the default 48 KB of dynamic shared memory.
+static cudaError_t staged_attributes() {
+    static std::once_flag once;
+    static cudaError_t rc = cudaSuccess;
+    std::call_once(once, [] {
+        const int full = int(staged::smem_bytes<true>()), part = int(staged::smem_bytes<false>());
+        rc = cudaFuncSetAttribute(cell_kernel_staged<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, full);
+        if (rc == cudaSuccess)
+            rc = cudaFuncSetAttribute(cell_kernel_staged<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, full);
+        if (rc == cudaSuccess)
+            rc = cudaFuncSetAttribute(cell_kernel_staged<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      part);
+        if (rc == cudaSuccess)
+            rc = cudaFuncSetAttribute(cell_kernel_staged<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      part);
+    });
+    return rc;
+}
+
+template <bool STATE>
+static void launch_staged(const StepLaunch &L, cudaStream_t s) {
+    auto *k = L.bido ? cell_kernel_staged<true, STATE> : cell_kernel_staged<false, STATE>;
+    k<<<L.cell_grid, kCellThreads, staged::smem_bytes<STATE>(), s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done,
+                                                                     L.n_jobs, L.err);
+}
+
 template <class R>
 static cudaError_t cell_launch_variant(const StepLaunch &L, cudaStream_t s) {
+    if (L.cell_variant >= kStagedVariant) {
+        if constexpr (std::is_same<R, float>::value) {
+            if (!L.ab2) {
+                cudaError_t e = staged_attributes();
+                if (e != cudaSuccess) return e;
+                if (L.cell_variant == kStagedVariant) launch_staged<true>(L, s);
+                else launch_staged<false>(L, s);
+                return cudaGetLastError();
+            }
+        }
+        StepLaunch L0 = L;   // FP64 or AB2: the plain variant 0
+        L0.cell_variant = 0;
+        return cell_launch_variant<R>(L0, s);
+    }
     switch (L.cell_variant) {
 #define EP_CELL_CASE(k, T, B)                                                                                  \
     case k:                                                                                                    \
@@ -464,6 +749,18 @@ cudaError_t launch_cell(int precision, const StepLaunch &L, cudaStream_t s) {
 template <class R>
 static int cell_blocks_variant(int variant) {
     int nb = 0;
+    if (variant >= kStagedVariant) {
+        if (std::is_same<R, float>::value && staged_attributes() == cudaSuccess) {
+            if (variant == kStagedVariant)
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_kernel_staged<false, true>, kCellThreads,
+                                                              staged::smem_bytes<true>());
+            else
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_kernel_staged<false, false>, kCellThreads,
+                                                              staged::smem_bytes<false>());
+        }
+        if (nb >= 1) return nb;
+        variant = 0;
+    }
     switch (variant) {
 #define EP_CELL_CASE(k, T, B)                                                                 \
     case k:                                                                                   \
@@ -476,6 +773,7 @@ static int cell_blocks_variant(int variant) {
 }
 
 int cell_variant_threads(int variant) {
+    if (variant >= kStagedVariant) return kCellThreads;
     switch (variant) {
 #define EP_CELL_CASE(k, T, B) \
     case k:                   \

@@ -22,6 +22,7 @@ struct StepLaunch {
     int graph_substeps;        // largest substep count of the jobs' graphs
     int bido;                  // some job is bidomain (cell kernel adds DevJob::xdiv)
     int ab2;                   // some job integrates by AB2 (cell kernel keeps rate histories)
+    unsigned *err;             // device error word of the context (bounded waits that gave up)
 };
 
 // Launch shapes of the cell kernel: (index, threads per block, minimum
@@ -33,7 +34,12 @@ struct StepLaunch {
     X(3, 128, 5)            \
     X(4, 128, 6)            \
     X(5, 64, 12)
-constexpr int kNumCellVariants = 6;
+// Variants 6 and 7: cell_kernel_staged (FP32 forward Euler, 256 threads;
+// streamed inputs staged by bulk copies: 6 everything, two blocks per SM;
+// 7 indices / coefficients / V / bytes, three blocks per SM); for FP64 or
+// AB2 batches they run variant 0.
+constexpr int kNumCellVariants = 8;
+constexpr int kStagedVariant = 6;
 int cell_variant_threads(int variant);
 
 // One time step of every job in the table: node values, the conduction

@@ -23,15 +23,18 @@ constexpr int kTTnr = 15, kSTWnr = 16, kTTna = 3;
 
 // Returns I_ion(V^n, s^n) in uA/uF and writes s^{n+1} (all but V).
 template <class R, bool PURKINJE, bool AB2 = false>
-__device__ __forceinline__ R tt_step(const DevRegion &rg, long long i, const DevParams &P, R V, R dt,
-                                     R i_stim, const Rates<R, AB2> &rt = Rates<R, AB2>{}) {
-    R *x = static_cast<R *>(rg.r) + i;
-    double *a = rg.a + i;
-    const long long st = rg.stride;
-    const R Cai = x[0], Cass = x[st], m = x[2 * st], h = x[3 * st], jj = x[4 * st];
-    const R xr1 = x[5 * st], xr2 = x[6 * st], xs = x[7 * st], r = x[8 * st], s = x[9 * st];
-    const R d = x[10 * st], f = x[11 * st], f2 = x[12 * st], fcass = x[13 * st], rr = x[14 * st];
-    const Accum<R> Nai_a = Accum<R>::load(a), Ki_a = Accum<R>::load(a + st), Casr_a = Accum<R>::load(a + 2 * st);
+__device__ __forceinline__ R tt_step(const CellIO<R> &io, const DevParams &P, R V, R dt, R i_stim,
+                                     const Rates<R, AB2> &rt = Rates<R, AB2>{}) {
+    const R *xi = io.xi;
+    const double *ai = io.ai;
+    const long long si = io.si;
+    R *xo = io.xo;
+    double *ao = io.ao;
+    const long long so = io.so;
+    const R Cai = xi[0], Cass = xi[si], m = xi[2 * si], h = xi[3 * si], jj = xi[4 * si];
+    const R xr1 = xi[5 * si], xr2 = xi[6 * si], xs = xi[7 * si], r = xi[8 * si], s = xi[9 * si];
+    const R d = xi[10 * si], f = xi[11 * si], f2 = xi[12 * si], fcass = xi[13 * si], rr = xi[14 * si];
+    const Accum<R> Nai_a = Accum<R>::load(ai), Ki_a = Accum<R>::load(ai + si), Casr_a = Accum<R>::load(ai + 2 * si);
     const R Nai = Nai_a.value(), Ki = Ki_a.value(), Casr = Casr_a.value();
 
     // constants (model papers' parameter tables)
@@ -89,7 +92,7 @@ __device__ __forceinline__ R tt_step(const DevRegion &rg, long long i, const Dev
     R Iion = INa + IK1 + Ito + IKr + IKs + ICaL + INaCa + INaK + IpCa + IpK + IbNa + IbCa;
     R IfNa = R(0), IfK = R(0), Isus = R(0), y = R(0);
     if (PURKINJE) {
-        y = x[15 * st];
+        y = xi[15 * si];
         IfNa = y * R(0.0145654) * (V - ENa);
         IfK = y * R(0.0234346) * (V - EK);
         Isus = R(0.0227) * logistic((R(5) - V) * R(1.0 / 17.0)) * (V - EK);
@@ -117,7 +120,7 @@ __device__ __forceinline__ R tt_step(const DevRegion &rg, long long i, const Dev
         yinf = R(1) / (e * e);
         al = logistic((R(-60) - V) * R(0.2));
         be = R(0.1) * logistic((V + R(35)) * R(0.2)) + R(0.1) * logistic((V - R(50)) * R(0.005));
-        x[2 * st] = rush_larsen(m, yinf, al * be, dt);
+        xo[2 * so] = rush_larsen(m, yinf, al * be, dt);
     }
     {
         const R e = R(1) + fexp((V + R(71.55)) * R(1.0 / 7.43));
@@ -135,32 +138,32 @@ __device__ __forceinline__ R tt_step(const DevRegion &rg, long long i, const Dev
                  logistic(R(0.311) * (V + R(79.23)));
             bj = R(0.02424) * fexp(R(-0.01052) * V) * logistic(R(-0.1378) * (V + R(40.14)));
         }
-        x[3 * st] = rush_larsen(h, hinf, R(1) / (ah + bh), dt);
-        x[4 * st] = rush_larsen(jj, hinf, R(1) / (aj + bj), dt);
+        xo[3 * so] = rush_larsen(h, hinf, R(1) / (ah + bh), dt);
+        xo[4 * so] = rush_larsen(jj, hinf, R(1) / (aj + bj), dt);
     }
     yinf = logistic((R(-26) - V) * R(1.0 / 7.0));
     al = R(450) * logistic((R(-45) - V) * R(0.1));
     be = R(6) * logistic((V + R(30)) * R(1.0 / 11.5));
-    x[5 * st] = rush_larsen(xr1, yinf, al * be, dt);
+    xo[5 * so] = rush_larsen(xr1, yinf, al * be, dt);
     yinf = logistic((V + R(88)) * R(1.0 / 24.0));
     al = R(3) * logistic((R(-60) - V) * R(0.05));
     be = R(1.12) * logistic((V - R(60)) * R(0.05));
-    x[6 * st] = rush_larsen(xr2, yinf, al * be, dt);
+    xo[6 * so] = rush_larsen(xr2, yinf, al * be, dt);
     yinf = logistic((R(-5) - V) * R(1.0 / 14.0));
     al = R(1400) / fsqrt(R(1) + fexp((R(5) - V) * R(1.0 / 6.0)));
     be = logistic((V - R(35)) * R(1.0 / 15.0));
-    x[7 * st] = rush_larsen(xs, yinf, al * be + R(80), dt);
+    xo[7 * so] = rush_larsen(xs, yinf, al * be + R(80), dt);
     if (PURKINJE) {
         yinf = logistic((R(20) - V) * R(1.0 / 13.0));
         tau = R(10.45) * fexp(-(V + R(40)) * (V + R(40)) * R(1.0 / 1800.0)) + R(7.3);
-        x[8 * st] = rush_larsen(r, yinf, tau, dt);
+        xo[8 * so] = rush_larsen(r, yinf, tau, dt);
         yinf = logistic((V + R(27)) * R(1.0 / 13.0));
         tau = R(85) * fexp(-(V + R(25)) * (V + R(25)) * R(1.0 / 320.0)) + R(5) * logistic((V - R(40)) * R(0.2)) + R(42);
-        x[9 * st] = rush_larsen(s, yinf, tau, dt);
+        xo[9 * so] = rush_larsen(s, yinf, tau, dt);
     } else {
         yinf = logistic((R(20) - V) * R(1.0 / 6.0));
         tau = R(9.5) * fexp(-(V + R(40)) * (V + R(40)) * R(1.0 / 1800.0)) + R(0.8);
-        x[8 * st] = rush_larsen(r, yinf, tau, dt);
+        xo[8 * so] = rush_larsen(r, yinf, tau, dt);
         if (P.variant == 2) {
             yinf = logistic((V + R(28)) * R(0.2));
             tau = R(1000) * fexp(-(V + R(67)) * (V + R(67)) * R(0.001)) + R(8);
@@ -168,41 +171,41 @@ __device__ __forceinline__ R tt_step(const DevRegion &rg, long long i, const Dev
             yinf = logistic((V + R(20)) * R(0.2));
             tau = R(85) * fexp(-(V + R(45)) * (V + R(45)) * R(1.0 / 320.0)) + R(5) * logistic((V - R(20)) * R(0.2)) + R(3);
         }
-        x[9 * st] = rush_larsen(s, yinf, tau, dt);
+        xo[9 * so] = rush_larsen(s, yinf, tau, dt);
     }
     yinf = logistic((R(-8) - V) * R(1.0 / 7.5));
     al = R(1.4) * logistic((R(-35) - V) * R(1.0 / 13.0)) + R(0.25);
     be = R(1.4) * logistic((V + R(5)) * R(0.2));
-    x[10 * st] = rush_larsen(d, yinf, al * be + logistic((R(50) - V) * R(0.05)), dt);
+    xo[10 * so] = rush_larsen(d, yinf, al * be + logistic((R(50) - V) * R(0.05)), dt);
     yinf = logistic((V + R(20)) * R(1.0 / 7.0));
     tau = R(1102.5) * fexp(-(V + R(27)) * (V + R(27)) * R(1.0 / 225.0)) + R(200) * logistic((R(13) - V) * R(0.1)) +
           R(180) * logistic((V + R(30)) * R(0.1)) + R(20);
-    x[11 * st] = rush_larsen(f, yinf, tau, dt);
+    xo[11 * so] = rush_larsen(f, yinf, tau, dt);
     yinf = R(0.67) * logistic((V + R(35)) * R(1.0 / 7.0)) + R(0.33);
     tau = R(562) * fexp(-(V + R(27)) * (V + R(27)) * R(1.0 / 240.0)) + R(31) * logistic((R(25) - V) * R(0.1)) +
           R(80) * logistic((V + R(30)) * R(0.1));
-    x[12 * st] = rush_larsen(f2, yinf, tau, dt);
+    xo[12 * so] = rush_larsen(f2, yinf, tau, dt);
     {
         const R cr = Cass * R(20);  // Ca_SS / 0.05
         const R den = R(1) / (R(1) + cr * cr);
-        x[13 * st] = rush_larsen(fcass, R(0.6) * den + R(0.4), R(80) * den + R(2), dt);
+        xo[13 * so] = rush_larsen(fcass, R(0.6) * den + R(0.4), R(80) * den + R(2), dt);
     }
     {
         const R rate = k2 * Cass + R(0.005);
-        x[14 * st] = rush_larsen(rr, R(0.005) / rate, R(1) / rate, dt);
+        xo[14 * so] = rush_larsen(rr, R(0.005) / rate, R(1) / rate, dt);
     }
     if (PURKINJE) {
         yinf = logistic((V + R(80.6)) * R(1.0 / 6.8));
         tau = R(4000) / (fexp(R(-2.9) - R(0.04) * V) + fexp(R(3.6) + R(0.11) * V));
-        x[15 * st] = rush_larsen(y, yinf, tau, dt);
+        xo[15 * so] = rush_larsen(y, yinf, tau, dt);
     }
 
     // ---- concentrations ----
-    x[0] = Cai + buffered_increment(Cai, dt * rt(3, dCai_tot), R(0.2), R(0.001));
-    x[st] = Cass + buffered_increment(Cass, dt * rt(5, dCass_tot), R(0.4), R(0.00025));
-    Nai_a.store_add(a, dt * rt(1, dNai));
-    Ki_a.store_add(a + st, dt * rt(2, dKi));
-    Casr_a.store_add(a + 2 * st, buffered_increment(Casr, dt * rt(4, dCasr_tot), R(10), R(0.3)));
+    xo[0] = Cai + buffered_increment(Cai, dt * rt(3, dCai_tot), R(0.2), R(0.001));
+    xo[so] = Cass + buffered_increment(Cass, dt * rt(5, dCass_tot), R(0.4), R(0.00025));
+    Nai_a.store_add(ao, dt * rt(1, dNai));
+    Ki_a.store_add(ao + so, dt * rt(2, dKi));
+    Casr_a.store_add(ao + 2 * so, buffered_increment(Casr, dt * rt(4, dCasr_tot), R(10), R(0.3)));
     return Iion;
 }
 

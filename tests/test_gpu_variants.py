@@ -48,3 +48,50 @@ def test_autotune_steps_are_real_steps():
     b.step(4 * ep.N_CELL_VARIANTS + 50)
     assert np.array_equal(a.V, b.V)
     ctx.close()
+
+
+@pytest.mark.parametrize("pname", ["mixed", "plain"])
+def test_variants_bitwise_on_mixed_models_and_graph(pname):
+    """All launch variants, including the staged kernel (bulk-copied tiles,
+    with its fallbacks for region starts and ragged tails that are not
+    16-byte aligned), on TP06 / Courtemanche / Stewart regions of uneven size
+    with a conduction graph and junction cells. The full staged kernel and
+    the 128-register shapes agree bitwise; under the tighter register limits
+    of the 80- and 96-register shapes the compiled Courtemanche arithmetic
+    can round differently in the last bits, so those are held to 1e-4 mV."""
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2112_12854_b300 import ep
+    prec = ep.EP_FP32_MIXED if pname == "mixed" else ep.EP_FP64_PLAIN
+    xyz, tets = w.kuhn_box(10, 7, 3, 0.25)
+    n = tets.shape[0]
+    c = w.tet_centroids(xyz, tets)
+    ps = np.where(np.arange(n) < 421, 0, np.where(np.arange(n) < 899, 1, 2)).astype(np.uint8)
+    case = w.TissueCase("slab", xyz, tets, w.fibres_uniform(n), ps, (c[:, 0] < 0.6).astype(np.uint8),
+                        [w.ParamSet(model=0), w.ParamSet(model=1), w.ParamSet(model=2)],
+                        [w.Stimulus(-80.0, 0.0, 1.0)], 0.02, 0, -20.0)
+    g = w.chain_graph(30, 0.2, start=(0.0, 1.0, 0.4), param_set=2, stim_nodes=0)
+    g.junction_node = np.array([29], np.int32)
+    g.junction_cell = np.array([int(np.argmin(np.linalg.norm(c - g.xyz[29], axis=1)))], np.int32)
+    g.junction_mode = np.array([w.JUNC_RESISTIVE], np.uint8)
+    g.params = w.GraphParams(g_cell=4.0)
+    ctx = ep.Context()
+    ref = None
+    for v in range(ep.N_CELL_VARIANTS):
+        ep.set_cell_variant(ctx, prec, v)
+        j = ep.job_from_case(ctx, case, precision=prec)
+        j.attach_graph(g, node_model=np.full(30, 2, np.uint8))
+        j.step(150)
+        state = [j.read(k, model=m) for m in range(3) for k in range(len(ep.model_varnames(m)))]
+        state += [j.activation_times(), j.graph_read(0, model=2)]
+        if ref is None:
+            ref = state
+        else:
+            for a, b in zip(state, ref):
+                if v in (2, 6):
+                    assert np.array_equal(a, b, equal_nan=True), v
+                else:
+                    assert np.allclose(a, b, rtol=1e-5, atol=1e-4, equal_nan=True), v
+        assert j.check_finite()
+        j.destroy()
+    ctx.close()
