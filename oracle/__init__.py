@@ -25,7 +25,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
-SOURCES = ["fv3d.c", "tp06.c", "crn.c", "stewart.c", "tissue.c", "purkinje.c"]
+SOURCES = ["fv3d.c", "fv2d.c", "tp06.c", "crn.c", "stewart.c", "tissue.c", "purkinje.c"]
 
 TP06, CRN, STEWART = 0, 1, 2
 MAXVAR = 24
@@ -105,6 +105,17 @@ def lib():
         L.orc_sim_create.argtypes = [ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P, _P,
                                      ctypes.c_int, _P, ctypes.c_int, _P,
                                      ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
+        L.orc_sim_create2.restype = _P
+        L.orc_sim_create2.argtypes = [ctypes.c_int64, _P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P, _P,
+                                      ctypes.c_int, _P, ctypes.c_int, _P,
+                                      ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
+        L.orc_shell_create.restype = _P
+        L.orc_shell_create.argtypes = [ctypes.c_int64, _P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_int)]
+        L.orc_shell_destroy.argtypes = [_P]
+        L.orc_shell_node_values.argtypes = [_P, _P, _P]
+        L.orc_shell_gradients.argtypes = [_P, _P, _P]
+        L.orc_shell_diffusion.argtypes = [_P, _P, _P, _P]
+        L.orc_shell_cell_info.argtypes = [_P, _P, _P, _P]
         L.orc_sim_destroy.argtypes = [_P]
         L.orc_sim_run.argtypes = [_P, ctypes.c_int64]
         L.orc_sim_step_index.restype = ctypes.c_int64
@@ -206,6 +217,53 @@ class Mesh:
         return out
 
 
+class Shell:
+    """Oracle geometry of a triangle surface (the Purkinje shell) and its
+    diffusion operator (see ``fv2d.c``)."""
+
+    def __init__(self, xyz, tris):
+        self.xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        self.tris = np.ascontiguousarray(tris, dtype=np.int32)
+        err = ctypes.c_int(0)
+        self._h = lib().orc_shell_create(self.xyz.shape[0], _ptr(self.xyz), self.tris.shape[0], _ptr(self.tris),
+                                         ctypes.byref(err))
+        if not self._h:
+            raise ValueError(f"oracle shell rejected (code {err.value})")
+        self.n_cells = self.tris.shape[0]
+        self.n_nodes = self.xyz.shape[0]
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().orc_shell_destroy(self._h)
+            self._h = None
+
+    def cell_info(self):
+        c = np.zeros((self.n_cells, 3))
+        a = np.zeros(self.n_cells)
+        nb = np.zeros((self.n_cells, 3), np.int32)
+        lib().orc_shell_cell_info(self._h, _ptr(c), _ptr(a), _ptr(nb))
+        return c, a, nb
+
+    def node_values(self, v):
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        out = np.zeros(self.n_nodes)
+        lib().orc_shell_node_values(self._h, _ptr(v), _ptr(out))
+        return out
+
+    def cell_gradients(self, vn):
+        vn = np.ascontiguousarray(vn, dtype=np.float64)
+        out = np.zeros((self.n_cells, 3))
+        lib().orc_shell_gradients(self._h, _ptr(vn), _ptr(out))
+        return out
+
+    def diffusion(self, D, v):
+        D = np.ascontiguousarray(np.broadcast_to(np.asarray(D, np.float64).reshape(-1, 9), (self.n_cells, 9)))
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        out = np.zeros(self.n_cells)
+        lib().orc_shell_diffusion(self._h, _ptr(D), _ptr(v), _ptr(out))
+        return out
+
+
 def model_nvar(model: int) -> int:
     return int(lib().orc_model_nvar(model))
 
@@ -271,14 +329,16 @@ class Sim:
         ns = len(case.stimuli)
         self.stims = (Stim * max(ns, 1))(*[_stim(s) for s in case.stimuli])
         err = ctypes.c_int(0)
-        self._h = lib().orc_sim_create(self.xyz.shape[0], _ptr(self.xyz), self.tets.shape[0],
-                                       _ptr(self.tets), _ptr(self.fibre), _ptr(self.pset),
-                                       _ptr(self.smask), len(case.param_sets),
-                                       ctypes.cast(self.sets, _P), ns, ctypes.cast(self.stims, _P),
-                                       float(case.dt), float(case.threshold), ctypes.byref(err))
+        tris = getattr(case, "tris", None)
+        self.tris = np.ascontiguousarray(tris if tris is not None else np.zeros((0, 3)), dtype=np.int32)
+        self._h = lib().orc_sim_create2(self.xyz.shape[0], _ptr(self.xyz), self.tets.shape[0],
+                                        _ptr(self.tets), self.tris.shape[0], _ptr(self.tris), _ptr(self.fibre),
+                                        _ptr(self.pset), _ptr(self.smask), len(case.param_sets),
+                                        ctypes.cast(self.sets, _P), ns, ctypes.cast(self.stims, _P),
+                                        float(case.dt), float(case.threshold), ctypes.byref(err))
         if not self._h:
             raise ValueError(f"oracle simulation rejected (code {err.value})")
-        self.n_cells = self.tets.shape[0]
+        self.n_cells = self.tets.shape[0] + self.tris.shape[0]
 
     def __del__(self):
         if getattr(self, "_h", None):

@@ -21,6 +21,7 @@
  *   - the stimulus of Eq. 4 and the activation time (first upward crossing of
  *     a threshold, Sec. 4);
  *   - the 1D vertex-based FV Purkinje graph and its junctions (Sec. 3.2, 3.3);
+ *   - the 2D Purkinje shell: triangles with the same cell-centred scheme (Sec. 2, 3.2);
  *   - the bidomain model (Eqs. 1, 5-6): the extracellular potential from the
  *     elliptic equation by restarted GMRES warm-started from the last step.
  *
@@ -95,6 +96,15 @@ void orc_cell_run(const orc_cellparams *p, double dt, int64_t n_steps,
                   const orc_stim *stim, int64_t record_every, double *v_out,
                   double *state_inout, int ab2);
 
+/* ---- the 2D Purkinje shell: triangles in 3D space (fv2d.c) ---- */
+typedef struct orc_shell orc_shell;
+orc_shell *orc_shell_create(int64_t n_nodes, const double *xyz, int64_t n_cells, const int32_t *tri, int *err);
+void orc_shell_destroy(orc_shell *s);
+void orc_shell_node_values(const orc_shell *s, const double *v, double *vn);
+void orc_shell_gradients(const orc_shell *s, const double *vn, double *grad);
+void orc_shell_diffusion(const orc_shell *s, const double *D, const double *v, double *out);
+void orc_shell_cell_info(const orc_shell *s, double *centroid, double *area, int32_t *neighbour);
+
 /* ---- tissue simulation (tissue.c) ---- */
 typedef struct orc_sim orc_sim;
 orc_sim *orc_sim_create(int64_t n_nodes, const double *xyz, int64_t n_cells,
@@ -103,6 +113,12 @@ orc_sim *orc_sim_create(int64_t n_nodes, const double *xyz, int64_t n_cells,
                         int n_sets, const orc_cellparams *sets,
                         int n_stim, const orc_stim *stim,
                         double dt, double threshold, int *err);
+orc_sim *orc_sim_create2(int64_t n_nodes, const double *xyz, int64_t n_tets,
+                         const int32_t *tet, int64_t n_tris, const int32_t *tri, const double *fibre,
+                         const uint8_t *param_set, const uint8_t *stim_mask,
+                         int n_sets, const orc_cellparams *sets,
+                         int n_stim, const orc_stim *stim,
+                         double dt, double threshold, int *err);
 void orc_sim_destroy(orc_sim *s);
 int orc_set_threads(int n);
 void orc_sim_run(orc_sim *s, int64_t n_steps);

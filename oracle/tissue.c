@@ -135,6 +135,9 @@ struct orc_sim {
     orc_graph *g;              /* optional conduction graph */
     double *i_extra, *s_extra, *vg_old, *v_new;
     double *fibre;             /* [n_cells][3] */
+    int64_t n_tets;            /* cells [0, n_tets) are tetrahedra, the rest shell triangles */
+    orc_shell *shell;
+    double *xyz;               /* node coordinates (kept for the shell) */
     int integrator;            /* 0 forward Euler, 1 AB2 for the non-gating variables */
     int64_t ab2_from;          /* step whose rates start the AB2 history (forward Euler there) */
     double *hist;              /* [n_cells][ORC_NHIST] */
@@ -149,19 +152,39 @@ struct orc_sim {
 
 static void bidomain_solve(orc_sim *s);
 
-orc_sim *orc_sim_create(int64_t n_nodes, const double *xyz, int64_t n_cells,
-                        const int32_t *tet, const double *fibre,
-                        const uint8_t *param_set, const uint8_t *stim_mask,
-                        int n_sets, const orc_cellparams *sets,
-                        int n_stim, const orc_stim *stim,
-                        double dt, double threshold, int *err) {
-    if (n_sets < 1 || n_sets > 256 || n_stim < 0 || n_stim > 8) { *err = 10; return NULL; }
+/* Cells 0 .. n_tets-1 are the tetrahedra, n_tets .. n_tets+n_tris-1 the
+ * triangles of the Purkinje shell (fv2d.c); per-cell arrays cover both. The
+ * two media share no face: they exchange current only through junctions. */
+orc_sim *orc_sim_create2(int64_t n_nodes, const double *xyz, int64_t n_tets,
+                         const int32_t *tet, int64_t n_tris, const int32_t *tri, const double *fibre,
+                         const uint8_t *param_set, const uint8_t *stim_mask,
+                         int n_sets, const orc_cellparams *sets,
+                         int n_stim, const orc_stim *stim,
+                         double dt, double threshold, int *err) {
+    const int64_t n_cells = n_tets + n_tris;
+    if (n_sets < 1 || n_sets > 256 || n_stim < 0 || n_stim > 8 || n_cells < 1) { *err = 10; return NULL; }
     for (int64_t c = 0; c < n_cells; ++c)
         if (param_set[c] >= n_sets) { *err = 11; return NULL; }
-    orc_mesh *m = orc_mesh_create(n_nodes, xyz, n_cells, tet, err);
-    if (!m) return NULL;
+    orc_mesh *m = NULL;
+    if (n_tets > 0) {
+        m = orc_mesh_create(n_nodes, xyz, n_tets, tet, err);
+        if (!m) return NULL;
+    }
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     s->m = m;
+    s->n_tets = n_tets;
+    if (n_tris > 0) {
+        s->xyz = (double *)malloc(sizeof(double) * 3 * n_nodes);
+        memcpy(s->xyz, xyz, sizeof(double) * 3 * n_nodes);
+        s->shell = orc_shell_create(n_nodes, s->xyz, n_tris, tri, err);
+        if (!s->shell) {
+            *err += 20;
+            orc_mesh_destroy(m);
+            free(s->xyz);
+            free(s);
+            return NULL;
+        }
+    }
     s->n_cells = n_cells;
     s->pset = (uint8_t *)malloc(n_cells);
     memcpy(s->pset, param_set, n_cells);
@@ -194,9 +217,33 @@ orc_sim *orc_sim_create(int64_t n_nodes, const double *xyz, int64_t n_cells,
     return s;
 }
 
+orc_sim *orc_sim_create(int64_t n_nodes, const double *xyz, int64_t n_cells,
+                        const int32_t *tet, const double *fibre,
+                        const uint8_t *param_set, const uint8_t *stim_mask,
+                        int n_sets, const orc_cellparams *sets,
+                        int n_stim, const orc_stim *stim,
+                        double dt, double threshold, int *err) {
+    return orc_sim_create2(n_nodes, xyz, n_cells, tet, 0, NULL, fibre, param_set, stim_mask, n_sets, sets, n_stim,
+                           stim, dt, threshold, err);
+}
+
+/* The diffusion term of every cell: fv3d.c on the tetrahedra, fv2d.c on the shell. */
+static void sim_diffusion(const orc_sim *s, const double *D, const double *v, double *out) {
+    if (s->m) orc_diffusion(s->m, D, v, out);
+    if (s->shell) orc_shell_diffusion(s->shell, D + 9 * s->n_tets, v + s->n_tets, out + s->n_tets);
+}
+
+/* Centroids of all cells (tetrahedra, then shell triangles). */
+static void sim_centroids(const orc_sim *s, double *cen) {
+    if (s->m) orc_mesh_cell_info(s->m, cen, NULL, NULL);
+    if (s->shell) orc_shell_cell_info(s->shell, cen + 3 * s->n_tets, NULL, NULL);
+}
+
 void orc_sim_destroy(orc_sim *s) {
     if (!s) return;
     orc_mesh_destroy(s->m);
+    orc_shell_destroy(s->shell);
+    free(s->xyz);
     orc_graph_free(s->g);
     free(s->i_extra); free(s->s_extra); free(s->vg_old); free(s->v_new);
     free(s->pset); free(s->smask); free(s->state); free(s->D); free(s->act);
@@ -216,9 +263,9 @@ void orc_sim_run(orc_sim *s, int64_t n_steps) {
         if (s->ve) {
             /* bidomain: intracellular flux of V + v_e (first line of Eq. 6) */
             for (int64_t c = 0; c < s->n_cells; ++c) s->u[c] = s->v[c] + s->ve[c];
-            orc_diffusion(s->m, s->D, s->u, s->diff);
+            sim_diffusion(s, s->D, s->u, s->diff);
         } else {
-            orc_diffusion(s->m, s->D, s->v, s->diff);
+            sim_diffusion(s, s->D, s->v, s->diff);
         }
         if (s->g) {
             memset(s->i_extra, 0, sizeof(double) * s->n_cells);
@@ -264,7 +311,7 @@ int orc_sim_attach_graph(orc_sim *s, int64_t n, const double *xyz, int64_t n_edg
     orc_graph_params q = *p;
     q.act_threshold = s->theta;
     double *cen = (double *)malloc(sizeof(double) * 3 * s->n_cells);
-    orc_mesh_cell_info(s->m, cen, NULL, NULL);
+    sim_centroids(s, cen);
     int err = 0;
     orc_graph *g = orc_graph_build(n, xyz, n_edges, edges, edge_D, pset, smask, s->n_sets, s->sets, s->dt,
                                    n_junc, jnode, jcell, jmode, &q, s->n_cells, cen, &err);
@@ -330,7 +377,7 @@ void orc_sim_get_act(const orc_sim *s, double *out) {
 }
 
 void orc_sim_diffusion(const orc_sim *s, const double *v, double *out) {
-    orc_diffusion(s->m, s->D, v, out);
+    sim_diffusion(s, s->D, v, out);
 }
 
 const orc_mesh *orc_sim_mesh(const orc_sim *s) { return s->m; }
@@ -463,6 +510,7 @@ static void bidomain_solve(orc_sim *s) {
 int orc_sim_set_bidomain(orc_sim *s, const double *De_l, const double *De_t, double tol, int restart,
                          int64_t max_iter) {
     if (!(tol > 0.0) || restart < 1 || max_iter < 1) return 20;
+    if (s->shell || !s->m) return 21;   /* the Purkinje shell is a monodomain medium (Table 2) */
     const int64_t n = s->n_cells;
     free(s->ve); free(s->Die); free(s->u); free(s->rhs);
     s->ve = (double *)calloc(n, sizeof(double));

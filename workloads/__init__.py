@@ -67,6 +67,35 @@ def kuhn_box(nx: int, ny: int, nz: int, h: float,
     return xyz, tets.reshape(-1, 4).astype(np.int32)
 
 
+def tri_box(nx: int, ny: int, h: float, origin=(0.0, 0.0, 0.0)):
+    """Flat rectangle of nx x ny squares of side h in the z = origin[2] plane,
+    each split into two triangles along the same diagonal (the 2D Kuhn
+    split: every interior node has six triangles, centrally symmetric).
+    Returns (xyz [n_nodes, 3], tris [2 nx ny, 3] int32)."""
+    ox, oy, oz = origin
+    gx, gy = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="ij")
+    xyz = np.stack([ox + h * gx.ravel(), oy + h * gy.ravel(), np.full(gx.size, oz)], axis=1).astype(np.float64)
+    nid = lambda i, j: i * (ny + 1) + j
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij")
+    i, j = i.ravel(), j.ravel()
+    a, b, c, d = nid(i, j), nid(i + 1, j), nid(i + 1, j + 1), nid(i, j + 1)
+    tris = np.concatenate([np.stack([a, b, c], 1), np.stack([a, c, d], 1)]).astype(np.int32)
+    return xyz, tris
+
+
+def tri_cylinder(n_theta: int, n_z: int, radius: float, height: float, arc: float = np.pi):
+    """A curved shell: the part of a cylinder of the given radius spanning
+    `arc` radians and `height` mm, split like tri_box."""
+    xyz, tris = tri_box(n_theta, n_z, 1.0)
+    th = xyz[:, 0] / n_theta * arc
+    z = xyz[:, 1] / n_z * height
+    return np.stack([radius * np.cos(th), radius * np.sin(th), z], axis=1), tris
+
+
+def tri_centroids(xyz: np.ndarray, tris: np.ndarray) -> np.ndarray:
+    return xyz[tris].mean(axis=1)
+
+
 def tet_centroids(xyz: np.ndarray, tets: np.ndarray) -> np.ndarray:
     """Vertex mean of each tet; used only to select input regions."""
     return xyz[tets].mean(axis=1)
@@ -126,10 +155,19 @@ class TissueCase:
     n_steps: int
     threshold: float
     output_steps: list = field(default_factory=list)
+    tris: np.ndarray | None = None  # Purkinje-shell triangles (cells after the tets), or None
+
+    @property
+    def n_tets(self) -> int:
+        return int(self.tets.shape[0])
+
+    @property
+    def n_tris(self) -> int:
+        return 0 if self.tris is None else int(self.tris.shape[0])
 
     @property
     def n_cells(self) -> int:
-        return int(self.tets.shape[0])
+        return self.n_tets + self.n_tris
 
     @property
     def n_nodes(self) -> int:
