@@ -103,12 +103,19 @@ typedef void (*ep_free_fn)(void *ptr, size_t bytes, void *user);
 
 /* Mesh of one job. xyz: 3*n_nodes doubles (mm), node k at xyz[3k..3k+2].
  * tet: 4*n_cells node indices; either orientation is accepted (the library
- * orders each tet positively). cell_model: n_cells bytes, EP_TP06 / EP_CRN /
- * EP_STEWART, or NULL for all EP_TP06. param_set: n_cells bytes indexing
- * ep_params.sets, or NULL for all 0. stim_mask: n_cells bytes, bit k set
- * = stimulus protocol k covers the cell, or NULL for none. fibre: 3*n_cells
- * doubles, the fibre direction of each cell (need not be normalised), or
- * NULL for isotropic tissue with diffusivity D_l. */
+ * orders each tet positively). tri: 3*n_tris node indices of the 2D
+ * Purkinje shell's triangles (Sec. 2: a surface medium, discretised by the
+ * same cell-centred scheme with edges as faces), or n_tris = 0. The job's
+ * cells are the n_cells tets followed by the n_tris triangles; the per-cell
+ * arrays below and every state / activation output cover all of them in
+ * that order. Tets and triangles share no face (they exchange current only
+ * through conduction-graph junctions). cell_model: EP_TP06 / EP_CRN /
+ * EP_STEWART per cell, or NULL for all EP_TP06. param_set: bytes indexing
+ * ep_params.sets, or NULL for all 0. stim_mask: bytes, bit k set =
+ * stimulus protocol k covers the cell, or NULL for none. fibre: 3 doubles
+ * per cell, the fibre direction (need not be normalised; a triangle's
+ * conductivity acts in its plane), or NULL for isotropic tissue with
+ * diffusivity D_l. */
 typedef struct {
     int64_t n_nodes;
     const double *xyz;
@@ -118,6 +125,8 @@ typedef struct {
     const uint8_t *param_set;
     const uint8_t *stim_mask;
     const double *fibre;
+    int64_t n_tris;
+    const int32_t *tri;
 } ep_mesh_desc;
 
 /* Parameters of one parameter set. variant (TP06 only): 0 epicardial,

@@ -1577,6 +1577,8 @@ int ep_bidomain_enable(ep_job *job, const double *De_l, const double *De_t, int3
     if (!job) return EP_EINVAL;
     ep_context *ctx = job->ctx;
     if (!job->has_params) return fail(ctx, EP_ESTATE, "ep_bidomain_enable: job has no parameters");
+    for (uint8_t k : job->mesh().kind)
+        if (k) return fail(ctx, EP_EINVAL, "ep_bidomain_enable: the Purkinje shell is a monodomain medium");
     if (!De_l || !De_t || n_sets != job->params.n_sets)
         return fail(ctx, EP_EINVAL, "ep_bidomain_enable: need one extracellular (D_l, D_t) per parameter set");
     ep_bidomain_solver sv;

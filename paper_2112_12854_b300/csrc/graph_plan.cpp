@@ -15,11 +15,12 @@ struct P3 {
 
 P3 centroid(const HostMesh &m, int64_t c) {
     P3 r{0, 0, 0};
-    for (int k = 0; k < 4; ++k) {
+    const int nv = (!m.kind.empty() && m.kind[c]) ? 3 : 4;   // a shell triangle or a tetrahedron
+    for (int k = 0; k < nv; ++k) {
         const int64_t v = m.tet[4 * c + k];
-        r.x += 0.25 * m.xyz[3 * v];
-        r.y += 0.25 * m.xyz[3 * v + 1];
-        r.z += 0.25 * m.xyz[3 * v + 2];
+        r.x += m.xyz[3 * v] / nv;
+        r.y += m.xyz[3 * v + 1] / nv;
+        r.z += m.xyz[3 * v + 2] / nv;
     }
     return r;
 }

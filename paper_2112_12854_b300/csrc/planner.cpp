@@ -51,6 +51,38 @@ TetGeom tet_geom(const std::vector<double> &xyz, const int32_t *t) {
     return g;
 }
 
+// Geometry of a shell triangle in the same form: area in `vol`, the
+// in-plane outward edge normals times edge lengths in S (edge k opposite
+// node k), edge midpoints in xf, b_k = -S_k / (2 A) (Gauss-Green of the
+// edge-averaged node values); slot 3 unused.
+TetGeom tri_geom(const std::vector<double> &xyz, const int32_t *t) {
+    TetGeom g;
+    V3 p[3];
+    for (int k = 0; k < 3; ++k) p[k] = node(xyz, t[k]);
+    g.c = (1.0 / 3.0) * (p[0] + p[1] + p[2]);
+    const V3 w = cross(p[1] - p[0], p[2] - p[0]);
+    const double nw = norm(w);
+    const V3 un = (1.0 / nw) * w;
+    g.vol = 0.5 * nw;
+    for (int k = 0; k < 3; ++k) {
+        const V3 &a = p[(k + 1) % 3], &b = p[(k + 2) % 3];
+        const V3 tv = b - a, mid = 0.5 * (a + b);
+        V3 n = cross(tv, un);
+        n = (1.0 / norm(n)) * n;
+        if (dot(n, mid - p[k]) < 0.0) n = -1.0 * n;
+        g.S[k] = norm(tv) * n;
+        g.xf[k] = mid;
+        g.b[k] = (-1.0 / (2.0 * g.vol)) * g.S[k];
+    }
+    g.S[3] = g.xf[3] = g.b[3] = V3{0.0, 0.0, 0.0};
+    return g;
+}
+
+TetGeom cell_geom(const HostMesh &m, int64_t c) {
+    const int32_t *t = &m.tet[4 * c];
+    return (!m.kind.empty() && m.kind[c]) ? tri_geom(m.xyz, t) : tet_geom(m.xyz, t);
+}
+
 void tensor(const HostMesh &m, const ep_params *p, int64_t c, double D[9]) {
     const ep_cell_params &cp = p->sets[m.pset[c]];
     if (m.fibre.empty()) {
@@ -74,16 +106,24 @@ struct FaceRec {
 }  // namespace
 
 int build_mesh(const ep_mesh_desc *d, HostMesh *m, std::string *err) {
-    const int64_t N = d->n_cells, NN = d->n_nodes;
-    if (N <= 0 || NN <= 0 || !d->xyz || !d->tet) {
-        *err = "mesh: empty mesh or NULL xyz/tet";
+    const int64_t NT = d->n_cells, NS = d->n_tris, N = NT + NS, NN = d->n_nodes;
+    if (NT < 0 || NS < 0 || N <= 0 || NN <= 0 || !d->xyz || (NT > 0 && !d->tet) || (NS > 0 && !d->tri)) {
+        *err = "mesh: empty mesh or NULL xyz/tet/tri";
         return EP_EINVAL;
     }
     if (N >= (int64_t(1) << 31) || NN >= (int64_t(1) << 31)) {
         *err = "mesh: more than 2^31-1 cells or nodes";
         return EP_EINVAL;
     }
-    std::vector<int32_t> tet(d->tet, d->tet + 4 * N);
+    // cells: the tets, then the shell triangles (slot 3 repeats the first node)
+    std::vector<int32_t> tet(4 * N);
+    std::vector<uint8_t> kind0(N, 0);
+    if (NT > 0) std::copy(d->tet, d->tet + 4 * NT, tet.begin());
+    for (int64_t s = 0; s < NS; ++s) {
+        for (int k = 0; k < 3; ++k) tet[4 * (NT + s) + k] = d->tri[3 * s + k];
+        tet[4 * (NT + s) + 3] = d->tri[3 * s];
+        kind0[NT + s] = 1;
+    }
     for (int64_t i = 0; i < 4 * N; ++i)
         if (tet[i] < 0 || tet[i] >= NN) {
             *err = "mesh: node index out of range in cell " + std::to_string(i / 4);
@@ -99,7 +139,21 @@ int build_mesh(const ep_mesh_desc *d, HostMesh *m, std::string *err) {
         }
     int bad = -1;
 #pragma omp parallel for schedule(static)
-    for (int64_t c = 0; c < N; ++c) {
+    for (int64_t c = NT; c < N; ++c) {   // triangles: non-zero area
+        const int32_t *t = &tet[4 * c];
+        V3 e1 = node(xyz0, t[1]) - node(xyz0, t[0]), e2 = node(xyz0, t[2]) - node(xyz0, t[0]);
+        double l = std::max(norm(e1), norm(e2));
+        if (!(norm(cross(e1, e2)) > 1e-12 * l * l)) {
+#pragma omp critical
+            bad = (bad < 0) ? int(c) : std::min(bad, int(c));
+        }
+    }
+    if (bad >= 0) {
+        *err = "mesh: degenerate (zero-area) triangle " + std::to_string(bad - NT);
+        return EP_EMESH;
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < NT; ++c) {
         int32_t *t = &tet[4 * c];
         V3 p0 = node(xyz0, t[0]), p1 = node(xyz0, t[1]), p2 = node(xyz0, t[2]), p3 = node(xyz0, t[3]);
         V3 e1 = p1 - p0, e2 = p2 - p0, e3 = p3 - p0;
@@ -117,7 +171,7 @@ int build_mesh(const ep_mesh_desc *d, HostMesh *m, std::string *err) {
     }
     // faces: bucket by smallest vertex, then sort each bucket
     std::vector<int64_t> bptr(NN + 1, 0);
-    for (int64_t c = 0; c < N; ++c)
+    for (int64_t c = 0; c < NT; ++c)
         for (int k = 0; k < 4; ++k) {
             int32_t a = INT32_MAX;
             for (int j = 0; j < 4; ++j)
@@ -125,10 +179,10 @@ int build_mesh(const ep_mesh_desc *d, HostMesh *m, std::string *err) {
             bptr[a + 1]++;
         }
     for (int64_t n = 0; n < NN; ++n) bptr[n + 1] += bptr[n];
-    std::vector<FaceRec> recs(4 * N);
+    std::vector<FaceRec> recs(4 * NT);
     {
         std::vector<int64_t> fill(bptr.begin(), bptr.end() - 1);
-        for (int64_t c = 0; c < N; ++c)
+        for (int64_t c = 0; c < NT; ++c)
             for (int k = 0; k < 4; ++k) {
                 int32_t v[3];
                 int j = 0;
@@ -168,6 +222,39 @@ int build_mesh(const ep_mesh_desc *d, HostMesh *m, std::string *err) {
     }
     recs.clear();
     recs.shrink_to_fit();
+    // shell edges: the edge opposite node k of a triangle, matched by its sorted node pair
+    {
+        struct EdgeRec {
+            int32_t a, b, cell;
+            int8_t local;
+        };
+        std::vector<EdgeRec> er;
+        er.reserve(3 * NS);
+        for (int64_t c = NT; c < N; ++c)
+            for (int k = 0; k < 3; ++k) {
+                int32_t a = tet[4 * c + (k + 1) % 3], b = tet[4 * c + (k + 2) % 3];
+                if (a > b) std::swap(a, b);
+                er.push_back(EdgeRec{a, b, int32_t(c), int8_t(k)});
+            }
+        std::sort(er.begin(), er.end(), [](const EdgeRec &x, const EdgeRec &y) {
+            if (x.a != y.a) return x.a < y.a;
+            if (x.b != y.b) return x.b < y.b;
+            return x.cell < y.cell;
+        });
+        for (size_t i = 0; i < er.size();) {
+            size_t e = i + 1;
+            while (e < er.size() && er[e].a == er[i].a && er[e].b == er[i].b) ++e;
+            if (e - i == 2) {
+                nbr0[4 * int64_t(er[i].cell) + er[i].local] = er[i + 1].cell;
+                nbr0[4 * int64_t(er[i + 1].cell) + er[i + 1].local] = er[i].cell;
+                ++n_int;
+            } else if (e - i > 2) {
+                *err = "mesh: an edge is shared by more than two shell triangles";
+                return EP_EMESH;
+            }
+            i = e;
+        }
+    }
 
     // model of each cell
     std::vector<uint8_t> model0(N, EP_TP06);
@@ -289,6 +376,7 @@ int build_mesh(const ep_mesh_desc *d, HostMesh *m, std::string *err) {
     for (int64_t n = 0; n < NN; ++n)
         for (int k = 0; k < 3; ++k) m->xyz[3 * n + k] = xyz0[3 * int64_t(m->node_new2old[n]) + k];
     m->tet.resize(4 * N);
+    m->kind.resize(N);
     m->nbr.resize(4 * N);
     m->opp.resize(4 * N);
     m->model.resize(N);
@@ -305,6 +393,7 @@ int build_mesh(const ep_mesh_desc *d, HostMesh *m, std::string *err) {
             m->nbr[4 * i + k] = nb < 0 ? -1 : old2new[nb];
         }
         m->model[i] = model0[o];
+        m->kind[i] = kind0[o];
         m->pset[i] = d->param_set ? d->param_set[o] : 0;
         m->smask[i] = d->stim_mask ? d->stim_mask[o] : 0;
         if (d->fibre)
@@ -319,23 +408,26 @@ int build_mesh(const ep_mesh_desc *d, HostMesh *m, std::string *err) {
                 return EP_EINVAL;
             }
         }
-    // neighbour's vertex opposite each interior face
+    // neighbour's vertex opposite each interior face (edge, for a triangle)
 #pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < N; ++i)
+    for (int64_t i = 0; i < N; ++i) {
+        const int nv = m->kind[i] ? 3 : 4;
         for (int k = 0; k < 4; ++k) {
             int32_t nb = m->nbr[4 * i + k];
             int32_t o = -1;
             if (nb >= 0) {
-                for (int j = 0; j < 4; ++j) {
+                const int nvb = m->kind[nb] ? 3 : 4;
+                for (int j = 0; j < nvb; ++j) {
                     int32_t v = m->tet[4 * int64_t(nb) + j];
                     bool in_face = false;
-                    for (int l = 0; l < 4; ++l)
+                    for (int l = 0; l < nv; ++l)
                         if (l != k && m->tet[4 * i + l] == v) in_face = true;
                     if (!in_face) o = v;
                 }
             }
             m->opp[4 * i + k] = o;
         }
+    }
     m->n_interior_faces = n_int;
     for (int mdl = 0; mdl <= EP_N_MODELS; ++mdl) m->model_off[mdl] = 0;
     for (int64_t i = 0; i < N; ++i) m->model_off[m->model[i] + 1]++;
@@ -343,13 +435,13 @@ int build_mesh(const ep_mesh_desc *d, HostMesh *m, std::string *err) {
     // node -> cell incidence, cells ascending
     m->n2c_ptr.assign(NN + 1, 0);
     for (int64_t i = 0; i < N; ++i)
-        for (int k = 0; k < 4; ++k) m->n2c_ptr[m->tet[4 * i + k] + 1]++;
+        for (int k = 0; k < (m->kind[i] ? 3 : 4); ++k) m->n2c_ptr[m->tet[4 * i + k] + 1]++;
     for (int64_t n = 0; n < NN; ++n) m->n2c_ptr[n + 1] += m->n2c_ptr[n];
-    m->n2c.resize(4 * N);
+    m->n2c.resize(m->n2c_ptr[NN]);
     {
         std::vector<int64_t> fill(m->n2c_ptr.begin(), m->n2c_ptr.end() - 1);
         for (int64_t i = 0; i < N; ++i)
-            for (int k = 0; k < 4; ++k) m->n2c[fill[m->tet[4 * i + k]]++] = int32_t(i);
+            for (int k = 0; k < (m->kind[i] ? 3 : 4); ++k) m->n2c[fill[m->tet[4 * i + k]]++] = int32_t(i);
     }
     return EP_OK;
 }
@@ -370,15 +462,17 @@ int build_coeffs(const HostMesh &m, const ep_params *p, Coeffs *cf, std::string 
 #pragma omp parallel for schedule(static) reduction(max : gmax)
     for (int64_t c = 0; c < N; ++c) {
         const int32_t *tc = &m.tet[4 * c];
-        TetGeom g = tet_geom(m.xyz, tc);
+        const bool tri = !m.kind.empty() && m.kind[c];
+        const int nv = tri ? 3 : 4;
+        TetGeom g = cell_geom(m, c);
         double Dc[9];
         tensor(m, p, c, Dc);
         double wa[4] = {0, 0, 0, 0}, wb[4] = {0, 0, 0, 0}, q[4] = {0, 0, 0, 0};
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < nv; ++k) {
             int32_t nb = m.nbr[4 * c + k];
             if (nb < 0) continue;  // zero-flux boundary face
             const int32_t *tn = &m.tet[4 * int64_t(nb)];
-            TetGeom gn = tet_geom(m.xyz, tn);
+            TetGeom gn = cell_geom(m, nb);
             double Dn[9];
             tensor(m, p, nb, Dn);
             const V3 xf = g.xf[k];
@@ -390,18 +484,29 @@ int build_coeffs(const HostMesh &m, const ep_params *p, Coeffs *cf, std::string 
             // a = D_f S (face tensor times outward area vector)
             double Df[9];
             for (int i = 0; i < 9; ++i) Df[i] = alpha * Dc[i] + (1.0 - alpha) * Dn[i];
-            const V3 S = g.S[k];
+            V3 S = g.S[k];
+            if (tri) {
+                // the two triangles of an edge may lie in different planes: both use the
+                // normalised mean of their outward normals (conservative edge flux)
+                int k2 = 0;
+                for (int l = 0; l < 3; ++l)
+                    if (m.nbr[4 * int64_t(nb) + l] == int32_t(c)) k2 = l;
+                const double L = norm(S);
+                V3 nrm = (1.0 / L) * S - (1.0 / norm(gn.S[k2])) * gn.S[k2];
+                S = (L / norm(nrm)) * nrm;
+            }
             V3 a{Df[0] * S.x + Df[1] * S.y + Df[2] * S.z, Df[3] * S.x + Df[4] * S.y + Df[5] * S.z,
                  Df[6] * S.x + Df[7] * S.y + Df[8] * S.z};
             double ae = dot(a, e);
             V3 pvec = a - ae * e;  // acts on the interpolated face gradient
             double qq = ae / dist; // acts on V_c - V_nb
-            for (int j = 0; j < 4; ++j) wa[j] += alpha * dot(pvec, g.b[j]);
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < nv; ++j) wa[j] += alpha * dot(pvec, g.b[j]);
+            const int nvn = (!m.kind.empty() && m.kind[nb]) ? 3 : 4;
+            for (int j = 0; j < nvn; ++j) {
                 double coef = (1.0 - alpha) * dot(pvec, gn.b[j]);
                 int32_t v = tn[j];
                 int slot = -1;
-                for (int l = 0; l < 4; ++l)
+                for (int l = 0; l < nv; ++l)
                     if (tc[l] == v) slot = l;
                 if (slot >= 0) wa[slot] += coef;
                 else wb[k] += coef;
@@ -424,8 +529,11 @@ int build_coeffs(const HostMesh &m, const ep_params *p, Coeffs *cf, std::string 
         V3 xn = node(m.xyz, n);
         double s = 0.0;
         for (int64_t j = m.n2c_ptr[n]; j < m.n2c_ptr[n + 1]; ++j) {
-            const int32_t *t = &m.tet[4 * int64_t(m.n2c[j])];
-            V3 xc = 0.25 * (node(m.xyz, t[0]) + node(m.xyz, t[1]) + node(m.xyz, t[2]) + node(m.xyz, t[3]));
+            const int64_t cc = m.n2c[j];
+            const int32_t *t = &m.tet[4 * cc];
+            V3 xc = (!m.kind.empty() && m.kind[cc])
+                        ? (1.0 / 3.0) * (node(m.xyz, t[0]) + node(m.xyz, t[1]) + node(m.xyz, t[2]))
+                        : 0.25 * (node(m.xyz, t[0]) + node(m.xyz, t[1]) + node(m.xyz, t[2]) + node(m.xyz, t[3]));
             double w = 1.0 / norm(xn - xc);
             cf->nw[j] = w;
             s += w;

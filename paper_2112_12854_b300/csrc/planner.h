@@ -13,7 +13,9 @@ namespace ep {
 struct HostMesh {
     int64_t n_nodes = 0, n_cells = 0;
     std::vector<double> xyz;          // [3 n_nodes], internal node order
-    std::vector<int32_t> tet;         // [4 n_cells], internal cell order, positive orientation
+    std::vector<int32_t> tet;         // [4 n_cells], internal cell order, positive orientation; a triangle
+                                      // (kind 1) holds its 3 nodes and repeats the first in slot 3
+    std::vector<uint8_t> kind;        // [n_cells] 0 tetrahedron, 1 shell triangle (face k = edge opposite node k)
     std::vector<int32_t> nbr;         // [4 n_cells] cell across the face opposite vertex k, -1 boundary
     std::vector<int32_t> opp;         // [4 n_cells] neighbour's vertex off that face, -1 boundary
     std::vector<uint8_t> model, pset, smask;

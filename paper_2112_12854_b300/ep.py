@@ -33,7 +33,8 @@ class EPError(RuntimeError):
 class MeshDesc(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("xyz", ctypes.c_void_p), ("n_cells", ctypes.c_int64),
                 ("tet", ctypes.c_void_p), ("cell_model", ctypes.c_void_p), ("param_set", ctypes.c_void_p),
-                ("stim_mask", ctypes.c_void_p), ("fibre", ctypes.c_void_p)]
+                ("stim_mask", ctypes.c_void_p), ("fibre", ctypes.c_void_p), ("n_tris", ctypes.c_int64),
+                ("tri", ctypes.c_void_p)]
 
 
 class CellParams(ctypes.Structure):
@@ -229,9 +230,9 @@ class Context:
         except Exception:
             pass
 
-    def mesh(self, xyz, tets, *, cell_model=None, param_set=None, stim_mask=None, fibre=None) -> "Job":
+    def mesh(self, xyz, tets, *, cell_model=None, param_set=None, stim_mask=None, fibre=None, tris=None) -> "Job":
         return Job(self, xyz, tets, cell_model=cell_model, param_set=param_set, stim_mask=stim_mask,
-                   fibre=fibre)
+                   fibre=fibre, tris=tris)
 
 
 def make_params(dt, sets, stimuli=(), *, precision=EP_FP32_MIXED, threshold=-20.0,
@@ -257,14 +258,17 @@ def make_params(dt, sets, stimuli=(), *, precision=EP_FP32_MIXED, threshold=-20.
     return p
 
 
-def _mesh_desc(xyz, tets, cell_model=None, param_set=None, stim_mask=None, fibre=None):
-    """ep_mesh_desc of numpy inputs; returns (desc, arrays to keep alive)."""
+def _mesh_desc(xyz, tets, cell_model=None, param_set=None, stim_mask=None, fibre=None, tris=None):
+    """ep_mesh_desc of numpy inputs (tets, then the shell triangles `tris`);
+    returns (desc, arrays to keep alive)."""
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
-    tets = np.ascontiguousarray(tets, dtype=np.int32)
-    n = tets.shape[0]
-    keep = [xyz, tets]
+    tets = np.ascontiguousarray(np.reshape(tets, (-1, 4)), dtype=np.int32)
+    tris = np.ascontiguousarray(np.zeros((0, 3)) if tris is None else np.reshape(tris, (-1, 3)), dtype=np.int32)
+    n = tets.shape[0] + tris.shape[0]
+    keep = [xyz, tets, tris]
     d = MeshDesc()
-    d.n_nodes, d.xyz, d.n_cells, d.tet = xyz.shape[0], _ptr(xyz), n, _ptr(tets)
+    d.n_nodes, d.xyz, d.n_cells, d.tet = xyz.shape[0], _ptr(xyz), tets.shape[0], _ptr(tets)
+    d.n_tris, d.tri = tris.shape[0], _ptr(tris)
     for name, arr, dt, width in (("cell_model", cell_model, np.uint8, 1), ("param_set", param_set, np.uint8, 1),
                                  ("stim_mask", stim_mask, np.uint8, 1), ("fibre", fibre, np.float64, 3)):
         if arr is None:
@@ -283,9 +287,9 @@ class Plan:
     safe to build in worker threads while the GPU steps other jobs."""
 
     def __init__(self, xyz, tets, params: Params | None = None, *, cell_model=None, param_set=None,
-                 stim_mask=None, fibre=None):
+                 stim_mask=None, fibre=None, tris=None):
         L = load()
-        d, keep = _mesh_desc(xyz, tets, cell_model, param_set, stim_mask, fibre)
+        d, keep = _mesh_desc(xyz, tets, cell_model, param_set, stim_mask, fibre, tris)
         h = _P()
         rc = L.ep_plan_create(ctypes.byref(d), ctypes.byref(params) if params is not None else None,
                               ctypes.byref(h))
@@ -309,7 +313,7 @@ class Plan:
 
 class Job:
     def __init__(self, ctx: Context, xyz=None, tets=None, *, plan: Plan | None = None, cell_model=None,
-                 param_set=None, stim_mask=None, fibre=None):
+                 param_set=None, stim_mask=None, fibre=None, tris=None):
         L = load()
         self.ctx = ctx
         h = _P()
@@ -319,9 +323,9 @@ class Job:
             if plan.params is not None:
                 self.params = plan.params
         else:
-            d, keep = _mesh_desc(xyz, tets, cell_model, param_set, stim_mask, fibre)
+            d, keep = _mesh_desc(xyz, tets, cell_model, param_set, stim_mask, fibre, tris)
             ctx.check(L.ep_mesh_create(ctx._h, ctypes.byref(d), ctypes.byref(h)))
-            self.n_cells = int(d.n_cells)
+            self.n_cells = int(d.n_cells) + int(d.n_tris)
         self._h = h
         ctx.jobs.add(self)
 
@@ -543,7 +547,7 @@ def plan_from_case(case, *, precision=EP_FP32_MIXED, integrator=0) -> Plan:
     params = make_params(case.dt, case.param_sets, case.stimuli, precision=precision, threshold=case.threshold,
                          integrator=integrator)
     return Plan(case.xyz, case.tets, params, cell_model=case_cell_model(case), param_set=case.param_set,
-                stim_mask=case.stim_mask, fibre=case.fibre)
+                stim_mask=case.stim_mask, fibre=case.fibre, tris=getattr(case, "tris", None))
 
 
 def job_from_case(ctx: Context, case, *, precision=EP_FP32_MIXED, cell_model=None, integrator=0) -> Job:
@@ -551,21 +555,24 @@ def job_from_case(ctx: Context, case, *, precision=EP_FP32_MIXED, cell_model=Non
     if cell_model is None:
         cell_model = case_cell_model(case)
     j = ctx.mesh(case.xyz, case.tets, cell_model=cell_model, param_set=case.param_set,
-                 stim_mask=case.stim_mask, fibre=case.fibre)
+                 stim_mask=case.stim_mask, fibre=case.fibre, tris=getattr(case, "tris", None))
     j.set_params(make_params(case.dt, case.param_sets, case.stimuli, precision=precision,
                              threshold=case.threshold, integrator=integrator))
     return j
 
 
-def plan_inspect(xyz, tets, params: Params, *, cell_model=None, param_set=None, fibre=None) -> dict:
-    """Run the host planner only (no GPU) and return its folded operator."""
+def plan_inspect(xyz, tets, params: Params, *, cell_model=None, param_set=None, fibre=None, tris=None) -> dict:
+    """Run the host planner only (no GPU) and return its folded operator
+    (cells: the tets, then the shell triangles)."""
     L = load()
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
-    tets = np.ascontiguousarray(tets, dtype=np.int32)
-    n, nn = tets.shape[0], xyz.shape[0]
-    keep = []
+    tets = np.ascontiguousarray(np.reshape(tets, (-1, 4)), dtype=np.int32)
+    tris = np.ascontiguousarray(np.zeros((0, 3)) if tris is None else np.reshape(tris, (-1, 3)), dtype=np.int32)
+    n, nn = tets.shape[0] + tris.shape[0], xyz.shape[0]
+    keep = [tris]
     d = MeshDesc()
-    d.n_nodes, d.xyz, d.n_cells, d.tet = nn, _ptr(xyz), n, _ptr(tets)
+    d.n_nodes, d.xyz, d.n_cells, d.tet = nn, _ptr(xyz), tets.shape[0], _ptr(tets)
+    d.n_tris, d.tri = tris.shape[0], _ptr(tris)
     for name, arr, dt in (("cell_model", cell_model, np.uint8), ("param_set", param_set, np.uint8),
                           ("fibre", fibre, np.float64)):
         if arr is None:

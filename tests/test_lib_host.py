@@ -178,3 +178,39 @@ def test_ab2_halves_the_explicit_stability_bound():
             with pytest.raises(ep.EPError) as e:
                 ep.plan_from_case(case, integrator=integ)
             assert e.value.code == ep.EP_EUNSTABLE
+
+
+def test_folded_operator_on_shell_triangles_equals_oracle():
+    """A job with tets and a curved, jittered Purkinje shell: the planner's
+    folded operator on the triangles equals the oracle's edge-by-edge shell
+    operator (fv2d), and on the tets the face-by-face one; the two media
+    share no face."""
+    import oracle
+    xyz_t, tets = w.kuhn_box(4, 3, 2, 0.5)
+    xyz_s, tris = w.tri_cylinder(12, 6, 4.0, 3.0)
+    rng = np.random.default_rng(4)
+    xyz_s = xyz_s + rng.uniform(-0.05, 0.05, xyz_s.shape)
+    xyz = np.concatenate([xyz_t, xyz_s + [0.0, 0.0, 5.0]])
+    tris = (tris + len(xyz_t)).astype(np.int32)
+    nt, ns = len(tets), len(tris)
+    fib = rng.standard_normal((nt + ns, 3))
+    sets = [w.ParamSet(D_l=0.154, D_t=0.0385), w.ParamSet(D_l=2.82, D_t=1.3)]
+    pset = np.concatenate([np.zeros(nt, np.uint8), np.ones(ns, np.uint8)])
+    plan = ep.plan_inspect(xyz, tets, _params(sets), param_set=pset, fibre=fib, tris=tris)
+    order = plan["cell_order"]
+    assert np.array_equal(np.sort(order), np.arange(nt + ns))
+    m, sh = oracle.Mesh(xyz_t, tets), oracle.Shell(xyz, tris)
+    D = np.stack([oracle.conductivity(fib[c], sets[pset[c]].D_l, sets[pset[c]].D_t).ravel() for c in range(nt + ns)])
+    for _ in range(3):
+        v = rng.uniform(-90, 40, nt + ns)
+        ref = np.concatenate([m.diffusion(D[:nt], v[:nt]), sh.diffusion(D[nt:], v[nt:])])
+        got = np.empty_like(ref)
+        got[order] = _apply(plan, v[order])
+        assert np.abs(got - ref).max() < 1e-11 * np.abs(ref).max()
+    # no folded coefficient links a triangle to a tet
+    nbr = plan["nbr"].reshape(-1, 4)
+    is_tri = np.isin(order, np.arange(nt, nt + ns))
+    for c in range(nt + ns):
+        for k in range(4):
+            if nbr[c, k] >= 0:
+                assert is_tri[nbr[c, k]] == is_tri[c]
