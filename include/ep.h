@@ -85,7 +85,9 @@ enum {
 /* ---- Purkinje-muscle junction coupling (Sec. 3.3) ---- */
 enum {
     EP_PMJ_RESISTIVE = 0, /* current (V_p - V_m)/R into both sides, scaled by each side's capacitance */
-    EP_PMJ_TRIGGERED = 1  /* threshold crossing at one side stimulates the other after a delay */
+    EP_PMJ_TRIGGERED = 1, /* threshold crossing at one side stimulates the other after a delay */
+    EP_PMJ_CELL = 2       /* a triggered communication node between two cells (the 2D shell and the
+                             3D myocardium): junction_node holds the source cell */
 };
 
 #define EP_MAX_PARAM_SETS 16
@@ -169,7 +171,10 @@ typedef struct {
 /* Create a context bound to one CUDA device (the current one) and stream.
  * alloc/free may both be NULL (then cudaMalloc/cudaFree are used); user is
  * passed back to them. cuda_stream is a cudaStream_t (NULL = legacy default
- * stream). *out receives the context. Errors: EP_EINVAL, EP_ECUDA. */
+ * stream). *out receives the context. Besides the memory it takes through
+ * alloc, the context holds one 4-byte device word of its own (cudaMalloc),
+ * where step kernels report bounded waits that gave up. Errors: EP_EINVAL,
+ * EP_ECUDA, EP_ENOMEM. */
 int ep_context_create(ep_alloc_fn alloc, ep_free_fn free_fn, void *user,
                       void *cuda_stream, ep_context **out);
 
@@ -367,7 +372,14 @@ int ep_step_noalloc(ep_job *job, int64_t n_steps);
  *     interpolated) stimulates every cell within `radius` mm of the junction
  *     cell with `amplitude` over [t_p + delay_ortho, t_p + delay_ortho +
  *     duration); with two_way, crossings by V_m at t_m stimulate the node over
- *     [t_m + delay_anti, ... + duration).
+ *     [t_m + delay_anti, ... + duration);
+ *   EP_PMJ_CELL: the same with a source cell s = junction_node[j] (caller
+ *     cell numbering, e.g. a shell triangle) in place of the node: crossings
+ *     by V_s stimulate the cells within `radius` of cell m, and with two_way
+ *     crossings by V_m stimulate cell s. A graph may consist of such
+ *     junctions alone (n_nodes = 0).
+ * Triggered targets are the cells of the junction cell's medium (tets or
+ * shell triangles) within `radius` of it.
  * xyz: 3 n_nodes doubles; edges: 2 n_edges node indices; edge_D: per-edge
  * diffusivity or NULL (then params->D); node_model / node_param_set /
  * node_stim_mask: per node or NULL (Stewart / 0 / none); junction_mode: per

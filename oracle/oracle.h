@@ -141,7 +141,11 @@ void orc_sim_bidomain_operator(const orc_sim *s, const double *x, double *out);
 int orc_stim_active(const orc_stim *st, double dt, int64_t n);
 
 /* ---- conduction graph and junctions (purkinje.c) ---- */
-enum { ORC_JUNC_RESISTIVE = 0, ORC_JUNC_TRIGGERED = 1 };
+/* junction modes: a graph node and a cell, by resistance or by a triggered
+ * stimulus; or a communication node between two cells (jnode is then the
+ * source cell, e.g. a Purkinje-shell triangle, jcell the target myocardial
+ * cell), triggered like ORC_JUNC_TRIGGERED */
+enum { ORC_JUNC_RESISTIVE = 0, ORC_JUNC_TRIGGERED = 1, ORC_JUNC_CELL = 2 };
 typedef struct {
     double D;                        /* default edge diffusivity, mm^2/ms */
     double g_graph, g_cell;          /* resistive coupling rates, 1/ms */
@@ -158,7 +162,7 @@ orc_graph *orc_graph_build(int64_t n, const double *xyz, int64_t n_edges, const 
                            int n_sets, const orc_cellparams *sets, double dt,
                            int64_t n_junc, const int32_t *jnode, const int32_t *jcell,
                            const uint8_t *jmode, const orc_graph_params *p,
-                           int64_t n_cells, const double *cell_centroid, int *err);
+                           int64_t n_cells, const double *cell_centroid, int64_t n_tets, int *err);
 void orc_graph_free(orc_graph *g);
 int orc_graph_substeps(const orc_graph *g);
 int64_t orc_graph_n(const orc_graph *g);

@@ -18,11 +18,17 @@
  *    g_cell (V_m - V_p) leaves cell m, both evaluated at step n;
  *  - triggered: each upward crossing of the threshold by V_p at time t_p
  *    (interpolated within the step) makes the stimulus `amplitude` act on
- *    every cell whose centroid lies within `radius` of cell m's centroid
+ *    every cell of cell m's medium (myocardium or Purkinje shell) whose
+ *    centroid lies within `radius` of cell m's centroid
  *    while t_p + delay_ortho <= t < t_p + delay_ortho + duration; with
  *    two_way, each upward crossing by V_m at t_m likewise stimulates node p
  *    over [t_m + delay_anti, t_m + delay_anti + duration).
  *    Crossings found in step n act from step n + 1 on.
+ * Communication nodes between two cells (Sec. 3.3: the 2D Purkinje shell and
+ * the 3D myocardium) work like the triggered junction with a source cell s
+ * (given in place of the graph node) instead of node p: each upward crossing
+ * by V_s stimulates the cells within `radius` of cell m after delay_ortho;
+ * with two_way, crossings by V_m stimulate cell s after delay_anti.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -60,15 +66,18 @@ orc_graph *orc_graph_build(int64_t n, const double *xyz, int64_t n_edges, const 
                            int n_sets, const orc_cellparams *sets, double dt,
                            int64_t n_junc, const int32_t *jnode, const int32_t *jcell,
                            const uint8_t *jmode, const orc_graph_params *p,
-                           int64_t n_cells, const double *cell_centroid, int *err) {
+                           int64_t n_cells, const double *cell_centroid, int64_t n_tets, int *err) {
     *err = 0;
     for (int64_t e = 0; e < n_edges; ++e)
         if (edges[2 * e] < 0 || edges[2 * e] >= n || edges[2 * e + 1] < 0 || edges[2 * e + 1] >= n ||
             edges[2 * e] == edges[2 * e + 1]) { *err = 20; return NULL; }
     for (int64_t i = 0; i < n; ++i)
         if (pset && pset[i] >= n_sets) { *err = 21; return NULL; }
-    for (int64_t j = 0; j < n_junc; ++j)
-        if (jnode[j] < 0 || jnode[j] >= n || jcell[j] < 0 || jcell[j] >= n_cells) { *err = 22; return NULL; }
+    for (int64_t j = 0; j < n_junc; ++j) {
+        const int cellsrc = jmode && jmode[j] == ORC_JUNC_CELL;
+        if (jnode[j] < 0 || jnode[j] >= (cellsrc ? n_cells : n) || jcell[j] < 0 || jcell[j] >= n_cells ||
+            (jmode && jmode[j] > ORC_JUNC_CELL)) { *err = 22; return NULL; }
+    }
     orc_graph *g = (orc_graph *)calloc(1, sizeof(orc_graph));
     g->n = n;
     g->p = *p;
@@ -134,9 +143,11 @@ orc_graph *orc_graph_build(int64_t n, const double *xyz, int64_t n_edges, const 
     for (int64_t j = 0; j < n_junc; ++j) {
         g->t_graph[j] = -INFINITY;
         g->t_cell[j] = -INFINITY;
-        if (g->jmode[j] == ORC_JUNC_TRIGGERED) {
+        if (g->jmode[j] == ORC_JUNC_TRIGGERED || g->jmode[j] == ORC_JUNC_CELL) {
             const double *x0 = cell_centroid + 3 * (int64_t)jcell[j];
+            const int shell = jcell[j] >= n_tets;   /* targets: cells of the target cell's medium */
             for (int64_t c = 0; c < n_cells; ++c) {
+                if ((c >= n_tets) != shell) continue;
                 const double *x = cell_centroid + 3 * c;
                 double dx = x[0] - x0[0], dy = x[1] - x0[1], dz = x[2] - x0[2];
                 if (c == jcell[j] || sqrt(dx * dx + dy * dy + dz * dz) <= p->radius) {
@@ -165,9 +176,13 @@ void orc_graph_cell_terms(const orc_graph *g, const double *V, double t, double 
         const int32_t p = g->jnode[j], m = g->jcell[j];
         if (g->jmode[j] == ORC_JUNC_RESISTIVE) {
             i_extra[m] += g->p.g_cell * (V[m] - g->state[ORC_MAXVAR * (int64_t)p]);
-        } else if (window_on(g->t_graph[j], g->p.delay_ortho, g->p.duration, t)) {
-            for (int64_t k = g->tgt_ptr[j]; k < g->tgt_ptr[j + 1]; ++k) s_extra[g->tgt[k]] += g->p.amplitude;
+            continue;
         }
+        if (window_on(g->t_graph[j], g->p.delay_ortho, g->p.duration, t))
+            for (int64_t k = g->tgt_ptr[j]; k < g->tgt_ptr[j + 1]; ++k) s_extra[g->tgt[k]] += g->p.amplitude;
+        /* the source cell of a cell-to-cell node, excited back (two-way) */
+        if (g->jmode[j] == ORC_JUNC_CELL && g->p.two_way && window_on(g->t_cell[j], g->p.delay_anti, g->p.duration, t))
+            s_extra[p] += g->p.amplitude;
     }
 }
 
@@ -184,7 +199,8 @@ void orc_graph_step(orc_graph *g, const double *V3, double t, double dt, int64_t
         const int32_t p = g->jnode[j], m = g->jcell[j];
         if (g->jmode[j] == ORC_JUNC_RESISTIVE)
             itot[p] += g->p.g_graph * (g->state[ORC_MAXVAR * (int64_t)p] - V3[m]);
-        else if (g->p.two_way && window_on(g->t_cell[j], g->p.delay_anti, g->p.duration, t))
+        else if (g->jmode[j] == ORC_JUNC_TRIGGERED && g->p.two_way &&
+                 window_on(g->t_cell[j], g->p.delay_anti, g->p.duration, t))
             sx[p] += g->p.amplitude;
     }
     /* reaction at (V^n, s^n), frozen over the substeps */
@@ -224,8 +240,10 @@ void orc_graph_triggers(orc_graph *g, const double *V3_old, const double *V3_new
                         double t, double dt) {
     const double th = g->p.threshold;
     for (int64_t j = 0; j < g->n_junc; ++j) {
-        if (g->jmode[j] != ORC_JUNC_TRIGGERED) continue;
-        const double a = Vg_old[g->jnode[j]], b = g->state[ORC_MAXVAR * (int64_t)g->jnode[j]];
+        if (g->jmode[j] == ORC_JUNC_RESISTIVE) continue;
+        const int cellsrc = g->jmode[j] == ORC_JUNC_CELL;   /* the source is a cell, not a graph node */
+        const double a = cellsrc ? V3_old[g->jnode[j]] : Vg_old[g->jnode[j]];
+        const double b = cellsrc ? V3_new[g->jnode[j]] : g->state[ORC_MAXVAR * (int64_t)g->jnode[j]];
         if (a < th && b >= th) g->t_graph[j] = t + dt * (th - a) / (b - a);
         const double c = V3_old[g->jcell[j]], d = V3_new[g->jcell[j]];
         if (g->p.two_way && c < th && d >= th) g->t_cell[j] = t + dt * (th - c) / (d - c);

@@ -314,7 +314,7 @@ int orc_sim_attach_graph(orc_sim *s, int64_t n, const double *xyz, int64_t n_edg
     sim_centroids(s, cen);
     int err = 0;
     orc_graph *g = orc_graph_build(n, xyz, n_edges, edges, edge_D, pset, smask, s->n_sets, s->sets, s->dt,
-                                   n_junc, jnode, jcell, jmode, &q, s->n_cells, cen, &err);
+                                   n_junc, jnode, jcell, jmode, &q, s->n_cells, cen, s->n_tets, &err);
     free(cen);
     if (!g) return err;
     orc_graph_free(s->g);

@@ -239,10 +239,12 @@ int ep_context_create(ep_alloc_fn alloc, ep_free_fn free_fn, void *user, void *c
         ctx->free_fn = free_fn;
         ctx->user = user;
         ctx->stream = static_cast<cudaStream_t>(cuda_stream);
-        if (dalloc(ctx, sizeof(unsigned), &ctx->err_word) ||
+        // the error word is the context's own (cudaMalloc), outside the caller's allocator budget
+        if (cudaMalloc(&ctx->err_word.p, sizeof(unsigned)) != cudaSuccess ||
             cudaMemset(ctx->err_word.p, 0, sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
             g_create_error = "ep_context_create: device allocation failed";
-            if (ctx->err_word.p) dfree(ctx, &ctx->err_word);
+            if (ctx->err_word.p) cudaFree(ctx->err_word.p);
             cudaStreamDestroy(ctx->capture);
             cudaStreamDestroy(ctx->upload);
             delete ctx;
@@ -269,7 +271,7 @@ int ep_context_destroy(ep_context *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto &p : ctx->plans) free_plan(ctx, p.get());
     ctx->plans.clear();
-    dfree(ctx, &ctx->err_word);
+    if (ctx->err_word.p) cudaFree(ctx->err_word.p);
     if (ctx->capture) cudaStreamDestroy(ctx->capture);
     if (ctx->upload) cudaStreamDestroy(ctx->upload);
     delete ctx;
@@ -614,6 +616,8 @@ int graph_apply(ep_job *job) {
     if (rc) return rc;
     G.n_tgt = int(g.tgt_cell.size());
     G.two_way = g.p.two_way;
+    G.cell_nodes = 0;
+    for (uint8_t md : g.jmode) G.cell_nodes |= md == EP_PMJ_CELL;
     G.substeps = g.substeps = std::max(1, int(std::ceil(job->params.dt * g.rho / 1.8)));
     G.g_graph = g.p.g_graph;
     G.g_cell = g.p.g_cell;

@@ -61,6 +61,7 @@ struct DevGraph {
     const int *tgt_cell, *tgt_junc;
     int n_tgt;
     int two_way;
+    int cell_nodes;             // some junction is a cell-to-cell communication node
     double g_graph, g_cell, threshold, delay_ortho, delay_anti, amplitude, duration, h;
     float g_graph_f, g_cell_f, amplitude_f, h_f;
 };
@@ -106,6 +107,7 @@ constexpr int kCellThreads = 256;
 constexpr int kHistSlots = 6;              // AB2 rate history per cell: V and five non-gating variables
 constexpr int kGraphThreads = 256;
 constexpr unsigned kJunctionFlag = 0x80;   // set in a cell's parameter-set byte when a junction touches it
+constexpr int kJunctionSource = 1 << 30;   // in DevGraph::tgt_junc: the cell is the source of a cell-to-cell node
 constexpr int kNodeThreads = 256;
 
 }  // namespace ep

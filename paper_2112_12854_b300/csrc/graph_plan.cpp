@@ -1,5 +1,6 @@
 // Host planning of a conduction graph (see graph_plan.h).
 #include "graph_plan.h"
+#include "devtypes.h"
 
 #include <algorithm>
 #include <cmath>
@@ -40,7 +41,7 @@ int build_graph(const HostMesh &m, const ep_graph_desc *d, const ep_graph_params
         return EP_EINVAL;
     }
     if (!(p->D >= 0.0) || !(p->radius >= 0.0) || !(p->duration >= 0.0) || !(p->delay_ortho >= 0.0) ||
-        !(p->delay_anti >= 0.0) || (p->default_mode != EP_PMJ_RESISTIVE && p->default_mode != EP_PMJ_TRIGGERED)) {
+        !(p->delay_anti >= 0.0) || p->default_mode < EP_PMJ_RESISTIVE || p->default_mode > EP_PMJ_CELL) {
         *err = "graph: bad coupling parameters";
         return EP_EINVAL;
     }
@@ -132,21 +133,25 @@ int build_graph(const HostMesh &m, const ep_graph_desc *d, const ep_graph_params
     for (int64_t j = 0; j < nj; ++j) {
         const int32_t a = d->junction_node[j], c = d->junction_cell[j];
         const uint8_t mode = d->junction_mode ? d->junction_mode[j] : uint8_t(p->default_mode);
-        if (a < 0 || a >= n || c < 0 || c >= m.n_cells || mode > EP_PMJ_TRIGGERED) {
+        const bool cellsrc = mode == EP_PMJ_CELL;   // the source is a cell, not a graph node
+        if (a < 0 || a >= (cellsrc ? m.n_cells : n) || c < 0 || c >= m.n_cells || mode > EP_PMJ_CELL) {
             *err = "graph: bad junction " + std::to_string(j);
             return EP_EINVAL;
         }
-        g->jnode[j] = old2new[a];
+        g->jnode[j] = cellsrc ? cell_old2new[a] : old2new[a];
         g->jcell[j] = cell_old2new[c];
         g->jmode[j] = mode;
     }
+    // junctions at each graph node (cell-to-cell nodes have no graph side)
     g->node_junc_ptr.assign(n + 1, 0);
-    for (int64_t j = 0; j < nj; ++j) g->node_junc_ptr[g->jnode[j] + 1]++;
+    for (int64_t j = 0; j < nj; ++j)
+        if (g->jmode[j] != EP_PMJ_CELL) g->node_junc_ptr[g->jnode[j] + 1]++;
     for (int64_t i = 0; i < n; ++i) g->node_junc_ptr[i + 1] += g->node_junc_ptr[i];
-    g->node_junc.resize(nj);
+    g->node_junc.resize(std::max<int64_t>(g->node_junc_ptr[n], 0));
     {
         std::vector<int32_t> fill(g->node_junc_ptr.begin(), g->node_junc_ptr.end() - 1);
-        for (int64_t j = 0; j < nj; ++j) g->node_junc[fill[g->jnode[j]]++] = int32_t(j);
+        for (int64_t j = 0; j < nj; ++j)
+            if (g->jmode[j] != EP_PMJ_CELL) g->node_junc[fill[g->jnode[j]]++] = int32_t(j);
     }
     // cell-side entries: the junction cell of resistive junctions, every cell within
     // `radius` of the junction cell for triggered ones (spatial hash of centroids)
@@ -155,6 +160,8 @@ int build_graph(const HostMesh &m, const ep_graph_desc *d, const ep_graph_params
     for (int64_t j = 0; j < nj; ++j) {
         if (g->jmode[j] == EP_PMJ_RESISTIVE) ent.push_back({g->jcell[j], int32_t(j)});
         else any_trig = true;
+        // the source cell of a cell-to-cell node: records its crossings, and is excited back (two-way)
+        if (g->jmode[j] == EP_PMJ_CELL) ent.push_back({g->jnode[j], int32_t(j) | kJunctionSource});
     }
     if (any_trig) {
         const double r = p->radius;
@@ -172,8 +179,9 @@ int build_graph(const HostMesh &m, const ep_graph_desc *d, const ep_graph_params
                     .push_back(int32_t(c));
             }
             for (int64_t j = 0; j < nj; ++j) {
-                if (g->jmode[j] != EP_PMJ_TRIGGERED) continue;
+                if (g->jmode[j] == EP_PMJ_RESISTIVE) continue;
                 const P3 x0 = cen[g->jcell[j]];
+                const uint8_t medium = m.kind.empty() ? 0 : m.kind[g->jcell[j]];
                 const int64_t bx = int64_t(std::floor(x0.x / cs)), by = int64_t(std::floor(x0.y / cs)),
                               bz = int64_t(std::floor(x0.z / cs));
                 for (int64_t dx = -1; dx <= 1; ++dx)
@@ -182,6 +190,7 @@ int build_graph(const HostMesh &m, const ep_graph_desc *d, const ep_graph_params
                             auto it = grid.find(key(bx + dx, by + dy, bz + dz));
                             if (it == grid.end()) continue;
                             for (int32_t c : it->second) {
+                                if ((m.kind.empty() ? 0 : m.kind[c]) != medium) continue;   // the target's medium
                                 const double ex = cen[c].x - x0.x, ey = cen[c].y - x0.y, ez = cen[c].z - x0.z;
                                 if (c == g->jcell[j] || std::sqrt(ex * ex + ey * ey + ez * ez) <= r)
                                     ent.push_back({c, int32_t(j)});
@@ -190,7 +199,7 @@ int build_graph(const HostMesh &m, const ep_graph_desc *d, const ep_graph_params
             }
         } else {
             for (int64_t j = 0; j < nj; ++j)
-                if (g->jmode[j] == EP_PMJ_TRIGGERED) ent.push_back({g->jcell[j], int32_t(j)});
+                if (g->jmode[j] != EP_PMJ_RESISTIVE) ent.push_back({g->jcell[j], int32_t(j)});
         }
     }
     std::sort(ent.begin(), ent.end());

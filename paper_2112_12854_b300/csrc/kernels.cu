@@ -51,6 +51,28 @@ __device__ __forceinline__ R stimulus(const DevJob &J, unsigned mask, long long 
     return is;
 }
 
+// Inverse-distance node value (S1) over the sliced-ELL entries b, b+32, ...
+// < e of one node. The loads of four entries are issued before their
+// products are accumulated, so four gathers are in flight at once; the sum
+// is still taken in entry order.
+template <class R>
+__device__ __forceinline__ R node_sum(const R *__restrict__ w, const int *__restrict__ col, const R *__restrict__ V,
+                                      long long b, long long e) {
+    R acc = R(0);
+    long long k = b;
+    for (; k + 96 < e; k += 128) {
+        const int c0 = col[k], c1 = col[k + 32], c2 = col[k + 64], c3 = col[k + 96];
+        const R w0 = w[k], w1 = w[k + 32], w2 = w[k + 64], w3 = w[k + 96];
+        const R v0 = V[c0], v1 = V[c1], v2 = V[c2], v3 = V[c3];
+        acc += w0 * v0;
+        acc += w1 * v1;
+        acc += w2 * v2;
+        acc += w3 * v3;
+    }
+    for (; k < e; k += 32) acc += w[k] * V[col[k]];
+    return acc;
+}
+
 template <class R>
 __global__ void __launch_bounds__(kNodeThreads) node_kernel(const DevJob *__restrict__ jobs,
                                                             const Tile *__restrict__ tiles, int n_tiles) {
@@ -65,9 +87,7 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const DevJob *__rest
         const R *__restrict__ w = static_cast<const R *>(J.nw);
         const long long s = node >> 5;
         const long long b = J.slice_ptr[s] + (node & 31), e = J.slice_ptr[s + 1];
-        R acc = R(0);
-        for (long long k = b; k < e; k += 32) acc += w[k] * V[J.ncol[k]];
-        static_cast<R *>(J.vn)[node] = acc;
+        static_cast<R *>(J.vn)[node] = node_sum<R>(w, J.ncol, V, b, e);
     }
 }
 
@@ -93,9 +113,15 @@ __device__ void junction_cell_terms(const DevJob &J, long long c, long long n, R
     const double t = double(n) * J.dt;
     int k = lo;
     for (; k < G.n_tgt && G.tgt_cell[k] == c; ++k) {
-        const int j = G.tgt_junc[k];
-        if (G.jmode[j] == EP_PMJ_RESISTIVE) ix += pick<R>(G.g_cell, G.g_cell_f) * (Vc - Vg[G.jnode[j]]);
-        else if (window_on(G.t_graph[j], G.delay_ortho, G.duration, t)) is += pick<R>(G.amplitude, G.amplitude_f);
+        const int e = G.tgt_junc[k], j = e & (kJunctionSource - 1);
+        if (e & kJunctionSource) {   // source of a cell-to-cell node, excited back (two-way)
+            if (G.two_way && window_on(G.t_cell[j], G.delay_anti, G.duration, t))
+                is += pick<R>(G.amplitude, G.amplitude_f);
+        } else if (G.jmode[j] == EP_PMJ_RESISTIVE) {
+            ix += pick<R>(G.g_cell, G.g_cell_f) * (Vc - Vg[G.jnode[j]]);
+        } else if (window_on(G.t_graph[j], G.delay_ortho, G.duration, t)) {
+            is += pick<R>(G.amplitude, G.amplitude_f);
+        }
     }
     last = k;
 }
@@ -106,10 +132,11 @@ __device__ void junction_cell_crossing(const DevJob &J, long long c, long long n
     const DevGraph &G = J.g;
     const double th = G.threshold;
     if (!(double(v0) < th && double(v1) >= th)) return;
+    const double tc = double(n) * J.dt + J.dt * (th - double(v0)) / (double(v1) - double(v0));
     for (int k = first; k < last; ++k) {
-        const int j = G.tgt_junc[k];
-        if (G.jmode[j] == EP_PMJ_TRIGGERED && G.jcell[j] == c)
-            G.t_cell[j] = double(n) * J.dt + J.dt * (th - double(v0)) / (double(v1) - double(v0));
+        const int e = G.tgt_junc[k], j = e & (kJunctionSource - 1);
+        if (e & kJunctionSource) G.t_graph[j] = tc;   // the source cell of a cell-to-cell node fires
+        else if (G.two_way && G.jmode[j] != EP_PMJ_RESISTIVE && G.jcell[j] == c) G.t_cell[j] = tc;
     }
 }
 
@@ -180,7 +207,7 @@ __device__ __forceinline__ void cell_update_from(const DevJob &J, int model, lon
     else iion = crn_step<R, AB2>(src.io, P, Vc, dt, rt);
     const R Vn = Vc + dt * rt(0, diff - iion - is - ix);
     Vnext[c] = Vn;
-    if ((ps & kJunctionFlag) && J.g.two_way) junction_cell_crossing<R>(J, c, n, Vc, Vn, jfirst, jlast);
+    if ((ps & kJunctionFlag) && (J.g.two_way || J.g.cell_nodes)) junction_cell_crossing<R>(J, c, n, Vc, Vn, jfirst, jlast);
     const R th = pick<R>(J.threshold, J.threshold_f);
     if (Vc < th && Vn >= th) {
         R *act = static_cast<R *>(J.act);
@@ -217,7 +244,7 @@ __global__ void __launch_bounds__(kGraphThreads) graph_ionic_kernel(const DevJob
             for (int k = G.node_junc_ptr[node]; k < G.node_junc_ptr[node + 1]; ++k) {
                 const int j = G.node_junc[k];
                 if (G.jmode[j] == EP_PMJ_RESISTIVE) ix += pick<R>(G.g_graph, G.g_graph_f) * (Vg - V3[G.jcell[j]]);
-                else if (G.two_way && window_on(G.t_cell[j], G.delay_anti, G.duration, tn))
+                else if (G.jmode[j] == EP_PMJ_TRIGGERED && G.two_way && window_on(G.t_cell[j], G.delay_anti, G.duration, tn))
                     is += pick<R>(G.amplitude, G.amplitude_f);
             }
             const DevParams &P = J.params[G.pset[node]];
@@ -853,9 +880,7 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel_noalloc(const DevJob
          node += (long long)gridDim.x * blockDim.x) {
         const long long s = node >> 5;
         const long long b = J.slice_ptr[s] + (node & 31), e = J.slice_ptr[s + 1];
-        R acc = R(0);
-        for (long long k = b; k < e; k += 32) acc += w[k] * V[J.ncol[k]];
-        vn[node] = acc;
+        vn[node] = node_sum<R>(w, J.ncol, V, b, e);
     }
 }
 

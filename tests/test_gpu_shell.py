@@ -104,3 +104,42 @@ def test_tets_shell_and_graph_junction(ctx, pname):
     with pytest.raises(ep.EPError):
         j.enable_bidomain(0.3, 0.1)                 # the shell is a monodomain medium
     j.destroy()
+
+
+@pytest.mark.parametrize("pname,two_way", [("mixed", 0), ("plain", 0), ("mixed", 1)])
+def test_cell_communication_nodes(ctx, pname, two_way):
+    """Communication nodes between shell cells and myocardial cells (Sec.
+    3.3, EP_PMJ_CELL, a graph without nodes): the shell's front excites the
+    slab through them after the orthodromic delay; with two-way coupling a
+    stimulated slab excites the shell back. V and activation times against
+    the oracle."""
+    import oracle
+    from paper_2112_12854_b300 import ep
+    from test_oracle_shell import _shell_and_slab
+    prec = _prec(pname)
+    tv, ta = tolerances(prec)
+    dt = 0.004
+    case, nt, ct, cs = _shell_and_slab(dt, stim_shell=not two_way, stim_slab=bool(two_way))
+    src = nt + np.array([int(np.argmin(np.linalg.norm(cs - p, axis=1))) for p in ([-0.3, 0.4, 0.25], [-3.0, 0.2, 0.25])])
+    dst = np.array([int(np.argmin(np.linalg.norm(ct - p, axis=1))) for p in ([0.2, 0.5, 0.25], [1.5, 0.5, 0.25])])
+    gp = w.GraphParams(delay_ortho=5.0, delay_anti=3.0, amplitude=-300.0, duration=1.0, radius=0.3,
+                       two_way=two_way)
+    g = w.Graph(np.zeros((0, 3)), np.zeros((0, 2), np.int32), np.zeros(0, np.uint8), np.zeros(0, np.uint8),
+                src.astype(np.int32), dst.astype(np.int32), np.full(2, w.JUNC_CELL, np.uint8), gp)
+    o = oracle.Sim(case)
+    o.attach_graph(g)
+    j = ep.job_from_case(ctx, case, precision=prec)
+    j.attach_graph(g, node_model=np.zeros(0, np.uint8))
+    done = 0
+    for k in (1500, 3000, 4000):
+        o.run(k - done)
+        j.step(k - done)
+        done = k
+        assert np.abs(j.V - o.V).max() <= tv
+    a, ao = j.activation_times(), o.activation_times()
+    assert act_error(a, ao) <= ta
+    if two_way:
+        assert np.isfinite(ao[nt:]).mean() > 0.9 and ao[src[0]] > ao[dst[0]] + gp.delay_anti
+    else:
+        assert np.isfinite(ao[:nt]).mean() > 0.9 and np.nanmin(ao[:nt]) > ao[src].min() + gp.delay_ortho
+    j.destroy()

@@ -159,3 +159,74 @@ def test_shell_with_tets_and_graph_junction(orc):
     a = s.activation_times()
     assert np.isfinite(a[nt:]).mean() > 0.9
     assert np.nanmin(a[nt:]) > s.graph_activation_times()[19] + 5.0
+
+
+def _shell_and_slab(dt, stim_shell=True, stim_slab=False):
+    xyz_t, tets = w.kuhn_box(12, 4, 2, 0.25)
+    xyz_s, tris = w.tri_box(15, 2, 0.4, origin=(-6.0, 0.0, 0.25))
+    xyz = np.concatenate([xyz_t, xyz_s])
+    tris = (tris + len(xyz_t)).astype(np.int32)
+    nt, ns = len(tets), len(tris)
+    ct = w.tet_centroids(xyz_t, tets)
+    cs = w.tri_centroids(xyz, tris)
+    ps = np.concatenate([np.zeros(nt, np.uint8), np.ones(ns, np.uint8)])
+    sm = np.concatenate([((ct[:, 0] > 2.5) if stim_slab else np.zeros(nt, bool)).astype(np.uint8),
+                         ((cs[:, 0] < -5.0) if stim_shell else np.zeros(ns, bool)).astype(np.uint8)])
+    case = w.TissueCase("shell+slab", xyz, tets, w.fibres_uniform(nt + ns), ps, sm,
+                        [w.ParamSet(model=0), w.ParamSet(model=2, D_l=2.82, D_t=2.82)],
+                        [w.Stimulus(-100.0, 0.0, 1.0)], dt, 0, 0.0, tris=tris)
+    return case, nt, ct, cs
+
+
+def test_cell_communication_node_equals_delayed_stimulus(orc):
+    """Sec. 3.3 between the 2D shell and the 3D myocardium: when the shell's
+    source cell crosses the threshold at t_s, the myocardial cells within R_S
+    of the target cell receive the stimulus over [t_s + delay, t_s + delay +
+    S_d). The result equals a run without the node in which those cells get
+    an ordinary stimulus protocol over the same whole steps."""
+    dt = 0.004
+    gp = w.GraphParams(delay_ortho=5.0, amplitude=-80.0, duration=1.0, radius=0.3)
+    case, nt, ct, cs = _shell_and_slab(dt)
+    src = nt + int(np.argmin(np.linalg.norm(cs - [-0.3, 0.4, 0.25], axis=1)))    # the shell's far end
+    dst = int(np.argmin(np.linalg.norm(ct - [0.2, 0.5, 0.25], axis=1)))
+    empty = w.Graph(np.zeros((0, 3)), np.zeros((0, 2), np.int32), np.zeros(0, np.uint8), np.zeros(0, np.uint8),
+                    np.array([src], np.int32), np.array([dst], np.int32), np.array([w.JUNC_CELL], np.uint8), gp)
+    s = orc.Sim(case)
+    s.attach_graph(empty)
+    steps = int(round(16 / dt))
+    s.run(steps)
+    ts = s.activation_times()[src]
+    near = np.linalg.norm(ct - ct[dst], axis=1) <= gp.radius
+    assert np.isfinite(ts) and near.sum() >= 3
+    on = [k for k in range(steps) if ts + gp.delay_ortho <= k * dt < ts + gp.delay_ortho + gp.duration]
+    assert len(on) == int(round(gp.duration / dt))
+    ref_case, _, _, _ = _shell_and_slab(dt)
+    ref_case.stim_mask[:nt][near] = 2
+    ref_case.stimuli = ref_case.stimuli + [w.Stimulus(gp.amplitude, on[0] * dt, len(on) * dt)]
+    r = orc.Sim(ref_case)
+    r.run(steps)
+    assert np.allclose(s.V, r.V, rtol=0, atol=1e-9)
+    a = s.activation_times()
+    assert np.all(a[:nt][near] > ts + gp.delay_ortho) and np.isfinite(a[:nt]).mean() > 0.9
+
+
+def test_cell_communication_node_two_way(orc):
+    """With two-way coupling the myocardium excites the shell back: the
+    slab's wave reaches the target cell at t_m, and the source cell is
+    stimulated from t_m + delay_anti; without two-way the shell stays at rest."""
+    dt = 0.004
+    for two_way in (0, 1):
+        gp = w.GraphParams(delay_anti=3.0, amplitude=-300.0, duration=1.0, radius=0.3, two_way=two_way)
+        case, nt, ct, cs = _shell_and_slab(dt, stim_shell=False, stim_slab=True)
+        src = nt + int(np.argmin(np.linalg.norm(cs - [-0.3, 0.4, 0.25], axis=1)))
+        dst = int(np.argmin(np.linalg.norm(ct - [0.2, 0.5, 0.25], axis=1)))
+        g = w.Graph(np.zeros((0, 3)), np.zeros((0, 2), np.int32), np.zeros(0, np.uint8), np.zeros(0, np.uint8),
+                    np.array([src], np.int32), np.array([dst], np.int32), np.array([w.JUNC_CELL], np.uint8), gp)
+        s = orc.Sim(case)
+        s.attach_graph(g)
+        s.run(int(round(14 / dt)))
+        a = s.activation_times()
+        if two_way:
+            assert np.isfinite(a[nt:]).mean() > 0.9 and a[src] > a[dst] + gp.delay_anti
+        else:
+            assert not np.isfinite(a[nt:]).any()

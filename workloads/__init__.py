@@ -398,7 +398,7 @@ class GraphParams:
     substeps: int = 0               # 0 = chosen from the stability bound
 
 
-JUNC_RESISTIVE, JUNC_TRIGGERED = 0, 1
+JUNC_RESISTIVE, JUNC_TRIGGERED, JUNC_CELL = 0, 1, 2   # JUNC_CELL: junction_node is a source cell
 
 
 @dataclass
