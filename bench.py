@@ -371,6 +371,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--tune-steps", type=int, default=5, help="steps per cell-kernel variant in the autotuner")
+    ap.add_argument("--cell-variant", type=int, default=-1,
+                    help="FP32 cell-kernel launch shape (0..7) instead of the autotuner's choice")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -422,7 +424,11 @@ def main():
 
     # warm-up (the autotuner's steps are part of it), then the timed region: K steps
     # (captured-graph replay) bracketed by barrier + sync
-    chosen, variant_ms = ep.autotune([job], args.tune_steps)
+    if args.cell_variant >= 0:
+        ep.set_cell_variant(ctx, ep.EP_FP32_MIXED, args.cell_variant)
+        chosen, variant_ms = np.array([args.cell_variant, -1]), None
+    else:
+        chosen, variant_ms = ep.autotune([job], args.tune_steps)
     job.step(args.warmup)
     torch.cuda.synchronize()
     clocks = Clocks(local)
@@ -456,7 +462,7 @@ def main():
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy)" if peak_kind == "measured"
                 else "fallback 6.4 TB/s",
                 "algorithmic_bytes_per_cell": CELL_BYTES, "cell_kernel_ms": cell_ms, "node_kernel_ms": node_ms,
-                "cell_variant": int(chosen[0]), "autotune_ms": [round(float(x), 4) for x in variant_ms[0]],
+                "cell_variant": int(chosen[0]), "autotune_ms": None if variant_ms is None else [round(float(x), 4) for x in variant_ms[0]],
                 "node_kernel_gbs": node_bytes / (node_ms * 1e-3) / 1e9,
                 "step_gbs": (CELL_BYTES * N + node_bytes) / ((cell_ms + node_ms) * 1e-3) / 1e9}
 
