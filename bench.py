@@ -60,7 +60,7 @@ def wedge_case(dims):
 # Sources the node and cell kernels are compiled from (the profiles under
 # profiles/ record the hash of these files at capture time).
 STEP_KERNEL_SOURCES = ("kernels.cu", "kernels.h", "devtypes.h", "cellmath.cuh", "ttcells.cuh", "crncell.cuh",
-                       "varmap.h")
+                       "varmap.h", "nodesum.cuh")
 
 
 def kernel_source_hash() -> str:

@@ -18,6 +18,7 @@
 #include <cmath>
 
 #include "bidomain.h"
+#include "nodesum.cuh"
 
 namespace ep {
 
@@ -119,9 +120,7 @@ __device__ void node_pass(const DevJob &J, const R *__restrict__ x, R scale, R *
     for (long long node = gtid; node < J.n_nodes; node += gsz) {
         const long long s = node >> 5;
         const long long b = J.slice_ptr[s] + (node & 31), e = J.slice_ptr[s + 1];
-        R acc = R(0);
-        for (long long k = b; k < e; k += 32) acc += w[k] * x[J.ncol[k]];
-        vn[node] = acc * scale;
+        vn[node] = node_sum<R>(w, J.ncol, x, b, e) * scale;
     }
 }
 

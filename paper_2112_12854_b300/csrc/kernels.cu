@@ -19,6 +19,7 @@
 
 #include "crncell.cuh"
 #include "kernels.h"
+#include "nodesum.cuh"
 #include "ttcells.cuh"
 #include "varmap.h"
 
@@ -49,28 +50,6 @@ __device__ __forceinline__ R stimulus(const DevJob &J, unsigned mask, long long 
         if (on) is += pick<R>(s.amp, s.amp_f);
     }
     return is;
-}
-
-// Inverse-distance node value (S1) over the sliced-ELL entries b, b+32, ...
-// < e of one node. The loads of four entries are issued before their
-// products are accumulated, so four gathers are in flight at once; the sum
-// is still taken in entry order.
-template <class R>
-__device__ __forceinline__ R node_sum(const R *__restrict__ w, const int *__restrict__ col, const R *__restrict__ V,
-                                      long long b, long long e) {
-    R acc = R(0);
-    long long k = b;
-    for (; k + 96 < e; k += 128) {
-        const int c0 = col[k], c1 = col[k + 32], c2 = col[k + 64], c3 = col[k + 96];
-        const R w0 = w[k], w1 = w[k + 32], w2 = w[k + 64], w3 = w[k + 96];
-        const R v0 = V[c0], v1 = V[c1], v2 = V[c2], v3 = V[c3];
-        acc += w0 * v0;
-        acc += w1 * v1;
-        acc += w2 * v2;
-        acc += w3 * v3;
-    }
-    for (; k < e; k += 32) acc += w[k] * V[col[k]];
-    return acc;
 }
 
 template <class R>

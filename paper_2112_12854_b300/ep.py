@@ -508,8 +508,8 @@ N_CELL_VARIANTS = 8
 
 def autotune(jobs, steps_per_variant: int = 10):
     """Pick the fastest cell-kernel launch shape per precision (ep_autotune).
-    Advances the jobs by 6 * steps_per_variant real steps. Returns
-    (chosen[2], ms[2][6])."""
+    Advances the jobs by N_CELL_VARIANTS * steps_per_variant real steps.
+    Returns (chosen[2], ms[2][N_CELL_VARIANTS])."""
     arr = (_P * len(jobs))(*[j._h for j in jobs])
     chosen = np.zeros(2, np.int32)
     ms = np.zeros(2 * N_CELL_VARIANTS, np.float64)
