@@ -2,7 +2,7 @@
 wedge (100 x 100 x 20 cubes of 0.25 mm, the wedge's construction: TP06
 endo / M / epi by depth, fibres rotating -60..+60 deg, corner stimulus):
 FP32 mixed and FP64 plain against one oracle run, V at every cell every
-5 ms and the activation map at the end."""
+5 ms, the activation map and every state variable at the end."""
 import numpy as np
 import pytest
 
@@ -43,5 +43,14 @@ def test_wedge_crop_every_5ms():
         # cells crossing within the last 0.1 ms may fall on either side of the final step
         settled = (np.where(np.isfinite(a), a, np.inf) < t_end - 0.1) | (np.where(np.isfinite(g), g, np.inf) < t_end - 0.1)
         assert act_error(g[settled], a[settled]) <= ta
+        # every TP06 state variable at 25 ms, relative to its largest magnitude on the crop
+        rel_tol = 1e-9 if p == ep.EP_FP64_PLAIN else 1e-3
+        for v, name in enumerate(ep.model_varnames(ep.EP_TP06)):
+            if v == 0:
+                continue
+            r = o.get(v)
+            rel = np.abs(j.read(v) - r).max() / np.abs(r).max()
+            print("mixed" if p == ep.EP_FP32_MIXED else "plain", f"{name:>6s} max|d|/max|ref| {rel:.2e}")
+            assert rel <= rel_tol, name
         j.destroy()
     ctx.close()
