@@ -317,7 +317,8 @@ def run_bidomain(ctx, args, dims, stream, torch, peak):
             "solve_phase_ms_per_step": {k: (b - a) / args.bido_steps for k, a, b in
                                         zip(("node_values", "fluxes_and_dots", "gs_pass2", "gs_pass3", "updates"),
                                             st0["phase_ms"], st1["phase_ms"])},
-            "solver": "restarted GMRES(12), classical Gram-Schmidt, tol 1e-5 relative / 1e-3 mV/ms per cell absolute",
+            "solver": "restarted GMRES(12), classical Gram-Schmidt, started from 2 v_e^n - v_e^(n-1), "
+                      "tol 1e-5 relative / 1e-3 mV/ms per cell absolute",
             "solve_roofline": {"bound": "hbm", "kernel": "bido_kernel<float>", "achieved": gbs, "peak": peak,
                                "unit": "GB/s", "frac": gbs / peak,
                                "alg_bytes_per_step": (st1["alg_bytes"] - st0["alg_bytes"]) / args.bido_steps},

@@ -444,8 +444,10 @@ typedef struct {
  *   1. updates V with the intracellular flux of V^n + v_e^n (first line of
  *      Eq. 6), everything else as in the monodomain step;
  *   2. solves the second line of Eq. 6, L_ie(v_e^{n+1}) = -L_i(V^{n+1}), by
- *      restarted GMRES started from v_e^n, L_ie being the same
- *      finite-volume operator for D_i + D_e;
+ *      restarted GMRES, L_ie being the same finite-volume operator for
+ *      D_i + D_e. The solve starts from 2 v_e^n - v_e^{n-1} once two
+ *      consecutive solutions are held, else from v_e^n; a v_e written by
+ *      ep_bidomain_write_ve counts as one solution;
  *   3. fixes v_e to zero volume-weighted mean (the equation leaves a
  *      constant free under zero-flux boundaries).
  * solver NULL takes the defaults: restart 12, CGS, max_iter 2000, and

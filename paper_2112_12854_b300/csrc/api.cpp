@@ -736,6 +736,8 @@ int bido_apply(ep_job *job) {
     if (!rc) rc = grab(N * r, &bb);
     if (!rc) rc = grab(a.ld * r, &w);
     if (!rc) rc = grab(size_t(B.restart + 1) * a.ld * r, &basis);
+    void *vprev = nullptr;
+    if (!rc) rc = grab(a.ld * r, &vprev);
     if (!rc) rc = grab(2 * size_t(kBidoMaxRestart + 1) * B.grid * sizeof(double), &part);
     if (!rc) rc = grab(sizeof(BidoStats), &st);
     if (!rc) rc = grab(sizeof(BidoSync), &sy);
@@ -749,6 +751,7 @@ int bido_apply(ep_job *job) {
     a.b = bb;
     a.w = w;
     a.basis = basis;
+    a.vprev = vprev;
     a.part = static_cast<double *>(part);
     a.stats = static_cast<BidoStats *>(st);
     a.sync = static_cast<BidoSync *>(sy);
@@ -764,6 +767,7 @@ int bido_apply(ep_job *job) {
     cudaError_t e = cudaMemsetAsync(ve, 0, a.ld * r, ctx->upload);
     if (e == cudaSuccess) e = cudaMemsetAsync(w, 0, a.ld * r, ctx->upload);
     if (e == cudaSuccess) e = cudaMemsetAsync(basis, 0, size_t(B.restart + 1) * a.ld * r, ctx->upload);
+    if (e == cudaSuccess) e = cudaMemsetAsync(vprev, 0, a.ld * r, ctx->upload);
     if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(BidoStats), ctx->upload);
     if (e == cudaSuccess) e = cudaMemsetAsync(sy, 0, sizeof(BidoSync), ctx->upload);
     if (e == cudaSuccess)

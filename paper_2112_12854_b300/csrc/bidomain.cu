@@ -217,11 +217,22 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
         // right-hand side b = -L_i(V^{n+1}) and its norm
         node_pass<R>(J, V, R(1), vn, gtid, gsz);
         BIDO_SYNC(0);
+        // initial guess: v_e^n, or 2 v_e^n - v_e^{n-1} once two consecutive solutions are held
+        // (a first-order extrapolation in time; the gauge of both is the same)
+        const int hist = A.stats->hist;
+        R *__restrict__ vp = static_cast<R *>(A.vprev);
         acc[0] = R(0);
         for (long long c = gtid; c < n; c += gsz) {
             const R bc = -flux<R>(J, J.wa, J.wb, J.q, vn, V, R(1), c);
             b[c] = bc;
             acc[0] += bc * bc;
+            if (hist >= 2) {
+                const R xc = x[c];
+                x[c] = R(2) * xc - vp[c];
+                vp[c] = xc;
+            } else if (hist == 1) {
+                vp[c] = x[c];
+            }
         }
         block_partials<R>(acc, 1, part_w(), red_sh);
         BIDO_SYNC(1);
@@ -417,8 +428,10 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
     BIDO_SYNC(0);
     R *__restrict__ xd = static_cast<R *>(A.xdiv);
     for (long long c = gtid; c < n; c += gsz) xd[c] = flux<R>(J, J.wa, J.wb, J.q, vn, x, R(1), c);
+    if (A.mode == 1 && blockIdx.x == 0 && threadIdx.x == 0) A.stats->hist = 1;   // v_e set from outside
     if (A.mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
         BidoStats *st = A.stats;
+        st->hist = st->hist < 2 ? st->hist + 1 : 2;
         st->last_iters = iters;
         st->total_iters += iters;
         st->solves += 1;

@@ -27,6 +27,8 @@ struct BidoStats {
     double phase_ms[5];      // device time by phase: node values, fluxes, GS pass 2, GS pass 3, updates
     int failed;              // some solve stopped at max_iter without converging
     int timeout;             // a grid barrier gave up (error flag)
+    int hist;                // consecutive solutions held: 0 none, 1 v_e^n, 2 also v_e^{n-1} (in vprev)
+    int pad;
 };
 
 // Grid barrier state of the cooperative solve kernel.
@@ -44,6 +46,7 @@ struct BidoArgs {
     void *ve, *w;                // [ld] each, zero past n_cells
     void *xdiv, *b;              // [n_cells] each
     void *basis;                 // [(restart + 1) * ld], zero past n_cells
+    void *vprev;                 // [ld]: the solution before the last one (initial-guess extrapolation)
     long long ld;
     double *part;                // [(kBidoMaxRestart + 1) * grid] block partials
     BidoStats *stats;
