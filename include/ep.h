@@ -452,7 +452,9 @@ typedef struct {
  *      constant free under zero-flux boundaries).
  * solver NULL takes the defaults: restart 12, CGS, max_iter 2000, and
  * tol 1e-5, atol 1e-3 mV/ms (FP32 mixed: about the rounding floor of an FP32
- * residual) or tol 1e-11, atol 0 (FP64 plain).
+ * residual) or tol 1e-11, atol 1e-11 mV/ms (FP64 plain: far above an FP64
+ * residual's rounding floor, so that a right-hand side near zero -- a
+ * uniform tissue at rest -- still meets the rule).
  * v_e is solved once from the current V before returning. Calling it again
  * replaces the settings; ep_params_set keeps them (and rebuilds the
  * operator). The solve is one cooperative launch per job and step on the

@@ -1594,7 +1594,7 @@ int ep_bidomain_enable(ep_job *job, const double *De_l, const double *De_t, int3
         sv = *solver;
     } else {
         const bool plain = job->precision == EP_FP64_PLAIN;
-        sv = ep_bidomain_solver{plain ? 1e-11 : 1e-5, plain ? 0.0 : 1e-3, 12, 0, 2000};
+        sv = ep_bidomain_solver{plain ? 1e-11 : 1e-5, plain ? 1e-11 : 1e-3, 12, 0, 2000};
     }
     if (!(sv.tol > 0.0) || !(sv.atol >= 0.0) || sv.restart < 1 || sv.restart > kBidoMaxRestart || sv.max_iter < 1 ||
         (sv.reorth != 0 && sv.reorth != 1))

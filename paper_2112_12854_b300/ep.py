@@ -457,7 +457,7 @@ class Job:
         if tol is not None or atol is not None or restart != 12 or reorth != 0 or max_iter != 2000:
             plain = params is not None and params.precision == EP_FP64_PLAIN
             sv = BidoSolver(float(tol if tol is not None else (1e-11 if plain else 1e-5)),
-                            float(atol if atol is not None else (0.0 if plain else 1e-3)),
+                            float(atol if atol is not None else (1e-11 if plain else 1e-3)),
                             int(restart), int(reorth), int(max_iter))
         self.ctx.check(load().ep_bidomain_enable(self._h, _ptr(el), _ptr(et), int(n_sets),
                                                  ctypes.byref(sv) if sv is not None else None))

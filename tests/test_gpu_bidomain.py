@@ -75,6 +75,46 @@ def test_bidomain_parity(ctx, pname, reorth):
     j.destroy()
 
 
+@pytest.mark.parametrize("pname", ["mixed", "plain"])
+def test_bidomain_long_run_and_restart_of_the_initial_guess(ctx, pname):
+    """The GPU solve starts from 2 v_e^n - v_e^{n-1} (the oracle from v_e^n).
+    While the front moves, the extrapolated start needs fewer Arnoldi steps
+    than the first solve after v_e is written from the host, which starts
+    from v_e^n; over 2500 steps (50 ms: the front crosses the slab and the
+    plateau begins) no solve fails and V and v_e stay within tolerance of
+    the oracle."""
+    import oracle
+    from paper_2112_12854_b300 import ep
+    prec = _prec(pname)
+    tv, _ = tolerances(prec)
+    case = _slab()
+    o = oracle.Sim(case)
+    o.set_bidomain(DEL, DET, tol=1e-11)
+    j = ep.job_from_case(ctx, case, precision=prec)
+    j.enable_bidomain(DEL, DET)
+    j.step(60)
+    t0 = j.bidomain_stats()["total_iters"]
+    j.step(20)
+    extrap = (j.bidomain_stats()["total_iters"] - t0) / 20
+    j.ve = j.ve                                  # host write: the next solve starts from v_e^n
+    j.step(1)
+    first = j.bidomain_stats()["last_iters"]
+    print(pname, "Arnoldi steps: extrapolated start", extrap, "first solve after a write", first)
+    assert extrap < first
+    done = 81
+    o.run(done)
+    for n in (500, 1500, 2500):
+        o.run(n - done)
+        j.step(n - done)
+        done = n
+        st = j.bidomain_stats()
+        dv, de = np.abs(j.V - o.V).max(), np.abs(j.ve - o.ve).max()
+        print(pname, n, "max|dV|", dv, "max|dve|", de, "mean Arnoldi steps", st["total_iters"] / st["solves"])
+        assert not st["failed"] and np.isfinite(j.V).all() and np.isfinite(j.ve).all()
+        assert dv <= tv and de <= TOL_VE[pname]
+    j.destroy()
+
+
 def test_parallel_tensors_reduce_to_monodomain_on_gpu(ctx):
     """M_e = lambda M_i: the GPU bidomain run equals the GPU monodomain run
     with M = lambda M_i / (1 + lambda) (FP64 plain, solver tolerance)."""
