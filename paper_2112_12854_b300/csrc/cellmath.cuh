@@ -22,6 +22,12 @@ template <class R>
 __device__ __forceinline__ R rush_larsen(R y, R yinf, R tau, R dt) {
     return yinf + (y - yinf) * fexp(-dt / tau);
 }
+// The same update for a gate whose time constant is 1 / rate (rate = alpha +
+// beta, or a multiple of it): no reciprocal of the rate is taken.
+template <class R>
+__device__ __forceinline__ R rush_larsen_rate(R y, R yinf, R rate, R dt) {
+    return yinf + (y - yinf) * fexp(-dt * rate);
+}
 
 // Logistic 1/(1 + exp(x)).
 template <class R>

@@ -90,7 +90,8 @@ __device__ __forceinline__ R crn_step(const CellIO<R> &io, const DevParams &P, R
     R al, be;
     al = R(0.32) * lin_over_1mexp(V + R(47.13), R(10));
     be = R(0.08) * fexp(-V * R(1.0 / 11.0));
-    xo[so] = rush_larsen(m, al / (al + be), R(1) / (al + be), dt);
+    R ab = al + be;
+    xo[so] = rush_larsen_rate(m, al / ab, ab, dt);
     if (V >= R(-40)) {
         al = R(0);
         be = R(1) / (R(0.13) * (R(1) + fexp(-(V + R(10.66)) * R(1.0 / 11.1))));
@@ -98,7 +99,8 @@ __device__ __forceinline__ R crn_step(const CellIO<R> &io, const DevParams &P, R
         al = R(0.135) * fexp(-(V + R(80)) * R(1.0 / 6.8));
         be = R(3.56) * fexp(R(0.079) * V) + R(3.1e5) * fexp(R(0.35) * V);
     }
-    xo[2 * so] = rush_larsen(h, al / (al + be), R(1) / (al + be), dt);
+    ab = al + be;
+    xo[2 * so] = rush_larsen_rate(h, al / ab, ab, dt);
     if (V >= R(-40)) {
         al = R(0);
         be = R(0.3) * fexp(R(-2.535e-7) * V) * logistic(R(-0.1) * (V + R(32)));
@@ -107,25 +109,26 @@ __device__ __forceinline__ R crn_step(const CellIO<R> &io, const DevParams &P, R
              logistic(R(0.311) * (V + R(79.23)));
         be = R(0.1212) * fexp(R(-0.01052) * V) * logistic(R(-0.1378) * (V + R(40.14)));
     }
-    xo[3 * so] = rush_larsen(jj, al / (al + be), R(1) / (al + be), dt);
+    ab = al + be;
+    xo[3 * so] = rush_larsen_rate(jj, al / ab, ab, dt);
     // oa and ua share their rate functions
     al = R(0.65) / (fexp(-(V + R(10)) * R(1.0 / 8.5)) + fexp(-(V - R(30)) * R(1.0 / 59.0)));
     be = R(0.65) / (R(2.5) + fexp((V + R(82)) * R(1.0 / 17.0)));
-    const R tau_a = R(1) / ((al + be) * R(3));
-    xo[4 * so] = rush_larsen(oa, logistic(-(V + R(20.47)) * R(1.0 / 17.54)), tau_a, dt);
-    xo[6 * so] = rush_larsen(ua, logistic(-(V + R(30.3)) * R(1.0 / 9.6)), tau_a, dt);
+    const R rate_a = (al + be) * R(3);
+    xo[4 * so] = rush_larsen_rate(oa, logistic(-(V + R(20.47)) * R(1.0 / 17.54)), rate_a, dt);
+    xo[6 * so] = rush_larsen_rate(ua, logistic(-(V + R(30.3)) * R(1.0 / 9.6)), rate_a, dt);
     al = R(1) / (R(18.53) + fexp((V + R(113.7)) * R(1.0 / 10.95)));
     be = R(1) / (R(35.56) + fexp(-(V + R(1.26)) * R(1.0 / 7.44)));
-    xo[5 * so] = rush_larsen(oi, logistic((V + R(43.1)) * R(1.0 / 5.3)), R(1) / ((al + be) * R(3)), dt);
+    xo[5 * so] = rush_larsen_rate(oi, logistic((V + R(43.1)) * R(1.0 / 5.3)), (al + be) * R(3), dt);
     al = R(1) / (R(21) + fexp(-(V - R(185)) * R(1.0 / 28.0)));
     be = fexp((V - R(158)) * R(1.0 / 16.0));
-    xo[7 * so] = rush_larsen(ui, logistic((V - R(99.45)) * R(1.0 / 27.48)), R(1) / ((al + be) * R(3)), dt);
+    xo[7 * so] = rush_larsen_rate(ui, logistic((V - R(99.45)) * R(1.0 / 27.48)), (al + be) * R(3), dt);
     al = R(0.0003) * lin_over_1mexp(V + R(14.1), R(5));
     be = R(7.3898e-5) * lin_over_expm1(V - R(3.3328), R(5.1237));
-    xo[8 * so] = rush_larsen(xr, logistic(-(V + R(14.1)) * R(1.0 / 6.5)), R(1) / (al + be), dt);
+    xo[8 * so] = rush_larsen_rate(xr, logistic(-(V + R(14.1)) * R(1.0 / 6.5)), al + be, dt);
     al = R(4e-5) * lin_over_1mexp(V - R(19.9), R(17));
     be = R(3.5e-5) * lin_over_expm1(V - R(19.9), R(9));
-    xo[9 * so] = rush_larsen(xs, R(1) / fsqrt(R(1) + fexp(-(V - R(19.9)) * R(1.0 / 12.7))), R(0.5) / (al + be), dt);
+    xo[9 * so] = rush_larsen_rate(xs, R(1) / fsqrt(R(1) + fexp(-(V - R(19.9)) * R(1.0 / 12.7))), (al + be) * R(2), dt);
     {
         const R yv = (V + R(10)) * R(1.0 / 6.24);
         const R g = yv == R(0) ? R(1) : -fexpm1(-yv) / yv;

@@ -138,8 +138,8 @@ __device__ __forceinline__ R tt_step(const CellIO<R> &io, const DevParams &P, R 
                  logistic(R(0.311) * (V + R(79.23)));
             bj = R(0.02424) * fexp(R(-0.01052) * V) * logistic(R(-0.1378) * (V + R(40.14)));
         }
-        xo[3 * so] = rush_larsen(h, hinf, R(1) / (ah + bh), dt);
-        xo[4 * so] = rush_larsen(jj, hinf, R(1) / (aj + bj), dt);
+        xo[3 * so] = rush_larsen_rate(h, hinf, ah + bh, dt);
+        xo[4 * so] = rush_larsen_rate(jj, hinf, aj + bj, dt);
     }
     yinf = logistic((R(-26) - V) * R(1.0 / 7.0));
     al = R(450) * logistic((R(-45) - V) * R(0.1));
@@ -192,7 +192,7 @@ __device__ __forceinline__ R tt_step(const CellIO<R> &io, const DevParams &P, R 
     }
     {
         const R rate = k2 * Cass + R(0.005);
-        xo[14 * so] = rush_larsen(rr, R(0.005) / rate, R(1) / rate, dt);
+        xo[14 * so] = rush_larsen_rate(rr, R(0.005) / rate, rate, dt);
     }
     if (PURKINJE) {
         yinf = logistic((V + R(80.6)) * R(1.0 / 6.8));
