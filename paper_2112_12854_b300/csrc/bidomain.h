@@ -1,8 +1,9 @@
 // Bidomain extension of a job (Eq. 1, Eqs. 5-6): the extracellular
 // potential v_e from the elliptic equation
 //     L_ie(v_e^{n+1}) = -L_i(V^{n+1}),
-// solved after each step by restarted GMRES started from v_e^n (Sec. 3.2),
-// and the intracellular flux of v_e, L_i(v_e), handed to the next step's
+// solved after each step by restarted GMRES (Sec. 3.2) started from the
+// extrapolation 2 v_e^n - v_e^{n-1} once two consecutive solutions are held
+// (from v_e^n before that, as the paper does), and the intracellular flux of v_e, L_i(v_e), handed to the next step's
 // cell update (which adds it to L_i(V)). L_i is the job's own folded
 // operator (the parameter sets' D_l, D_t are the intracellular
 // diffusivities); L_ie the same operator folded with D_i + D_e.
