@@ -133,3 +133,45 @@ def test_stimulus_schedule(orc):
     s = orc.Stim(-52.0, 2.0, 0.5, 10.0)
     on = [orc.stim_active(s, 0.5, n) for n in range(30)]
     assert [n for n in range(30) if on[n]] == [4, 24]
+
+
+# TP06 / Stewart geometry and calcium buffers (the models' parameter tables)
+_F, _CM, _VC, _VSR, _VSS = 96485.3415, 0.185, 0.016404, 0.001094, 0.00005468
+_BUF = {"Ca_i": (0.2, 0.001, _VC), "Ca_SR": (10.0, 0.3, _VSR), "Ca_SS": (0.4, 0.00025, _VSS)}
+
+
+def _charge(orc, model, s):
+    """C_m V minus the ionic charge held in the cell, F [V_c (Na_i + K_i) +
+    2 sum over compartments of volume x total (free + buffered) calcium]. The
+    model's V equation, C_m dV/dt = -C_m (I_ion + I_stim), and its
+    concentration equations move the same charge (the stimulus is carried by
+    K+), so this is constant along any trajectory."""
+    names = orc.model_varnames(model)
+    x = {n: s[k] for k, n in enumerate(names)}
+    ca = sum(vol * (x[n] + B * x[n] / (x[n] + K)) for n, (B, K, vol) in _BUF.items())
+    return _CM * x["V"] - _F * (_VC * (x["Na_i"] + x["K_i"]) + 2.0 * ca)
+
+
+@pytest.mark.parametrize("model,variant", [(0, 0), (0, 1), (0, 2), (2, 0)])
+@pytest.mark.parametrize("integrator", [0, 1])
+def test_charge_conservation(orc, model, variant, integrator):
+    """Forward Euler (or AB2) on the currents and on the buffered calcium
+    totals, Rush-Larsen on the gates: every current appears in the V equation
+    and in the concentration equations with the same sign and valence, the
+    SR and subspace fluxes only move calcium between compartments, so the
+    charge balance holds step by step to rounding -- through the stimulus,
+    the upstroke and the whole action potential. A dropped current, a wrong
+    valence or a wrong compartment volume breaks it by about C_m x (the
+    current) x (the time it flows), orders of magnitude above the bound."""
+    ps = w.ParamSet(model=model, variant=variant)
+    s = orc.model_init(ps)
+    q0 = _charge(orc, model, s)
+    stim = orc.Stim(-52.0, 0.0, 1.0, 0.0)
+    v, s = orc.cell_run(ps, DT, 200, stim, 1, s, integrator=integrator)       # stimulus and upstroke
+    q1 = _charge(orc, model, s)
+    v2, s = orc.cell_run(ps, DT, 20000, None, 100, s, integrator=integrator)  # the rest of a 400 ms beat
+    q2 = _charge(orc, model, s)
+    swing = _CM * (max(v.max(), v2.max()) - min(v.min(), v2.min()))
+    assert swing > 15.0                          # an action potential happened
+    assert abs(q1 - q0) < 1e-6 * swing and abs(q2 - q0) < 1e-6 * swing
+
