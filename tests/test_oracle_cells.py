@@ -175,3 +175,42 @@ def test_charge_conservation(orc, model, variant, integrator):
     assert swing > 15.0                          # an action potential happened
     assert abs(q1 - q0) < 1e-6 * swing and abs(q2 - q0) < 1e-6 * swing
 
+
+
+# Courtemanche geometry and calcium buffers (the model's parameter table)
+_CRN = dict(F=96.4867, Cm=100.0, Vi=13668.0, Vup=1109.52, Vrel=96.48)
+
+
+def _charge_crn(orc, s):
+    """The same balance for Courtemanche: cytosolic calcium buffered by
+    calmodulin and troponin, release-store calcium by calsequestrin, the
+    uptake store unbuffered."""
+    x = dict(zip(orc.model_varnames(1), s))
+    cai, cr = x["Ca_i"], x["Ca_rel"]
+    cat = cai + 0.05 * cai / (cai + 0.00238) + 0.07 * cai / (cai + 0.0005)
+    crt = cr + 10.0 * cr / (cr + 0.8)
+    c = _CRN
+    return c["Cm"] * x["V"] - c["F"] * (c["Vi"] * (x["Na_i"] + x["K_i"])
+                                        + 2.0 * (c["Vi"] * cat + c["Vup"] * x["Ca_up"] + c["Vrel"] * crt))
+
+
+def test_courtemanche_charge_balance_first_order():
+    """Courtemanche carries its stimulus on no ion, so the balance moves by
+    exactly the stimulus charge, C_m x 52 x 1 ms; and it advances the free
+    cytosolic and release-store calcium with the buffering factor, so what
+    remains is a first-order error: it halves with dt and extrapolates to
+    zero. A dropped or mis-signed current would leave a part that does not
+    shrink with dt."""
+    import oracle as orc
+    ps = w.ParamSet(model=1)
+    res, swing = {}, 0.0
+    for dt in (0.02, 0.01, 0.005):
+        s = orc.model_init(ps)
+        q0 = _charge_crn(orc, s)
+        v, s = orc.cell_run(ps, dt, int(round(400.0 / dt)), orc.Stim(-52.0, 0.0, 1.0, 0.0), 1, s)
+        res[dt] = _charge_crn(orc, s) - q0 - _CRN["Cm"] * 52.0 * int(round(1.0 / dt)) * dt
+        swing = _CRN["Cm"] * (v.max() - v.min())
+    assert swing > 5000.0
+    for a, b in ((0.02, 0.01), (0.01, 0.005)):
+        assert abs(res[a] / res[b] - 2.0) < 0.05
+        assert abs(2.0 * res[b] - res[a]) < 1e-3 * swing
