@@ -10,10 +10,16 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
   - geometry, S1-S3 diffusion operator: pinned (conservation, row sums,
     linear patch test, cosine-eigenmode decay and its O(h^2) convergence,
     fibre-rotation decay rates, two-point symmetry, hand-derived two-tet case);
-  - TP06 / Courtemanche / Stewart: physiological pins only (rest potential,
-    APD, plateau, RL closed form, first-order time convergence). Parity with
-    the published model traces is unpinned: the model papers' figures and
-    reference code are not available here.
+  - TP06 / Courtemanche / Stewart: physiological pins (rest potential, APD,
+    plateau, RL closed form, first-order time convergence) and the charge
+    balance between the V equation and the ion concentrations (exact for
+    TP06 and Stewart, exact up to the stimulus charge and a first-order
+    buffering error for Courtemanche). Parity with the published model
+    traces is unpinned: the model papers' figures and reference code are not
+    available here;
+  - the conduction graph, the 2D shell, the bidomain solve and AB2: pinned in
+    their own test files (conservation, closed forms, convergence orders,
+    reductions to the monodomain case).
 """
 from __future__ import annotations
 
