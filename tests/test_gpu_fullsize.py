@@ -87,3 +87,37 @@ def test_wedge_full_size_sampled_one_step(pname):
             tol = (1e-5 * max(1.0, abs(ref))) if pname == "mixed" else 1e-11 * max(1.0, abs(ref))
             assert abs(got - ref) <= tol, (int(c), v, got, ref)
     print(pname, "cells checked", len(sample), "front cells", len(front), "max |dV| one step", worst)
+
+
+def test_wedge_full_size_charge_balance_fp64():
+    """A property that holds at any size, checked on the full 9.6M-cell wedge
+    (plain FP64, captured-graph replay): the face fluxes cancel in the
+    volume-weighted sum and TP06 moves in ions the charge its V equation
+    moves (stimulus carried by K+), so sum_c vol_c [C_m V - F (V_c (Na_i +
+    K_i) + 2 sum volume x total calcium)] stays constant to rounding while
+    the corner stimulus fires and the front spreads (300 steps)."""
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2112_12854_b300 import ep
+    from test_oracle_cells import _BUF, _CM, _F, _VC
+    case = w.wedge_case()
+    x = case.xyz[case.tets]
+    vol = np.abs(np.einsum("ij,ij->i", np.cross(x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]), x[:, 3] - x[:, 0])) / 6.0
+    del x
+    ctx = ep.Context()
+    job = ep.job_from_case(ctx, case, precision=ep.EP_FP64_PLAIN)
+    names = ep.model_varnames(ep.EP_TP06)
+    keep = ["V", "Na_i", "K_i"] + list(_BUF)
+    s0 = {n: job.read(names.index(n)) for n in keep}
+    job.step(300)
+    s1 = {n: job.read(names.index(n)) for n in keep}
+    job.destroy()
+    ctx.close()
+    tot = lambda c, B, K: c + B * c / (c + K)
+    dq = _CM * (s1["V"] - s0["V"]) - _F * _VC * ((s1["Na_i"] - s0["Na_i"]) + (s1["K_i"] - s0["K_i"]))
+    for n, (B, K, v) in _BUF.items():
+        dq -= 2.0 * _F * v * (tot(s1[n], B, K) - tot(s0[n], B, K))
+    swing = _CM * float(np.dot(vol, np.abs(s1["V"] - s0["V"])))
+    imbalance = float(np.dot(vol, dq))
+    print("charge swing", swing, "imbalance", imbalance)
+    assert swing > 50.0 and abs(imbalance) < 1e-7 * swing   # measured 1.25e-9 of the swing

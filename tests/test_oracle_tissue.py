@@ -54,3 +54,31 @@ def test_slab_activation_map(orc):
     bins = [a[order][(xs >= k) & (xs < k + 1)].mean() for k in range(8)]
     assert all(b2 > b1 for b1, b2 in zip(bins[1:], bins[2:]))
     assert s.step_index == 1000
+
+
+def test_tissue_charge_balance(orc):
+    """Zero-flux boundaries and face fluxes that leave one cell and enter its
+    neighbour make the diffusion term sum to zero over the cells (weighted
+    by volume), and TP06 moves in ions exactly the charge its V equation
+    moves (stimulus carried by K+). So the volume-weighted charge balance of
+    the slab, C_m V - F [V_c (Na_i + K_i) + 2 sum volume x total calcium],
+    stays constant to rounding while the front crosses it. A diffusion term
+    divided by the wrong volume, or a boundary face that lets current out,
+    breaks it by the order of the C_m V swing."""
+    from test_oracle_cells import _charge
+    case = w.slab_case()
+    x = case.xyz[case.tets]
+    vol = np.abs(np.einsum("ij,ij->i", np.cross(x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]), x[:, 3] - x[:, 0])) / 6.0
+    s = orc.Sim(case)
+    names = orc.model_varnames(0)
+
+    def balance():
+        state = np.stack([s.V if n == "V" else s.get(k) for k, n in enumerate(names)])
+        q = _charge(orc, 0, state)
+        return float(np.dot(vol, q)), float(np.dot(vol, state[0]))
+    q0, v0 = balance()
+    for n in (100, 500, 1000):
+        s.run(n - s.step_index)
+        q, v = balance()
+        swing = 0.185 * abs(v - v0)
+        assert swing > 100.0 and abs(q - q0) < 1e-9 * swing
