@@ -2,6 +2,7 @@
 loads and exports the C ABI, and its planner's folded FP64 operator equals
 the oracle's face-by-face evaluation of Eqs. 7-8 (an identity, not shared
 code: the planner folds S1-S3 into per-cell coefficients independently)."""
+import ctypes
 import os
 import re
 
@@ -147,6 +148,27 @@ def test_planner_rejects_bad_meshes(case):
     with pytest.raises(ep.EPError) as e:
         ep.plan_inspect(xyz, tets, _params([w.ParamSet()]))
     assert e.value.code == ep.EP_EMESH
+
+
+@pytest.mark.parametrize("n_cells,n_nodes", [(0, 4), (1 << 31, 4), (1, 1 << 31)])
+def test_planner_rejects_empty_and_oversized_meshes(n_cells, n_nodes):
+    """Cell and node indices are 32-bit on the device: an empty mesh and one
+    with 2^31 cells or nodes are refused with EP_EINVAL before any array is
+    read or allocated (the descriptor's arrays here are far too short)."""
+    xyz = np.zeros((4, 3))
+    tet = np.zeros((1, 4), np.int32)
+    d = ep.MeshDesc()
+    d.n_nodes, d.xyz, d.n_cells, d.tet = n_nodes, xyz.ctypes.data, n_cells, tet.ctypes.data
+    d.n_tris, d.tri = 0, None
+    for name in ("cell_model", "param_set", "stim_mask", "fibre"):
+        setattr(d, name, None)
+    prm = _params([w.ParamSet()])
+    out = ctypes.c_void_p()
+    L = ep.load()
+    rc = L.ep_plan_create(ctypes.byref(d), ctypes.byref(prm), ctypes.byref(out))
+    assert rc == ep.EP_EINVAL and not out.value
+    msg = L.ep_last_error(None).decode()
+    assert ("empty" in msg) if n_cells == 0 else ("2^31" in msg)
 
 
 def test_planner_rejects_missing_param_set():
