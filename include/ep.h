@@ -230,7 +230,13 @@ int ep_job_create(ep_context *ctx, const ep_plan *plan, ep_job **out);
  * cell launch covering every resident cell of every job of the same
  * precision. Repeated calls with the same job list replay a captured CUDA
  * graph. Asynchronous on the context's stream. Errors: EP_EINVAL (jobs of
- * another context, repeated job, job without params), EP_ECUDA. */
+ * another context, repeated job, job without params), EP_ECUDA, and
+ * EP_ETIMEOUT when a staged cell kernel (launch-shape variants 6 and 7) of an
+ * earlier call gave up its bounded wait for a tile's copies: that call's
+ * error word is read back asynchronously after it, so the error surfaces at
+ * a later ep_step or ep_check_finite. The state of every job stepped since
+ * the failed step is then undefined; restore the jobs from a checkpoint
+ * (ep_write_state, ep_set_step_index) and call ep_clear_error. */
 int ep_step(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps);
 
 /* Copy variable var of cell model `model` to host_out (n = number of cells,
@@ -261,6 +267,11 @@ int ep_set_step_index(ep_job *job, int64_t n);
  * bounded wait (the staged cell kernel waits at most 1 s for the bulk copies
  * of a tile; the state is then not valid). Synchronises. */
 int ep_check_finite(ep_job *job);
+
+/* Clear the context's record of a step kernel's bounded wait that gave up
+ * (after the jobs were restored from a checkpoint): later ep_step calls run
+ * again. Synchronises the context's stream. */
+int ep_clear_error(ep_context *ctx);
 
 /* Job information: cells, nodes, interior faces, device bytes held. */
 int ep_job_info(const ep_job *job, int64_t *n_cells, int64_t *n_nodes,
@@ -343,10 +354,13 @@ int ep_plan_inspect(const ep_mesh_desc *desc, const ep_params *params, int64_t *
  * node values and a ticket counter) lives in one static device array of the
  * library, 256 bytes + EP_NOALLOC_MAX_NODES doubles (16 MiB + 256 B), held by
  * every GPU that loads the library until the process exits. Results equal
- * those of ep_step.
+ * those of ep_step bit for bit (the same per-cell arithmetic, other launch
+ * shapes and another place for the node values).
  *   - Rejects meshes with more than EP_NOALLOC_MAX_NODES nodes (EP_EINVAL).
- *   - The first call on a device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *   - The first call in a CUDA context (one per device, unless the caller
+ *     re-creates it, e.g. after cudaDeviceReset) looks up the array's device
+ *     address with that context current; make that first call before any
+ *     stream capture.
  *   - All calls share the array and it keeps the last call's contents: calls
  *     that overlap on the GPU (other streams, threads or contexts on the same
  *     device) race on it; serialise them.
@@ -429,12 +443,17 @@ int ep_graph_info(const ep_job *job, int64_t *n_nodes, int32_t *substeps, int64_
  * when ||b - L_ie v_e|| <= max(tol ||b||, atol sqrt(n_cells)) (2-norms over
  * cells, b in mV/ms per cell) or after max_iter Arnoldi steps; the Krylov
  * basis restarts every `restart` steps (1..30) from the true residual;
- * reorth = 1 applies classical Gram-Schmidt twice (CGS2), 0 once (CGS). */
+ * reorth = 1 applies classical Gram-Schmidt twice (CGS2), 0 once (CGS).
+ * barrier_limit_s bounds each wait of the solve kernel's grid barriers
+ * (seconds; <= 0 takes the default of 2 s): past it the waiting block raises
+ * the solve's error flag and every block leaves the kernel at its next
+ * barrier (see ep_bidomain_stats). */
 typedef struct {
     double tol, atol;
     int32_t restart;
     int32_t reorth;
     int64_t max_iter;
+    double barrier_limit_s;
 } ep_bidomain_solver;
 
 /* Switch a job to the bidomain model. The parameter sets' (D_l, D_t) become
@@ -471,8 +490,8 @@ int ep_bidomain_disable(ep_job *job);
 
 /* v_e (mV) in the caller's cell order, read or written through host
  * buffers of n = n_cells doubles. A write also recomputes L_i(v_e) for the
- * next step. Synchronise. Errors: EP_EINVAL (length), EP_ESTATE (not
- * bidomain). */
+ * next step and clears the job's barrier-timeout record (ep_bidomain_stats).
+ * Synchronise. Errors: EP_EINVAL (length), EP_ESTATE (not bidomain). */
 int ep_bidomain_read_ve(ep_job *job, double *host_out, int64_t n);
 int ep_bidomain_write_ve(ep_job *job, const double *host_in, int64_t n);
 
@@ -489,11 +508,17 @@ typedef struct {
                               the first Gram-Schmidt dots), second and third Gram-Schmidt
                               passes, updates of v_e and the gauge */
     int32_t failed;        /* some solve stopped at max_iter unconverged */
-    int32_t pad;
+    int32_t timeout;       /* some solve's grid-barrier wait gave up (sticky, see below) */
 } ep_bidomain_stats_t;
 
-/* Fill *out. Synchronises. Returns EP_ETIMEOUT if a grid barrier of the
- * solve kernel gave up waiting (2 s limit; v_e may then be partly updated). */
+/* Fill *out. Synchronises. Returns EP_ETIMEOUT (with *out filled) if a grid
+ * barrier wait of some solve since the last ep_bidomain_enable or
+ * ep_bidomain_write_ve gave up (ep_bidomain_solver.barrier_limit_s, 2 s by
+ * default). Every block of that solve left the kernel; its v_e and the V of
+ * the steps after it are undefined. Each later solve re-arms the barrier and
+ * runs normally, and other jobs are unaffected. Recovery: restore the job's
+ * state and v_e from a checkpoint (ep_write_state, ep_bidomain_write_ve,
+ * which clears the record). */
 int ep_bidomain_stats(ep_job *job, ep_bidomain_stats_t *out);
 
 /* Number of state variables of a model and the name of each

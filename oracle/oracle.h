@@ -37,10 +37,13 @@ extern "C" {
 
 #define ORC_MAXVAR 24
 
-enum { ORC_TP06 = 0, ORC_CRN = 1, ORC_STEWART = 2 };
+/* ORC_PASSIVE: a membrane with no ionic current (I_ion = 0, V its only
+ * state variable, 0 mV at start); V then moves by diffusion and stimulus
+ * alone, which gives closed forms to pin the tissue step against. */
+enum { ORC_TP06 = 0, ORC_CRN = 1, ORC_STEWART = 2, ORC_PASSIVE = 3 };
 
 typedef struct {
-    int32_t model;      /* ORC_TP06 / ORC_CRN / ORC_STEWART */
+    int32_t model;      /* ORC_TP06 / ORC_CRN / ORC_STEWART / ORC_PASSIVE */
     int32_t variant;    /* TP06: 0 epi, 1 mid, 2 endo */
     double D_l, D_t;    /* monodomain diffusivity along / across the fibre, mm^2/ms */
     double gks_scale, gkr_scale;

@@ -59,6 +59,7 @@ int orc_model_nvar(int model) {
     case ORC_TP06: return orc_tp06_nvar();
     case ORC_CRN: return orc_crn_nvar();
     case ORC_STEWART: return orc_stewart_nvar();
+    case ORC_PASSIVE: return 1;
     }
     return 0;
 }
@@ -68,6 +69,7 @@ const char *orc_model_varname(int model, int var) {
     case ORC_TP06: return orc_tp06_varname(var);
     case ORC_CRN: return orc_crn_varname(var);
     case ORC_STEWART: return orc_stewart_varname(var);
+    case ORC_PASSIVE: return var == 0 ? "V" : 0;
     }
     return 0;
 }
@@ -81,7 +83,8 @@ void orc_model_init(const orc_cellparams *p, double *s) {
     }
 }
 
-/* Advances every state variable except V (index 0); returns I_ion(V^n, s^n). */
+/* Advances every state variable except V (index 0); returns I_ion(V^n, s^n)
+ * (zero for the passive membrane, which has no other state). */
 double orc_model_step(double *s, double dt, double i_stim, const orc_cellparams *p, orc_ab2 *ab) {
     switch (p->model) {
     case ORC_TP06: return orc_tp06_step(s, dt, i_stim, p, ab);

@@ -3,6 +3,7 @@
 // the method runs in the kernels of kernels.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -55,6 +56,7 @@ struct Plan {
 struct BidoHost {
     std::vector<double> De_l, De_t;   // extracellular diffusivities per parameter set
     double tol = 1e-6, atol = 0.0;
+    double barrier_limit_s = 2.0;
     int restart = 12;
     int reorth = 0;
     int64_t max_iter = 2000;
@@ -79,6 +81,7 @@ struct ep_context {
     int sm_count = 148;
     int cell_variant[2] = {0, 0};   // launch shape of the cell kernel per precision (ep_autotune)
     DevBuf err_word;                 // device word: a bounded wait in a step kernel gave up
+    unsigned *err_host = nullptr;    // pinned copy of err_word, refreshed after each ep_step of staged kernels
 };
 
 struct ep_job {
@@ -250,6 +253,17 @@ int ep_context_create(ep_alloc_fn alloc, ep_free_fn free_fn, void *user, void *c
             delete ctx;
             return EP_ENOMEM;
         }
+        if (cudaHostAlloc(reinterpret_cast<void **>(&ctx->err_host), sizeof(unsigned), cudaHostAllocDefault) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            g_create_error = "ep_context_create: pinned host allocation failed";
+            cudaFree(ctx->err_word.p);
+            cudaStreamDestroy(ctx->capture);
+            cudaStreamDestroy(ctx->upload);
+            delete ctx;
+            return EP_ENOMEM;
+        }
+        *ctx->err_host = 0u;
         *out = ctx;
         return EP_OK;
     } catch (...) {
@@ -272,9 +286,21 @@ int ep_context_destroy(ep_context *ctx) {
     for (auto &p : ctx->plans) free_plan(ctx, p.get());
     ctx->plans.clear();
     if (ctx->err_word.p) cudaFree(ctx->err_word.p);
+    if (ctx->err_host) cudaFreeHost(ctx->err_host);
     if (ctx->capture) cudaStreamDestroy(ctx->capture);
     if (ctx->upload) cudaStreamDestroy(ctx->upload);
     delete ctx;
+    return EP_OK;
+}
+
+int ep_clear_error(ep_context *ctx) {
+    if (!ctx) return EP_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->err_word.p, 0, sizeof(unsigned), ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_clear_error");
+    *ctx->err_host = 0u;
     return EP_OK;
 }
 
@@ -761,6 +787,7 @@ int bido_apply(ep_job *job) {
     a.restart = B.restart;
     a.mode = 0;
     a.reorth = B.reorth;
+    a.barrier_limit_ns = static_cast<unsigned long long>(B.barrier_limit_s * 1e9);
     B.args = a;
     job->dj.xdiv = xd;
     // v_e = 0; the vector pads past n_cells must stay zero for the basis passes
@@ -1074,11 +1101,18 @@ int ep_step(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps) {
     ep_context *ctx = jobs[0]->ctx;
     int rc = check_jobs(jobs, n_jobs, n_steps, "ep_step");
     if (rc) return rc;
+    // a staged cell kernel of an earlier call gave up waiting for its copies (the word is
+    // read back asynchronously after each call that ran one)
+    if (*ctx->err_host)
+        return fail(ctx, EP_ETIMEOUT, "ep_step: an earlier step's bounded wait gave up; the state of the jobs "
+                                      "stepped since is undefined (restore a checkpoint, then ep_clear_error)");
     if (n_steps == 0) return EP_OK;
     DeviceGuard g(ctx->device);
     try {
         Plan *pl = nullptr;
         if ((rc = get_plan(ctx, jobs, n_jobs, &pl))) return rc;
+        bool staged = false;
+        for (auto &gr : pl->groups) staged = staged || gr.L.cell_variant >= kStagedVariant;
         int64_t left = n_steps;
         if (n_steps >= kGraphMinSteps && pl->bido.empty()) {   // cooperative solves launch directly
             if (!pl->exec) {
@@ -1097,6 +1131,8 @@ int ep_step(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps) {
             }
         }
         cudaError_t e = enqueue_steps(pl, left, ctx->stream);
+        if (e == cudaSuccess && staged)
+            e = cudaMemcpyAsync(ctx->err_host, ctx->err_word.p, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_step: launch");
         return EP_OK;
     } catch (const std::bad_alloc &) {
@@ -1409,7 +1445,10 @@ int ep_check_finite(ep_job *job) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     dfree(ctx, &b);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_check_finite");
-    if (werr) return fail(ctx, EP_ETIMEOUT, "a step kernel's wait for its staged copies hit its time limit");
+    if (werr) {
+        *ctx->err_host = werr;
+        return fail(ctx, EP_ETIMEOUT, "a step kernel's wait for its staged copies hit its time limit");
+    }
     if (cnt) return fail(ctx, EP_ENONFINITE, std::to_string(cnt) + " non-finite state values");
     return EP_OK;
 }
@@ -1594,8 +1633,11 @@ int ep_bidomain_enable(ep_job *job, const double *De_l, const double *De_t, int3
         sv = *solver;
     } else {
         const bool plain = job->precision == EP_FP64_PLAIN;
-        sv = ep_bidomain_solver{plain ? 1e-11 : 1e-5, plain ? 1e-11 : 1e-3, 12, 0, 2000};
+        sv = ep_bidomain_solver{plain ? 1e-11 : 1e-5, plain ? 1e-11 : 1e-3, 12, 0, 2000, 0.0};
     }
+    if (!(sv.barrier_limit_s > 0.0)) sv.barrier_limit_s = 2.0;
+    if (sv.barrier_limit_s > 60.0)
+        return fail(ctx, EP_EINVAL, "ep_bidomain_enable: barrier_limit_s above 60 s");
     if (!(sv.tol > 0.0) || !(sv.atol >= 0.0) || sv.restart < 1 || sv.restart > kBidoMaxRestart || sv.max_iter < 1 ||
         (sv.reorth != 0 && sv.reorth != 1))
         return fail(ctx, EP_EINVAL, "ep_bidomain_enable: tol > 0, atol >= 0, restart 1..30, reorth 0/1, max_iter >= 1");
@@ -1613,6 +1655,7 @@ int ep_bidomain_enable(ep_job *job, const double *De_l, const double *De_t, int3
         B.restart = sv.restart;
         B.reorth = sv.reorth;
         B.max_iter = sv.max_iter;
+        B.barrier_limit_s = sv.barrier_limit_s;
         int rc = bido_apply(job);
         if (rc) bido_drop(job);
         return rc;
@@ -1644,6 +1687,10 @@ static int transfer_ve(ep_job *job, double *host, int64_t n, bool write) {
         a.mode = 1;   // refresh L_i(v_e) for the next step
         e = cudaMemcpyAsync(buf, host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess) e = launch_field_scatter(job->precision, buf, job->perm_dev, n, a.ve, ctx->stream);
+        // a restored v_e ends the record of a solve whose barrier gave up
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(reinterpret_cast<char *>(a.stats) + offsetof(BidoStats, timeout), 0, sizeof(int),
+                                ctx->stream);
         if (e == cudaSuccess) e = launch_bido(job->precision, a, job->bido->grid, ctx->stream);
     } else {
         e = launch_field_gather(job->precision, job->bido->args.ve, job->perm_dev, n, buf, ctx->stream);
@@ -1676,10 +1723,8 @@ int ep_bidomain_stats(ep_job *job, ep_bidomain_stats_t *out) {
     if (!job->bido) return fail(ctx, EP_ESTATE, "job is not bidomain (ep_bidomain_enable)");
     DeviceGuard g(ctx->device);
     BidoStats st{};
-    BidoSync sy{};
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpy(&st, job->bido->args.stats, sizeof(st), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(&sy, job->bido->args.sync, sizeof(sy), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_bidomain_stats");
     *out = ep_bidomain_stats_t{};
     out->last_iters = st.last_iters;
@@ -1690,7 +1735,8 @@ int ep_bidomain_stats(ep_job *job, ep_bidomain_stats_t *out) {
     out->alg_bytes = st.alg_bytes;
     for (int k = 0; k < 5; ++k) out->phase_ms[k] = st.phase_ms[k];
     out->failed = st.failed;
-    if (sy.err) return fail(ctx, EP_ETIMEOUT, "bidomain solve: a grid barrier wait hit its time limit");
+    out->timeout = st.timeout;
+    if (st.timeout) return fail(ctx, EP_ETIMEOUT, "bidomain solve: a grid barrier wait hit its time limit");
     return EP_OK;
 }
 

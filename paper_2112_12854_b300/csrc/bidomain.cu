@@ -35,7 +35,6 @@ template <> struct VW<double> { using type = double2; static constexpr int n = 2
 
 constexpr int kWarps = kBidoThreads / 32;
 constexpr int KP = kBidoMaxRestart + 1;
-constexpr unsigned long long kBarrierLimitNs = 2000000000ull;   // 2 s
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -44,9 +43,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Grid barrier of a cooperative launch (all blocks co-resident). The wait is
-// bounded: past the limit the block sets the error flag and every block
+// bounded: past limit_ns the block sets the error flag and every block
 // leaves the kernel at its next barrier. Returns false on error.
-__device__ bool grid_sync(BidoSync *s, int *flag_sh) {
+__device__ bool grid_sync(BidoSync *s, int *flag_sh, unsigned long long limit_ns) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *vgen = &s->gen;
@@ -60,7 +59,7 @@ __device__ bool grid_sync(BidoSync *s, int *flag_sh) {
         } else {
             const unsigned long long t0 = global_ns();
             while (*vgen == g && *verr == 0) {
-                if (global_ns() - t0 > kBarrierLimitNs) {
+                if (global_ns() - t0 > limit_ns) {
                     atomicExch(&s->err, 1);
                     break;
                 }
@@ -196,7 +195,13 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
     }
 #define BIDO_SYNC(ph)                                          \
     do {                                                       \
-        if (!grid_sync(A.sync, &flag_sh)) return;              \
+        if (!grid_sync(A.sync, &flag_sh, A.barrier_limit_ns)) { \
+            if (threadIdx.x == 0) {                            \
+                A.stats->timeout = 1;                          \
+                A.stats->hist = 0;                             \
+            }                                                  \
+            return;                                            \
+        }                                                      \
         if (blockIdx.x == 0 && threadIdx.x == 0) {             \
             const unsigned long long t_ = global_ns();         \
             ph_sh[ph] += t_ - t_last_sh;                       \
@@ -482,6 +487,8 @@ int bido_grid(int precision, int sm_count, long long n_cells) {
 cudaError_t launch_bido(int precision, const BidoArgs &a, int grid, cudaStream_t s) {
     BidoArgs arg = a;
     void *args[] = {&arg};
+    const cudaError_t e = cudaMemsetAsync(a.sync, 0, sizeof(BidoSync), s);
+    if (e != cudaSuccess) return e;
     if (precision == EP_FP64_PLAIN)
         return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(bido_kernel<double>), dim3(grid),
                                            dim3(kBidoThreads), args, 0, s);

@@ -27,12 +27,13 @@ struct BidoStats {
     double alg_bytes;        // algorithmic bytes of all solves (every array a phase touches, once)
     double phase_ms[5];      // device time by phase: node values, fluxes, GS pass 2, GS pass 3, updates
     int failed;              // some solve stopped at max_iter without converging
-    int timeout;             // a grid barrier gave up (error flag)
+    int timeout;             // a grid barrier of some solve gave up (sticky until v_e is written)
     int hist;                // consecutive solutions held: 0 none, 1 v_e^n, 2 also v_e^{n-1} (in vprev)
     int pad;
 };
 
-// Grid barrier state of the cooperative solve kernel.
+// Grid barrier state of the cooperative solve kernel, zeroed before every
+// launch (a solve whose barrier gave up leaves it inconsistent).
 struct BidoSync {
     unsigned count;
     unsigned gen;
@@ -58,6 +59,7 @@ struct BidoArgs {
     int mode;                    // 0: solve, then L_i(v_e); 1: only L_i(v_e) from the current v_e
     int reorth;                  // 1: Gram-Schmidt twice (CGS2); 0: once (CGS)
     int pad;
+    unsigned long long barrier_limit_ns;   // bound of each grid-barrier wait
 };
 
 // Grid of the cooperative solve kernel for a job of n_cells: co-resident on
@@ -66,8 +68,8 @@ struct BidoArgs {
 // depend on the batch it is stepped in.
 int bido_grid(int precision, int sm_count, long long n_cells);
 
-// One solve (mode 0) or flux refresh (mode 1) of one job, a cooperative
-// launch on stream s.
+// One solve (mode 0) or flux refresh (mode 1) of one job on stream s: the
+// barrier state is zeroed, then one cooperative launch.
 cudaError_t launch_bido(int precision, const BidoArgs &a, int grid, cudaStream_t s);
 
 // out[perm[c]] = src[c] (as double), and the reverse.

@@ -828,24 +828,60 @@ constexpr long long kNoAllocMaxNodes = EP_NOALLOC_MAX_NODES;
 constexpr size_t kNoAllocHeader = 256;  // ticket counter, padded to keep node values 256-byte aligned
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocHeader + kNoAllocMaxNodes * sizeof(double)];
 
-// Device address of g_noalloc_scratch, looked up once per device with that
-// device current (in host code the symbol's name is only a host-side stand-in).
-static void *g_noalloc_addr[256];
+// Device address of g_noalloc_scratch, looked up once per CUDA context with
+// that context current (in host code the symbol's name is only a host-side
+// stand-in). The cache is keyed on the context's unique id, so a context
+// re-created after cudaDeviceReset looks the address up again instead of
+// reusing one from the context it replaced.
+struct NoAllocAddr {
+    unsigned long long ctx_id;
+    void *p;
+};
+static NoAllocAddr g_noalloc_addr[64];
+static int g_noalloc_n = 0;
 static std::mutex g_noalloc_mutex;
 
-static cudaError_t noalloc_scratch_address(void **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
+// Unique id of the calling thread's current context (cuCtxGetId, reached
+// through the runtime's driver entry point so the library needs no link
+// against the driver library).
+static cudaError_t current_context_id(unsigned long long *id) {
+    using CtxGetId = int (*)(void *, unsigned long long *);
+    static CtxGetId fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetId>(p);
+    });
+    if (!fn) return cudaErrorNotSupported;
+    if (fn(nullptr, id) == 0) return cudaSuccess;
+    // no context current on this thread yet: make the device's primary one current
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return e;
+    return fn(nullptr, id) == 0 ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+static cudaError_t noalloc_scratch_address(void **out) {
+    unsigned long long id = 0;
+    cudaError_t e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    for (int k = 0; k < g_noalloc_n; ++k)
+        if (g_noalloc_addr[k].ctx_id == id) {
+            *out = g_noalloc_addr[k].p;
+            return cudaSuccess;
+        }
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    // contexts are rarely re-created; past 64 the oldest entry is replaced
+    const int slot = g_noalloc_n < 64 ? g_noalloc_n++ : int(id % 64);
+    g_noalloc_addr[slot] = NoAllocAddr{id, p};
+    *out = p;
     return cudaSuccess;
 }
 

@@ -56,13 +56,13 @@ class Params(ctypes.Structure):
 
 class BidoSolver(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("atol", ctypes.c_double), ("restart", ctypes.c_int32),
-                ("reorth", ctypes.c_int32), ("max_iter", ctypes.c_int64)]
+                ("reorth", ctypes.c_int32), ("max_iter", ctypes.c_int64), ("barrier_limit_s", ctypes.c_double)]
 
 
 class BidoStats(ctypes.Structure):
     _fields_ = [("last_iters", ctypes.c_int64), ("total_iters", ctypes.c_int64), ("solves", ctypes.c_int64),
                 ("last_res", ctypes.c_double), ("last_bnorm", ctypes.c_double), ("alg_bytes", ctypes.c_double),
-                ("phase_ms", ctypes.c_double * 5), ("failed", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("phase_ms", ctypes.c_double * 5), ("failed", ctypes.c_int32), ("timeout", ctypes.c_int32)]
 
 
 class GraphDesc(ctypes.Structure):
@@ -95,7 +95,7 @@ EXPORTS = ["ep_context_create", "ep_context_set_stream", "ep_context_destroy", "
            "ep_plan_info", "ep_plan_destroy", "ep_job_create", "ep_graph_attach", "ep_graph_read_state",
            "ep_graph_write_state", "ep_graph_activation_times", "ep_graph_info", "ep_alu_peaks",
            "ep_bidomain_enable", "ep_bidomain_disable", "ep_bidomain_read_ve", "ep_bidomain_write_ve",
-           "ep_bidomain_stats"]
+           "ep_bidomain_stats", "ep_clear_error"]
 
 _lib = None
 _P = ctypes.c_void_p
@@ -125,6 +125,7 @@ def load():
         "ep_step_index": ([_P, ctypes.POINTER(_I64)], ctypes.c_int),
         "ep_set_step_index": ([_P, _I64], ctypes.c_int),
         "ep_check_finite": ([_P], ctypes.c_int),
+        "ep_clear_error": ([_P], ctypes.c_int),
         "ep_job_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                          ctypes.POINTER(_I64)], ctypes.c_int),
         "ep_estimate_bytes": ([_I64, _I64, ctypes.c_int32], _I64),
@@ -216,6 +217,10 @@ class Context:
     def check(self, rc):
         if rc:
             raise EPError(rc, load().ep_last_error(self._h).decode())
+
+    def clear_error(self):
+        """Forget a step kernel's bounded wait that gave up (ep_clear_error)."""
+        self.check(load().ep_clear_error(self._h))
 
     def close(self):
         for j in list(self.jobs):
@@ -443,7 +448,7 @@ class Job:
         return dict(n_nodes=a.value, substeps=b.value, n_junctions=c.value)
 
     def enable_bidomain(self, De_l, De_t, *, tol=None, atol=None, restart=12, reorth=0, max_iter=2000,
-                        n_sets=None):
+                        n_sets=None, barrier_limit_s=0.0):
         """Bidomain model (ep_bidomain_enable): De_l, De_t are the
         extracellular diffusivities, scalars or one per parameter set; the
         parameter sets' own (D_l, D_t) become the intracellular ones. tol /
@@ -454,11 +459,12 @@ class Job:
         el = np.ascontiguousarray(np.broadcast_to(np.asarray(De_l, np.float64), (n_sets,)))
         et = np.ascontiguousarray(np.broadcast_to(np.asarray(De_t, np.float64), (n_sets,)))
         sv = None
-        if tol is not None or atol is not None or restart != 12 or reorth != 0 or max_iter != 2000:
+        if (tol is not None or atol is not None or restart != 12 or reorth != 0 or max_iter != 2000
+                or barrier_limit_s > 0.0):
             plain = params is not None and params.precision == EP_FP64_PLAIN
             sv = BidoSolver(float(tol if tol is not None else (1e-11 if plain else 1e-5)),
                             float(atol if atol is not None else (1e-11 if plain else 1e-3)),
-                            int(restart), int(reorth), int(max_iter))
+                            int(restart), int(reorth), int(max_iter), float(barrier_limit_s))
         self.ctx.check(load().ep_bidomain_enable(self._h, _ptr(el), _ptr(et), int(n_sets),
                                                  ctypes.byref(sv) if sv is not None else None))
 
@@ -482,7 +488,7 @@ class Job:
         self.ctx.check(load().ep_bidomain_stats(self._h, ctypes.byref(st)))
         return {"last_iters": st.last_iters, "total_iters": st.total_iters, "solves": st.solves,
                 "last_res": st.last_res, "last_bnorm": st.last_bnorm, "alg_bytes": st.alg_bytes,
-                "phase_ms": list(st.phase_ms), "failed": bool(st.failed)}
+                "phase_ms": list(st.phase_ms), "failed": bool(st.failed), "timeout": bool(st.timeout)}
 
     def destroy(self):
         if getattr(self, "_h", None):

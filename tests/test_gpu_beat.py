@@ -1,0 +1,96 @@
+"""Parity over a whole beat (400 ms: upstroke, plateau, repolarisation and
+rest; Sec. 4's slab benchmark run through a full action potential, Sec. 5's
+one beat): FP32 mixed and FP64 plain against one oracle run, V at every cell
+every 5 ms, the activation map, and every state variable at the end.
+
+  - the 16 x 16 x 4-cube TP06 epicardial slab (6144 cells, 20000 steps);
+  - a crop of the benchmark wedge's construction, 50 x 50 x 10 cubes of
+    0.25 mm (150,000 cells: TP06 endo / M / epi by depth thirds, fibres
+    rotating -60..+60 deg, corner stimulus), 20000 steps.
+
+The error statistics of every result are printed (run with -s to see them)."""
+import numpy as np
+import pytest
+
+import workloads as w
+from gpu_common import act_error, tolerances
+
+pytestmark = pytest.mark.gpu
+
+BEAT_STEPS = 20000          # 400 ms at dt = 0.02 ms
+EVERY = 250                 # 5 ms
+
+
+def _beat(case, label):
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import oracle
+    from paper_2112_12854_b300 import ep
+    ctx = ep.Context()
+    precs = {"mixed": ep.EP_FP32_MIXED, "plain": ep.EP_FP64_PLAIN}
+    jobs = {name: ep.job_from_case(ctx, case, precision=p) for name, p in precs.items()}
+    o = oracle.Sim(case)
+    errs = {name: [] for name in precs}
+    peak = {name: (0.0, 0) for name in precs}
+    v_min = np.inf
+    for k in range(EVERY, BEAT_STEPS + 1, EVERY):
+        o.run(EVERY)
+        for j in jobs.values():
+            j.step(EVERY)
+        ref = o.V
+        v_min = min(v_min, float(ref.min()))
+        for name, j in jobs.items():
+            d = np.abs(j.V - ref)
+            errs[name].append(d.astype(np.float32))
+            if d.max() > peak[name][0]:
+                peak[name] = (float(d.max()), k)
+            tv, _ = tolerances(precs[name])
+            assert d.max() <= tv, (label, name, k * case.dt, float(d.max()))
+    a = o.activation_times()
+    assert np.all(np.isfinite(a)), "the beat activates every cell"
+    print(f"{label}: V at 400 ms between {ref.min():.1f} and {ref.max():.1f} mV "
+          f"({np.mean(ref < -70.0):.1%} of cells below -70 mV)")
+    out = {}
+    for name, j in jobs.items():
+        p = precs[name]
+        _, ta = tolerances(p)
+        e = np.concatenate(errs[name])
+        ea = act_error(j.activation_times(), a)
+        assert ea <= ta, (label, name, ea)
+        # state variables at 400 ms relative to their largest magnitude: FP64 to
+        # rounding; FP32 within 1 % (the slow gates' Rush-Larsen steps change
+        # them by dt/tau ~ 1e-5 of their value per step, near FP32 resolution)
+        rel_tol = 1e-9 if name == "plain" else 1e-2
+        var_err = {}
+        models = sorted({int(ps.model) for ps in case.param_sets})
+        for m in models:
+            for v, vname in enumerate(ep.model_varnames(m)):
+                if v == 0:
+                    continue
+                r = o.get(v)
+                g = j.read(v, model=m)
+                sel = np.isfinite(g)
+                rel = float(np.abs(g[sel] - r[sel]).max() / np.abs(r[sel]).max())
+                var_err[vname] = rel
+                assert rel <= rel_tol, (label, name, vname, rel)
+        out[name] = var_err
+        worst = sorted(var_err.items(), key=lambda kv: -kv[1])[:3]
+        print(f"{label} {name}: |dV| over {BEAT_STEPS // EVERY} outputs x {case.n_cells} cells: "
+              f"max {e.max():.3e} mV (at {peak[name][1] * case.dt:.0f} ms), mean {e.mean():.3e}, "
+              f"p99 {np.percentile(e, 99):.3e}; max|dt_act| {ea:.3e} ms; "
+              f"worst state variables (max|d|/max|ref| at 400 ms): "
+              + ", ".join(f"{n} {x:.1e}" for n, x in worst))
+        j.destroy()
+    ctx.close()
+    return out
+
+
+def test_slab_6144_cells_full_beat():
+    case = w.slab_case(n_steps=BEAT_STEPS)
+    _beat(case, "slab 6144")
+
+
+def test_wedge_crop_150k_cells_full_beat():
+    case = w.wedge_case(nx=50, ny=50, nz=10, h=0.25, n_steps=BEAT_STEPS)
+    assert case.n_cells == 150_000
+    _beat(case, "wedge crop 150k")

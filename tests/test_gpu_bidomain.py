@@ -163,3 +163,47 @@ def test_bidomain_batched_bitwise_and_ve_io(ctx):
     assert np.abs(b.V - alone.V).max() < 1e-4
     for j in (alone, a1, b, other):
         j.destroy()
+
+
+def test_barrier_wait_gives_up_and_other_jobs_are_unaffected(ctx):
+    """The solve kernel's grid-barrier waits are bounded. With the bound set
+    to 1 ns on a multi-block solve, a block that has to wait at all gives up:
+    it raises the solve's error flag, every block leaves at its next barrier
+    (the launch completes: the stream synchronises), and ep_bidomain_stats
+    reports EP_ETIMEOUT. A second bidomain job stepped in the same batch is
+    bitwise equal to the same job stepped alone, and once the first job's
+    v_e is restored (which clears the record) and the default bound is back,
+    its solves run normally again. No GPU fault is involved: the kernel
+    returns an error status that the host reads."""
+    from paper_2112_12854_b300 import ep
+    case = _slab(cubes=(40, 30, 6))                      # 43200 cells: tens of blocks per solve
+    bad = ep.job_from_case(ctx, case)
+    good = ep.job_from_case(ctx, case)
+    alone = ep.job_from_case(ctx, case)
+    bad.enable_bidomain(DEL, DET, barrier_limit_s=1e-9)
+    good.enable_bidomain(DEL, DET)
+    alone.enable_bidomain(DEL, DET)
+    ep.step([bad, good], 20)
+    alone.step(20)
+    import torch
+    torch.cuda.synchronize()                             # every block of every solve has returned
+    with pytest.raises(ep.EPError) as e:
+        bad.bidomain_stats()
+    assert e.value.code == ep.EP_ETIMEOUT
+    st = good.bidomain_stats()
+    assert not st["timeout"] and not st["failed"] and st["solves"] == 21
+    assert np.array_equal(good.V, alone.V)
+    assert np.array_equal(good.ve, alone.ve)
+    # recovery: default bound, state and v_e restored from the healthy job
+    bad.enable_bidomain(DEL, DET)
+    for v in range(19):
+        bad.write(v, alone.read(v))
+    bad.step_index = alone.step_index
+    bad.ve = alone.ve
+    assert not bad.bidomain_stats()["timeout"]
+    ep.step([bad], 10)
+    alone.step(10)
+    assert not bad.bidomain_stats()["timeout"]
+    assert np.abs(bad.V - alone.V).max() < 1e-3
+    for j in (bad, good, alone):
+        j.destroy()

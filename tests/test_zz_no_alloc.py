@@ -2,8 +2,9 @@
 device memory while stepping (for example a process whose device memory is
 entirely reserved by another runtime's pool, or a latency-critical loop that
 may not call cudaMalloc/cudaFree). It keeps the node values in the library's
-static device array instead of job memory; its results must equal those of
-ep_step on the same inputs, call after call.
+static device array instead of job memory and runs the same per-cell
+arithmetic as ep_step, so its results must equal ep_step's bit for bit, call
+after call.
 
 Kept in a file of its own that pytest collects last, so a run that stops at
 the first failure has already run every other test."""
@@ -11,19 +12,36 @@ import numpy as np
 import pytest
 
 import workloads as w
-from gpu_common import tolerances
 
 pytestmark = pytest.mark.gpu
 
 
+def _three_model_slab():
+    """13x7x3 cubes (1638 cells: several tiles, a ragged tail) split into
+    TP06 (endo) / Courtemanche / Stewart thirds along x, fibres rotating with
+    depth, two stimuli: every model region of the no-allocation kernel."""
+    xyz, tets = w.kuhn_box(13, 7, 3, 0.25)
+    c = w.tet_centroids(xyz, tets)
+    model = np.where(c[:, 0] < 1.1, 0, np.where(c[:, 0] < 2.2, 1, 2)).astype(np.uint8)
+    sets = [w.ParamSet(model=0, variant=2), w.ParamSet(model=1), w.ParamSet(model=2)]
+    stim = ((c[:, 0] < 0.5).astype(np.uint8) | ((c[:, 0] > 2.9).astype(np.uint8) << 1))
+    return w.TissueCase("mix", xyz, tets, w.fibres_transmural(c[:, 2], 0.0, 0.75), model, stim, sets,
+                        [w.Stimulus(-52.0, 0.0, 1.0), w.Stimulus(-40.0, 5.0, 2.0)], 0.01, 0, -10.0)
+
+
+CASES = {"tp06_slab": lambda: w.slab_case(nx=13, ny=9, nz=3, h=0.5),   # 2106 cells
+         "three_models": _three_model_slab}
+
+
+@pytest.mark.parametrize("cname", sorted(CASES))
 @pytest.mark.parametrize("pname", ["mixed", "plain"])
-def test_step_noalloc_matches_ep_step_two_calls(pname):
+def test_step_noalloc_equals_ep_step_two_calls(pname, cname):
     import torch
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
     from paper_2112_12854_b300 import ep
     prec = ep.EP_FP32_MIXED if pname == "mixed" else ep.EP_FP64_PLAIN
-    tv, ta = tolerances(prec)
-    case = w.slab_case(nx=13, ny=9, nz=3, h=0.5)      # 2106 cells: several tiles and a ragged tail
+    case = CASES[cname]()
+    models = sorted({int(ps.model) for ps in case.param_sets})
     ctx = ep.Context()
     ref = ep.job_from_case(ctx, case, precision=prec)
     job = ep.job_from_case(ctx, case, precision=prec)
@@ -31,16 +49,13 @@ def test_step_noalloc_matches_ep_step_two_calls(pname):
         ref.step(160)
         ep.step_noalloc(job, 160)
         assert job.step_index == ref.step_index == 160 * (call + 1)
-        dv = np.abs(job.V - ref.V).max()
-        assert dv <= tv, (call, dv)
-        for var in range(1, 19):
-            a, b = job.read(var), ref.read(var)
-            assert np.abs(a - b).max() <= tv * max(1.0, np.abs(b).max()), (call, var)
-        a, b = job.activation_times(), ref.activation_times()
-        fin = np.isfinite(b)
-        assert np.array_equal(np.isfinite(a), fin)
-        if fin.any():
-            assert np.abs(a[fin] - b[fin]).max() <= ta
+        assert np.array_equal(job.V, ref.V), (call, np.abs(job.V - ref.V).max())
+        for m in models:
+            for var in range(1, len(ep.model_varnames(m))):
+                a, b = job.read(var, model=m), ref.read(var, model=m)
+                assert np.array_equal(a, b, equal_nan=True), (call, m, ep.model_varnames(m)[var])
+        assert np.array_equal(job.activation_times(), ref.activation_times()), call
+    assert np.isfinite(ref.activation_times()).any()
     ref.destroy()
     job.destroy()
     ctx.close()
