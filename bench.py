@@ -42,15 +42,27 @@ UNIT = "cell-updates/s"
 WEDGE = dict(nx=200, ny=200, nz=40, h=0.25)
 CROP = dict(nx=50, ny=50, nz=10, h=0.25)       # oracle sample: same construction, 150k cells
 OUTPUT_EVERY = 250                              # V read back every 5 ms of simulated time (e2e)
-# algorithmic bytes per cell-update of the fused cell kernel (TP06, FP32 mixed):
-#   per-cell coefficients and indices: nodes_a, nodes_b, nbr (3 x int4), wa, wb, q (3 x float4) = 96
+# Algorithmic bytes per cell-update of the fused cell kernel (TP06, FP32 mixed):
+#   gather indices: 8 node + 4 neighbour indices, as 16-bit offsets (24 B) or 32-bit (48 B)
+#   folded coefficients wa, wb, q (3 x float4) = 48
 #   own V read 4, pset + stim mask 2, state read 15 x 4 + 3 x 8 = 84
 #   V^{n+1} write 4, state write 84
 # (node-value and neighbour-potential gathers are L2 hits by design and not counted)
-CELL_BYTES = 96 + 4 + 2 + 84 + 4 + 84
-# node kernel: sliced-ELL entries (4-byte cell index + 4-byte weight) per incidence (4 per cell),
-# plus the node-value write (N_nodes / N_cells x 4 bytes)
-NODE_BYTES_PER_INCIDENCE = 8
+def cell_bytes(index_width):
+    return (24 if index_width == 16 else 48) + 48 + 4 + 2 + 84 + 4 + 84
+
+
+# node kernel: sliced-ELL entries (a 2- or 4-byte cell index + 4-byte weight) per incidence
+# (4 per cell), plus the node-value write (N_nodes / N_cells x 4 bytes)
+def node_bytes_per_incidence(index_width):
+    return (2 if index_width == 16 else 4) + 4
+
+
+# The survey's floor for one whole TP06 step in mixed precision (state, cell->node indices, node
+# CSR, shared face coefficients, volume and parameter byte): 277 B per cell-update, of which the
+# node CSR is 32 B; the cell kernel's part is the other 245 B.
+SURVEY_STEP_FLOOR = 277
+SURVEY_CELL_FLOOR = 277 - 32
 
 
 def wedge_case(dims):
@@ -89,6 +101,28 @@ def traffic_from_profile(n_cells):
     """DRAM bytes of one cell-kernel launch (FP32) from the ncu summary."""
     b = profile_value("cell_kernel_wedge.md", "dram_bytes_per_cell")
     return None if b is None else b * n_cells
+
+
+def alu_side(n_cells, cell_ms, alu):
+    """The FP32 cell kernel against its two ALU roofs: FP32 FMA-pipe and
+    MUFU (XU-pipe) thread operations per cell, counted by ncu on the crop
+    (committed summary, current kernel source only), times the cell-update
+    rate, over the measured issue rates of those pipes (ep_alu_peaks)."""
+    fma = profile_value("cell_kernel_wedge.md", "fma_pipe_thread_ops_per_cell")
+    xu = profile_value("cell_kernel_wedge.md", "xu_pipe_thread_ops_per_cell")
+    rate = n_cells / (cell_ms * 1e-3)
+    out = {"source": "ncu instruction counts per pipe on the crop (profiles/cell_kernel_wedge.md) x "
+                     "cell-updates/s; peaks from ep_alu_peaks"}
+    if fma is not None:
+        # an FMA-pipe instruction counts one operation; the measured FMA peak counts two flops per FMA
+        ach = fma * rate / 1e12
+        pk = alu["fp32_fma_flops"] / 2e12
+        out["fma"] = {"achieved_tops": ach, "peak_tops": pk, "frac": ach / pk, "ops_per_cell": fma}
+    if xu is not None:
+        ach = xu * rate / 1e12
+        pk = alu["mufu_ex2_ops"] / 1e12
+        out["mufu"] = {"achieved_tops": ach, "peak_tops": pk, "frac": ach / pk, "ops_per_cell": xu}
+    return out
 
 
 class Clocks:
@@ -455,17 +489,28 @@ def main():
     node_ms, cell_ms = ep.time_kernels([job], min(args.steps, 200))
     peak, peak_kind = measured_peaks()
     incid = 4.0 * N
-    cell_gbs = CELL_BYTES * N / (cell_ms * 1e-3) / 1e9
-    node_bytes = NODE_BYTES_PER_INCIDENCE * incid + 4.0 * info["n_nodes"]
+    iw = info["index_width"]
+    cell_b = cell_bytes(iw)
+    cell_gbs = cell_b * N / (cell_ms * 1e-3) / 1e9
+    node_bytes = node_bytes_per_incidence(iw) * incid + 4.0 * info["n_nodes"]
     traffic = traffic_from_profile(N)
+    step_s = ms / args.steps * 1e-3
     roofline = {"bound": "hbm", "kernel": "cell_kernel<float>", "achieved": cell_gbs, "peak": peak,
                 "unit": "GB/s", "frac": cell_gbs / peak, "traffic": traffic,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy)" if peak_kind == "measured"
                 else "fallback 6.4 TB/s",
-                "algorithmic_bytes_per_cell": CELL_BYTES, "cell_kernel_ms": cell_ms, "node_kernel_ms": node_ms,
+                "algorithmic_bytes_per_cell": cell_b, "index_width": iw,
+                "cell_kernel_ms": cell_ms, "node_kernel_ms": node_ms,
                 "cell_variant": int(chosen[0]), "autotune_ms": None if variant_ms is None else [round(float(x), 4) for x in variant_ms[0]],
                 "node_kernel_gbs": node_bytes / (node_ms * 1e-3) / 1e9,
-                "step_gbs": (CELL_BYTES * N + node_bytes) / ((cell_ms + node_ms) * 1e-3) / 1e9}
+                "step_gbs": (cell_b * N + node_bytes) / ((cell_ms + node_ms) * 1e-3) / 1e9,
+                # the same kernels against the survey's byte floor (277 B per step, 245 B of it the
+                # cell kernel's), the step taken from the timed region
+                "survey_floor": {"step_bytes_per_cell": SURVEY_STEP_FLOOR,
+                                 "step_frac": SURVEY_STEP_FLOOR * N / step_s / 1e9 / peak,
+                                 "cell_bytes_per_cell": SURVEY_CELL_FLOOR,
+                                 "cell_frac": SURVEY_CELL_FLOOR * N / (cell_ms * 1e-3) / 1e9 / peak},
+                "alu": alu_side(N, cell_ms, alu)}
 
     # end to end through the public API with host buffers: the initial state uploaded from pinned
     # host memory, K steps, V read back every OUTPUT_EVERY steps, the activation map at the end
@@ -560,7 +605,8 @@ def main():
                           "cells": N, "nodes": info["n_nodes"], "dt_ms": case.dt,
                           "precision": "FP32 with two-float compensated [Na]i/[K]i/[Ca]SR accumulation",
                           "l2": f"inputs larger than L2 ({info['device_bytes'] / 1e9:.2f} GB resident, "
-                                f"~{(CELL_BYTES * N + node_bytes) / 1e9:.2f} GB moved per step > 126 MB)",
+                                f"~{(cell_b * N + node_bytes) / 1e9:.2f} GB moved per step > 126 MB)",
+                          "index_width": iw,
                           "parallelism": f"replicas x{world}", "graph_replay": True},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": 2 * args.steps, "fp64_plain": fp64,

@@ -117,7 +117,14 @@ typedef void (*ep_free_fn)(void *ptr, size_t bytes, void *user);
  * stimulus protocol k covers the cell, or NULL for none. fibre: 3 doubles
  * per cell, the fibre direction (need not be normalised; a triangle's
  * conductivity acts in its plane), or NULL for isotropic tissue with
- * diffusivity D_l. */
+ * diffusivity D_l. index_width: 0 (the default) stores the step's gather
+ * indices as 16-bit offsets where the library's cell and node numbering
+ * allows it (a cell's neighbours within 32767 cells of it, the nodes of
+ * each run of 256 cells and the cells of each run of 32 nodes within a
+ * window of 65536: true of any mesh whose reverse Cuthill-McKee bandwidth is
+ * below about 10^4 cells), else as 32-bit indices; 32 always stores 32-bit
+ * indices. Both give bitwise identical results; the 16-bit form moves 32
+ * fewer bytes per cell and step. */
 typedef struct {
     int64_t n_nodes;
     const double *xyz;
@@ -129,6 +136,8 @@ typedef struct {
     const double *fibre;
     int64_t n_tris;
     const int32_t *tri;
+    int32_t index_width;
+    int32_t pad;
 } ep_mesh_desc;
 
 /* Parameters of one parameter set. variant (TP06 only): 0 epicardial,
@@ -221,7 +230,9 @@ int ep_params_set(ep_job *job, const ep_params *params);
  * (the job keeps the host mesh it shares with the plan). */
 int ep_plan_create(const ep_mesh_desc *desc, const ep_params *params, ep_plan **out);
 int64_t ep_plan_bytes(const ep_plan *plan);
-int ep_plan_info(const ep_plan *plan, int64_t *n_cells, int64_t *n_nodes);
+/* ep_plan_info: cells, nodes, and the width (16 or 32 bits) the job's gather
+ * indices will be stored with (ep_mesh_desc.index_width). */
+int ep_plan_info(const ep_plan *plan, int64_t *n_cells, int64_t *n_nodes, int32_t *index_width);
 int ep_plan_destroy(ep_plan *plan);
 int ep_job_create(ep_context *ctx, const ep_plan *plan, ep_job **out);
 
@@ -273,9 +284,10 @@ int ep_check_finite(ep_job *job);
  * again. Synchronises the context's stream. */
 int ep_clear_error(ep_context *ctx);
 
-/* Job information: cells, nodes, interior faces, device bytes held. */
+/* Job information: cells, nodes, interior faces, device bytes held, and
+ * the width (16 or 32 bits) of its stored gather indices. */
 int ep_job_info(const ep_job *job, int64_t *n_cells, int64_t *n_nodes,
-                int64_t *n_interior_faces, int64_t *device_bytes);
+                int64_t *n_interior_faces, int64_t *device_bytes, int32_t *index_width);
 
 /* Device bytes a job of this size would hold (planner estimate used for
  * admission by free memory). */
@@ -350,22 +362,29 @@ int ep_plan_inspect(const ep_mesh_desc *desc, const ep_params *params, int64_t *
  * job list, and each job holds its own node-value buffer.
  *
  * The job's state and coefficient arrays (created earlier through the
- * context's allocator) are the inputs and outputs; the step's scratch (the
- * node values and a ticket counter) lives in one static device array of the
- * library, 256 bytes + EP_NOALLOC_MAX_NODES doubles (16 MiB + 256 B), held by
- * every GPU that loads the library until the process exits. Results equal
- * those of ep_step bit for bit (the same per-cell arithmetic, other launch
- * shapes and another place for the node values).
- *   - Rejects meshes with more than EP_NOALLOC_MAX_NODES nodes (EP_EINVAL).
+ * context's allocator) are the inputs and outputs. Everything else the step
+ * needs -- a copy of the job's descriptor, its tile tables, a ticket counter
+ * and the node values -- lives in one static device array of the library
+ * (about 17.3 MiB: EP_NOALLOC_MAX_NODES doubles of node values plus the tile
+ * tables of EP_NOALLOC_MAX_CELLS cells), held by every GPU that loads the
+ * library until the process exits; the descriptor and tiles are copied in
+ * from host memory on every call. The step then runs the same kernels as
+ * ep_step (in the context's current launch shape, no graph replay), so the
+ * results equal ep_step's bit for bit.
+ *   - Rejects meshes with more than EP_NOALLOC_MAX_NODES nodes or
+ *     EP_NOALLOC_MAX_CELLS cells (EP_EINVAL), and jobs with a conduction
+ *     graph, bidomain or AB2 (EP_EINVAL: use ep_step).
  *   - The first call in a CUDA context (one per device, unless the caller
  *     re-creates it, e.g. after cudaDeviceReset) looks up the array's device
  *     address with that context current; make that first call before any
  *     stream capture.
- *   - All calls share the array and it keeps the last call's contents: calls
- *     that overlap on the GPU (other streams, threads or contexts on the same
- *     device) race on it; serialise them.
+ *   - All calls share the array and it keeps the last call's contents (the
+ *     ticket is cleared by each call): calls that overlap on the GPU (other
+ *     streams, threads or contexts on the same device) race on it;
+ *     serialise them.
  * Asynchronous on the context's stream. */
 #define EP_NOALLOC_MAX_NODES 2097152
+#define EP_NOALLOC_MAX_CELLS 16777216
 int ep_step_noalloc(ep_job *job, int64_t n_steps);
 
 /* ---- conduction graph (Purkinje network, 1D bundles) and junctions ---- */

@@ -380,36 +380,48 @@ int plan_params(const HostMesh &m, const ep_params *p, Coeffs *cf, std::string *
 // Upload a job's precision-independent arrays (on the context's upload stream).
 int job_upload_topology(ep_context *ctx, ep_job *j) {
     const HostMesh &m = j->mesh();
+    const Sell &sl = j->sell();
     const int64_t N = m.n_cells;
-    std::vector<int4> na(N), nb(N), nc(N);
-    for (int64_t c = 0; c < N; ++c) {
-        const int32_t *t = &m.tet[4 * c];
-        na[c] = make_int4(t[0], t[1], t[2], t[3]);
-        int o[4], q[4];
-        for (int k = 0; k < 4; ++k) {
-            o[k] = m.opp[4 * c + k] >= 0 ? m.opp[4 * c + k] : t[0];
-            q[k] = m.nbr[4 * c + k] >= 0 ? m.nbr[4 * c + k] : int(c);
-        }
-        nb[c] = make_int4(o[0], o[1], o[2], o[3]);
-        nc[c] = make_int4(q[0], q[1], q[2], q[3]);
-    }
     void *p;
     int rc;
-    if ((rc = upload(ctx, na, &j->topo, &p))) return rc;
-    j->dj.nodes_a = static_cast<const int4 *>(p);
-    if ((rc = upload(ctx, nb, &j->topo, &p))) return rc;
-    j->dj.nodes_b = static_cast<const int4 *>(p);
-    if ((rc = upload(ctx, nc, &j->topo, &p))) return rc;
-    j->dj.nbr = static_cast<const int4 *>(p);
+    j->dj.idx16 = sl.idx16 ? 1 : 0;
+    if (sl.idx16) {
+        // 16-bit gather indices (offsets; see Sell)
+        if ((rc = upload(ctx, sl.cidx16, &j->topo, &p))) return rc;
+        j->dj.cidx16 = static_cast<const uint4 *>(p);
+        if ((rc = upload(ctx, sl.nbr16, &j->topo, &p))) return rc;
+        j->dj.nbr16 = static_cast<const uint2 *>(p);
+        if ((rc = upload(ctx, sl.nbase, &j->topo, &p))) return rc;
+        j->dj.nbase = static_cast<const int *>(p);
+        if ((rc = upload(ctx, sl.col16, &j->topo, &p))) return rc;
+        j->dj.ncol16 = static_cast<const unsigned short *>(p);
+        if ((rc = upload(ctx, sl.cbase, &j->topo, &p))) return rc;
+        j->dj.cbase = static_cast<const int *>(p);
+    } else {
+        std::vector<int4> na(N), nb(N), nc(N);
+        for (int64_t c = 0; c < N; ++c) {
+            int32_t a[4], b[4], q[4];
+            cell_gather_indices(m, c, a, b, q);
+            na[c] = make_int4(a[0], a[1], a[2], a[3]);
+            nb[c] = make_int4(b[0], b[1], b[2], b[3]);
+            nc[c] = make_int4(q[0], q[1], q[2], q[3]);
+        }
+        if ((rc = upload(ctx, na, &j->topo, &p))) return rc;
+        j->dj.nodes_a = static_cast<const int4 *>(p);
+        if ((rc = upload(ctx, nb, &j->topo, &p))) return rc;
+        j->dj.nodes_b = static_cast<const int4 *>(p);
+        if ((rc = upload(ctx, nc, &j->topo, &p))) return rc;
+        j->dj.nbr = static_cast<const int4 *>(p);
+        if ((rc = upload(ctx, sl.col, &j->topo, &p))) return rc;
+        j->dj.ncol = static_cast<const int *>(p);
+    }
     if ((rc = upload(ctx, m.pset, &j->topo, &p))) return rc;
     j->dj.pset = static_cast<const uint8_t *>(p);
     if ((rc = upload(ctx, m.smask, &j->topo, &p))) return rc;
     j->dj.smask = static_cast<const uint8_t *>(p);
-    std::vector<long long> sp(j->sell().slice_ptr.begin(), j->sell().slice_ptr.end());
+    std::vector<long long> sp(sl.slice_ptr.begin(), sl.slice_ptr.end());
     if ((rc = upload(ctx, sp, &j->topo, &p))) return rc;
     j->dj.slice_ptr = static_cast<const long long *>(p);
-    if ((rc = upload(ctx, j->sell().col, &j->topo, &p))) return rc;
-    j->dj.ncol = static_cast<const int *>(p);
     if ((rc = upload(ctx, m.cell_new2old, &j->topo, &p))) return rc;
     j->perm_dev = static_cast<const int *>(p);
     DevBuf b;
@@ -557,8 +569,10 @@ int job_apply_params(ep_job *job, const ep_params *p, const Coeffs &cf) {
 int64_t job_bytes(const HostMesh &m, const Sell &sl, int precision, int integrator = EP_INTEGRATOR_FE) {
     auto rnd = [](int64_t b) { return std::max<int64_t>(b, 256); };
     const int64_t N = m.n_cells, r = precision == EP_FP64_PLAIN ? 8 : 4, E = int64_t(sl.col.size());
-    int64_t b = 3 * rnd(16 * N) + 2 * rnd(N) + rnd(8 * int64_t(sl.slice_ptr.size())) + rnd(4 * E) + rnd(4 * N) + 256 +
-                rnd(sizeof(DevJob));
+    const int64_t ns = int64_t(sl.slice_ptr.size()) - 1;
+    int64_t b = 2 * rnd(N) + rnd(8 * int64_t(sl.slice_ptr.size())) + rnd(4 * N) + 256 + rnd(sizeof(DevJob));
+    b += sl.idx16 ? rnd(16 * N) + rnd(8 * N) + rnd(4 * ((N + 255) / 256)) + rnd(2 * E) + rnd(4 * ns)
+                  : 3 * rnd(16 * N) + rnd(4 * E);
     b += 3 * rnd(4 * r * N) + rnd(r * E) + 3 * rnd(r * N) + rnd(r * m.n_nodes);
     for (int md = 0; md < EP_N_MODELS; ++md) {
         const int64_t n = m.model_off[md + 1] - m.model_off[md];
@@ -932,10 +946,11 @@ int64_t ep_plan_bytes(const ep_plan *plan) {
                      plan->has_params ? plan->params.integrator : EP_INTEGRATOR_FE);
 }
 
-int ep_plan_info(const ep_plan *plan, int64_t *n_cells, int64_t *n_nodes) {
+int ep_plan_info(const ep_plan *plan, int64_t *n_cells, int64_t *n_nodes, int32_t *index_width) {
     if (!plan) return EP_EINVAL;
     if (n_cells) *n_cells = plan->mesh->n_cells;
     if (n_nodes) *n_nodes = plan->mesh->n_nodes;
+    if (index_width) *index_width = plan->sell->idx16 ? 16 : 32;
     return EP_OK;
 }
 
@@ -975,7 +990,7 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
     for (int prec : {EP_FP32_MIXED, EP_FP64_PLAIN}) {
         std::vector<DevJob> tab;
         std::vector<Tile> nt, ct, gt;
-        int max_sub = 0, any_bido = 0, any_ab2 = 0;
+        int max_sub = 0, any_bido = 0, any_ab2 = 0, any_idx16 = 0;
         for (int i = 0; i < n; ++i) {
             if (jobs[i]->precision != prec) continue;
             const int jid = int(tab.size());
@@ -983,6 +998,7 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
             for (Tile t : jobs[i]->node_tiles) nt.push_back(Tile{jid, t.model, t.start, t.count});
             for (Tile t : jobs[i]->cell_tiles) ct.push_back(Tile{jid, t.model, t.start, t.count});
             if (jobs[i]->params.integrator == EP_INTEGRATOR_AB2) any_ab2 = 1;
+            if (jobs[i]->dj.idx16) any_idx16 = 1;
             if (jobs[i]->bido) {
                 any_bido = 1;
                 pl->bido.push_back(jobs[i]);
@@ -1020,6 +1036,7 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
         g.L.graph_grid = 1;
         g.L.bido = any_bido;
         g.L.ab2 = any_ab2;
+        g.L.idx16 = any_idx16;
         g.L.err = static_cast<unsigned *>(ctx->err_word.p);
         if (!gt.empty()) {
             if ((rc = upload(ctx, gt, &tmp, &p))) return rc;
@@ -1454,8 +1471,9 @@ int ep_check_finite(ep_job *job) {
 }
 
 int ep_job_info(const ep_job *job, int64_t *n_cells, int64_t *n_nodes, int64_t *n_interior_faces,
-                int64_t *device_bytes) {
+                int64_t *device_bytes, int32_t *index_width) {
     if (!job) return EP_EINVAL;
+    if (index_width) *index_width = job->sell().idx16 ? 16 : 32;
     if (n_cells) *n_cells = job->mesh().n_cells;
     if (n_nodes) *n_nodes = job->mesh().n_nodes;
     if (n_interior_faces) *n_interior_faces = job->mesh().n_interior_faces;
@@ -1541,10 +1559,18 @@ int ep_step_noalloc(ep_job *job, int64_t n_steps) {
         return fail(ctx, EP_EINVAL, "ep_step_noalloc: the mesh has " + std::to_string(job->mesh().n_nodes) +
                                         " nodes; at most " + std::to_string(EP_NOALLOC_MAX_NODES) +
                                         " fit the static node-value array");
+    if (job->mesh().n_cells > EP_NOALLOC_MAX_CELLS)
+        return fail(ctx, EP_EINVAL, "ep_step_noalloc: the mesh has " + std::to_string(job->mesh().n_cells) +
+                                        " cells; at most " + std::to_string(EP_NOALLOC_MAX_CELLS) +
+                                        " fit the static tile tables");
+    if (*ctx->err_host)
+        return fail(ctx, EP_ETIMEOUT, "ep_step_noalloc: an earlier step's bounded wait gave up (ep_clear_error)");
     if (n_steps == 0) return EP_OK;
     DeviceGuard g(ctx->device);
-    cudaError_t e = launch_step_noalloc(job->precision, static_cast<const DevJob *>(job->dj_dev.p), job->mesh().n_nodes,
-                                        job->mesh().n_cells, n_steps, ctx->stream);
+    cudaError_t e = launch_step_noalloc(job->precision, job->dj, job->node_tiles.data(), int(job->node_tiles.size()),
+                                        job->cell_tiles.data(), int(job->cell_tiles.size()),
+                                        ctx->cell_variant[job->precision], ctx->sm_count,
+                                        static_cast<unsigned *>(ctx->err_word.p), n_steps, ctx->stream);
     return e == cudaSuccess ? EP_OK : cuda_fail(ctx, e, "ep_step_noalloc");
 }
 

@@ -115,13 +115,10 @@ __device__ void grid_totals(const double *part, int count, double *tot_sh) {
 template <class R>
 __device__ void node_pass(const DevJob &J, const R *__restrict__ x, R scale, R *__restrict__ vn, long long gtid,
                           long long gsz) {
-    const R *__restrict__ w = static_cast<const R *>(J.nw);
     for (long long node = gtid; node < J.n_nodes; node += gsz) {
-        const long long s = node >> 5;
-        const long long b = J.slice_ptr[s] + (node & 31), e = J.slice_ptr[s + 1];
         // one entry per iteration: in this kernel (80 registers, three blocks per SM) six-deep
         // gathers made the node phase slower (3.13 against 2.65 ms per step on the 9.6M-cell wedge)
-        vn[node] = node_sum<R, 1>(w, J.ncol, x, b, e) * scale;
+        vn[node] = node_value<R, 1>(J, x, node) * scale;
     }
 }
 
@@ -131,7 +128,8 @@ template <class R>
 __device__ __forceinline__ R flux(const DevJob &J, const void *wa_, const void *wb_, const void *q_,
                                   const R *__restrict__ vn, const R *__restrict__ x, R scale, long long c) {
     using R4 = typename V4<R>::type;
-    const int4 na = J.nodes_a[c], nb = J.nodes_b[c], nc = J.nbr[c];
+    int4 na, nb, nc;
+    cell_indices(J, c, na, nb, nc);
     const R4 wa = static_cast<const R4 *>(wa_)[c];
     const R4 wb = static_cast<const R4 *>(wb_)[c];
     const R4 q = static_cast<const R4 *>(q_)[c];
@@ -215,8 +213,9 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
     // algorithmic bytes of each phase: every array it touches counted once
     // (the node table as stored, coefficients, indices, fields, basis vectors)
     const double RB = double(sizeof(R)), dn = double(n), dnn = double(J.n_nodes);
-    const double node_b = double(J.slice_ptr[(J.n_nodes + 31) >> 5]) * (4.0 + RB) + dn * RB + dnn * RB;
-    const double flux_b = dn * (48.0 + 12.0 * RB) + dnn * RB + 2.0 * dn * RB;
+    const double IB = J.idx16 ? 2.0 : 4.0;   // bytes of one stored gather index
+    const double node_b = double(J.slice_ptr[(J.n_nodes + 31) >> 5]) * (IB + RB) + dn * RB + dnn * RB;
+    const double flux_b = dn * (12.0 * IB + 12.0 * RB) + dnn * RB + 2.0 * dn * RB;
     double bytes = 0.0;
     if (A.mode == 0) {
         // right-hand side b = -L_i(V^{n+1}) and its norm

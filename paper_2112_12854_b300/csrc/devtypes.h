@@ -67,17 +67,27 @@ struct DevGraph {
 };
 
 struct DevJob {
+    // Gather indices of the step, in one of two forms (idx16 selects):
+    // 32-bit --
     const int4 *nodes_a;      // the cell's 4 vertices
     const int4 *nodes_b;      // vertex of the neighbour opposite each face (own vertex 0 on the boundary)
     const int4 *nbr;          // neighbour across each face (the cell itself on the boundary)
+    const int *ncol;          // sliced-ELL node -> cell entries
+    // 16-bit offsets --
+    const uint4 *cidx16;      // per cell 8 x u16: nodes_a then nodes_b, from nbase[c >> 8]
+    const uint2 *nbr16;       // per cell 4 x s16: nbr relative to the cell
+    const int *nbase;         // per run of 256 cells
+    const unsigned short *ncol16;  // ELL entries relative to cbase[slice]
+    const int *cbase;         // per slice of 32 nodes
+    int idx16;
+    int pad3;
     const void *wa, *wb, *q;  // float4 or double4 per cell (folded Eqs. 7-8 coefficients / V_c)
     const uint8_t *pset;
     const uint8_t *smask;
     void *V[2];               // double-buffered transmembrane potential
     void *vn;                 // node values (scratch of the step)
     void *act;                // activation times
-    const long long *slice_ptr;  // sliced-ELL node -> cell table
-    const int *ncol;
+    const long long *slice_ptr;  // sliced-ELL node -> cell table (entries: ncol / ncol16, nw)
     const void *nw;
     long long n_cells, n_nodes;
     DevRegion reg[EP_N_MODELS];

@@ -63,10 +63,7 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const DevJob *__rest
         const long long node = (long long)tl.start + i;
         const long long n = *J.step;
         const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
-        const R *__restrict__ w = static_cast<const R *>(J.nw);
-        const long long s = node >> 5;
-        const long long b = J.slice_ptr[s] + (node & 31), e = J.slice_ptr[s + 1];
-        static_cast<R *>(J.vn)[node] = node_sum<R>(w, J.ncol, V, b, e);
+        static_cast<R *>(J.vn)[node] = node_value<R>(J, V, node);
     }
 }
 
@@ -119,13 +116,14 @@ __device__ void junction_cell_crossing(const DevJob &J, long long c, long long n
     }
 }
 
-// Where a cell's streamed step inputs are read: straight from the job's
-// arrays in global memory, or from a shared-memory stage filled by bulk
-// copies (cell_kernel_staged). The gathered inputs (node values, neighbour
-// potentials) are always read from global memory.
+// A cell's streamed step inputs: its gather indices (decoded), and where the
+// rest is read -- straight from the job's arrays in global memory, or from a
+// shared-memory stage filled by bulk copies (cell_kernel_staged). The
+// gathered inputs (node values, neighbour potentials) are always read from
+// global memory.
 template <class R>
 struct CellSrc {
-    const int4 *na, *nb, *nc;
+    int4 na, nb, nc;
     const typename Vec4T<R>::type *wa, *wb, *q;
     const R *Vc;
     const uint8_t *smask, *pset;
@@ -136,8 +134,9 @@ template <class R>
 __device__ __forceinline__ CellSrc<R> global_src(const DevJob &J, int model, long long c, const R *V) {
     using R4 = typename Vec4T<R>::type;
     const DevRegion &rg = J.reg[model];
-    return CellSrc<R>{J.nodes_a + c, J.nodes_b + c, J.nbr + c,
-                      static_cast<const R4 *>(J.wa) + c, static_cast<const R4 *>(J.wb) + c,
+    int4 na, nb, nc;
+    cell_indices(J, c, na, nb, nc);
+    return CellSrc<R>{na, nb, nc, static_cast<const R4 *>(J.wa) + c, static_cast<const R4 *>(J.wb) + c,
                       static_cast<const R4 *>(J.q) + c, V + c, J.smask + c, J.pset + c,
                       region_io<R>(rg, c - rg.off)};
 }
@@ -152,7 +151,7 @@ __device__ __forceinline__ void cell_update_from(const DevJob &J, int model, lon
     using R4 = typename Vec4T<R>::type;
     R *__restrict__ Vnext = static_cast<R *>(J.V[(n & 1) ^ 1]);
     const R *__restrict__ vn = static_cast<const R *>(J.vn);
-    const int4 na = *src.na, nb = *src.nb, nc = *src.nc;
+    const int4 na = src.na, nb = src.nb, nc = src.nc;
     const R4 wa = *src.wa;
     const R4 wb = *src.wb;
     const R4 q = *src.q;
@@ -494,7 +493,7 @@ __global__ void __launch_bounds__(kCellThreads, STATE ? 2 : 3)
                 io.ai = &S.a[0][tid];
                 io.si = kCells;
             }
-            CellSrc<float> src{S.na + tid, S.nb + tid, S.nc + tid, S.wa + tid, S.wb + tid, S.q + tid,
+            CellSrc<float> src{S.na[tid], S.nb[tid], S.nc[tid], S.wa + tid, S.wb + tid, S.q + tid,
                                (fl & 1) ? S.V + tid : V + c, (fl & 2) ? S.smask + tid : J.smask + c,
                                (fl & 2) ? S.pset + tid : J.pset + c, io};
             cell_update_from<float, XD, false>(J, tl.model, c, n, V, src);
@@ -723,7 +722,7 @@ template <class R>
 static cudaError_t cell_launch_variant(const StepLaunch &L, cudaStream_t s) {
     if (L.cell_variant >= kStagedVariant) {
         if constexpr (std::is_same<R, float>::value) {
-            if (!L.ab2) {
+            if (!L.ab2 && !L.idx16) {
                 cudaError_t e = staged_attributes();
                 if (e != cudaSuccess) return e;
                 if (L.cell_variant == kStagedVariant) launch_staged<true>(L, s);
@@ -731,7 +730,7 @@ static cudaError_t cell_launch_variant(const StepLaunch &L, cudaStream_t s) {
                 return cudaGetLastError();
             }
         }
-        StepLaunch L0 = L;   // FP64 or AB2: the plain variant 0
+        StepLaunch L0 = L;   // FP64, AB2 or 16-bit indices: the plain variant 0
         L0.cell_variant = 0;
         return cell_launch_variant<R>(L0, s);
     }
@@ -818,15 +817,29 @@ int node_blocks_per_sm(int precision) {
 // memory pool (a new cudaMalloc would fail or fragment that pool), or a
 // latency-critical loop that may not call cudaMalloc/cudaFree because those
 // can take a global lock or synchronise the device. The variant below keeps
-// the step's only scratch -- the node values of S1 and the ticket counter that
-// advances the step -- in this file-scope array instead of memory owned by
-// the job. Every GPU that loads the library holds the array until the process
-// exits. All calls share it and it keeps the last call's contents: calls that
-// overlap on the GPU (different streams, threads or contexts on one device)
-// race on it and must be serialised by the caller.
-constexpr long long kNoAllocMaxNodes = EP_NOALLOC_MAX_NODES;
-constexpr size_t kNoAllocHeader = 256;  // ticket counter, padded to keep node values 256-byte aligned
-static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocHeader + kNoAllocMaxNodes * sizeof(double)];
+// everything the step needs beyond the job's own arrays -- the job's
+// descriptor, its node and cell tile tables, the ticket counter that
+// advances the step, and the node values of S1 -- in this file-scope array
+// instead of memory allocated per batch, and then runs the very kernels
+// ep_step runs, so the results are the same bit for bit. Every GPU that loads
+// the library holds the array until the process exits. All calls share it
+// and it keeps the last call's contents: calls that overlap on the GPU
+// (different streams, threads or contexts on one device) race on it and must
+// be serialised by the caller.
+//
+// Layout: [0, 256) the ticket; the descriptor; the node tiles; the cell tiles;
+// the node values (each part 256-byte aligned).
+namespace noalloc {
+constexpr size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kMaxNodeTiles = (EP_NOALLOC_MAX_NODES + kNodeThreads - 1) / kNodeThreads;
+constexpr size_t kMaxCellTiles = (EP_NOALLOC_MAX_CELLS + kCellThreads - 1) / kCellThreads + EP_N_MODELS;
+constexpr size_t kJob = 256;
+constexpr size_t kNodeTiles = kJob + round256(sizeof(DevJob));
+constexpr size_t kCellTiles = kNodeTiles + round256(kMaxNodeTiles * sizeof(Tile));
+constexpr size_t kVn = kCellTiles + round256(kMaxCellTiles * sizeof(Tile));
+constexpr size_t kBytes = kVn + size_t(EP_NOALLOC_MAX_NODES) * sizeof(double);
+}  // namespace noalloc
+static __device__ __align__(256) unsigned char g_noalloc_scratch[noalloc::kBytes];
 
 // Device address of g_noalloc_scratch, looked up once per CUDA context with
 // that context current (in host code the symbol's name is only a host-side
@@ -885,83 +898,48 @@ static cudaError_t noalloc_scratch_address(void **out) {
     return cudaSuccess;
 }
 
-template <class R>
-__global__ void __launch_bounds__(kNodeThreads) node_kernel_noalloc(const DevJob *__restrict__ job, R *__restrict__ vn) {
-    const DevJob &J = *job;
-    const long long n = *J.step;
-    const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
-    const R *__restrict__ w = static_cast<const R *>(J.nw);
-    for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < J.n_nodes;
-         node += (long long)gridDim.x * blockDim.x) {
-        const long long s = node >> 5;
-        const long long b = J.slice_ptr[s] + (node & 31), e = J.slice_ptr[s + 1];
-        vn[node] = node_sum<R>(w, J.ncol, V, b, e);
-    }
-}
-
-template <class R>
-__global__ void __launch_bounds__(kCellThreads) cell_kernel_noalloc(const DevJob *__restrict__ job, R *vn,
-                                                                    unsigned *ticket) {
-    // the job's descriptor with its node-value pointer redirected to the static scratch
-    __shared__ DevJob Js;
-    {
-        const long long *src = reinterpret_cast<const long long *>(job);
-        long long *dst = reinterpret_cast<long long *>(&Js);
-        for (int i = threadIdx.x; i < int(sizeof(DevJob) / sizeof(long long)); i += blockDim.x) dst[i] = src[i];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) Js.vn = vn;
-    __syncthreads();
-    const long long end0 = Js.reg[0].off + Js.reg[0].n, end1 = Js.reg[1].off + Js.reg[1].n;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < Js.n_cells;
-         c += (long long)gridDim.x * blockDim.x) {
-        const int model = c < end0 ? 0 : (c < end1 ? 1 : 2);
-        cell_update<R>(Js, model, c);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(ticket, 1u);
-        if (prev == gridDim.x - 1) {
-            *Js.step += 1;
-            *ticket = 0u;
-            __threadfence();
-        }
-    }
-}
-
-template <class R>
-static cudaError_t step_noalloc_impl(const DevJob *job, long long n_nodes, long long n_cells, long long n_steps,
-                                     cudaStream_t s) {
+cudaError_t launch_step_noalloc(int precision, const DevJob &job, const Tile *node_tiles, int n_node_tiles,
+                                const Tile *cell_tiles, int n_cell_tiles, int cell_variant, int sm_count,
+                                unsigned *err, long long n_steps, cudaStream_t s) {
+    using namespace noalloc;
+    if (job.n_nodes < 1 || job.n_nodes > EP_NOALLOC_MAX_NODES || job.n_cells < 1 ||
+        job.n_cells > EP_NOALLOC_MAX_CELLS || n_node_tiles > int(kMaxNodeTiles) || n_cell_tiles > int(kMaxCellTiles))
+        return cudaErrorInvalidValue;
     void *base = nullptr;
     cudaError_t e = noalloc_scratch_address(&base);
     if (e != cudaSuccess) return e;
-    unsigned *ticket = static_cast<unsigned *>(base);
-    R *vn = reinterpret_cast<R *>(static_cast<unsigned char *>(base) + kNoAllocHeader);
-    // the ticket must start at zero; the array keeps whatever the last call left
-    e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), s);
+    unsigned char *b = static_cast<unsigned char *>(base);
+    DevJob dj = job;
+    dj.vn = b + kVn;
+    // the descriptor and the tile tables (host copies, stream-ordered); the ticket must
+    // start at zero -- the array keeps whatever the last call left
+    e = cudaMemcpyAsync(b + kJob, &dj, sizeof(DevJob), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + kNodeTiles, node_tiles, size_t(n_node_tiles) * sizeof(Tile), cudaMemcpyHostToDevice,
+                            s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + kCellTiles, cell_tiles, size_t(n_cell_tiles) * sizeof(Tile), cudaMemcpyHostToDevice,
+                            s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 148, nb_node = 1, nb_cell = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_node, node_kernel_noalloc<R>, kNodeThreads, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_cell, cell_kernel_noalloc<R>, kCellThreads, 0);
-    const long long gn = std::min<long long>((n_nodes + kNodeThreads - 1) / kNodeThreads,
-                                             (long long)sms * std::max(nb_node, 1));
-    const long long gc = std::min<long long>((n_cells + kCellThreads - 1) / kCellThreads,
-                                             (long long)sms * std::max(nb_cell, 1));
+    StepLaunch L{};
+    L.jobs = reinterpret_cast<const DevJob *>(b + kJob);
+    L.n_jobs = 1;
+    L.node_tiles = reinterpret_cast<const Tile *>(b + kNodeTiles);
+    L.n_node_tiles = n_node_tiles;
+    L.cell_tiles = reinterpret_cast<const Tile *>(b + kCellTiles);
+    L.n_cell_tiles = n_cell_tiles;
+    L.done = reinterpret_cast<unsigned *>(b);
+    L.cell_variant = cell_variant;
+    L.idx16 = job.idx16;
+    L.err = err;
+    L.node_grid = std::max(1, std::min(n_node_tiles, sm_count * node_blocks_per_sm(precision)));
+    L.cell_grid = std::max(1, std::min(n_cell_tiles, sm_count * cell_blocks_per_sm(precision, cell_variant)));
     for (long long it = 0; it < n_steps; ++it) {
-        node_kernel_noalloc<R><<<int(std::max(gn, 1LL)), kNodeThreads, 0, s>>>(job, vn);
-        cell_kernel_noalloc<R><<<int(std::max(gc, 1LL)), kCellThreads, 0, s>>>(job, vn, ticket);
+        e = launch_step(precision, L, s);
+        if (e != cudaSuccess) return e;
     }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_step_noalloc(int precision, const DevJob *job, long long n_nodes, long long n_cells,
-                                long long n_steps, cudaStream_t s) {
-    if (n_nodes < 1 || n_nodes > kNoAllocMaxNodes) return cudaErrorInvalidValue;
-    return precision == EP_FP64_PLAIN ? step_noalloc_impl<double>(job, n_nodes, n_cells, n_steps, s)
-                                      : step_noalloc_impl<float>(job, n_nodes, n_cells, n_steps, s);
+    return cudaSuccess;
 }
 
 }  // namespace ep

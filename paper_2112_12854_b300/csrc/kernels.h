@@ -22,6 +22,7 @@ struct StepLaunch {
     int graph_substeps;        // largest substep count of the jobs' graphs
     int bido;                  // some job is bidomain (cell kernel adds DevJob::xdiv)
     int ab2;                   // some job integrates by AB2 (cell kernel keeps rate histories)
+    int idx16;                 // some job stores 16-bit gather indices (the staged variants need 32-bit)
     unsigned *err;             // device error word of the context (bounded waits that gave up)
 };
 
@@ -34,10 +35,10 @@ struct StepLaunch {
     X(3, 128, 5)            \
     X(4, 128, 6)            \
     X(5, 64, 12)
-// Variants 6 and 7: cell_kernel_staged (FP32 forward Euler, 256 threads;
-// streamed inputs staged by bulk copies: 6 everything, two blocks per SM;
-// 7 indices / coefficients / V / bytes, three blocks per SM); for FP64 or
-// AB2 batches they run variant 0.
+// Variants 6 and 7: cell_kernel_staged (FP32 forward Euler, 32-bit indices,
+// 256 threads; streamed inputs staged by bulk copies: 6 everything, two
+// blocks per SM; 7 indices / coefficients / V / bytes, three blocks per SM);
+// for FP64, AB2 or 16-bit-index batches they run variant 0.
 constexpr int kNumCellVariants = 8;
 constexpr int kStagedVariant = 6;
 int cell_variant_threads(int variant);
@@ -72,15 +73,20 @@ cudaError_t launch_reset_act(int precision, const DevJob *job, long long n_cells
 cudaError_t launch_check_finite(int precision, const DevJob *job, long long n_cells, unsigned *count,
                                 cudaStream_t s);
 
-// Step one job n_steps times with its node values in a static device array
-// instead of job memory (no allocation; at most EP_NOALLOC_MAX_NODES nodes).
+
 // Pipe issue-rate probe (peaks.cu): kind 0 FP32 FMA, 1 MUFU ex2, 2 FP64
 // FMA. *ops receives the operations (flops for FMA kinds) of the launch.
 cudaError_t launch_alu_probe(int kind, int blocks, int iters, double *sink, cudaStream_t s, double *ops);
 int alu_probe_threads();
 
-cudaError_t launch_step_noalloc(int precision, const DevJob *job, long long n_nodes, long long n_cells,
-                                long long n_steps, cudaStream_t s);
+// Step one job n_steps times like launch_step, with its descriptor, tile
+// tables, ticket and node values in a static device array instead of
+// allocated memory (at most EP_NOALLOC_MAX_NODES nodes and
+// EP_NOALLOC_MAX_CELLS cells). job, node_tiles and cell_tiles are host
+// copies (tiles of job 0).
+cudaError_t launch_step_noalloc(int precision, const DevJob &job, const Tile *node_tiles, int n_node_tiles,
+                                const Tile *cell_tiles, int n_cell_tiles, int cell_variant, int sm_count,
+                                unsigned *err, long long n_steps, cudaStream_t s);
 
 // Kernel attributes for sizing persistent grids.
 int cell_blocks_per_sm(int precision, int variant);

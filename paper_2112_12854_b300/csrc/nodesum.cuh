@@ -1,24 +1,27 @@
-// Node interpolation (S1, Sec. 3.2) over the sliced-ELL node -> cell table,
-// shared by the monodomain node kernels and the bidomain solve's node passes.
+// Gather-index decoding and node interpolation (S1, Sec. 3.2), shared by the
+// monodomain step kernels and the bidomain solve.
 #pragma once
+
+#include "devtypes.h"
 
 namespace ep {
 
 // Inverse-distance node value (S1) over the sliced-ELL entries b, b+32, ...
-// < e of one node. The loads of D entries are issued before their products
-// are accumulated, so D gathers are in flight at once (D = 6: an interior
-// node of a Kuhn mesh has 24 cells, four groups; the fastest of 4, 6, 8 and
-// 12 on the B300); the sum is still taken in entry order.
-template <class R, int D = 6>
-__device__ __forceinline__ R node_sum(const R *__restrict__ w, const int *__restrict__ col, const R *__restrict__ V,
-                                      long long b, long long e) {
+// < e of one node; the cell of entry k is base + col[k]. The loads of D
+// entries are issued before their products are accumulated, so D gathers
+// are in flight at once (D = 6: an interior node of a Kuhn mesh has 24
+// cells, four groups; the fastest of 4, 6, 8 and 12 on the B300); the sum
+// is still taken in entry order.
+template <class R, int D = 6, class C>
+__device__ __forceinline__ R node_sum(const R *__restrict__ w, const C *__restrict__ col, int base,
+                                      const R *__restrict__ V, long long b, long long e) {
     R acc = R(0);
     long long k = b;
     for (; k + 32 * (D - 1) < e; k += 32 * D) {
         int c[D];
         R wk[D], v[D];
 #pragma unroll
-        for (int i = 0; i < D; ++i) c[i] = col[k + 32 * i];
+        for (int i = 0; i < D; ++i) c[i] = base + int(col[k + 32 * i]);
 #pragma unroll
         for (int i = 0; i < D; ++i) wk[i] = w[k + 32 * i];
 #pragma unroll
@@ -26,8 +29,40 @@ __device__ __forceinline__ R node_sum(const R *__restrict__ w, const int *__rest
 #pragma unroll
         for (int i = 0; i < D; ++i) acc += wk[i] * v[i];
     }
-    for (; k < e; k += 32) acc += w[k] * V[col[k]];
+    for (; k < e; k += 32) acc += w[k] * V[base + int(col[k])];
     return acc;
+}
+
+// S1 at one node of a job, in the job's index form.
+template <class R, int D = 6>
+__device__ __forceinline__ R node_value(const DevJob &J, const R *__restrict__ V, long long node) {
+    const R *__restrict__ w = static_cast<const R *>(J.nw);
+    const long long s = node >> 5;
+    const long long b = J.slice_ptr[s] + (node & 31), e = J.slice_ptr[s + 1];
+    if (J.idx16) return node_sum<R, D>(w, J.ncol16, J.cbase[s], V, b, e);
+    return node_sum<R, D>(w, J.ncol, 0, V, b, e);
+}
+
+// The gather indices of cell c: its vertices (na), the vertex of the
+// neighbour opposite each face (nb) and the neighbours (nc).
+__device__ __forceinline__ void cell_indices(const DevJob &J, long long c, int4 &na, int4 &nb, int4 &nc) {
+    if (J.idx16) {
+        const uint4 u = J.cidx16[c];
+        const int base = J.nbase[c >> 8];
+        na = make_int4(base + int(u.x & 0xffffu), base + int(u.x >> 16), base + int(u.y & 0xffffu),
+                       base + int(u.y >> 16));
+        nb = make_int4(base + int(u.z & 0xffffu), base + int(u.z >> 16), base + int(u.w & 0xffffu),
+                       base + int(u.w >> 16));
+        const uint2 o = J.nbr16[c];
+        const int ci = int(c);
+        // low halves sign-extended through a 16-bit signed value, high halves by an arithmetic shift
+        nc = make_int4(ci + int(short(o.x & 0xffffu)), ci + (int(o.x) >> 16), ci + int(short(o.y & 0xffffu)),
+                       ci + (int(o.y) >> 16));
+    } else {
+        na = J.nodes_a[c];
+        nb = J.nodes_b[c];
+        nc = J.nbr[c];
+    }
 }
 
 }  // namespace ep

@@ -107,6 +107,11 @@ struct FaceRec {
 
 int build_mesh(const ep_mesh_desc *d, HostMesh *m, std::string *err) {
     const int64_t NT = d->n_cells, NS = d->n_tris, N = NT + NS, NN = d->n_nodes;
+    if (d->index_width != 0 && d->index_width != 32) {
+        *err = "mesh: index_width must be 0 (automatic) or 32";
+        return EP_EINVAL;
+    }
+    m->index_width = d->index_width;
     if (NT < 0 || NS < 0 || N <= 0 || NN <= 0 || !d->xyz || (NT > 0 && !d->tet) || (NS > 0 && !d->tri)) {
         *err = "mesh: empty mesh or NULL xyz/tet/tri";
         return EP_EINVAL;
@@ -580,6 +585,61 @@ double power_radius(const HostMesh &m, const Coeffs &cf, int iters) {
     return lam;
 }
 
+void cell_gather_indices(const HostMesh &m, int64_t c, int32_t na[4], int32_t nb[4], int32_t nc[4]) {
+    const int32_t *t = &m.tet[4 * c];
+    for (int k = 0; k < 4; ++k) {
+        na[k] = t[k];
+        nb[k] = m.opp[4 * c + k] >= 0 ? m.opp[4 * c + k] : t[0];
+        nc[k] = m.nbr[4 * c + k] >= 0 ? m.nbr[4 * c + k] : int32_t(c);
+    }
+}
+
+// 16-bit form of the gather indices (see Sell), if every offset fits.
+static bool build_idx16(const HostMesh &m, Sell *s) {
+    const int64_t N = m.n_cells, NN = m.n_nodes;
+    const int64_t ns = int64_t(s->slice_ptr.size()) - 1;
+    s->cbase.assign(ns, 0);
+    s->col16.assign(s->col.size(), 0);
+    for (int64_t sl = 0; sl < ns; ++sl) {
+        const int64_t b = s->slice_ptr[sl], e = s->slice_ptr[sl + 1];
+        if (b == e) continue;
+        int32_t lo = s->col[b], hi = s->col[b];
+        for (int64_t k = b; k < e; ++k) lo = std::min(lo, s->col[k]), hi = std::max(hi, s->col[k]);
+        if (int64_t(hi) - lo > 65535) return false;
+        s->cbase[sl] = lo;
+        for (int64_t k = b; k < e; ++k) s->col16[k] = uint16_t(s->col[k] - lo);
+    }
+    const int64_t nblk = (N + 255) / 256;
+    s->nbase.assign(nblk, 0);
+    s->cidx16.assign(8 * N, 0);
+    s->nbr16.assign(4 * N, 0);
+    for (int64_t blk = 0; blk < nblk; ++blk) {
+        const int64_t c0 = 256 * blk, c1 = std::min(N, c0 + 256);
+        int32_t lo = int32_t(NN), hi = 0;
+        int32_t na[4], nb[4], nc[4];
+        for (int64_t c = c0; c < c1; ++c) {
+            cell_gather_indices(m, c, na, nb, nc);
+            for (int k = 0; k < 4; ++k) {
+                lo = std::min({lo, na[k], nb[k]});
+                hi = std::max({hi, na[k], nb[k]});
+            }
+        }
+        if (int64_t(hi) - lo > 65535) return false;
+        s->nbase[blk] = lo;
+        for (int64_t c = c0; c < c1; ++c) {
+            cell_gather_indices(m, c, na, nb, nc);
+            for (int k = 0; k < 4; ++k) {
+                s->cidx16[8 * c + k] = uint16_t(na[k] - lo);
+                s->cidx16[8 * c + 4 + k] = uint16_t(nb[k] - lo);
+                const int64_t d = int64_t(nc[k]) - c;
+                if (d < -32768 || d > 32767) return false;
+                s->nbr16[4 * c + k] = int16_t(d);
+            }
+        }
+    }
+    return true;
+}
+
 void build_sell(const HostMesh &m, Sell *s) {
     const int64_t NN = m.n_nodes;
     const int64_t ns = (NN + 31) / 32;
@@ -610,6 +670,14 @@ void build_sell(const HostMesh &m, Sell *s) {
                 }
             }
         }
+    }
+    s->idx16 = m.index_width != 32 && build_idx16(m, s);
+    if (!s->idx16) {
+        s->col16.clear();
+        s->cbase.clear();
+        s->cidx16.clear();
+        s->nbr16.clear();
+        s->nbase.clear();
     }
 }
 

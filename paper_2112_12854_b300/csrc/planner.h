@@ -25,6 +25,7 @@ struct HostMesh {
     int64_t n_interior_faces = 0;
     std::vector<int64_t> n2c_ptr;     // node -> incident cells (internal numbering, sorted)
     std::vector<int32_t> n2c;
+    int index_width = 0;              // ep_mesh_desc::index_width (0: 16-bit where it fits; 32: 32-bit)
 };
 
 // Validate, orient, match faces, renumber (RCM, grouped by model).
@@ -44,13 +45,32 @@ int build_coeffs(const HostMesh &m, const ep_params *p, Coeffs *c, std::string *
 // Spectral radius estimate of the folded operator by power iteration.
 double power_radius(const HostMesh &m, const Coeffs &c, int iters);
 
-// Sliced-ELL (slices of 32 nodes, column-major inside a slice) layout of the
-// node -> cell table. src[e] indexes HostMesh::n2c (and Coeffs::nw); -1 = pad.
+// Device index layout of a job's step: the sliced-ELL node -> cell table
+// (slices of 32 nodes, column-major inside a slice; src[e] indexes
+// HostMesh::n2c and Coeffs::nw, -1 = pad) and the cells' gather indices
+// (own vertices, the vertex of the neighbour opposite each face, the
+// neighbour across each face; on a boundary face the cell's own vertex 0 and
+// the cell itself). Indices are stored either as 32-bit values or, where the
+// numbering allows (idx16), as 16-bit offsets:
+//   - a cell's 8 node indices relative to nbase[c >> 8] (unsigned; the base is
+//     the smallest node index of the 256-cell run);
+//   - a cell's 4 neighbours relative to the cell itself (signed);
+//   - the ELL entries of a slice relative to cbase[slice] (unsigned).
 struct Sell {
     std::vector<int64_t> slice_ptr;   // [n_slices + 1] entry offsets
     std::vector<int32_t> col;         // cell index per entry (pads repeat a valid cell)
     std::vector<int64_t> src;
+    bool idx16 = false;
+    std::vector<uint16_t> col16;      // [entries] ELL offsets from cbase
+    std::vector<int32_t> cbase;       // [n_slices]
+    std::vector<uint16_t> cidx16;     // [8 n_cells] na then nb offsets from nbase
+    std::vector<int16_t> nbr16;       // [4 n_cells] neighbour offsets from the cell
+    std::vector<int32_t> nbase;       // [(n_cells + 255) / 256]
 };
 void build_sell(const HostMesh &m, Sell *s);
+
+// The 32-bit gather indices of cell c: own vertices, opposite vertices,
+// neighbours (boundary faces: own vertex 0 and the cell itself).
+void cell_gather_indices(const HostMesh &m, int64_t c, int32_t na[4], int32_t nb[4], int32_t nc[4]);
 
 }  // namespace ep

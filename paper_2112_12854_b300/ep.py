@@ -34,7 +34,7 @@ class MeshDesc(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("xyz", ctypes.c_void_p), ("n_cells", ctypes.c_int64),
                 ("tet", ctypes.c_void_p), ("cell_model", ctypes.c_void_p), ("param_set", ctypes.c_void_p),
                 ("stim_mask", ctypes.c_void_p), ("fibre", ctypes.c_void_p), ("n_tris", ctypes.c_int64),
-                ("tri", ctypes.c_void_p)]
+                ("tri", ctypes.c_void_p), ("index_width", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class CellParams(ctypes.Structure):
@@ -85,6 +85,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 
 # every symbol declared in include/ep.h
 NOALLOC_MAX_NODES = 2097152
+NOALLOC_MAX_CELLS = 16777216
 
 EXPORTS = ["ep_context_create", "ep_context_set_stream", "ep_context_destroy", "ep_last_error",
            "ep_mesh_create", "ep_params_set", "ep_step", "ep_read_state", "ep_write_state",
@@ -127,7 +128,7 @@ def load():
         "ep_check_finite": ([_P], ctypes.c_int),
         "ep_clear_error": ([_P], ctypes.c_int),
         "ep_job_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
-                         ctypes.POINTER(_I64)], ctypes.c_int),
+                         ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "ep_estimate_bytes": ([_I64, _I64, ctypes.c_int32], _I64),
         "ep_job_destroy": ([_P], ctypes.c_int),
         "ep_model_nvar": ([ctypes.c_int32], ctypes.c_int32),
@@ -141,7 +142,8 @@ def load():
                           ctypes.c_int),
         "ep_plan_create": ([ctypes.POINTER(MeshDesc), ctypes.POINTER(Params), ctypes.POINTER(_P)], ctypes.c_int),
         "ep_plan_bytes": ([_P], _I64),
-        "ep_plan_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
+        "ep_plan_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int32)],
+                         ctypes.c_int),
         "ep_plan_destroy": ([_P], ctypes.c_int),
         "ep_job_create": ([_P, _P, ctypes.POINTER(_P)], ctypes.c_int),
         "ep_autotune": ([ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32, _P, _P], ctypes.c_int),
@@ -235,9 +237,10 @@ class Context:
         except Exception:
             pass
 
-    def mesh(self, xyz, tets, *, cell_model=None, param_set=None, stim_mask=None, fibre=None, tris=None) -> "Job":
+    def mesh(self, xyz, tets, *, cell_model=None, param_set=None, stim_mask=None, fibre=None, tris=None,
+             index_width=0) -> "Job":
         return Job(self, xyz, tets, cell_model=cell_model, param_set=param_set, stim_mask=stim_mask,
-                   fibre=fibre, tris=tris)
+                   fibre=fibre, tris=tris, index_width=index_width)
 
 
 def make_params(dt, sets, stimuli=(), *, precision=EP_FP32_MIXED, threshold=-20.0,
@@ -263,7 +266,7 @@ def make_params(dt, sets, stimuli=(), *, precision=EP_FP32_MIXED, threshold=-20.
     return p
 
 
-def _mesh_desc(xyz, tets, cell_model=None, param_set=None, stim_mask=None, fibre=None, tris=None):
+def _mesh_desc(xyz, tets, cell_model=None, param_set=None, stim_mask=None, fibre=None, tris=None, index_width=0):
     """ep_mesh_desc of numpy inputs (tets, then the shell triangles `tris`);
     returns (desc, arrays to keep alive)."""
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
@@ -274,6 +277,7 @@ def _mesh_desc(xyz, tets, cell_model=None, param_set=None, stim_mask=None, fibre
     d = MeshDesc()
     d.n_nodes, d.xyz, d.n_cells, d.tet = xyz.shape[0], _ptr(xyz), tets.shape[0], _ptr(tets)
     d.n_tris, d.tri = tris.shape[0], _ptr(tris)
+    d.index_width = int(index_width)
     for name, arr, dt, width in (("cell_model", cell_model, np.uint8, 1), ("param_set", param_set, np.uint8, 1),
                                  ("stim_mask", stim_mask, np.uint8, 1), ("fibre", fibre, np.float64, 3)):
         if arr is None:
@@ -292,9 +296,9 @@ class Plan:
     safe to build in worker threads while the GPU steps other jobs."""
 
     def __init__(self, xyz, tets, params: Params | None = None, *, cell_model=None, param_set=None,
-                 stim_mask=None, fibre=None, tris=None):
+                 stim_mask=None, fibre=None, tris=None, index_width=0):
         L = load()
-        d, keep = _mesh_desc(xyz, tets, cell_model, param_set, stim_mask, fibre, tris)
+        d, keep = _mesh_desc(xyz, tets, cell_model, param_set, stim_mask, fibre, tris, index_width)
         h = _P()
         rc = L.ep_plan_create(ctypes.byref(d), ctypes.byref(params) if params is not None else None,
                               ctypes.byref(h))
@@ -302,9 +306,9 @@ class Plan:
             raise EPError(rc, L.ep_last_error(None).decode())
         self._h = h
         self.params = params
-        a, b = _I64(), _I64()
-        L.ep_plan_info(h, ctypes.byref(a), ctypes.byref(b))
-        self.n_cells, self.n_nodes = int(a.value), int(b.value)
+        a, b, iw = _I64(), _I64(), ctypes.c_int32()
+        L.ep_plan_info(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(iw))
+        self.n_cells, self.n_nodes, self.index_width = int(a.value), int(b.value), int(iw.value)
         self.device_bytes = int(L.ep_plan_bytes(h))
 
     def destroy(self):
@@ -318,7 +322,7 @@ class Plan:
 
 class Job:
     def __init__(self, ctx: Context, xyz=None, tets=None, *, plan: Plan | None = None, cell_model=None,
-                 param_set=None, stim_mask=None, fibre=None, tris=None):
+                 param_set=None, stim_mask=None, fibre=None, tris=None, index_width=0):
         L = load()
         self.ctx = ctx
         h = _P()
@@ -328,7 +332,7 @@ class Job:
             if plan.params is not None:
                 self.params = plan.params
         else:
-            d, keep = _mesh_desc(xyz, tets, cell_model, param_set, stim_mask, fibre, tris)
+            d, keep = _mesh_desc(xyz, tets, cell_model, param_set, stim_mask, fibre, tris, index_width)
             ctx.check(L.ep_mesh_create(ctx._h, ctypes.byref(d), ctypes.byref(h)))
             self.n_cells = int(d.n_cells) + int(d.n_tris)
         self._h = h
@@ -388,10 +392,11 @@ class Job:
         return True
 
     def info(self) -> dict:
-        a, b, c, d = _I64(), _I64(), _I64(), _I64()
+        a, b, c, d, iw = _I64(), _I64(), _I64(), _I64(), ctypes.c_int32()
         self.ctx.check(load().ep_job_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
-                                          ctypes.byref(d)))
-        return dict(n_cells=a.value, n_nodes=b.value, n_interior_faces=c.value, device_bytes=d.value)
+                                          ctypes.byref(d), ctypes.byref(iw)))
+        return dict(n_cells=a.value, n_nodes=b.value, n_interior_faces=c.value, device_bytes=d.value,
+                    index_width=iw.value)
 
     def attach_graph(self, graph, *, node_model=None):
         """Attach a conduction graph (an object like ``workloads.Graph``:
@@ -548,20 +553,23 @@ def case_cell_model(case):
     return np.array([case.param_sets[k].model for k in range(len(case.param_sets))], np.uint8)[case.param_set]
 
 
-def plan_from_case(case, *, precision=EP_FP32_MIXED, integrator=0) -> Plan:
+def plan_from_case(case, *, precision=EP_FP32_MIXED, integrator=0, index_width=0) -> Plan:
     """Host-only plan of a ``workloads.TissueCase`` (mesh + parameters)."""
     params = make_params(case.dt, case.param_sets, case.stimuli, precision=precision, threshold=case.threshold,
                          integrator=integrator)
     return Plan(case.xyz, case.tets, params, cell_model=case_cell_model(case), param_set=case.param_set,
-                stim_mask=case.stim_mask, fibre=case.fibre, tris=getattr(case, "tris", None))
+                stim_mask=case.stim_mask, fibre=case.fibre, tris=getattr(case, "tris", None),
+                index_width=index_width)
 
 
-def job_from_case(ctx: Context, case, *, precision=EP_FP32_MIXED, cell_model=None, integrator=0) -> Job:
+def job_from_case(ctx: Context, case, *, precision=EP_FP32_MIXED, cell_model=None, integrator=0,
+                  index_width=0) -> Job:
     """Create a job from a ``workloads.TissueCase`` and set its parameters."""
     if cell_model is None:
         cell_model = case_cell_model(case)
     j = ctx.mesh(case.xyz, case.tets, cell_model=cell_model, param_set=case.param_set,
-                 stim_mask=case.stim_mask, fibre=case.fibre, tris=getattr(case, "tris", None))
+                 stim_mask=case.stim_mask, fibre=case.fibre, tris=getattr(case, "tris", None),
+                 index_width=index_width)
     j.set_params(make_params(case.dt, case.param_sets, case.stimuli, precision=precision,
                              threshold=case.threshold, integrator=integrator))
     return j

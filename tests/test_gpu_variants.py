@@ -79,7 +79,8 @@ def test_variants_bitwise_on_mixed_models_and_graph(pname):
     ref = None
     for v in range(ep.N_CELL_VARIANTS):
         ep.set_cell_variant(ctx, prec, v)
-        j = ep.job_from_case(ctx, case, precision=prec)
+        # 32-bit indices: the staged variants (6, 7) run only on those
+        j = ep.job_from_case(ctx, case, precision=prec, index_width=32)
         j.attach_graph(g, node_model=np.full(30, 2, np.uint8))
         j.step(150)
         state = [j.read(k, model=m) for m in range(3) for k in range(len(ep.model_varnames(m)))]
@@ -94,4 +95,67 @@ def test_variants_bitwise_on_mixed_models_and_graph(pname):
                     assert np.allclose(a, b, rtol=1e-5, atol=1e-4, equal_nan=True), v
         assert j.check_finite()
         j.destroy()
+    ctx.close()
+
+
+def _three_model_case():
+    xyz, tets = w.kuhn_box(13, 7, 3, 0.25)
+    c = w.tet_centroids(xyz, tets)
+    model = np.where(c[:, 0] < 1.1, 0, np.where(c[:, 0] < 2.2, 1, 2)).astype(np.uint8)
+    sets = [w.ParamSet(model=0, variant=2), w.ParamSet(model=1), w.ParamSet(model=2)]
+    stim = ((c[:, 0] < 0.5).astype(np.uint8) | ((c[:, 0] > 2.9).astype(np.uint8) << 1))
+    return w.TissueCase("mix", xyz, tets, w.fibres_transmural(c[:, 2], 0.0, 0.75), model, stim, sets,
+                        [w.Stimulus(-52.0, 0.0, 1.0), w.Stimulus(-40.0, 5.0, 2.0)], 0.01, 0, -10.0)
+
+
+def _state(j):
+    from paper_2112_12854_b300 import ep
+    st = [j.read(k, model=m) for m in range(3) for k in range(len(ep.model_varnames(m)))]
+    return st + [j.activation_times()]
+
+
+@pytest.mark.parametrize("pname", ["mixed", "plain"])
+def test_index_widths_bitwise_identical(pname):
+    """The gather indices stored as 16-bit offsets (the default where they
+    fit) and as 32-bit indices (ep_mesh_desc.index_width = 32) give bitwise
+    the same state, each alone and the two batched together (TP06 /
+    Courtemanche / Stewart regions, two stimuli, 1638 cells: several tiles,
+    ragged tails)."""
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2112_12854_b300 import ep
+    prec = ep.EP_FP32_MIXED if pname == "mixed" else ep.EP_FP64_PLAIN
+    case = _three_model_case()
+    ctx = ep.Context()
+    a16 = ep.job_from_case(ctx, case, precision=prec)
+    a32 = ep.job_from_case(ctx, case, precision=prec, index_width=32)
+    b16 = ep.job_from_case(ctx, case, precision=prec)
+    b32 = ep.job_from_case(ctx, case, precision=prec, index_width=32)
+    assert a16.info()["index_width"] == 16 and a32.info()["index_width"] == 32
+    assert a16.info()["device_bytes"] < a32.info()["device_bytes"]
+    a16.step(300)
+    a32.step(300)
+    ep.step([b16, b32], 300)
+    ref = _state(a32)
+    for j in (a16, b16, b32):
+        for x, y in zip(_state(j), ref):
+            assert np.array_equal(x, y, equal_nan=True)
+    assert np.isfinite(ref[-1]).any()
+    ctx.close()
+
+
+def test_index_widths_bitwise_identical_bidomain():
+    """The bidomain solve (node passes and fluxes of the elliptic operator)
+    reads the same 16-bit or 32-bit indices: V and v_e agree bitwise."""
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2112_12854_b300 import ep
+    case = w.slab_case(nx=12, ny=8, nz=3, h=0.25)
+    ctx = ep.Context()
+    jobs = [ep.job_from_case(ctx, case, index_width=iw) for iw in (0, 32)]
+    for j in jobs:
+        j.enable_bidomain(0.62 / 1.4, 0.24 / 1.4)
+        j.step(80)
+    assert np.array_equal(jobs[0].V, jobs[1].V)
+    assert np.array_equal(jobs[0].ve, jobs[1].ve)
     ctx.close()

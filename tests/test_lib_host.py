@@ -236,3 +236,45 @@ def test_folded_operator_on_shell_triangles_equals_oracle():
         for k in range(4):
             if nbr[c, k] >= 0:
                 assert is_tri[nbr[c, k]] == is_tri[c]
+
+
+def _coned_sphere(levels):
+    """Tets coning every triangle of a subdivided octahedron to the centre:
+    one node shared by every cell (its node -> cell entries span the whole
+    numbering), neighbours only across the cone sides."""
+    v = [np.array(p, float) for p in ([1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1])]
+    tris = [(0, 2, 4), (2, 1, 4), (1, 3, 4), (3, 0, 4), (2, 0, 5), (1, 2, 5), (3, 1, 5), (0, 3, 5)]
+    for _ in range(levels):
+        mid, new = {}, []
+
+        def m(a, b):
+            k = (min(a, b), max(a, b))
+            if k not in mid:
+                p = v[a] + v[b]
+                v.append(p / np.linalg.norm(p))
+                mid[k] = len(v) - 1
+            return mid[k]
+        for a, b, c in tris:
+            ab, bc, ca = m(a, b), m(b, c), m(c, a)
+            new += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        tris = new
+    xyz = np.vstack(v + [np.zeros(3)]) * 5.0
+    tets = np.array([(a, b, c, len(v)) for a, b, c in tris], np.int32)
+    return xyz, tets
+
+
+def test_index_width_chosen_by_the_numbering():
+    """16-bit gather indices where every offset fits (a slab), 32-bit where
+    they cannot (a node shared by 131072 cells), and 32-bit on request."""
+    params = ep.make_params(0.01, [w.ParamSet()])
+    case = w.slab_case(nx=20, ny=10, nz=4, h=0.5)
+    assert ep.Plan(case.xyz, case.tets, params).index_width == 16
+    assert ep.Plan(case.xyz, case.tets, params, index_width=32).index_width == 32
+    xyz, tets = _coned_sphere(7)            # (no parameters: only the mesh is planned)
+    assert tets.shape[0] == 131072
+    assert ep.Plan(xyz, tets).index_width == 32
+    xyz, tets = _coned_sphere(5)
+    assert ep.Plan(xyz, tets).index_width == 16
+    with pytest.raises(ep.EPError) as e:
+        ep.Plan(case.xyz, case.tets, params, index_width=16)
+    assert e.value.code == ep.EP_EINVAL
