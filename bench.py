@@ -492,14 +492,15 @@ def main():
     iw = info["index_width"]
     cell_b = cell_bytes(iw)
     cell_gbs = cell_b * N / (cell_ms * 1e-3) / 1e9
-    node_bytes = node_bytes_per_incidence(iw) * incid + 4.0 * info["n_nodes"]
+    niw = info["node_index_width"]
+    node_bytes = node_bytes_per_incidence(niw) * incid + 4.0 * info["n_nodes"]
     traffic = traffic_from_profile(N)
     step_s = ms / args.steps * 1e-3
     roofline = {"bound": "hbm", "kernel": "cell_kernel<float>", "achieved": cell_gbs, "peak": peak,
                 "unit": "GB/s", "frac": cell_gbs / peak, "traffic": traffic,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy)" if peak_kind == "measured"
                 else "fallback 6.4 TB/s",
-                "algorithmic_bytes_per_cell": cell_b, "index_width": iw,
+                "algorithmic_bytes_per_cell": cell_b, "index_width": iw, "node_index_width": niw,
                 "cell_kernel_ms": cell_ms, "node_kernel_ms": node_ms,
                 "cell_variant": int(chosen[0]), "autotune_ms": None if variant_ms is None else [round(float(x), 4) for x in variant_ms[0]],
                 "node_kernel_gbs": node_bytes / (node_ms * 1e-3) / 1e9,

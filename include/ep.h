@@ -119,12 +119,15 @@ typedef void (*ep_free_fn)(void *ptr, size_t bytes, void *user);
  * conductivity acts in its plane), or NULL for isotropic tissue with
  * diffusivity D_l. index_width: 0 (the default) stores the step's gather
  * indices as 16-bit offsets where the library's cell and node numbering
- * allows it (a cell's neighbours within 32767 cells of it, the nodes of
- * each run of 256 cells and the cells of each run of 32 nodes within a
- * window of 65536: true of any mesh whose reverse Cuthill-McKee bandwidth is
- * below about 10^4 cells), else as 32-bit indices; 32 always stores 32-bit
- * indices. Both give bitwise identical results; the 16-bit form moves 32
- * fewer bytes per cell and step. */
+ * allows it, else as 32-bit indices -- the cells' indices (a cell's
+ * neighbours within 32767 cells of it and the nodes of each run of 256
+ * cells within a window of 65536: meshes whose reverse Cuthill-McKee
+ * bandwidth is below about 3 x 10^4 cells, e.g. the 9.6M-cell wedge) and
+ * the node -> cell entries (the cells of each run of 32 nodes within a
+ * window of 65536, which spans about six RCM levels: smaller meshes)
+ * independently; 32 always stores 32-bit indices. Both forms give bitwise
+ * identical results; the 16-bit forms move 24 fewer bytes per cell and 2 per
+ * node -> cell entry and step. */
 typedef struct {
     int64_t n_nodes;
     const double *xyz;
@@ -230,9 +233,11 @@ int ep_params_set(ep_job *job, const ep_params *params);
  * (the job keeps the host mesh it shares with the plan). */
 int ep_plan_create(const ep_mesh_desc *desc, const ep_params *params, ep_plan **out);
 int64_t ep_plan_bytes(const ep_plan *plan);
-/* ep_plan_info: cells, nodes, and the width (16 or 32 bits) the job's gather
- * indices will be stored with (ep_mesh_desc.index_width). */
-int ep_plan_info(const ep_plan *plan, int64_t *n_cells, int64_t *n_nodes, int32_t *index_width);
+/* ep_plan_info: cells, nodes, and the widths (16 or 32 bits) the job's
+ * cell gather indices and node -> cell entries will be stored with
+ * (ep_mesh_desc.index_width). */
+int ep_plan_info(const ep_plan *plan, int64_t *n_cells, int64_t *n_nodes, int32_t *index_width,
+                 int32_t *node_index_width);
 int ep_plan_destroy(ep_plan *plan);
 int ep_job_create(ep_context *ctx, const ep_plan *plan, ep_job **out);
 
@@ -285,9 +290,11 @@ int ep_check_finite(ep_job *job);
 int ep_clear_error(ep_context *ctx);
 
 /* Job information: cells, nodes, interior faces, device bytes held, and
- * the width (16 or 32 bits) of its stored gather indices. */
+ * the widths (16 or 32 bits) of its stored cell gather indices and node ->
+ * cell entries (the node-value pass's table). */
 int ep_job_info(const ep_job *job, int64_t *n_cells, int64_t *n_nodes,
-                int64_t *n_interior_faces, int64_t *device_bytes, int32_t *index_width);
+                int64_t *n_interior_faces, int64_t *device_bytes, int32_t *index_width,
+                int32_t *node_index_width);
 
 /* Device bytes a job of this size would hold (planner estimate used for
  * admission by free memory). */
@@ -304,21 +311,28 @@ int ep_job_destroy(ep_job *job);
  * Synchronises. The results equal those of ep_step. */
 int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double *node_ms, double *cell_ms);
 
-/* Autotuner of the cell kernel's launch shape. Variants 0-5: threads per
- * block and resident blocks per SM of the plain kernel; variants 6 and 7:
- * the staged FP32 kernel, whose streamed inputs are brought into shared
- * memory by bulk asynchronous copies, double-buffered (6: all of them, two
- * blocks per SM; 7: indices, coefficients, V and bytes, three blocks per
- * SM); FP64 and AB2 batches run variant 0 for them. Advances the jobs by
- * 8 * steps_per_variant real time steps, timing the cell launch of each
- * variant with CUDA events, and keeps the fastest variant per precision for
- * every later ep_step of the context. The variants compute the same
- * arithmetic; TP06 and Stewart cells agree bitwise across all of them,
- * Courtemanche cells can differ in the last bits between the
- * register-limited shapes and the others. chosen[2] (may be NULL) receives
- * the variant picked for EP_FP32_MIXED and EP_FP64_PLAIN (-1 if no job of
- * that precision); variant_ms[2 * 8] (may be NULL) the mean cell-kernel time
- * per variant. Synchronises. */
+/* Autotuner of the step's launch shape. Variants 0-5: threads per block and
+ * resident blocks per SM of the cell kernel, after its own node-value
+ * launch; variants 6 and 7: the staged FP32 cell kernel, whose streamed
+ * inputs are brought into shared memory by bulk asynchronous copies,
+ * double-buffered (6: all of them, two blocks per SM; 7: indices,
+ * coefficients, V and bytes, three blocks per SM), for jobs with 32-bit
+ * gather indices (FP64, AB2 and 16-bit-index batches run variant 0 for
+ * them); variants 8 and 9: the fused step, node values and cell update of
+ * every job in ONE persistent launch (128 threads x 6 blocks per SM, 256 x
+ * 3), node tiles and cell tiles taken in dependency order with bounded
+ * waits on per-tile ready flags (a wait that gives up sets the context's
+ * error word, reported as EP_ETIMEOUT by ep_step and ep_check_finite).
+ * Advances the jobs by 10 * steps_per_variant real time steps, timing each
+ * variant's whole step (node values, conduction graphs, cell update) with
+ * CUDA events, and keeps the fastest variant per precision for every later
+ * ep_step of the context. The variants compute the same arithmetic; TP06
+ * and Stewart cells agree bitwise across all of them, Courtemanche cells can
+ * differ in the last bits between the register-limited shapes and the
+ * others. chosen[2] (may be NULL) receives the variant picked for
+ * EP_FP32_MIXED and EP_FP64_PLAIN (-1 if no job of that precision);
+ * variant_ms[2 * 10] (may be NULL) the mean step time per variant.
+ * Synchronises. */
 int ep_autotune(ep_job *const *jobs, int32_t n_jobs, int32_t steps_per_variant, int32_t *chosen,
                 double *variant_ms);
 
@@ -333,7 +347,8 @@ int ep_autotune(ep_job *const *jobs, int32_t n_jobs, int32_t steps_per_variant, 
  * synchronises. */
 int ep_alu_peaks(ep_context *ctx, double *out);
 
-/* Force the cell kernel's launch-shape variant (0..7) for one precision. */
+/* Force the step's launch-shape variant (0..9, see ep_autotune) for one
+ * precision. */
 int ep_set_cell_variant(ep_context *ctx, int32_t precision, int32_t variant);
 
 /* Host-only inspection of the planner (no device work, no GPU needed): run

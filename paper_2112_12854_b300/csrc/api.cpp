@@ -43,7 +43,7 @@ struct Plan {
     struct Group {
         int precision;
         int n_jobs;
-        DevBuf jobtab, node_tiles, cell_tiles, done, graph_tiles;
+        DevBuf jobtab, node_tiles, cell_tiles, done, graph_tiles, work;
         StepLaunch L;
     };
     std::vector<Group> groups;
@@ -101,6 +101,7 @@ struct ep_job {
     std::vector<DevBuf> topo;     // precision-independent device arrays
     std::vector<DevBuf> prec;     // precision-dependent device arrays
     std::vector<Tile> cell_tiles, node_tiles;
+    std::vector<int2> cell_deps;  // per cell tile: the node tiles (node >> 8) its gathers read, [x, y]
     int64_t device_bytes = 0;
     // conduction graph (ep_graph_attach)
     std::unique_ptr<GraphPlan> gp;
@@ -184,6 +185,7 @@ void free_plan(ep_context *ctx, Plan *p) {
         dfree(ctx, &g.cell_tiles);
         dfree(ctx, &g.done);
         dfree(ctx, &g.graph_tiles);
+        dfree(ctx, &g.work);
     }
 }
 
@@ -216,6 +218,33 @@ void build_tiles(ep_job *j) {
             j->cell_tiles.push_back(Tile{0, m, int(s), int(std::min<int64_t>(kCellThreads, j->mesh().model_off[m + 1] - s))});
     for (int64_t s = 0; s < j->mesh().n_nodes; s += kNodeThreads)
         j->node_tiles.push_back(Tile{0, 0, int(s), int(std::min<int64_t>(kNodeThreads, j->mesh().n_nodes - s))});
+    j->cell_deps.clear();
+    for (const Tile &t : j->cell_tiles) {
+        int32_t lo = INT32_MAX, hi = 0, na[4], nb[4], nc[4];
+        for (int64_t c = t.start; c < t.start + t.count; ++c) {
+            cell_gather_indices(j->mesh(), c, na, nb, nc);
+            for (int k = 0; k < 4; ++k) lo = std::min({lo, na[k], nb[k]}), hi = std::max({hi, na[k], nb[k]});
+        }
+        j->cell_deps.push_back(make_int2(lo / kNodeThreads, hi / kNodeThreads));
+    }
+}
+
+// Work list of the fused step for one job whose tiles sit at node_off / cell_off
+// in the launch's tile tables: every cell tile is preceded by the node tiles its
+// gathers read -- node tiles are queued in increasing order up to the largest
+// one needed by the next kFusedLookahead cell tiles -- so a cell tile only ever
+// waits for node tiles claimed before it.
+void append_work(const ep_job *j, int node_off, int cell_off, std::vector<Work> *w) {
+    const int nct = int(j->cell_tiles.size()), nnt = int(j->node_tiles.size());
+    std::vector<int> pmax(nct);
+    for (int t = 0; t < nct; ++t) pmax[t] = std::max(t ? pmax[t - 1] : 0, j->cell_deps[t].y);
+    int next = 0;
+    for (int t = 0; t < nct; ++t) {
+        const int need = pmax[std::min(nct - 1, t + kFusedLookahead)];
+        for (; next <= need && next < nnt; ++next) w->push_back(Work{-1 - (node_off + next), 0, 0, 0});
+        w->push_back(Work{cell_off + t, j->cell_deps[t].x, j->cell_deps[t].y, 0});
+    }
+    for (; next < nnt; ++next) w->push_back(Work{-1 - (node_off + next), 0, 0, 0});
 }
 
 }  // namespace
@@ -385,6 +414,16 @@ int job_upload_topology(ep_context *ctx, ep_job *j) {
     void *p;
     int rc;
     j->dj.idx16 = sl.idx16 ? 1 : 0;
+    j->dj.col16 = sl.col16ok ? 1 : 0;
+    if (sl.col16ok) {
+        if ((rc = upload(ctx, sl.col16, &j->topo, &p))) return rc;
+        j->dj.ncol16 = static_cast<const unsigned short *>(p);
+        if ((rc = upload(ctx, sl.cbase, &j->topo, &p))) return rc;
+        j->dj.cbase = static_cast<const int *>(p);
+    } else {
+        if ((rc = upload(ctx, sl.col, &j->topo, &p))) return rc;
+        j->dj.ncol = static_cast<const int *>(p);
+    }
     if (sl.idx16) {
         // 16-bit gather indices (offsets; see Sell)
         if ((rc = upload(ctx, sl.cidx16, &j->topo, &p))) return rc;
@@ -393,10 +432,6 @@ int job_upload_topology(ep_context *ctx, ep_job *j) {
         j->dj.nbr16 = static_cast<const uint2 *>(p);
         if ((rc = upload(ctx, sl.nbase, &j->topo, &p))) return rc;
         j->dj.nbase = static_cast<const int *>(p);
-        if ((rc = upload(ctx, sl.col16, &j->topo, &p))) return rc;
-        j->dj.ncol16 = static_cast<const unsigned short *>(p);
-        if ((rc = upload(ctx, sl.cbase, &j->topo, &p))) return rc;
-        j->dj.cbase = static_cast<const int *>(p);
     } else {
         std::vector<int4> na(N), nb(N), nc(N);
         for (int64_t c = 0; c < N; ++c) {
@@ -412,8 +447,6 @@ int job_upload_topology(ep_context *ctx, ep_job *j) {
         j->dj.nodes_b = static_cast<const int4 *>(p);
         if ((rc = upload(ctx, nc, &j->topo, &p))) return rc;
         j->dj.nbr = static_cast<const int4 *>(p);
-        if ((rc = upload(ctx, sl.col, &j->topo, &p))) return rc;
-        j->dj.ncol = static_cast<const int *>(p);
     }
     if ((rc = upload(ctx, m.pset, &j->topo, &p))) return rc;
     j->dj.pset = static_cast<const uint8_t *>(p);
@@ -425,10 +458,17 @@ int job_upload_topology(ep_context *ctx, ep_job *j) {
     if ((rc = upload(ctx, m.cell_new2old, &j->topo, &p))) return rc;
     j->perm_dev = static_cast<const int *>(p);
     DevBuf b;
-    if ((rc = dalloc(ctx, sizeof(long long), &b))) return rc;
+    // the step counter, and beside it the fused launches' counter (tags of the node-tile flags)
+    if ((rc = dalloc(ctx, 2 * sizeof(long long), &b))) return rc;
     j->step_dev = b;
-    cudaError_t e = cudaMemsetAsync(b.p, 0, sizeof(long long), ctx->upload);
+    cudaError_t e = cudaMemsetAsync(b.p, 0, 2 * sizeof(long long), ctx->upload);
     j->dj.step = static_cast<long long *>(b.p);
+    j->dj.gen = reinterpret_cast<unsigned *>(static_cast<long long *>(b.p) + 1);
+    const int64_t n_node_tiles = (m.n_nodes + kNodeThreads - 1) / kNodeThreads;
+    if ((rc = dalloc(ctx, size_t(n_node_tiles) * sizeof(unsigned), &b))) return rc;
+    j->topo.push_back(b);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.p, 0, size_t(n_node_tiles) * sizeof(unsigned), ctx->upload);
+    j->dj.ntflag = static_cast<unsigned *>(b.p);
     if ((rc = dalloc(ctx, sizeof(DevJob), &b))) return rc;
     j->dj_dev = b;
     j->dj.n_cells = N;
@@ -570,9 +610,10 @@ int64_t job_bytes(const HostMesh &m, const Sell &sl, int precision, int integrat
     auto rnd = [](int64_t b) { return std::max<int64_t>(b, 256); };
     const int64_t N = m.n_cells, r = precision == EP_FP64_PLAIN ? 8 : 4, E = int64_t(sl.col.size());
     const int64_t ns = int64_t(sl.slice_ptr.size()) - 1;
-    int64_t b = 2 * rnd(N) + rnd(8 * int64_t(sl.slice_ptr.size())) + rnd(4 * N) + 256 + rnd(sizeof(DevJob));
-    b += sl.idx16 ? rnd(16 * N) + rnd(8 * N) + rnd(4 * ((N + 255) / 256)) + rnd(2 * E) + rnd(4 * ns)
-                  : 3 * rnd(16 * N) + rnd(4 * E);
+    int64_t b = 2 * rnd(N) + rnd(8 * int64_t(sl.slice_ptr.size())) + rnd(4 * N) + 256 + rnd(sizeof(DevJob)) +
+                rnd(4 * ((m.n_nodes + kNodeThreads - 1) / kNodeThreads));
+    b += sl.idx16 ? rnd(16 * N) + rnd(8 * N) + rnd(4 * ((N + 255) / 256)) : 3 * rnd(16 * N);
+    b += sl.col16ok ? rnd(2 * E) + rnd(4 * ns) : rnd(4 * E);
     b += 3 * rnd(4 * r * N) + rnd(r * E) + 3 * rnd(r * N) + rnd(r * m.n_nodes);
     for (int md = 0; md < EP_N_MODELS; ++md) {
         const int64_t n = m.model_off[md + 1] - m.model_off[md];
@@ -946,11 +987,13 @@ int64_t ep_plan_bytes(const ep_plan *plan) {
                      plan->has_params ? plan->params.integrator : EP_INTEGRATOR_FE);
 }
 
-int ep_plan_info(const ep_plan *plan, int64_t *n_cells, int64_t *n_nodes, int32_t *index_width) {
+int ep_plan_info(const ep_plan *plan, int64_t *n_cells, int64_t *n_nodes, int32_t *index_width,
+                 int32_t *node_index_width) {
     if (!plan) return EP_EINVAL;
     if (n_cells) *n_cells = plan->mesh->n_cells;
     if (n_nodes) *n_nodes = plan->mesh->n_nodes;
     if (index_width) *index_width = plan->sell->idx16 ? 16 : 32;
+    if (node_index_width) *node_index_width = plan->sell->col16ok ? 16 : 32;
     return EP_OK;
 }
 
@@ -990,11 +1033,13 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
     for (int prec : {EP_FP32_MIXED, EP_FP64_PLAIN}) {
         std::vector<DevJob> tab;
         std::vector<Tile> nt, ct, gt;
+        std::vector<Work> wk;
         int max_sub = 0, any_bido = 0, any_ab2 = 0, any_idx16 = 0;
         for (int i = 0; i < n; ++i) {
             if (jobs[i]->precision != prec) continue;
             const int jid = int(tab.size());
             tab.push_back(jobs[i]->dj);
+            append_work(jobs[i], int(nt.size()), int(ct.size()), &wk);
             for (Tile t : jobs[i]->node_tiles) nt.push_back(Tile{jid, t.model, t.start, t.count});
             for (Tile t : jobs[i]->cell_tiles) ct.push_back(Tile{jid, t.model, t.start, t.count});
             if (jobs[i]->params.integrator == EP_INTEGRATOR_AB2) any_ab2 = 1;
@@ -1021,8 +1066,14 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
         g.node_tiles = tmp.back();
         if ((rc = upload(ctx, ct, &tmp, &p))) return rc;
         g.cell_tiles = tmp.back();
-        if ((rc = dalloc(ctx, sizeof(unsigned), &g.done))) return rc;
-        cudaMemsetAsync(g.done.p, 0, sizeof(unsigned), ctx->upload);
+        if ((rc = upload(ctx, wk, &tmp, &p))) return rc;
+        g.work = tmp.back();
+        // [0] the cell launch's ticket, [1] the fused launch's work counter
+        if ((rc = dalloc(ctx, 2 * sizeof(unsigned), &g.done))) return rc;
+        cudaMemsetAsync(g.done.p, 0, 2 * sizeof(unsigned), ctx->upload);
+        g.L.work = static_cast<const Work *>(g.work.p);
+        g.L.n_work = int(wk.size());
+        g.L.head = static_cast<unsigned *>(g.done.p) + 1;
         g.L.jobs = static_cast<const DevJob *>(g.jobtab.p);
         g.L.n_jobs = g.n_jobs;
         g.L.node_tiles = static_cast<const Tile *>(g.node_tiles.p);
@@ -1121,14 +1172,15 @@ int ep_step(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps) {
     // a staged cell kernel of an earlier call gave up waiting for its copies (the word is
     // read back asynchronously after each call that ran one)
     if (*ctx->err_host)
-        return fail(ctx, EP_ETIMEOUT, "ep_step: an earlier step's bounded wait gave up; the state of the jobs "
-                                      "stepped since is undefined (restore a checkpoint, then ep_clear_error)");
+        return fail(ctx, EP_ETIMEOUT, "ep_step: an earlier step's bounded wait gave up (staged copies or fused "
+                                      "node tiles); the state of the jobs stepped since is undefined (restore a "
+                                      "checkpoint, then ep_clear_error)");
     if (n_steps == 0) return EP_OK;
     DeviceGuard g(ctx->device);
     try {
         Plan *pl = nullptr;
         if ((rc = get_plan(ctx, jobs, n_jobs, &pl))) return rc;
-        bool staged = false;
+        bool staged = false;   // staged or fused: kernels with bounded waits that report through the error word
         for (auto &gr : pl->groups) staged = staged || gr.L.cell_variant >= kStagedVariant;
         int64_t left = n_steps;
         if (n_steps >= kGraphMinSteps && pl->bido.empty()) {   // cooperative solves launch directly
@@ -1300,9 +1352,10 @@ int ep_autotune(ep_job *const *jobs, int32_t n_jobs, int32_t steps_per_variant, 
                     // every group of the plan advances together, so all jobs stay in step
                     for (auto &other : pl->groups) {
                         if (&other == &gr) {
-                            e = launch_node(gr.precision, gr.L, ctx->stream);
+                            // the whole step: the fused variants do the node values in their one launch
+                            e = cudaEventRecord(e0, ctx->stream);
+                            if (e == cudaSuccess) e = launch_node(gr.precision, gr.L, ctx->stream);
                             if (e == cudaSuccess) e = launch_graph(gr.precision, gr.L, ctx->stream);
-                            if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
                             if (e == cudaSuccess) e = launch_cell(gr.precision, gr.L, ctx->stream);
                             if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
                             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -1464,16 +1517,18 @@ int ep_check_finite(ep_job *job) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ep_check_finite");
     if (werr) {
         *ctx->err_host = werr;
-        return fail(ctx, EP_ETIMEOUT, "a step kernel's wait for its staged copies hit its time limit");
+        return fail(ctx, EP_ETIMEOUT, (werr & 1u) ? "a step kernel's wait for its staged copies hit its time limit"
+                                                  : "a fused step's wait for its node tiles hit its time limit");
     }
     if (cnt) return fail(ctx, EP_ENONFINITE, std::to_string(cnt) + " non-finite state values");
     return EP_OK;
 }
 
 int ep_job_info(const ep_job *job, int64_t *n_cells, int64_t *n_nodes, int64_t *n_interior_faces,
-                int64_t *device_bytes, int32_t *index_width) {
+                int64_t *device_bytes, int32_t *index_width, int32_t *node_index_width) {
     if (!job) return EP_EINVAL;
     if (index_width) *index_width = job->sell().idx16 ? 16 : 32;
+    if (node_index_width) *node_index_width = job->sell().col16ok ? 16 : 32;
     if (n_cells) *n_cells = job->mesh().n_cells;
     if (n_nodes) *n_nodes = job->mesh().n_nodes;
     if (n_interior_faces) *n_interior_faces = job->mesh().n_interior_faces;
@@ -1567,9 +1622,12 @@ int ep_step_noalloc(ep_job *job, int64_t n_steps) {
         return fail(ctx, EP_ETIMEOUT, "ep_step_noalloc: an earlier step's bounded wait gave up (ep_clear_error)");
     if (n_steps == 0) return EP_OK;
     DeviceGuard g(ctx->device);
+    std::vector<Work> wk;
+    const int variant = ctx->cell_variant[job->precision];
+    if (variant >= kFusedVariant) append_work(job, 0, 0, &wk);
     cudaError_t e = launch_step_noalloc(job->precision, job->dj, job->node_tiles.data(), int(job->node_tiles.size()),
-                                        job->cell_tiles.data(), int(job->cell_tiles.size()),
-                                        ctx->cell_variant[job->precision], ctx->sm_count,
+                                        job->cell_tiles.data(), int(job->cell_tiles.size()), wk.data(),
+                                        int(wk.size()), variant, ctx->sm_count,
                                         static_cast<unsigned *>(ctx->err_word.p), n_steps, ctx->stream);
     return e == cudaSuccess ? EP_OK : cuda_fail(ctx, e, "ep_step_noalloc");
 }

@@ -67,20 +67,18 @@ struct DevGraph {
 };
 
 struct DevJob {
-    // Gather indices of the step, in one of two forms (idx16 selects):
-    // 32-bit --
+    // Gather indices of the step: the cells' (idx16 selects the form) and the
+    // node -> cell entries (col16 selects), each as 32-bit indices or 16-bit offsets.
     const int4 *nodes_a;      // the cell's 4 vertices
     const int4 *nodes_b;      // vertex of the neighbour opposite each face (own vertex 0 on the boundary)
     const int4 *nbr;          // neighbour across each face (the cell itself on the boundary)
-    const int *ncol;          // sliced-ELL node -> cell entries
-    // 16-bit offsets --
     const uint4 *cidx16;      // per cell 8 x u16: nodes_a then nodes_b, from nbase[c >> 8]
     const uint2 *nbr16;       // per cell 4 x s16: nbr relative to the cell
     const int *nbase;         // per run of 256 cells
-    const unsigned short *ncol16;  // ELL entries relative to cbase[slice]
+    const int *ncol;          // sliced-ELL node -> cell entries
+    const unsigned short *ncol16;  // the same relative to cbase[slice]
     const int *cbase;         // per slice of 32 nodes
-    int idx16;
-    int pad3;
+    int idx16, col16;
     const void *wa, *wb, *q;  // float4 or double4 per cell (folded Eqs. 7-8 coefficients / V_c)
     const uint8_t *pset;
     const uint8_t *smask;
@@ -98,6 +96,8 @@ struct DevJob {
     double dt, threshold;
     float dt_f, threshold_f;
     long long *step;          // steps taken (device counter)
+    unsigned *gen;            // fused launches taken (device counter; tags the node tiles' ready flags)
+    unsigned *ntflag;         // per node tile of 256 nodes: gen + 1 of the fused launch that wrote it
     DevGraph g;
     const void *xdiv;         // bidomain: intracellular flux of v_e, added to the diffusion term (else NULL)
     int integrator;           // EP_INTEGRATOR_FE or EP_INTEGRATOR_AB2 (non-gating variables)
@@ -111,6 +111,16 @@ struct Tile {
     int model;
     int start;
     int count;
+};
+
+// Work item of the fused step kernel: a node tile (tile < 0: node tile
+// -1 - tile of the launch's node tiles) or a cell tile (tile >= 0) with the
+// range [dep_lo, dep_hi] of its job's node tiles (local indices, node >> 8)
+// whose values it gathers.
+struct Work {
+    int tile;
+    int dep_lo, dep_hi;
+    int pad;
 };
 
 constexpr int kCellThreads = 256;

@@ -141,24 +141,35 @@ __device__ __forceinline__ CellSrc<R> global_src(const DevJob &J, int model, lon
                       region_io<R>(rg, c - rg.off)};
 }
 
+// Node value k for the cell update: through L1 when the node values were
+// written by an earlier launch; from L2 (ld.global.cg) in the fused kernel,
+// where other blocks of the same launch write them.
+template <class R, bool CG>
+__device__ __forceinline__ R node_at(const R *vn, int k) {
+    if constexpr (CG) return __ldcg(vn + k);
+    else return vn[k];
+}
+
 // XD: the batch holds bidomain jobs, whose cells add L_i(v_e^n) (first line
 // of Eq. 6) to the diffusion term; AB2: the batch holds jobs that advance the
 // non-gating variables by second-order Adams-Bashforth. Batches without them
-// compile without the code.
-template <class R, bool XD = false, bool AB2 = false>
+// compile without the code. CG: the node values come from the same launch.
+template <class R, bool XD = false, bool AB2 = false, bool CG = false>
 __device__ __forceinline__ void cell_update_from(const DevJob &J, int model, long long c, long long n, const R *V,
                                                  const CellSrc<R> &src) {
     using R4 = typename Vec4T<R>::type;
     R *__restrict__ Vnext = static_cast<R *>(J.V[(n & 1) ^ 1]);
-    const R *__restrict__ vn = static_cast<const R *>(J.vn);
+    const R *vn = static_cast<const R *>(J.vn);
     const int4 na = src.na, nb = src.nb, nc = src.nc;
     const R4 wa = *src.wa;
     const R4 wb = *src.wb;
     const R4 q = *src.q;
     const R Vc = *src.Vc;
     // diffusion term of Eq. 7 (S2 + S3 folded): eight node values, four neighbours
-    R diff = wa.x * vn[na.x] + wa.y * vn[na.y] + wa.z * vn[na.z] + wa.w * vn[na.w];
-    diff += wb.x * vn[nb.x] + wb.y * vn[nb.y] + wb.z * vn[nb.z] + wb.w * vn[nb.w];
+    R diff = wa.x * node_at<R, CG>(vn, na.x) + wa.y * node_at<R, CG>(vn, na.y) + wa.z * node_at<R, CG>(vn, na.z) +
+             wa.w * node_at<R, CG>(vn, na.w);
+    diff += wb.x * node_at<R, CG>(vn, nb.x) + wb.y * node_at<R, CG>(vn, nb.y) + wb.z * node_at<R, CG>(vn, nb.z) +
+            wb.w * node_at<R, CG>(vn, nb.w);
     diff += q.x * (V[nc.x] - Vc) + q.y * (V[nc.y] - Vc) + q.z * (V[nc.z] - Vc) + q.w * (V[nc.w] - Vc);
     if (XD && J.xdiv) diff += static_cast<const R *>(J.xdiv)[c];
 
@@ -193,11 +204,11 @@ __device__ __forceinline__ void cell_update_from(const DevJob &J, int model, lon
     }
 }
 
-template <class R, bool XD = false, bool AB2 = false>
+template <class R, bool XD = false, bool AB2 = false, bool CG = false>
 __device__ __forceinline__ void cell_update(const DevJob &J, int model, long long c) {
     const long long n = *J.step;
     const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
-    cell_update_from<R, XD, AB2>(J, model, c, n, V, global_src<R>(J, model, c, V));
+    cell_update_from<R, XD, AB2, CG>(J, model, c, n, V, global_src<R>(J, model, c, V));
 }
 
 // Conduction graph, part 1 (Sec. 3.2 / 3.3): the reaction of every graph node
@@ -306,6 +317,103 @@ __global__ void __launch_bounds__(T, MINB) cell_kernel(const DevJob *__restrict_
         const unsigned prev = atomicAdd(done, 1u);
         if (prev == gridDim.x - 1) {
             for (int j = 0; j < n_jobs; ++j) *jobs[j].step += 1;
+            *done = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused step: the node values (S1) and the cell update of every job in ONE
+// persistent launch. The launch works through a list of node tiles and cell
+// tiles (Work), claimed in order from a device counter. A cell tile of a job
+// needs the values of a bounded range of that job's node tiles (the gather
+// indices of an RCM-numbered mesh are local), and the host orders the list
+// so that those node tiles come first, queued kFusedLookahead cell tiles
+// ahead. A block that finishes a node tile publishes it with a release store
+// of the launch's tag (gen + 1) into the tile's flag; a block that claims a
+// cell tile waits (acquire loads, bounded) until every flag of its range
+// carries the tag, then updates its cells, reading node values from L2. A
+// claimed node tile is always being worked on by a running block, so every
+// wait ends. The V^n a node tile reads is read again soon after by the cell
+// tiles of the same region, from L2. The last block to finish advances each
+// job's step and launch counters and re-arms the work counter.
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr unsigned long long kFusedWaitLimitNs = 1000000000ull;   // 1 s
+
+template <class R, int T, int MINB, bool XD, bool AB2>
+__global__ void __launch_bounds__(T, MINB)
+    fused_kernel(const DevJob *__restrict__ jobs, const Tile *__restrict__ node_tiles,
+                 const Tile *__restrict__ cell_tiles, const Work *__restrict__ work, int n_work, unsigned *head,
+                 unsigned *done, int n_jobs, unsigned *err) {
+    __shared__ int item_sh;
+    for (;;) {
+        if (threadIdx.x == 0) item_sh = int(atomicAdd(head, 1u));
+        __syncthreads();
+        const int it = item_sh;
+        __syncthreads();   // item_sh is written again at the next claim
+        if (it >= n_work) break;
+        const Work wk = work[it];
+        if (wk.tile < 0) {
+            const Tile tl = node_tiles[-1 - wk.tile];
+            const DevJob &J = jobs[tl.job];
+            const long long n = *J.step;
+            const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
+            R *vn = static_cast<R *>(J.vn);
+            for (int i = threadIdx.x; i < tl.count; i += T) {
+                const long long node = (long long)tl.start + i;
+                vn[node] = node_value<R>(J, V, node);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                st_release(J.ntflag + (tl.start >> 8), *J.gen + 1u);
+            }
+        } else {
+            const Tile tl = cell_tiles[wk.tile];
+            const DevJob &J = jobs[tl.job];
+            if (threadIdx.x < 32) {
+                const unsigned tag = *J.gen + 1u;
+                for (int k = wk.dep_lo + int(threadIdx.x); k <= wk.dep_hi; k += 32) {
+                    if (ld_acquire(J.ntflag + k) == tag) continue;
+                    const unsigned long long t0 = global_timer_ns();
+                    while (ld_acquire(J.ntflag + k) != tag) {
+                        if (global_timer_ns() - t0 > kFusedWaitLimitNs) {
+                            atomicOr(err, 2u);   // reported by ep_step / ep_check_finite; the tile goes on
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                }
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < tl.count; i += T)
+                cell_update<R, XD, AB2, true>(J, tl.model, (long long)tl.start + i);
+        }
+    }
+    // Every block has read the counters; the last one to finish advances them.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(done, 1u);
+        if (prev == gridDim.x - 1) {
+            for (int j = 0; j < n_jobs; ++j) {
+                *jobs[j].step += 1;
+                *jobs[j].gen += 1u;
+            }
+            *head = 0u;
             *done = 0u;
             __threadfence();
         }
@@ -628,7 +736,9 @@ cudaError_t launch_graph(int precision, const StepLaunch &L, cudaStream_t s) {
 
 template <class R>
 static cudaError_t step_impl(const StepLaunch &L, cudaStream_t s) {
-    node_kernel<R><<<L.node_grid, kNodeThreads, 0, s>>>(L.jobs, L.node_tiles, L.n_node_tiles);
+    // the conduction graphs read no node values: with the fused variants they run first
+    if (L.cell_variant < kFusedVariant)
+        node_kernel<R><<<L.node_grid, kNodeThreads, 0, s>>>(L.jobs, L.node_tiles, L.n_node_tiles);
     graph_impl<R>(L, s);
     return launch_cell(sizeof(R) == 8 ? EP_FP64_PLAIN : EP_FP32_MIXED, L, s);
 }
@@ -678,6 +788,7 @@ cudaError_t launch_reset_act(int precision, const DevJob *job, long long n_cells
 }
 
 cudaError_t launch_node(int precision, const StepLaunch &L, cudaStream_t s) {
+    if (L.cell_variant >= kFusedVariant) return cudaSuccess;   // the fused launch computes the node values
     if (precision == EP_FP64_PLAIN)
         node_kernel<double><<<L.node_grid, kNodeThreads, 0, s>>>(L.jobs, L.node_tiles, L.n_node_tiles);
     else
@@ -718,8 +829,29 @@ static void launch_staged(const StepLaunch &L, cudaStream_t s) {
                                                                      L.n_jobs, L.err);
 }
 
+template <class R, int T, int B>
+static void launch_fused_kernel(const StepLaunch &L, cudaStream_t s) {
+    auto *k = L.bido ? (L.ab2 ? fused_kernel<R, T, B, true, true> : fused_kernel<R, T, B, true, false>)
+                     : (L.ab2 ? fused_kernel<R, T, B, false, true> : fused_kernel<R, T, B, false, false>);
+    k<<<L.cell_grid, T, 0, s>>>(L.jobs, L.node_tiles, L.cell_tiles, L.work, L.n_work, L.head, L.done, L.n_jobs,
+                                L.err);
+}
+
 template <class R>
 static cudaError_t cell_launch_variant(const StepLaunch &L, cudaStream_t s) {
+    if (L.cell_variant >= kFusedVariant) {
+        switch (L.cell_variant) {
+#define EP_FUSED_CASE(k, T, B)                                                                                 \
+    case k:                                                                                                    \
+        launch_fused_kernel<R, T, B>(L, s);                                                                    \
+        break;
+            EP_FUSED_VARIANTS(EP_FUSED_CASE)
+#undef EP_FUSED_CASE
+        default:
+            return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     if (L.cell_variant >= kStagedVariant) {
         if constexpr (std::is_same<R, float>::value) {
             if (!L.ab2 && !L.idx16) {
@@ -754,6 +886,17 @@ cudaError_t launch_cell(int precision, const StepLaunch &L, cudaStream_t s) {
 template <class R>
 static int cell_blocks_variant(int variant) {
     int nb = 0;
+    if (variant >= kFusedVariant) {
+        switch (variant) {
+#define EP_FUSED_CASE(k, T, B)                                                                              \
+    case k:                                                                                                 \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_kernel<R, T, B, false, false>, T, 0);      \
+        break;
+            EP_FUSED_VARIANTS(EP_FUSED_CASE)
+#undef EP_FUSED_CASE
+        }
+        return nb < 1 ? 1 : nb;
+    }
     if (variant >= kStagedVariant) {
         if (std::is_same<R, float>::value && staged_attributes() == cudaSuccess) {
             if (variant == kStagedVariant)
@@ -778,15 +921,15 @@ static int cell_blocks_variant(int variant) {
 }
 
 int cell_variant_threads(int variant) {
-    if (variant >= kStagedVariant) return kCellThreads;
     switch (variant) {
 #define EP_CELL_CASE(k, T, B) \
     case k:                   \
         return T;
         EP_CELL_VARIANTS(EP_CELL_CASE)
+        EP_FUSED_VARIANTS(EP_CELL_CASE)
 #undef EP_CELL_CASE
     }
-    return 0;
+    return variant >= kStagedVariant && variant < kFusedVariant ? kCellThreads : 0;
 }
 
 cudaError_t launch_check_finite(int precision, const DevJob *job, long long n_cells, unsigned *count,
@@ -827,8 +970,9 @@ int node_blocks_per_sm(int precision) {
 // (different streams, threads or contexts on one device) race on it and must
 // be serialised by the caller.
 //
-// Layout: [0, 256) the ticket; the descriptor; the node tiles; the cell tiles;
-// the node values (each part 256-byte aligned).
+// Layout: [0, 256) the ticket and the work counter; the descriptor; the node
+// tiles; the cell tiles; the work list; the node values (each part 256-byte
+// aligned).
 namespace noalloc {
 constexpr size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t kMaxNodeTiles = (EP_NOALLOC_MAX_NODES + kNodeThreads - 1) / kNodeThreads;
@@ -836,7 +980,8 @@ constexpr size_t kMaxCellTiles = (EP_NOALLOC_MAX_CELLS + kCellThreads - 1) / kCe
 constexpr size_t kJob = 256;
 constexpr size_t kNodeTiles = kJob + round256(sizeof(DevJob));
 constexpr size_t kCellTiles = kNodeTiles + round256(kMaxNodeTiles * sizeof(Tile));
-constexpr size_t kVn = kCellTiles + round256(kMaxCellTiles * sizeof(Tile));
+constexpr size_t kWork = kCellTiles + round256(kMaxCellTiles * sizeof(Tile));
+constexpr size_t kVn = kWork + round256((kMaxNodeTiles + kMaxCellTiles) * sizeof(Work));
 constexpr size_t kBytes = kVn + size_t(EP_NOALLOC_MAX_NODES) * sizeof(double);
 }  // namespace noalloc
 static __device__ __align__(256) unsigned char g_noalloc_scratch[noalloc::kBytes];
@@ -899,11 +1044,13 @@ static cudaError_t noalloc_scratch_address(void **out) {
 }
 
 cudaError_t launch_step_noalloc(int precision, const DevJob &job, const Tile *node_tiles, int n_node_tiles,
-                                const Tile *cell_tiles, int n_cell_tiles, int cell_variant, int sm_count,
-                                unsigned *err, long long n_steps, cudaStream_t s) {
+                                const Tile *cell_tiles, int n_cell_tiles, const Work *work, int n_work,
+                                int cell_variant, int sm_count, unsigned *err, long long n_steps, cudaStream_t s) {
     using namespace noalloc;
     if (job.n_nodes < 1 || job.n_nodes > EP_NOALLOC_MAX_NODES || job.n_cells < 1 ||
-        job.n_cells > EP_NOALLOC_MAX_CELLS || n_node_tiles > int(kMaxNodeTiles) || n_cell_tiles > int(kMaxCellTiles))
+        job.n_cells > EP_NOALLOC_MAX_CELLS || n_node_tiles > int(kMaxNodeTiles) ||
+        n_cell_tiles > int(kMaxCellTiles) || n_work > int(kMaxNodeTiles + kMaxCellTiles) ||
+        (cell_variant >= kFusedVariant && n_work != n_node_tiles + n_cell_tiles))
         return cudaErrorInvalidValue;
     void *base = nullptr;
     cudaError_t e = noalloc_scratch_address(&base);
@@ -920,7 +1067,9 @@ cudaError_t launch_step_noalloc(int precision, const DevJob &job, const Tile *no
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b + kCellTiles, cell_tiles, size_t(n_cell_tiles) * sizeof(Tile), cudaMemcpyHostToDevice,
                             s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess && n_work > 0)
+        e = cudaMemcpyAsync(b + kWork, work, size_t(n_work) * sizeof(Work), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b, 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     StepLaunch L{};
     L.jobs = reinterpret_cast<const DevJob *>(b + kJob);
@@ -930,6 +1079,9 @@ cudaError_t launch_step_noalloc(int precision, const DevJob &job, const Tile *no
     L.cell_tiles = reinterpret_cast<const Tile *>(b + kCellTiles);
     L.n_cell_tiles = n_cell_tiles;
     L.done = reinterpret_cast<unsigned *>(b);
+    L.head = reinterpret_cast<unsigned *>(b) + 1;
+    L.work = reinterpret_cast<const Work *>(b + kWork);
+    L.n_work = n_work;
     L.cell_variant = cell_variant;
     L.idx16 = job.idx16;
     L.err = err;

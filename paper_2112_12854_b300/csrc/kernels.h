@@ -24,6 +24,9 @@ struct StepLaunch {
     int ab2;                   // some job integrates by AB2 (cell kernel keeps rate histories)
     int idx16;                 // some job stores 16-bit gather indices (the staged variants need 32-bit)
     unsigned *err;             // device error word of the context (bounded waits that gave up)
+    const Work *work;          // fused variants: node and cell tiles in dependency order
+    int n_work;
+    unsigned *head;            // fused variants: next work item (device counter)
 };
 
 // Launch shapes of the cell kernel: (index, threads per block, minimum
@@ -39,8 +42,16 @@ struct StepLaunch {
 // 256 threads; streamed inputs staged by bulk copies: 6 everything, two
 // blocks per SM; 7 indices / coefficients / V / bytes, three blocks per SM);
 // for FP64, AB2 or 16-bit-index batches they run variant 0.
-constexpr int kNumCellVariants = 8;
+// Variants 8 and 9: the fused step (fused_kernel: node tiles and cell tiles
+// of every job in one persistent launch, in dependency order; 128 threads x
+// 6 blocks per SM and 256 x 3).
+#define EP_FUSED_VARIANTS(X) \
+    X(8, 128, 6)             \
+    X(9, 256, 3)
+constexpr int kNumCellVariants = 10;
 constexpr int kStagedVariant = 6;
+constexpr int kFusedVariant = 8;
+constexpr int kFusedLookahead = 1024;   // cell tiles whose node tiles are queued ahead of them
 int cell_variant_threads(int variant);
 
 // One time step of every job in the table: node values, the conduction
@@ -53,7 +64,8 @@ cudaError_t launch_step(int precision, const StepLaunch &L, cudaStream_t s);
 cudaError_t launch_init(int precision, const DevJob *job, long long n_cells, cudaStream_t s);
 
 // The parts of launch_step, separately (for timing): node values, the
-// conduction graphs (no launch when no job has one), the cell update.
+// conduction graphs (no launch when no job has one), the cell update. With a
+// fused variant the node part is empty and the cell part is the fused launch.
 cudaError_t launch_node(int precision, const StepLaunch &L, cudaStream_t s);
 cudaError_t launch_graph(int precision, const StepLaunch &L, cudaStream_t s);
 cudaError_t launch_cell(int precision, const StepLaunch &L, cudaStream_t s);
@@ -80,13 +92,13 @@ cudaError_t launch_alu_probe(int kind, int blocks, int iters, double *sink, cuda
 int alu_probe_threads();
 
 // Step one job n_steps times like launch_step, with its descriptor, tile
-// tables, ticket and node values in a static device array instead of
-// allocated memory (at most EP_NOALLOC_MAX_NODES nodes and
-// EP_NOALLOC_MAX_CELLS cells). job, node_tiles and cell_tiles are host
-// copies (tiles of job 0).
+// tables, work list (fused variants), counters and node values in a static
+// device array instead of allocated memory (at most EP_NOALLOC_MAX_NODES
+// nodes and EP_NOALLOC_MAX_CELLS cells). job, node_tiles, cell_tiles and
+// work are host copies (tiles of job 0).
 cudaError_t launch_step_noalloc(int precision, const DevJob &job, const Tile *node_tiles, int n_node_tiles,
-                                const Tile *cell_tiles, int n_cell_tiles, int cell_variant, int sm_count,
-                                unsigned *err, long long n_steps, cudaStream_t s);
+                                const Tile *cell_tiles, int n_cell_tiles, const Work *work, int n_work,
+                                int cell_variant, int sm_count, unsigned *err, long long n_steps, cudaStream_t s);
 
 // Kernel attributes for sizing persistent grids.
 int cell_blocks_per_sm(int precision, int variant);

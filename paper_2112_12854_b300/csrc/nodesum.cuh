@@ -39,7 +39,7 @@ __device__ __forceinline__ R node_value(const DevJob &J, const R *__restrict__ V
     const R *__restrict__ w = static_cast<const R *>(J.nw);
     const long long s = node >> 5;
     const long long b = J.slice_ptr[s] + (node & 31), e = J.slice_ptr[s + 1];
-    if (J.idx16) return node_sum<R, D>(w, J.ncol16, J.cbase[s], V, b, e);
+    if (J.col16) return node_sum<R, D>(w, J.ncol16, J.cbase[s], V, b, e);
     return node_sum<R, D>(w, J.ncol, 0, V, b, e);
 }
 

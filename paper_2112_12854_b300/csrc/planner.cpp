@@ -594,9 +594,8 @@ void cell_gather_indices(const HostMesh &m, int64_t c, int32_t na[4], int32_t nb
     }
 }
 
-// 16-bit form of the gather indices (see Sell), if every offset fits.
-static bool build_idx16(const HostMesh &m, Sell *s) {
-    const int64_t N = m.n_cells, NN = m.n_nodes;
+// 16-bit form of the ELL entries (see Sell), if every slice's offsets fit.
+static bool build_col16(Sell *s) {
     const int64_t ns = int64_t(s->slice_ptr.size()) - 1;
     s->cbase.assign(ns, 0);
     s->col16.assign(s->col.size(), 0);
@@ -609,6 +608,12 @@ static bool build_idx16(const HostMesh &m, Sell *s) {
         s->cbase[sl] = lo;
         for (int64_t k = b; k < e; ++k) s->col16[k] = uint16_t(s->col[k] - lo);
     }
+    return true;
+}
+
+// 16-bit form of the cells' gather indices (see Sell), if every offset fits.
+static bool build_idx16(const HostMesh &m, Sell *s) {
+    const int64_t N = m.n_cells, NN = m.n_nodes;
     const int64_t nblk = (N + 255) / 256;
     s->nbase.assign(nblk, 0);
     s->cidx16.assign(8 * N, 0);
@@ -673,11 +678,14 @@ void build_sell(const HostMesh &m, Sell *s) {
     }
     s->idx16 = m.index_width != 32 && build_idx16(m, s);
     if (!s->idx16) {
-        s->col16.clear();
-        s->cbase.clear();
         s->cidx16.clear();
         s->nbr16.clear();
         s->nbase.clear();
+    }
+    s->col16ok = m.index_width != 32 && build_col16(s);
+    if (!s->col16ok) {
+        s->col16.clear();
+        s->cbase.clear();
     }
 }
 

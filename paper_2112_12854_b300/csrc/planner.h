@@ -51,16 +51,19 @@ double power_radius(const HostMesh &m, const Coeffs &c, int iters);
 // (own vertices, the vertex of the neighbour opposite each face, the
 // neighbour across each face; on a boundary face the cell's own vertex 0 and
 // the cell itself). Indices are stored either as 32-bit values or, where the
-// numbering allows (idx16), as 16-bit offsets:
+// numbering allows, as 16-bit offsets -- the cells' gather indices (idx16)
+// and the ELL entries (col16) independently:
 //   - a cell's 8 node indices relative to nbase[c >> 8] (unsigned; the base is
 //     the smallest node index of the 256-cell run);
 //   - a cell's 4 neighbours relative to the cell itself (signed);
-//   - the ELL entries of a slice relative to cbase[slice] (unsigned).
+//   - the ELL entries of a slice relative to cbase[slice] (unsigned). The
+//     cells around one node span several RCM levels (about six times the
+//     neighbour bandwidth), so this form fits smaller meshes only.
 struct Sell {
     std::vector<int64_t> slice_ptr;   // [n_slices + 1] entry offsets
     std::vector<int32_t> col;         // cell index per entry (pads repeat a valid cell)
     std::vector<int64_t> src;
-    bool idx16 = false;
+    bool idx16 = false, col16ok = false;
     std::vector<uint16_t> col16;      // [entries] ELL offsets from cbase
     std::vector<int32_t> cbase;       // [n_slices]
     std::vector<uint16_t> cidx16;     // [8 n_cells] na then nb offsets from nbase

@@ -128,7 +128,8 @@ def load():
         "ep_check_finite": ([_P], ctypes.c_int),
         "ep_clear_error": ([_P], ctypes.c_int),
         "ep_job_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
-                         ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+                         ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
+                        ctypes.c_int),
         "ep_estimate_bytes": ([_I64, _I64, ctypes.c_int32], _I64),
         "ep_job_destroy": ([_P], ctypes.c_int),
         "ep_model_nvar": ([ctypes.c_int32], ctypes.c_int32),
@@ -142,8 +143,8 @@ def load():
                           ctypes.c_int),
         "ep_plan_create": ([ctypes.POINTER(MeshDesc), ctypes.POINTER(Params), ctypes.POINTER(_P)], ctypes.c_int),
         "ep_plan_bytes": ([_P], _I64),
-        "ep_plan_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int32)],
-                         ctypes.c_int),
+        "ep_plan_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int32),
+                          ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "ep_plan_destroy": ([_P], ctypes.c_int),
         "ep_job_create": ([_P, _P, ctypes.POINTER(_P)], ctypes.c_int),
         "ep_autotune": ([ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32, _P, _P], ctypes.c_int),
@@ -306,9 +307,10 @@ class Plan:
             raise EPError(rc, L.ep_last_error(None).decode())
         self._h = h
         self.params = params
-        a, b, iw = _I64(), _I64(), ctypes.c_int32()
-        L.ep_plan_info(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(iw))
-        self.n_cells, self.n_nodes, self.index_width = int(a.value), int(b.value), int(iw.value)
+        a, b, iw, niw = _I64(), _I64(), ctypes.c_int32(), ctypes.c_int32()
+        L.ep_plan_info(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(iw), ctypes.byref(niw))
+        self.n_cells, self.n_nodes = int(a.value), int(b.value)
+        self.index_width, self.node_index_width = int(iw.value), int(niw.value)
         self.device_bytes = int(L.ep_plan_bytes(h))
 
     def destroy(self):
@@ -392,11 +394,11 @@ class Job:
         return True
 
     def info(self) -> dict:
-        a, b, c, d, iw = _I64(), _I64(), _I64(), _I64(), ctypes.c_int32()
+        a, b, c, d, iw, niw = _I64(), _I64(), _I64(), _I64(), ctypes.c_int32(), ctypes.c_int32()
         self.ctx.check(load().ep_job_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
-                                          ctypes.byref(d), ctypes.byref(iw)))
+                                          ctypes.byref(d), ctypes.byref(iw), ctypes.byref(niw)))
         return dict(n_cells=a.value, n_nodes=b.value, n_interior_faces=c.value, device_bytes=d.value,
-                    index_width=iw.value)
+                    index_width=iw.value, node_index_width=niw.value)
 
     def attach_graph(self, graph, *, node_model=None):
         """Attach a conduction graph (an object like ``workloads.Graph``:
@@ -514,7 +516,7 @@ def step_noalloc(job, n_steps: int):
     job.ctx.check(load().ep_step_noalloc(job._h, int(n_steps)))
 
 
-N_CELL_VARIANTS = 8
+N_CELL_VARIANTS = 10
 
 
 def autotune(jobs, steps_per_variant: int = 10):

@@ -132,6 +132,7 @@ def test_index_widths_bitwise_identical(pname):
     b16 = ep.job_from_case(ctx, case, precision=prec)
     b32 = ep.job_from_case(ctx, case, precision=prec, index_width=32)
     assert a16.info()["index_width"] == 16 and a32.info()["index_width"] == 32
+    assert a16.info()["node_index_width"] == 16 and a32.info()["node_index_width"] == 32
     assert a16.info()["device_bytes"] < a32.info()["device_bytes"]
     a16.step(300)
     a32.step(300)
@@ -158,4 +159,74 @@ def test_index_widths_bitwise_identical_bidomain():
         j.step(80)
     assert np.array_equal(jobs[0].V, jobs[1].V)
     assert np.array_equal(jobs[0].ve, jobs[1].ve)
+    ctx.close()
+
+
+@pytest.mark.parametrize("pname", ["mixed", "plain"])
+@pytest.mark.parametrize("fused,plain", [(8, 4), (9, 1)])
+def test_fused_step_equals_two_launch_step(pname, fused, plain):
+    """The fused step (node values and cell update in one launch, node tiles
+    and cell tiles in dependency order) gives bitwise the state of the
+    two-launch step with the same block shape and register budget (128 x 6
+    and 256 x 3), on a slab large enough for many tiles of both kinds to be
+    in flight at once (27648 cells, 108 cell tiles, 22 node tiles)."""
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2112_12854_b300 import ep
+    prec = ep.EP_FP32_MIXED if pname == "mixed" else ep.EP_FP64_PLAIN
+    case = w.slab_case(nx=24, ny=24, nz=8, h=0.25, stim_x=0.6)
+    ctx = ep.Context()
+    out = []
+    for v in (plain, fused):
+        ep.set_cell_variant(ctx, prec, v)
+        j = ep.job_from_case(ctx, case, precision=prec)
+        j.step(400)                                          # captured-graph replay and direct launches
+        out.append([j.read(k) for k in range(19)] + [j.activation_times()])
+        assert j.check_finite()
+        j.destroy()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b, equal_nan=True)
+    assert np.isfinite(out[0][-1]).sum() > 1000
+    ctx.close()
+
+
+@pytest.mark.parametrize("variant", [8, 9])
+def test_fused_step_batched_equals_alone(variant):
+    """One fused launch serves a batch of jobs of different sizes and index
+    forms (work lists concatenated, a ready flag per node tile and a launch
+    counter per job): every job is bitwise what it is stepped alone, with
+    forward Euler and AB2 FP32 jobs and a bidomain job in the FP32 batch, and
+    an FP64 job in its own group."""
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2112_12854_b300 import ep
+    ctx = ep.Context()
+    for p in (ep.EP_FP32_MIXED, ep.EP_FP64_PLAIN):
+        ep.set_cell_variant(ctx, p, variant)
+    specs = [(w.slab_case(nx=9, ny=5, nz=3, h=0.5), {}, None),
+             (w.slab_case(nx=20, ny=14, nz=4, h=0.25, D_l=0.1, D_t=0.05), {"index_width": 32}, None),
+             (w.slab_case(nx=12, ny=8, nz=3, h=0.25), {"integrator": 1}, None),
+             (w.slab_case(nx=10, ny=10, nz=3, h=0.25), {"precision": ep.EP_FP64_PLAIN}, None),
+             (w.slab_case(nx=12, ny=8, nz=3, h=0.25), {}, "bido")]
+
+    def make():
+        js = []
+        for case, kw, extra in specs:
+            j = ep.job_from_case(ctx, case, **kw)
+            if extra == "bido":
+                j.enable_bidomain(0.62 / 1.4, 0.24 / 1.4)
+            js.append(j)
+        return js
+    alone = make()
+    for j in alone:
+        j.step(150)
+    batch = make()
+    ep.step(batch, 150)
+    for a, b in zip(alone, batch):
+        assert a.step_index == b.step_index == 150
+        assert np.array_equal(a.V, b.V)
+        assert np.array_equal(a.activation_times(), b.activation_times())
+        for k in range(1, 19):
+            assert np.array_equal(a.read(k), b.read(k))
+    assert np.array_equal(alone[-1].ve, batch[-1].ve)
     ctx.close()

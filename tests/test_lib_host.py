@@ -264,17 +264,22 @@ def _coned_sphere(levels):
 
 
 def test_index_width_chosen_by_the_numbering():
-    """16-bit gather indices where every offset fits (a slab), 32-bit where
-    they cannot (a node shared by 131072 cells), and 32-bit on request."""
+    """16-bit gather indices where every offset fits (a slab), 32-bit
+    node -> cell entries where they cannot (a node shared by 131072 cells:
+    its cells span the whole numbering, while each cell's own neighbours and
+    nodes stay close), and 32-bit everywhere on request."""
     params = ep.make_params(0.01, [w.ParamSet()])
     case = w.slab_case(nx=20, ny=10, nz=4, h=0.5)
-    assert ep.Plan(case.xyz, case.tets, params).index_width == 16
-    assert ep.Plan(case.xyz, case.tets, params, index_width=32).index_width == 32
+    p = ep.Plan(case.xyz, case.tets, params)
+    assert (p.index_width, p.node_index_width) == (16, 16)
+    p = ep.Plan(case.xyz, case.tets, params, index_width=32)
+    assert (p.index_width, p.node_index_width) == (32, 32)
     xyz, tets = _coned_sphere(7)            # (no parameters: only the mesh is planned)
     assert tets.shape[0] == 131072
-    assert ep.Plan(xyz, tets).index_width == 32
-    xyz, tets = _coned_sphere(5)
-    assert ep.Plan(xyz, tets).index_width == 16
+    p = ep.Plan(xyz, tets)
+    assert (p.index_width, p.node_index_width) == (16, 32)
+    p = ep.Plan(*_coned_sphere(5))
+    assert (p.index_width, p.node_index_width) == (16, 16)
     with pytest.raises(ep.EPError) as e:
         ep.Plan(case.xyz, case.tets, params, index_width=16)
     assert e.value.code == ep.EP_EINVAL
