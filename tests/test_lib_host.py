@@ -264,10 +264,13 @@ def _coned_sphere(levels):
 
 
 def test_index_width_chosen_by_the_numbering():
-    """16-bit gather indices where every offset fits (a slab), 32-bit
-    node -> cell entries where they cannot (a node shared by 131072 cells:
-    its cells span the whole numbering, while each cell's own neighbours and
-    nodes stay close), and 32-bit everywhere on request."""
+    """16-bit gather indices where every offset fits (a slab); on a
+    150 x 150 x 30-cube wedge (4.05M cells, RCM neighbour bandwidth about
+    12.5k cells) 16-bit cell gathers but 32-bit node -> cell entries (the
+    cells around one node span about six RCM levels, 75k cells); 32-bit
+    everywhere where a node is shared by 131072 cells (its cells span the
+    whole numbering, and so do the nodes of a run of cells next to it); and
+    32-bit on request."""
     params = ep.make_params(0.01, [w.ParamSet()])
     case = w.slab_case(nx=20, ny=10, nz=4, h=0.5)
     p = ep.Plan(case.xyz, case.tets, params)
@@ -277,6 +280,9 @@ def test_index_width_chosen_by_the_numbering():
     xyz, tets = _coned_sphere(7)            # (no parameters: only the mesh is planned)
     assert tets.shape[0] == 131072
     p = ep.Plan(xyz, tets)
+    assert (p.index_width, p.node_index_width) == (32, 32)
+    wedge = w.wedge_case(nx=150, ny=150, nz=30, h=0.25)
+    p = ep.Plan(wedge.xyz, wedge.tets)
     assert (p.index_width, p.node_index_width) == (16, 32)
     p = ep.Plan(*_coned_sphere(5))
     assert (p.index_width, p.node_index_width) == (16, 16)
