@@ -372,10 +372,13 @@ def run_serving(ctx, args, capacity_cups, rank, world, dist):
     mean_work = float(np.mean([r.n_cells * r.n_steps for r in probe]))
     cap_jobs = capacity_cups / mean_work
     out = {"capacity_jobs_per_s": cap_jobs, "mean_job_cell_updates": mean_work}
-    for name, rate, limit in (("load_%.2f" % args.serve_load, args.serve_load * cap_jobs * world,
-                               args.serve_window + 90.0),
-                              ("configured_%g_per_s" % args.serve_rate, args.serve_rate, args.serve_window)):
-        reqs = config5_requests(rate, args.serve_window, seed=1 if name.startswith("conf") else 0)
+    for name, rate, window, limit in (("load_%.2f" % args.serve_load, args.serve_load * cap_jobs * world,
+                                       args.serve_window, args.serve_window + 90.0),
+                                      ("configured_%g_per_s" % args.serve_rate, args.serve_rate,
+                                       args.serve_window_configured, args.serve_window_configured)):
+        if window <= 0:
+            continue
+        reqs = config5_requests(rate, window, seed=1 if name.startswith("conf") else 0)
         srv = Server(LibBackend(ctx), steps_per_iter=250, workers=4, rank=rank, world=world)
         t0 = time.perf_counter()
         res = srv.run(reqs, time_limit=limit)
@@ -390,8 +393,8 @@ def run_serving(ctx, args, capacity_cups, rank, world, dist):
                     "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
                     "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None}
         else:
-            summ = summarize(res, wall, srv.log)
-        summ.update({"offered_jobs_per_s": rate, "arrivals": len(reqs), "window_s": args.serve_window,
+            summ = summarize(res, wall, srv.log, srv.unfinished_ages)
+        summ.update({"offered_jobs_per_s": rate, "arrivals": len(reqs), "window_s": window,
                      "time_limit_s": limit, "wall_s": wall, "unfinished": len(srv.unfinished) * world,
                      "max_resident": max((x["resident"] for x in srv.log), default=0)})
         out[name] = summ
@@ -413,18 +416,32 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="debug: 1/8-volume crop instead of the full wedge")
     ap.add_argument("--heart-steps", type=int, default=200, help="timed steps of the whole-heart leg (0 = skip)")
-    ap.add_argument("--sweep-jobs", type=int, default=64, help="jobs of the batched parametric sweep (0 = skip; "
+    ap.add_argument("--sweep-jobs", type=int, default=256, help="jobs of the batched parametric sweep (0 = skip; "
                     "the configured sweep has 256)")
     ap.add_argument("--sweep-steps", type=int, default=200)
     ap.add_argument("--bido-steps", type=int, default=100, help="timed steps of the bidomain leg (0 = skip)")
     ap.add_argument("--bido-warmup", type=int, default=100)
-    ap.add_argument("--serve-window", type=float, default=40.0,
-                    help="seconds of Poisson arrivals in each serving run (0 = no serving leg)")
+    ap.add_argument("--serve-window", type=float, default=640.0,
+                    help="seconds of Poisson arrivals in the serving run at --serve-load x capacity (0 = no serving "
+                         "leg at all); at 0.7 x capacity 640 s gives about 300 completions")
+    ap.add_argument("--serve-window-configured", type=float, default=60.0,
+                    help="seconds of arrivals at the configured rate (overloaded; cut off at the same time)")
     ap.add_argument("--serve-load", type=float, default=0.7, help="offered load of the first serving run, "
                     "as a fraction of the measured capacity")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="arrival rate of the configured (overloaded) run")
+    ap.add_argument("--time-budget", type=float, default=1500.0,
+                    help="seconds after which the optional legs (sweep, bidomain, heart, serving) are skipped")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    t_start = time.perf_counter()
+    skipped = []
+
+    def budget_left(leg, needs_s):
+        """True if the leg (about needs_s seconds) fits the time budget; else it is skipped."""
+        if time.perf_counter() - t_start + needs_s <= args.time_budget:
+            return True
+        skipped.append(leg)
+        return False
     if args.impl == "reference":
         run_reference(args)
         return
@@ -570,19 +587,19 @@ def main():
                          "node_kernel_ms": node64_ms}}
 
     sweep = None
-    if args.sweep_jobs > 0:
+    if args.sweep_jobs > 0 and budget_left("batched_sweep", 240.0):
         sweep = run_sweep(ctx, args, stream, torch)
 
     bido = None
-    if args.bido_steps > 0:
+    if args.bido_steps > 0 and budget_left("bidomain", 60.0):
         bido = run_bidomain(ctx, args, dims, stream, torch, peak)
 
     heart = None
-    if args.heart_steps > 0:
+    if args.heart_steps > 0 and budget_left("whole_heart", 90.0):
         heart = run_heart(ctx, args, stream, torch)
 
     serving = None
-    if args.serve_window > 0:
+    if args.serve_window > 0 and budget_left("serving", 900.0):
         serving = run_serving(ctx, args, value / world, rank, world, dist)
 
     cpu = None
@@ -616,7 +633,8 @@ def main():
                              "fp64_fma_tflops": alu["fp64_fma_flops"] / 1e12,
                              "source": "ep_alu_peaks: independent FMA / ex2 chains on every SM, CUDA events"},
                "speedup_vs_fp64_plain": value / world / fp64["value"], "state_finite": finite,
-               "batched_sweep": sweep, "bidomain": bido, "whole_heart": heart, "serving": serving}
+               "batched_sweep": sweep, "bidomain": bido, "whole_heart": heart, "serving": serving,
+               "legs_skipped_for_time": skipped, "bench_wall_s": time.perf_counter() - t_start}
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist is not None:

@@ -464,10 +464,10 @@ int job_upload_topology(ep_context *ctx, ep_job *j) {
     cudaError_t e = cudaMemsetAsync(b.p, 0, 2 * sizeof(long long), ctx->upload);
     j->dj.step = static_cast<long long *>(b.p);
     j->dj.gen = reinterpret_cast<unsigned *>(static_cast<long long *>(b.p) + 1);
-    const int64_t n_node_tiles = (m.n_nodes + kNodeThreads - 1) / kNodeThreads;
-    if ((rc = dalloc(ctx, size_t(n_node_tiles) * sizeof(unsigned), &b))) return rc;
+    const int64_t n_chunks = ((m.n_nodes + kNodeThreads - 1) / kNodeThreads + kFusedChunk - 1) / kFusedChunk;
+    if ((rc = dalloc(ctx, size_t(n_chunks) * sizeof(unsigned), &b))) return rc;
     j->topo.push_back(b);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b.p, 0, size_t(n_node_tiles) * sizeof(unsigned), ctx->upload);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.p, 0, size_t(n_chunks) * sizeof(unsigned), ctx->upload);
     j->dj.ntflag = static_cast<unsigned *>(b.p);
     if ((rc = dalloc(ctx, sizeof(DevJob), &b))) return rc;
     j->dj_dev = b;
@@ -611,7 +611,7 @@ int64_t job_bytes(const HostMesh &m, const Sell &sl, int precision, int integrat
     const int64_t N = m.n_cells, r = precision == EP_FP64_PLAIN ? 8 : 4, E = int64_t(sl.col.size());
     const int64_t ns = int64_t(sl.slice_ptr.size()) - 1;
     int64_t b = 2 * rnd(N) + rnd(8 * int64_t(sl.slice_ptr.size())) + rnd(4 * N) + 256 + rnd(sizeof(DevJob)) +
-                rnd(4 * ((m.n_nodes + kNodeThreads - 1) / kNodeThreads));
+                rnd(4 * (((m.n_nodes + kNodeThreads - 1) / kNodeThreads + kFusedChunk - 1) / kFusedChunk));
     b += sl.idx16 ? rnd(16 * N) + rnd(8 * N) + rnd(4 * ((N + 255) / 256)) : 3 * rnd(16 * N);
     b += sl.col16ok ? rnd(2 * E) + rnd(4 * ns) : rnd(4 * E);
     b += 3 * rnd(4 * r * N) + rnd(r * E) + 3 * rnd(r * N) + rnd(r * m.n_nodes);
@@ -1099,6 +1099,7 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
         }
         g.L.node_grid = std::max(1, std::min<int>(int(nt.size()), ctx->sm_count * node_blocks_per_sm(prec)));
         g.L.cell_variant = ctx->cell_variant[prec];
+        g.L.cell_grid0 = std::max(1, std::min<int>(int(ct.size()), ctx->sm_count * cell_blocks_per_sm(prec, 0)));
         g.L.cell_grid =
             std::max(1, std::min<int>(int(ct.size()), ctx->sm_count * cell_blocks_per_sm(prec, g.L.cell_variant)));
         pl->groups.push_back(g);

@@ -96,8 +96,8 @@ struct DevJob {
     double dt, threshold;
     float dt_f, threshold_f;
     long long *step;          // steps taken (device counter)
-    unsigned *gen;            // fused launches taken (device counter; tags the node tiles' ready flags)
-    unsigned *ntflag;         // per node tile of 256 nodes: gen + 1 of the fused launch that wrote it
+    unsigned *gen;            // fused launches taken (device counter)
+    unsigned *ntflag;         // per chunk of node tiles: node tiles completed over all fused launches
     DevGraph g;
     const void *xdiv;         // bidomain: intracellular flux of v_e, added to the diffusion term (else NULL)
     int integrator;           // EP_INTEGRATOR_FE or EP_INTEGRATOR_AB2 (non-gating variables)

@@ -330,22 +330,26 @@ __global__ void __launch_bounds__(T, MINB) cell_kernel(const DevJob *__restrict_
 // needs the values of a bounded range of that job's node tiles (the gather
 // indices of an RCM-numbered mesh are local), and the host orders the list
 // so that those node tiles come first, queued kFusedLookahead cell tiles
-// ahead. A block that finishes a node tile publishes it with a release store
-// of the launch's tag (gen + 1) into the tile's flag; a block that claims a
-// cell tile waits (acquire loads, bounded) until every flag of its range
-// carries the tag, then updates its cells, reading node values from L2. A
-// claimed node tile is always being worked on by a running block, so every
-// wait ends. The V^n a node tile reads is read again soon after by the cell
-// tiles of the same region, from L2. The last block to finish advances each
-// job's step and launch counters and re-arms the work counter.
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+// ahead. Node tiles are counted complete per chunk of kFusedChunk tiles: a
+// block that finishes a node tile adds one to its chunk's counter with
+// release semantics, so after g fused launches a chunk of k tiles holds
+// g k, and in launch g (the job's launch counter, read at the start) the
+// chunk is complete once it holds (g + 1) k. A block that claims a cell tile
+// polls the chunks of its range with relaxed loads (one lane each), then
+// acquires with one fence per lane, and reads node values from L2. A claimed
+// node tile is always being worked on by a running block, so every wait ends
+// (bounded all the same). The V^n a node tile reads is read again soon after
+// by the cell tiles of the same region, from L2. The last block to finish
+// advances each job's step and launch counters and re-arms the work counter.
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
     unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ unsigned long long global_timer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -372,24 +376,34 @@ __global__ void __launch_bounds__(T, MINB)
             const long long n = *J.step;
             const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
             R *vn = static_cast<R *>(J.vn);
-            for (int i = threadIdx.x; i < tl.count; i += T) {
-                const long long node = (long long)tl.start + i;
-                vn[node] = node_value<R>(J, V, node);
+            // two nodes per thread at a time, their gathers in flight together
+            for (int i = threadIdx.x; i < tl.count; i += 2 * T) {
+                const long long a = (long long)tl.start + i, b = a + T;
+                const bool hb = i + T < tl.count;
+                const R va = node_value<R>(J, V, a);
+                const R vb = hb ? node_value<R>(J, V, b) : R(0);
+                vn[a] = va;
+                if (hb) vn[b] = vb;
             }
             __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();
-                st_release(J.ntflag + (tl.start >> 8), *J.gen + 1u);
+                red_release_add(J.ntflag + ((tl.start / kNodeThreads) / kFusedChunk), 1u);
             }
         } else {
             const Tile tl = cell_tiles[wk.tile];
             const DevJob &J = jobs[tl.job];
             if (threadIdx.x < 32) {
                 const unsigned tag = *J.gen + 1u;
-                for (int k = wk.dep_lo + int(threadIdx.x); k <= wk.dep_hi; k += 32) {
-                    if (ld_acquire(J.ntflag + k) == tag) continue;
+                const int n_nt = int((J.n_nodes + kNodeThreads - 1) / kNodeThreads);
+                const int c0 = wk.dep_lo / kFusedChunk, c1 = wk.dep_hi / kFusedChunk;
+                bool polled = false;
+                for (int ch = c0 + int(threadIdx.x); ch <= c1; ch += 32) {
+                    const unsigned want = tag * unsigned(min(kFusedChunk, n_nt - ch * kFusedChunk));
+                    polled = true;
+                    if (ld_relaxed(J.ntflag + ch) >= want) continue;
                     const unsigned long long t0 = global_timer_ns();
-                    while (ld_acquire(J.ntflag + k) != tag) {
+                    while (ld_relaxed(J.ntflag + ch) < want) {
                         if (global_timer_ns() - t0 > kFusedWaitLimitNs) {
                             atomicOr(err, 2u);   // reported by ep_step / ep_check_finite; the tile goes on
                             break;
@@ -397,6 +411,7 @@ __global__ void __launch_bounds__(T, MINB)
                         __nanosleep(64);
                     }
                 }
+                if (polled) fence_acq_rel_gpu();   // acquire what the chunks' releases published
             }
             __syncthreads();
             for (int i = threadIdx.x; i < tl.count; i += T)
@@ -862,8 +877,9 @@ static cudaError_t cell_launch_variant(const StepLaunch &L, cudaStream_t s) {
                 return cudaGetLastError();
             }
         }
-        StepLaunch L0 = L;   // FP64, AB2 or 16-bit indices: the plain variant 0
+        StepLaunch L0 = L;   // FP64, AB2 or 16-bit indices: the plain variant 0, with its own grid
         L0.cell_variant = 0;
+        L0.cell_grid = L.cell_grid0;
         return cell_launch_variant<R>(L0, s);
     }
     switch (L.cell_variant) {
@@ -1087,6 +1103,7 @@ cudaError_t launch_step_noalloc(int precision, const DevJob &job, const Tile *no
     L.err = err;
     L.node_grid = std::max(1, std::min(n_node_tiles, sm_count * node_blocks_per_sm(precision)));
     L.cell_grid = std::max(1, std::min(n_cell_tiles, sm_count * cell_blocks_per_sm(precision, cell_variant)));
+    L.cell_grid0 = std::max(1, std::min(n_cell_tiles, sm_count * cell_blocks_per_sm(precision, 0)));
     for (long long it = 0; it < n_steps; ++it) {
         e = launch_step(precision, L, s);
         if (e != cudaSuccess) return e;

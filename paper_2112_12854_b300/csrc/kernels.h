@@ -15,6 +15,7 @@ struct StepLaunch {
     int n_cell_tiles;
     unsigned *done;            // device counter used to advance the step counters
     int node_grid, cell_grid;  // persistent grid sizes
+    int cell_grid0;            // the grid of variant 0 (what staged variants fall back to)
     int cell_variant;          // launch shape of the cell kernel (EP_CELL_VARIANTS)
     const Tile *graph_tiles;   // conduction-graph nodes of all jobs (none: n_graph_tiles = 0)
     int n_graph_tiles;
@@ -52,6 +53,7 @@ constexpr int kNumCellVariants = 10;
 constexpr int kStagedVariant = 6;
 constexpr int kFusedVariant = 8;
 constexpr int kFusedLookahead = 1024;   // cell tiles whose node tiles are queued ahead of them
+constexpr int kFusedChunk = 8;          // node tiles per completion counter of the fused step
 int cell_variant_threads(int variant);
 
 // One time step of every job in the table: node values, the conduction

@@ -129,6 +129,9 @@ class Server:
         self.clock, self.sleep = clock, sleep
         self.rank, self.world = rank, world
         self.log: list[dict] = []
+        self.unfinished: list[int] = []
+        self.unfinished_ages: list[float] = []
+        self.cut_s: float | None = None
         self.cancelled: set[int] = set()
 
     def cancel(self, rid: int):
@@ -220,28 +223,46 @@ class Server:
                                               V=V, act=act, error=err))
                     inflight.clear()               # finish() synchronised the stream
         finally:
+            t_cut = self.clock() - t0
             pool.shutdown(wait=True, cancel_futures=True)
             for r, job, _, _ in resident:          # stopped by the time limit: release, no result
                 self.b.finish(job, False)
             self.unfinished = [x[0].rid for x in resident] + [r.rid for r, _ in ready] + \
                               [r.rid for r, _ in preparing] + [r.rid for r in queue] + [r.rid for r in pending]
+            # age at the cut-off of every job that had arrived but not finished: a lower bound
+            # of its latency (the latency distribution is censored there)
+            arrived = [x[0] for x in resident] + [r for r, _ in ready] + [r for r, _ in preparing] + queue
+            self.unfinished_ages = [t_cut - r.arrival for r in arrived]
+            self.cut_s = t_cut
         return results
 
 
-def summarize(results: list[Result], wall_s: float, log: list[dict] | None = None) -> dict:
+def summarize(results: list[Result], wall_s: float, log: list[dict] | None = None,
+              unfinished_ages: list[float] | None = None) -> dict:
     """Completed-job throughput and latency percentiles; with the server log,
-    also the cell-updates/s the GPU executed (unfinished jobs included)."""
+    also the cell-updates/s the GPU executed (unfinished jobs included). With
+    the ages at the cut-off of the jobs that had arrived but not finished,
+    also the percentiles over every arrived job, each unfinished one counted
+    at its age: lower bounds of the true percentiles when the run was cut
+    off (a censored sample)."""
     ok = [r for r in results if r.error is None]
     lat = np.array([r.latency for r in ok]) if ok else np.zeros(0)
     work = float(sum(r.n_cells * r.n_steps for r in ok))
-    return {"completed": len(ok), "failed": len(results) - len(ok),
-            "cell_updates_per_s": work / wall_s if wall_s > 0 else 0.0,
-            "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
-            "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
-            "mean_latency_s": float(lat.mean()) if len(lat) else None,
-            "executed_cell_updates_per_s": (sum(x["steps"] * x["cells"] for x in log) / wall_s
-                                            if log and wall_s > 0 else None),
-            "errors": sorted({r.error for r in results if r.error})[:3]}
+    out = {"completed": len(ok), "failed": len(results) - len(ok),
+           "cell_updates_per_s": work / wall_s if wall_s > 0 else 0.0,
+           "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
+           "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
+           "mean_latency_s": float(lat.mean()) if len(lat) else None,
+           "executed_cell_updates_per_s": (sum(x["steps"] * x["cells"] for x in log) / wall_s
+                                           if log and wall_s > 0 else None),
+           "errors": sorted({r.error for r in results if r.error})[:3]}
+    if unfinished_ages is not None:
+        allv = np.concatenate([lat, np.asarray(unfinished_ages, float)])
+        out["censored"] = {"arrived_unfinished": len(unfinished_ages),
+                           "p50_latency_lower_bound_s": float(np.percentile(allv, 50)) if len(allv) else None,
+                           "p99_latency_lower_bound_s": float(np.percentile(allv, 99)) if len(allv) else None,
+                           "max_age_at_cutoff_s": float(max(unfinished_ages)) if unfinished_ages else None}
+    return out
 
 
 def poisson_arrivals(rate_per_s: float, duration_s: float, rng) -> np.ndarray:
