@@ -472,6 +472,19 @@ int ep_graph_write_state(ep_job *job, int32_t model, int32_t var, const double *
 int ep_graph_activation_times(ep_job *job, double *host_out, int64_t n);
 int ep_graph_info(const ep_job *job, int64_t *n_nodes, int32_t *substeps, int64_t *n_junctions);
 
+/* How a step advances the conduction graphs' diffusion substeps (Sec. 3.2:
+ * the vertex-based 1D FV, subcycled for explicit stability):
+ * EP_GRAPH_SUBSTEPS_LOCAL (the default) runs all substeps of a step in one
+ * launch, each block on a tile of 256 graph nodes and every node within
+ * `substeps` hops of it in shared memory (the tile's own values are exact:
+ * an error at the rim of the neighbourhood moves one hop per substep);
+ * EP_GRAPH_SUBSTEPS_LAUNCHES launches one pass over all graph nodes per
+ * substep. Both give bitwise identical results. A batch whose largest
+ * neighbourhood does not fit 48 KB of shared memory takes the launches. */
+#define EP_GRAPH_SUBSTEPS_LAUNCHES 0
+#define EP_GRAPH_SUBSTEPS_LOCAL 1
+int ep_set_graph_kernel(ep_context *ctx, int32_t mode);
+
 /* ---- bidomain (Eq. 1, Eqs. 5-6) -------------------------------------------
  * Settings of the elliptic solve (restarted GMRES, Sec. 3.2). A solve stops
  * when ||b - L_ie v_e|| <= max(tol ||b||, atol sqrt(n_cells)) (2-norms over

@@ -43,7 +43,7 @@ struct Plan {
     struct Group {
         int precision;
         int n_jobs;
-        DevBuf jobtab, node_tiles, cell_tiles, done, graph_tiles, work;
+        DevBuf jobtab, node_tiles, cell_tiles, done, graph_tiles, graph_sub_tiles, work;
         StepLaunch L;
     };
     std::vector<Group> groups;
@@ -80,6 +80,7 @@ struct ep_context {
     std::vector<std::unique_ptr<Plan>> plans;
     int sm_count = 148;
     int cell_variant[2] = {0, 0};   // launch shape of the cell kernel per precision (ep_autotune)
+    int graph_mode = EP_GRAPH_SUBSTEPS_LOCAL;   // ep_set_graph_kernel
     DevBuf err_word;                 // device word: a bounded wait in a step kernel gave up
     unsigned *err_host = nullptr;    // pinned copy of err_word, refreshed after each ep_step of staged kernels
 };
@@ -107,6 +108,7 @@ struct ep_job {
     std::unique_ptr<GraphPlan> gp;
     std::vector<DevBuf> gbufs;
     std::vector<Tile> graph_tiles;
+    int graph_lmax = 0;              // largest local slot count of the graph's tiles (one-launch substeps)
     const int *gperm_dev = nullptr;
     DevBuf graph_view;               // DevJob whose V/act/regions are the graph's (init, I/O)
     // bidomain (ep_bidomain_enable)
@@ -185,6 +187,7 @@ void free_plan(ep_context *ctx, Plan *p) {
         dfree(ctx, &g.cell_tiles);
         dfree(ctx, &g.done);
         dfree(ctx, &g.graph_tiles);
+        dfree(ctx, &g.graph_sub_tiles);
         dfree(ctx, &g.work);
     }
 }
@@ -319,6 +322,18 @@ int ep_context_destroy(ep_context *ctx) {
     if (ctx->capture) cudaStreamDestroy(ctx->capture);
     if (ctx->upload) cudaStreamDestroy(ctx->upload);
     delete ctx;
+    return EP_OK;
+}
+
+int ep_set_graph_kernel(ep_context *ctx, int32_t mode) {
+    if (!ctx) return EP_EINVAL;
+    if (mode != EP_GRAPH_SUBSTEPS_LAUNCHES && mode != EP_GRAPH_SUBSTEPS_LOCAL)
+        return fail(ctx, EP_EINVAL, "ep_set_graph_kernel: unknown mode");
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    ctx->graph_mode = mode;
+    for (auto &p : ctx->plans) free_plan(ctx, p.get());   // rebuilt with the new mode on next use
+    ctx->plans.clear();
     return EP_OK;
 }
 
@@ -739,6 +754,50 @@ int graph_apply(ep_job *job) {
         for (int64_t s = g.model_off[md]; s < g.model_off[md + 1]; s += kGraphThreads)
             job->graph_tiles.push_back(
                 Tile{0, md, int(s), int(std::min<int64_t>(kGraphThreads, g.model_off[md + 1] - s))});
+    // local tables of the one-launch substeps: each tile's nodes, then every node within
+    // `substeps` hops of them (breadth first), with the neighbours as local indices
+    {
+        std::vector<int> lt_ptr{0}, lcol, mark(size_t(std::max<int64_t>(n, 1)), -1), nodes;
+        std::vector<int2> lslot;
+        int lmax = 0;
+        for (const Tile &tl : job->graph_tiles) {
+            nodes.clear();
+            for (int i = 0; i < tl.count; ++i) {
+                nodes.push_back(tl.start + i);
+                mark[tl.start + i] = i;
+            }
+            size_t from = 0;
+            for (int hop = 0; hop < g.substeps; ++hop) {
+                const size_t to = nodes.size();
+                for (size_t q = from; q < to; ++q)
+                    for (int e = g.row[nodes[q]]; e < g.row[nodes[q] + 1]; ++e)
+                        if (mark[g.col[e]] < 0) {
+                            mark[g.col[e]] = int(nodes.size());
+                            nodes.push_back(g.col[e]);
+                        }
+                from = to;
+            }
+            for (int u : nodes) {
+                lslot.push_back(make_int2(u, int(lcol.size())));
+                for (int e = g.row[u]; e < g.row[u + 1]; ++e) lcol.push_back(mark[g.col[e]]);
+            }
+            for (int u : nodes) mark[u] = -1;
+            lt_ptr.push_back(int(lslot.size()));
+            lmax = std::max(lmax, int(nodes.size()));
+        }
+        if (lcol.empty()) lcol.push_back(-1);
+        if (lslot.empty()) lslot.push_back(make_int2(0, 0));
+        DevGraph &DG = job->dj.g;
+        if (!rc) rc = put(lt_ptr, &q), DG.lt_ptr = static_cast<const int *>(q);
+        if (!rc) rc = put(lslot, &q), DG.lslot = static_cast<const int2 *>(q);
+        if (!rc) rc = put(lcol, &q), DG.lcol = static_cast<const int *>(q);
+        if (rc) return rc;
+        DG.lmax = lmax;
+        job->graph_lmax = lmax;
+        e = cudaMemcpyAsync(job->dj_dev.p, &job->dj, sizeof(DevJob), cudaMemcpyHostToDevice, ctx->upload);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->upload);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph upload");
+    }
     job->version++;
     for (auto &b : job->gbufs) job->device_bytes += b.bytes;
     return EP_OK;
@@ -1032,8 +1091,9 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
     for (int i = 0; i < n; ++i) pl->versions.push_back(jobs[i]->version);
     for (int prec : {EP_FP32_MIXED, EP_FP64_PLAIN}) {
         std::vector<DevJob> tab;
-        std::vector<Tile> nt, ct, gt;
+        std::vector<Tile> nt, ct, gt, gst;
         std::vector<Work> wk;
+        int max_lmax = 0;
         int max_sub = 0, any_bido = 0, any_ab2 = 0, any_idx16 = 0;
         for (int i = 0; i < n; ++i) {
             if (jobs[i]->precision != prec) continue;
@@ -1049,8 +1109,13 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
                 pl->bido.push_back(jobs[i]);
             }
             if (jobs[i]->gp) {
-                for (Tile t : jobs[i]->graph_tiles) gt.push_back(Tile{jid, t.model, t.start, t.count});
+                int k = 0;
+                for (Tile t : jobs[i]->graph_tiles) {
+                    gt.push_back(Tile{jid, t.model, t.start, t.count});
+                    gst.push_back(Tile{jid, k++, t.start, t.count});
+                }
                 max_sub = std::max(max_sub, jobs[i]->gp->substeps);
+                max_lmax = std::max(max_lmax, jobs[i]->graph_lmax);
             }
         }
         if (tab.empty()) continue;
@@ -1095,6 +1160,11 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
             g.L.graph_tiles = static_cast<const Tile *>(g.graph_tiles.p);
             g.L.n_graph_tiles = int(gt.size());
             g.L.graph_substeps = max_sub;
+            if ((rc = upload(ctx, gst, &tmp, &p))) return rc;
+            g.graph_sub_tiles = tmp.back();
+            g.L.graph_sub_tiles = static_cast<const Tile *>(g.graph_sub_tiles.p);
+            g.L.graph_lmax = max_lmax;
+            g.L.graph_local = ctx->graph_mode == EP_GRAPH_SUBSTEPS_LOCAL;
             g.L.graph_grid = std::max(1, std::min<int>(int(gt.size()), ctx->sm_count * 4));
         }
         g.L.node_grid = std::max(1, std::min<int>(int(nt.size()), ctx->sm_count * node_blocks_per_sm(prec)));

@@ -62,6 +62,15 @@ struct DevGraph {
     int n_tgt;
     int two_way;
     int cell_nodes;             // some junction is a cell-to-cell communication node
+    // local tables of the one-launch substeps (graph_substeps_kernel): graph tile t
+    // works on local slots [lt_ptr[t], lt_ptr[t+1]) -- its own nodes first, then every
+    // node within `substeps` hops -- slot = (graph node, offset of its neighbours'
+    // local indices in lcol, -1 for a neighbour outside the tile's set)
+    const int *lt_ptr;
+    const int2 *lslot;
+    const int *lcol;
+    int lmax;                   // largest slot count of a tile
+    int pad_g;
     double g_graph, g_cell, threshold, delay_ortho, delay_anti, amplitude, duration, h;
     float g_graph_f, g_cell_f, amplitude_f, h_f;
 };

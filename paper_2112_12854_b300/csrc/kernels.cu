@@ -141,12 +141,14 @@ __device__ __forceinline__ CellSrc<R> global_src(const DevJob &J, int model, lon
                       region_io<R>(rg, c - rg.off)};
 }
 
-// Node value k for the cell update: through L1 when the node values were
-// written by an earlier launch; from L2 (ld.global.cg) in the fused kernel,
-// where other blocks of the same launch write them.
+// Node value k for the cell update. In the fused kernel, where other warps
+// of the same launch write the node values, the loads are plain weak loads
+// (ld.global.ca), never the non-coherent read-only path: they follow the
+// warp's acquire of the node tiles, and a line of node values is first
+// loaded in a launch only after its tile is complete.
 template <class R, bool CG>
 __device__ __forceinline__ R node_at(const R *vn, int k) {
-    if constexpr (CG) return __ldcg(vn + k);
+    if constexpr (CG) return __ldca(vn + k);
     else return vn[k];
 }
 
@@ -296,6 +298,80 @@ __global__ void __launch_bounds__(kGraphThreads) graph_diffuse_kernel(const DevJ
     }
 }
 
+// Conduction graph, part 2, all substeps in one launch: each block takes a
+// graph tile and its nodes' neighbourhood up to the job's substep count in
+// hops (host tables), runs every substep in shared memory -- the values of
+// the tile's own nodes stay exact, since an error at the rim of the
+// neighbourhood travels one hop per substep -- and writes the tile's
+// V^{n+1}, activation times and junction crossings. Per node the arithmetic
+// and its order are those of graph_diffuse_kernel, so the results are the
+// same bit for bit, with one launch per step instead of one per substep.
+template <class R>
+__global__ void __launch_bounds__(kGraphThreads) graph_substeps_kernel(const DevJob *__restrict__ jobs,
+                                                                       const Tile *__restrict__ tiles, int n_tiles,
+                                                                       int n_sub, int lmax) {
+    extern __shared__ __align__(16) unsigned char gsm[];
+    R *const wa = reinterpret_cast<R *>(gsm);
+    R *const wb = wa + lmax;
+    R *const it = wb + lmax;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        const DevJob &J = jobs[tl.job];
+        const DevGraph &G = J.g;
+        const long long n = *J.step;
+        const int s0 = G.lt_ptr[tl.model], L = G.lt_ptr[tl.model + 1] - s0;
+        const R *Vin = static_cast<const R *>(G.V[n & 1]);
+        const R *itot = static_cast<const R *>(G.itot);
+        const R *cf = static_cast<const R *>(G.coef);
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            const int u = G.lslot[s0 + i].x;
+            wa[i] = Vin[u];
+            it[i] = itot[u];
+        }
+        __syncthreads();
+        R *cur = wa, *nxt = wb;
+        for (int s = 0; s < n_sub; ++s) {
+            for (int i = threadIdx.x; i < L; i += blockDim.x) {
+                const R w = cur[i];
+                R out = w;
+                if (s < G.substeps) {
+                    const int2 sl = G.lslot[s0 + i];
+                    R lap = R(0);
+                    for (int e = G.row[sl.x], k = sl.y; e < G.row[sl.x + 1]; ++e, ++k) {
+                        const int j = G.lcol[k];
+                        lap += cf[e] * ((j >= 0 ? cur[j] : w) - w);   // -1: beyond the rim, never read by the tile
+                    }
+                    out = w + pick<R>(G.h, G.h_f) * (lap - it[i]);
+                }
+                nxt[i] = out;
+            }
+            __syncthreads();
+            R *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+        for (int i = threadIdx.x; i < tl.count; i += blockDim.x) {
+            const long long node = (long long)tl.start + i;
+            const R out = cur[i];
+            static_cast<R *>(G.V[(n & 1) ^ 1])[node] = out;
+            const R v0 = Vin[node];
+            const R th = pick<R>(J.threshold, J.threshold_f);
+            if (v0 < th && out >= th) {
+                R *act = static_cast<R *>(G.act);
+                if (isinf(act[node])) act[node] = R(double(n) * J.dt) + pick<R>(J.dt, J.dt_f) * (th - v0) / (out - v0);
+            }
+            const double gth = G.threshold;
+            if (double(v0) < gth && double(out) >= gth)
+                for (int k = G.node_junc_ptr[node]; k < G.node_junc_ptr[node + 1]; ++k) {
+                    const int j = G.node_junc[k];
+                    if (G.jmode[j] == EP_PMJ_TRIGGERED)
+                        G.t_graph[j] = double(n) * J.dt + J.dt * (gth - double(v0)) / (double(out) - double(v0));
+                }
+        }
+        __syncthreads();   // the shared arrays are refilled for the next tile
+    }
+}
+
 // Launch-shape variants of the cell kernel, chosen by ep_autotune: threads
 // per block and the minimum number of resident blocks per SM requested from
 // the register allocator. All variants run the same per-cell arithmetic, so
@@ -326,7 +402,7 @@ __global__ void __launch_bounds__(T, MINB) cell_kernel(const DevJob *__restrict_
 // ---------------------------------------------------------------------------
 // Fused step: the node values (S1) and the cell update of every job in ONE
 // persistent launch. The launch works through a list of node tiles and cell
-// tiles (Work), claimed in order from a device counter. A cell tile of a job
+// tiles (Work), claimed in order from a device counter by each warp. A cell tile of a job
 // needs the values of a bounded range of that job's node tiles (the gather
 // indices of an RCM-numbered mesh are local), and the host orders the list
 // so that those node tiles come first, queued kFusedLookahead cell tiles
@@ -334,11 +410,10 @@ __global__ void __launch_bounds__(T, MINB) cell_kernel(const DevJob *__restrict_
 // block that finishes a node tile adds one to its chunk's counter with
 // release semantics, so after g fused launches a chunk of k tiles holds
 // g k, and in launch g (the job's launch counter, read at the start) the
-// chunk is complete once it holds (g + 1) k. A block that claims a cell tile
+// chunk is complete once it holds (g + 1) k. A warp that claims a cell tile
 // polls the chunks of its range with relaxed loads (one lane each), then
-// acquires with one fence per lane, and reads node values from L2. A claimed
-// node tile is always being worked on by a running block, so every wait ends
-// (bounded all the same). The V^n a node tile reads is read again soon after
+// acquires with one fence per lane, then reads the node values. Every wait
+// ends (see the kernel), and is bounded all the same. The V^n a node tile reads is read again soon after
 // by the cell tiles of the same region, from L2. The last block to finish
 // advances each job's step and launch counters and re-arms the work counter.
 __device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
@@ -362,13 +437,20 @@ __global__ void __launch_bounds__(T, MINB)
     fused_kernel(const DevJob *__restrict__ jobs, const Tile *__restrict__ node_tiles,
                  const Tile *__restrict__ cell_tiles, const Work *__restrict__ work, int n_work, unsigned *head,
                  unsigned *done, int n_jobs, unsigned *err) {
-    __shared__ int item_sh;
-    for (;;) {
-        if (threadIdx.x == 0) item_sh = int(atomicAdd(head, 1u));
-        __syncthreads();
-        const int it = item_sh;
-        __syncthreads();   // item_sh is written again at the next claim
-        if (it >= n_work) break;
+    // Every warp claims and works through whole items on its own (no block
+    // barrier per item), and claims its next item before working on the
+    // current one, so the claim's latency overlaps the work. A warp's items
+    // are in increasing list order, so the oldest claimed, unfinished item is
+    // always being worked on and its wait (if a cell tile) is on finished
+    // node tiles: every wait ends.
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int next = 0;
+    if (lane == 0) next = int(atomicAdd(head, 1u));
+    next = __shfl_sync(full, next, 0);
+    while (next < n_work) {
+        const int it = next;
+        if (lane == 0) next = int(atomicAdd(head, 1u));
         const Work wk = work[it];
         if (wk.tile < 0) {
             const Tile tl = node_tiles[-1 - wk.tile];
@@ -376,49 +458,48 @@ __global__ void __launch_bounds__(T, MINB)
             const long long n = *J.step;
             const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
             R *vn = static_cast<R *>(J.vn);
-            // two nodes per thread at a time, their gathers in flight together
-            for (int i = threadIdx.x; i < tl.count; i += 2 * T) {
-                const long long a = (long long)tl.start + i, b = a + T;
-                const bool hb = i + T < tl.count;
+            // two nodes per lane at a time, their gathers in flight together
+            for (int i = lane; i < tl.count; i += 64) {
+                const long long a = (long long)tl.start + i, b = a + 32;
+                const bool hb = i + 32 < tl.count;
                 const R va = node_value<R>(J, V, a);
                 const R vb = hb ? node_value<R>(J, V, b) : R(0);
                 vn[a] = va;
                 if (hb) vn[b] = vb;
             }
-            __syncthreads();
-            if (threadIdx.x == 0) {
+            __syncwarp();
+            if (lane == 0) {
                 __threadfence();
                 red_release_add(J.ntflag + ((tl.start / kNodeThreads) / kFusedChunk), 1u);
             }
         } else {
             const Tile tl = cell_tiles[wk.tile];
             const DevJob &J = jobs[tl.job];
-            if (threadIdx.x < 32) {
-                const unsigned tag = *J.gen + 1u;
-                const int n_nt = int((J.n_nodes + kNodeThreads - 1) / kNodeThreads);
-                const int c0 = wk.dep_lo / kFusedChunk, c1 = wk.dep_hi / kFusedChunk;
-                bool polled = false;
-                for (int ch = c0 + int(threadIdx.x); ch <= c1; ch += 32) {
-                    const unsigned want = tag * unsigned(min(kFusedChunk, n_nt - ch * kFusedChunk));
-                    polled = true;
-                    if (ld_relaxed(J.ntflag + ch) >= want) continue;
-                    const unsigned long long t0 = global_timer_ns();
-                    while (ld_relaxed(J.ntflag + ch) < want) {
-                        if (global_timer_ns() - t0 > kFusedWaitLimitNs) {
-                            atomicOr(err, 2u);   // reported by ep_step / ep_check_finite; the tile goes on
-                            break;
-                        }
-                        __nanosleep(64);
+            const unsigned tag = *J.gen + 1u;
+            const int n_nt = int((J.n_nodes + kNodeThreads - 1) / kNodeThreads);
+            const int c0 = wk.dep_lo / kFusedChunk, c1 = wk.dep_hi / kFusedChunk;
+            bool polled = false;
+            for (int ch = c0 + lane; ch <= c1; ch += 32) {
+                const unsigned want = tag * unsigned(min(kFusedChunk, n_nt - ch * kFusedChunk));
+                polled = true;
+                if (ld_relaxed(J.ntflag + ch) >= want) continue;
+                const unsigned long long t0 = global_timer_ns();
+                while (ld_relaxed(J.ntflag + ch) < want) {
+                    if (global_timer_ns() - t0 > kFusedWaitLimitNs) {
+                        atomicOr(err, 2u);   // reported by ep_step / ep_check_finite; the tile goes on
+                        break;
                     }
+                    __nanosleep(64);
                 }
-                if (polled) fence_acq_rel_gpu();   // acquire what the chunks' releases published
             }
-            __syncthreads();
-            for (int i = threadIdx.x; i < tl.count; i += T)
+            if (polled) fence_acq_rel_gpu();   // acquire what the chunks' releases published
+            __syncwarp();
+            for (int i = lane; i < tl.count; i += 32)
                 cell_update<R, XD, AB2, true>(J, tl.model, (long long)tl.start + i);
         }
+        next = __shfl_sync(full, next, 0);
     }
-    // Every block has read the counters; the last one to finish advances them.
+    // Every warp has read the counters; the last block to finish advances them.
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -738,9 +819,15 @@ template <class R>
 static cudaError_t graph_impl(const StepLaunch &L, cudaStream_t s) {
     if (L.n_graph_tiles > 0) {
         graph_ionic_kernel<R><<<L.graph_grid, kGraphThreads, 0, s>>>(L.jobs, L.graph_tiles, L.n_graph_tiles);
-        for (int k = 0; k < L.graph_substeps; ++k)
-            graph_diffuse_kernel<R><<<L.graph_grid, kGraphThreads, 0, s>>>(L.jobs, L.graph_tiles, L.n_graph_tiles, k,
-                                                                           k == L.graph_substeps - 1);
+        if (L.graph_local && 3 * size_t(L.graph_lmax) * sizeof(R) <= kGraphLocalMaxBytes) {
+            graph_substeps_kernel<R><<<L.graph_grid, kGraphThreads, 3 * size_t(L.graph_lmax) * sizeof(R), s>>>(
+                L.jobs, L.graph_sub_tiles, L.n_graph_tiles, L.graph_substeps, L.graph_lmax);
+        } else {
+            for (int k = 0; k < L.graph_substeps; ++k)
+                graph_diffuse_kernel<R><<<L.graph_grid, kGraphThreads, 0, s>>>(L.jobs, L.graph_tiles,
+                                                                               L.n_graph_tiles, k,
+                                                                               k == L.graph_substeps - 1);
+        }
     }
     return cudaGetLastError();
 }

@@ -21,6 +21,9 @@ struct StepLaunch {
     int n_graph_tiles;
     int graph_grid;
     int graph_substeps;        // largest substep count of the jobs' graphs
+    const Tile *graph_sub_tiles;   // graph tiles with the job-local tile index in Tile::model
+    int graph_local;           // all substeps in one launch per tile (graph_substeps_kernel)
+    int graph_lmax;            // largest local slot count over the jobs' graph tiles
     int bido;                  // some job is bidomain (cell kernel adds DevJob::xdiv)
     int ab2;                   // some job integrates by AB2 (cell kernel keeps rate histories)
     int idx16;                 // some job stores 16-bit gather indices (the staged variants need 32-bit)
@@ -52,7 +55,7 @@ struct StepLaunch {
 constexpr int kNumCellVariants = 10;
 constexpr int kStagedVariant = 6;
 constexpr int kFusedVariant = 8;
-constexpr int kFusedLookahead = 1024;   // cell tiles whose node tiles are queued ahead of them
+constexpr int kFusedLookahead = 8192;   // cell tiles whose node tiles are queued ahead of them
 constexpr int kFusedChunk = 8;          // node tiles per completion counter of the fused step
 int cell_variant_threads(int variant);
 
@@ -60,6 +63,12 @@ int cell_variant_threads(int variant);
 // graphs (reaction, then the diffusion substeps), then the fused diffusion +
 // cell-model + activation update.
 cudaError_t launch_step(int precision, const StepLaunch &L, cudaStream_t s);
+
+// Graph substep modes: one launch per substep over all graph nodes, or all
+// substeps of a step in one launch, each tile on its own nodes and their
+// neighbourhood in shared memory (when three arrays of graph_lmax values fit
+// kGraphLocalMaxBytes; else the batch takes one launch per substep).
+constexpr size_t kGraphLocalMaxBytes = 48 * 1024;
 
 // Set the state of every cell to its model's resting state, activation
 // times to +inf (job given by a device pointer to its DevJob).

@@ -84,6 +84,7 @@ ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 
 # every symbol declared in include/ep.h
+EP_GRAPH_SUBSTEPS_LAUNCHES, EP_GRAPH_SUBSTEPS_LOCAL = 0, 1
 NOALLOC_MAX_NODES = 2097152
 NOALLOC_MAX_CELLS = 16777216
 
@@ -96,7 +97,7 @@ EXPORTS = ["ep_context_create", "ep_context_set_stream", "ep_context_destroy", "
            "ep_plan_info", "ep_plan_destroy", "ep_job_create", "ep_graph_attach", "ep_graph_read_state",
            "ep_graph_write_state", "ep_graph_activation_times", "ep_graph_info", "ep_alu_peaks",
            "ep_bidomain_enable", "ep_bidomain_disable", "ep_bidomain_read_ve", "ep_bidomain_write_ve",
-           "ep_bidomain_stats", "ep_clear_error"]
+           "ep_bidomain_stats", "ep_clear_error", "ep_set_graph_kernel"]
 
 _lib = None
 _P = ctypes.c_void_p
@@ -127,6 +128,7 @@ def load():
         "ep_set_step_index": ([_P, _I64], ctypes.c_int),
         "ep_check_finite": ([_P], ctypes.c_int),
         "ep_clear_error": ([_P], ctypes.c_int),
+        "ep_set_graph_kernel": ([_P, ctypes.c_int32], ctypes.c_int),
         "ep_job_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                          ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
                         ctypes.c_int),
@@ -220,6 +222,11 @@ class Context:
     def check(self, rc):
         if rc:
             raise EPError(rc, load().ep_last_error(self._h).decode())
+
+    def set_graph_kernel(self, mode: int):
+        """EP_GRAPH_SUBSTEPS_LOCAL (one launch for all substeps, the default) or
+        EP_GRAPH_SUBSTEPS_LAUNCHES (one launch per substep)."""
+        self.check(load().ep_set_graph_kernel(self._h, int(mode)))
 
     def clear_error(self):
         """Forget a step kernel's bounded wait that gave up (ep_clear_error)."""

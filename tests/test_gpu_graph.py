@@ -154,3 +154,49 @@ def test_graph_jobs_batched_bitwise(ctx):
         assert np.array_equal(j.graph_read(0, model=1), alone.graph_read(0, model=1))
     for j in (alone, a1, a2, other):
         j.destroy()
+
+
+@pytest.mark.parametrize("pname", PRECISIONS)
+def test_graph_substeps_one_launch_equals_launches(pname):
+    """All diffusion substeps of a step in one launch (each block on a tile
+    of graph nodes and its neighbourhood in shared memory) give bitwise the
+    results of one launch per substep: the quarter-scale whole heart with its
+    conduction system (trees, bundles, resistive and triggered junctions),
+    batched with a branched-tree slab job whose graph has a different
+    substep count, over 3000 steps (the front through the graph and into the
+    ventricles)."""
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2112_12854_b300 import ep
+    prec = _prec(pname)
+    case, g = w.whole_heart(h=w.heart_h_for_cells(25000, 0.25), scale=0.25, n_tree=1500, n_pmj=150)
+    node_model = np.array([ps.model for ps in case.param_sets], np.uint8)[g.param_set]
+    rng = np.random.default_rng(3)
+    xyz, edges, ends = _tree(rng)
+    slab = _slab(dt=0.01, stim=True)
+    c = w.tet_centroids(slab.xyz, slab.tets)
+    sm = np.zeros(len(xyz), np.uint8)
+    sm[:6] = 1
+    jn = np.array(ends[1:4], np.int32)
+    jc = np.array([int(np.argmin(np.linalg.norm(c - xyz[e], axis=1))) for e in jn], np.int32)
+    tg = w.Graph(xyz, edges, np.ones(len(xyz), np.uint8), sm, jn, jc, np.full(3, w.JUNC_RESISTIVE, np.uint8),
+                 w.GraphParams(g_cell=4.0))
+    out = []
+    for mode in (ep.EP_GRAPH_SUBSTEPS_LAUNCHES, ep.EP_GRAPH_SUBSTEPS_LOCAL):
+        ctx = ep.Context()
+        ctx.set_graph_kernel(mode)
+        a = ep.job_from_case(ctx, case, precision=prec)
+        a.attach_graph(g, node_model=node_model)
+        b = ep.job_from_case(ctx, slab, precision=prec)
+        b.attach_graph(tg, node_model=np.full(len(xyz), 2, np.uint8))
+        assert a.graph_info()["substeps"] != b.graph_info()["substeps"]
+        ep.step([a, b], 3000)
+        res = []
+        for j in (a, b):
+            res += [j.V, j.activation_times(), j.graph_activation_times()]
+            res += [j.graph_read(k, model=m) for m in (1, 2) for k in range(len(ep.model_varnames(m)))]
+        out.append(res)
+        ctx.close()
+    for x, y in zip(*out):
+        assert np.array_equal(x, y, equal_nan=True)
+    assert np.isfinite(out[0][2]).any()
