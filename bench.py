@@ -299,20 +299,29 @@ def run_heart(ctx, args, stream, torch):
     job.attach_graph(g, node_model=node_model)
     gi = job.graph_info()
     ep.autotune([job], 2)
-    job.step(5)
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    job.step(args.heart_steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.heart_steps
-    node_graph_ms, cell_ms = ep.time_kernels([job], 20)
+    modes = {}
+    # the graph's diffusion substeps: one launch per substep, then all substeps in one launch
+    # (the library default); the same steps, bitwise the same results
+    for name, mode in (("launch_per_substep", ep.EP_GRAPH_SUBSTEPS_LAUNCHES),
+                       ("one_launch", ep.EP_GRAPH_SUBSTEPS_LOCAL)):
+        ctx.set_graph_kernel(mode)
+        job.step(5)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        job.step(args.heart_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.heart_steps
+        node_graph_ms, cell_ms = ep.time_kernels([job], 20)
+        modes[name] = {"ms_per_step": ms, "node_and_graph_kernels_ms": node_graph_ms, "cell_kernel_ms": cell_ms}
     job.destroy()
+    ms = modes["one_launch"]["ms_per_step"]
     return {"cells": case.n_cells, "graph_nodes": gi["n_nodes"], "junctions": gi["n_junctions"],
             "graph_substeps": gi["substeps"], "steps": args.heart_steps, "ms_per_step": ms,
             "cell_updates_per_s": case.n_cells / (ms * 1e-3),
-            "node_and_graph_kernels_ms": node_graph_ms, "cell_kernel_ms": cell_ms}
+            "node_and_graph_kernels_ms": modes["one_launch"]["node_and_graph_kernels_ms"],
+            "cell_kernel_ms": modes["one_launch"]["cell_kernel_ms"], "graph_substep_modes": modes}
 
 
 def run_bidomain(ctx, args, dims, stream, torch, peak):

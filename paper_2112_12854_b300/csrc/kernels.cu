@@ -52,7 +52,9 @@ __device__ __forceinline__ R stimulus(const DevJob &J, unsigned mask, long long 
     return is;
 }
 
-template <class R>
+// F: the form of the batch's node -> cell entries (0 all 32-bit, 1 all
+// 16-bit, 2 mixed), so that a uniform batch compiles one form only.
+template <class R, int F>
 __global__ void __launch_bounds__(kNodeThreads) node_kernel(const DevJob *__restrict__ jobs,
                                                             const Tile *__restrict__ tiles, int n_tiles) {
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
@@ -63,8 +65,14 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const DevJob *__rest
         const long long node = (long long)tl.start + i;
         const long long n = *J.step;
         const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
-        static_cast<R *>(J.vn)[node] = node_value<R>(J, V, node);
+        static_cast<R *>(J.vn)[node] = node_value<R, 6, F>(J, V, node);
     }
+}
+
+template <class R>
+static void launch_node_kernel(const StepLaunch &L, cudaStream_t s) {
+    auto *k = L.node_form == 0 ? node_kernel<R, 0> : (L.node_form == 1 ? node_kernel<R, 1> : node_kernel<R, 2>);
+    k<<<L.node_grid, kNodeThreads, 0, s>>>(L.jobs, L.node_tiles, L.n_node_tiles);
 }
 
 __device__ __forceinline__ bool window_on(double t_trig, double delay, double dur, double t) {
@@ -839,8 +847,7 @@ cudaError_t launch_graph(int precision, const StepLaunch &L, cudaStream_t s) {
 template <class R>
 static cudaError_t step_impl(const StepLaunch &L, cudaStream_t s) {
     // the conduction graphs read no node values: with the fused variants they run first
-    if (L.cell_variant < kFusedVariant)
-        node_kernel<R><<<L.node_grid, kNodeThreads, 0, s>>>(L.jobs, L.node_tiles, L.n_node_tiles);
+    if (L.cell_variant < kFusedVariant) launch_node_kernel<R>(L, s);
     graph_impl<R>(L, s);
     return launch_cell(sizeof(R) == 8 ? EP_FP64_PLAIN : EP_FP32_MIXED, L, s);
 }
@@ -891,10 +898,8 @@ cudaError_t launch_reset_act(int precision, const DevJob *job, long long n_cells
 
 cudaError_t launch_node(int precision, const StepLaunch &L, cudaStream_t s) {
     if (L.cell_variant >= kFusedVariant) return cudaSuccess;   // the fused launch computes the node values
-    if (precision == EP_FP64_PLAIN)
-        node_kernel<double><<<L.node_grid, kNodeThreads, 0, s>>>(L.jobs, L.node_tiles, L.n_node_tiles);
-    else
-        node_kernel<float><<<L.node_grid, kNodeThreads, 0, s>>>(L.jobs, L.node_tiles, L.n_node_tiles);
+    if (precision == EP_FP64_PLAIN) launch_node_kernel<double>(L, s);
+    else launch_node_kernel<float>(L, s);
     return cudaGetLastError();
 }
 
@@ -1049,9 +1054,9 @@ int cell_blocks_per_sm(int precision, int variant) {
 int node_blocks_per_sm(int precision) {
     int nb = 0;
     if (precision == EP_FP64_PLAIN)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, node_kernel<double>, kNodeThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, node_kernel<double, 2>, kNodeThreads, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, node_kernel<float>, kNodeThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, node_kernel<float, 2>, kNodeThreads, 0);
     return nb < 1 ? 1 : nb;
 }
 
@@ -1187,6 +1192,7 @@ cudaError_t launch_step_noalloc(int precision, const DevJob &job, const Tile *no
     L.n_work = n_work;
     L.cell_variant = cell_variant;
     L.idx16 = job.idx16;
+    L.node_form = job.col16;
     L.err = err;
     L.node_grid = std::max(1, std::min(n_node_tiles, sm_count * node_blocks_per_sm(precision)));
     L.cell_grid = std::max(1, std::min(n_cell_tiles, sm_count * cell_blocks_per_sm(precision, cell_variant)));

@@ -7,14 +7,36 @@
 namespace ep {
 
 // Inverse-distance node value (S1) over the sliced-ELL entries b, b+32, ...
-// < e of one node; the cell of entry k is base + col[k]. The loads of D
-// entries are issued before their products are accumulated, so D gathers
-// are in flight at once (D = 6: an interior node of a Kuhn mesh has 24
-// cells, four groups; the fastest of 4, 6, 8 and 12 on the B300); the sum
-// is still taken in entry order.
-template <class R, int D = 6, class C>
-__device__ __forceinline__ R node_sum(const R *__restrict__ w, const C *__restrict__ col, int base,
-                                      const R *__restrict__ V, long long b, long long e) {
+// < e of one node (32-bit cell indices col). The loads of D entries are
+// issued before their products are accumulated, so D gathers are in flight
+// at once (D = 6: an interior node of a Kuhn mesh has 24 cells, four groups;
+// the fastest of 4, 6, 8 and 12 on the B300); the sum is still taken in
+// entry order.
+template <class R, int D = 6>
+__device__ __forceinline__ R node_sum(const R *__restrict__ w, const int *__restrict__ col, const R *__restrict__ V,
+                                      long long b, long long e) {
+    R acc = R(0);
+    long long k = b;
+    for (; k + 32 * (D - 1) < e; k += 32 * D) {
+        int c[D];
+        R wk[D], v[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) c[i] = col[k + 32 * i];
+#pragma unroll
+        for (int i = 0; i < D; ++i) wk[i] = w[k + 32 * i];
+#pragma unroll
+        for (int i = 0; i < D; ++i) v[i] = V[c[i]];
+#pragma unroll
+        for (int i = 0; i < D; ++i) acc += wk[i] * v[i];
+    }
+    for (; k < e; k += 32) acc += w[k] * V[col[k]];
+    return acc;
+}
+
+// The same over 16-bit entries: the cell of entry k is base + col[k].
+template <class R, int D = 6>
+__device__ __forceinline__ R node_sum16(const R *__restrict__ w, const unsigned short *__restrict__ col, int base,
+                                        const R *__restrict__ V, long long b, long long e) {
     R acc = R(0);
     long long k = b;
     for (; k + 32 * (D - 1) < e; k += 32 * D) {
@@ -33,14 +55,15 @@ __device__ __forceinline__ R node_sum(const R *__restrict__ w, const C *__restri
     return acc;
 }
 
-// S1 at one node of a job, in the job's index form.
-template <class R, int D = 6>
+// S1 at one node of a job. F: the form of the job's node -> cell entries --
+// 0 32-bit, 1 16-bit, 2 either (read from the job).
+template <class R, int D = 6, int F = 2>
 __device__ __forceinline__ R node_value(const DevJob &J, const R *__restrict__ V, long long node) {
     const R *__restrict__ w = static_cast<const R *>(J.nw);
     const long long s = node >> 5;
     const long long b = J.slice_ptr[s] + (node & 31), e = J.slice_ptr[s + 1];
-    if (J.col16) return node_sum<R, D>(w, J.ncol16, J.cbase[s], V, b, e);
-    return node_sum<R, D>(w, J.ncol, 0, V, b, e);
+    if (F == 1 || (F == 2 && J.col16)) return node_sum16<R, D>(w, J.ncol16, J.cbase[s], V, b, e);
+    return node_sum<R, D>(w, J.ncol, V, b, e);
 }
 
 // The gather indices of cell c: its vertices (na), the vertex of the
