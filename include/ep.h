@@ -117,17 +117,19 @@ typedef void (*ep_free_fn)(void *ptr, size_t bytes, void *user);
  * stimulus protocol k covers the cell, or NULL for none. fibre: 3 doubles
  * per cell, the fibre direction (need not be normalised; a triangle's
  * conductivity acts in its plane), or NULL for isotropic tissue with
- * diffusivity D_l. index_width: 0 (the default) stores the step's gather
- * indices as 16-bit offsets where the library's cell and node numbering
- * allows it, else as 32-bit indices -- the cells' indices (a cell's
- * neighbours within 32767 cells of it and the nodes of each run of 256
- * cells within a window of 65536: meshes whose reverse Cuthill-McKee
- * bandwidth is below about 3 x 10^4 cells, e.g. the 9.6M-cell wedge) and
- * the node -> cell entries (the cells of each run of 32 nodes within a
- * window of 65536, which spans about six RCM levels: smaller meshes)
- * independently; 32 always stores 32-bit indices. Both forms give bitwise
- * identical results; the 16-bit forms move 24 fewer bytes per cell and 2 per
- * node -> cell entry and step. */
+ * diffusivity D_l. index_width: how the step's gather indices are stored,
+ * as 32-bit indices or as 16-bit offsets (bitwise identical results):
+ *   - 0 (the default): the cells' indices as 16-bit offsets where the
+ *     library's numbering allows it (a cell's neighbours within 32767 cells
+ *     of it and the nodes of each run of 256 cells within a window of 65536:
+ *     meshes whose reverse Cuthill-McKee bandwidth is below about 3 x 10^4
+ *     cells, e.g. the 9.6M-cell wedge), 24 bytes per cell and step fewer;
+ *     the node -> cell entries as 32-bit indices;
+ *   - 16: also the node -> cell entries as 16-bit offsets where they fit
+ *     (the cells of each run of 32 nodes within a window of 65536, which
+ *     spans about six RCM levels: smaller meshes), 2 bytes per entry fewer,
+ *     though the node pass measured slower than with 32-bit entries;
+ *   - 32: every index 32-bit. */
 typedef struct {
     int64_t n_nodes;
     const double *xyz;

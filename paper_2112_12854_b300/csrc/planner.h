@@ -25,7 +25,7 @@ struct HostMesh {
     int64_t n_interior_faces = 0;
     std::vector<int64_t> n2c_ptr;     // node -> incident cells (internal numbering, sorted)
     std::vector<int32_t> n2c;
-    int index_width = 0;              // ep_mesh_desc::index_width (0: 16-bit where it fits; 32: 32-bit)
+    int index_width = 0;              // ep_mesh_desc::index_width (0 automatic, 16, 32)
 };
 
 // Validate, orient, match faces, renumber (RCM, grouped by model).

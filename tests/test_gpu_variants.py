@@ -116,23 +116,26 @@ def _state(j):
 
 @pytest.mark.parametrize("pname", ["mixed", "plain"])
 def test_index_widths_bitwise_identical(pname):
-    """The gather indices stored as 16-bit offsets (the default where they
-    fit) and as 32-bit indices (ep_mesh_desc.index_width = 32) give bitwise
-    the same state, each alone and the two batched together (TP06 /
-    Courtemanche / Stewart regions, two stimuli, 1638 cells: several tiles,
-    ragged tails)."""
+    """The gather indices stored as 16-bit offsets (cell gathers and node
+    table: index_width 16), as the default mix (16-bit cell gathers, 32-bit
+    node table) and as 32-bit indices (index_width 32) give bitwise the same
+    state, each alone and batched together -- a batch of mixed node-table
+    forms takes the node kernel that reads both (TP06 / Courtemanche /
+    Stewart regions, two stimuli, 1638 cells: several tiles, ragged
+    tails)."""
     import torch
     assert torch.cuda.is_available()
     from paper_2112_12854_b300 import ep
     prec = ep.EP_FP32_MIXED if pname == "mixed" else ep.EP_FP64_PLAIN
     case = _three_model_case()
     ctx = ep.Context()
-    a16 = ep.job_from_case(ctx, case, precision=prec)
+    a16 = ep.job_from_case(ctx, case, precision=prec, index_width=16)
     a32 = ep.job_from_case(ctx, case, precision=prec, index_width=32)
-    b16 = ep.job_from_case(ctx, case, precision=prec)
-    b32 = ep.job_from_case(ctx, case, precision=prec, index_width=32)
+    b16 = ep.job_from_case(ctx, case, precision=prec, index_width=16)
+    b32 = ep.job_from_case(ctx, case, precision=prec)                 # the default: 16-bit cells only
     assert a16.info()["index_width"] == 16 and a32.info()["index_width"] == 32
     assert a16.info()["node_index_width"] == 16 and a32.info()["node_index_width"] == 32
+    assert (b32.info()["index_width"], b32.info()["node_index_width"]) == (16, 32)
     assert a16.info()["device_bytes"] < a32.info()["device_bytes"]
     a16.step(300)
     a32.step(300)
@@ -153,7 +156,7 @@ def test_index_widths_bitwise_identical_bidomain():
     from paper_2112_12854_b300 import ep
     case = w.slab_case(nx=12, ny=8, nz=3, h=0.25)
     ctx = ep.Context()
-    jobs = [ep.job_from_case(ctx, case, index_width=iw) for iw in (0, 32)]
+    jobs = [ep.job_from_case(ctx, case, index_width=iw) for iw in (16, 32)]
     for j in jobs:
         j.enable_bidomain(0.62 / 1.4, 0.24 / 1.4)
         j.step(80)

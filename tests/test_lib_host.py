@@ -264,7 +264,8 @@ def _coned_sphere(levels):
 
 
 def test_index_width_chosen_by_the_numbering():
-    """16-bit gather indices where every offset fits (a slab); on a
+    """By default 16-bit cell gathers and a 32-bit node -> cell table; with
+    index_width 16 both 16-bit where every offset fits (a slab); on a
     150 x 150 x 30-cube wedge (4.05M cells, RCM neighbour bandwidth about
     12.5k cells) 16-bit cell gathers but 32-bit node -> cell entries (the
     cells around one node span about six RCM levels, 75k cells); 32-bit
@@ -274,18 +275,20 @@ def test_index_width_chosen_by_the_numbering():
     params = ep.make_params(0.01, [w.ParamSet()])
     case = w.slab_case(nx=20, ny=10, nz=4, h=0.5)
     p = ep.Plan(case.xyz, case.tets, params)
+    assert (p.index_width, p.node_index_width) == (16, 32)          # the default: 16-bit cell gathers
+    p = ep.Plan(case.xyz, case.tets, params, index_width=16)
     assert (p.index_width, p.node_index_width) == (16, 16)
     p = ep.Plan(case.xyz, case.tets, params, index_width=32)
     assert (p.index_width, p.node_index_width) == (32, 32)
     xyz, tets = _coned_sphere(7)            # (no parameters: only the mesh is planned)
     assert tets.shape[0] == 131072
-    p = ep.Plan(xyz, tets)
+    p = ep.Plan(xyz, tets, index_width=16)
     assert (p.index_width, p.node_index_width) == (32, 32)
     wedge = w.wedge_case(nx=150, ny=150, nz=30, h=0.25)
-    p = ep.Plan(wedge.xyz, wedge.tets)
+    p = ep.Plan(wedge.xyz, wedge.tets, index_width=16)
     assert (p.index_width, p.node_index_width) == (16, 32)
-    p = ep.Plan(*_coned_sphere(5))
+    p = ep.Plan(*_coned_sphere(5), index_width=16)
     assert (p.index_width, p.node_index_width) == (16, 16)
     with pytest.raises(ep.EPError) as e:
-        ep.Plan(case.xyz, case.tets, params, index_width=16)
+        ep.Plan(case.xyz, case.tets, params, index_width=8)
     assert e.value.code == ep.EP_EINVAL
