@@ -57,3 +57,27 @@ def test_allocation_failure_leaves_other_jobs_intact():
     a.destroy()
     ctx.close()
     assert not state["live"]                  # everything handed out was returned
+
+
+@pytest.mark.parametrize("variant", [6, 8])
+def test_clear_error_on_a_healthy_context(variant):
+    """The recovery path of a step kernel's bounded wait, exercised without
+    making a wait run out: on a context whose staged (6) or fused (8) step
+    variant reads its error word back after every ep_step, ep_clear_error
+    synchronises and re-arms it, and the job then steps on exactly as an
+    uninterrupted one."""
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2112_12854_b300 import ep
+    case = w.slab_case(nx=10, ny=6, nz=3, h=0.5)
+    ctx = ep.Context()
+    ep.set_cell_variant(ctx, ep.EP_FP32_MIXED, variant)
+    a = ep.job_from_case(ctx, case, index_width=32)      # the staged variants read 32-bit indices
+    a.step(100)
+    assert a.check_finite()
+    ctx.clear_error()
+    a.step(100)
+    b = ep.job_from_case(ctx, case, index_width=32)
+    b.step(200)
+    assert np.array_equal(a.V, b.V) and a.check_finite()
+    ctx.close()
