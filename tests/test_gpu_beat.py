@@ -6,9 +6,13 @@ every 5 ms, the activation map, and every state variable at the end.
   - the 16 x 16 x 4-cube TP06 epicardial slab (6144 cells, 20000 steps);
   - a crop of the benchmark wedge's construction, 50 x 50 x 10 cubes of
     0.25 mm (150,000 cells: TP06 endo / M / epi by depth thirds, fibres
-    rotating -60..+60 deg, corner stimulus), 20000 steps.
+    rotating -60..+60 deg, corner stimulus), 20000 steps;
+  - on request (about 20 minutes), the wedge's 1/8-volume crop, 100 x 100 x
+    20 cubes (1.2M cells), 20000 steps.
 
 The error statistics of every result are printed (run with -s to see them)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -94,3 +98,15 @@ def test_wedge_crop_150k_cells_full_beat():
     case = w.wedge_case(nx=50, ny=50, nz=10, h=0.25, n_steps=BEAT_STEPS)
     assert case.n_cells == 150_000
     _beat(case, "wedge crop 150k")
+
+
+@pytest.mark.skipif(os.environ.get("EP_LONG_GPU_TESTS") != "1",
+                    reason="about 20 minutes (the oracle's 2.4e10 cell-updates on the host cores); "
+                           "set EP_LONG_GPU_TESTS=1 to run")
+def test_wedge_crop_1p2m_cells_full_beat():
+    """The 1/8-volume crop of the benchmark wedge (100 x 100 x 20 cubes,
+    1.2M cells) run in full by the oracle, the FP64 plain GPU step and the
+    FP32 step: a whole 400 ms beat, every cell every 5 ms."""
+    case = w.wedge_case(nx=100, ny=100, nz=20, h=0.25, n_steps=BEAT_STEPS)
+    assert case.n_cells == 1_200_000
+    _beat(case, "wedge crop 1.2M")
