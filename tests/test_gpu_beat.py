@@ -55,16 +55,19 @@ def _beat(case, label):
     print(f"{label}: V at 400 ms between {ref.min():.1f} and {ref.max():.1f} mV "
           f"({np.mean(ref < -70.0):.1%} of cells below -70 mV)")
     out = {}
+    failures = []
     for name, j in jobs.items():
         p = precs[name]
         _, ta = tolerances(p)
         e = np.concatenate(errs[name])
         ea = act_error(j.activation_times(), a)
-        assert ea <= ta, (label, name, ea)
-        # state variables at 400 ms relative to their largest magnitude: FP64 to
-        # rounding; FP32 within 1 % (the slow gates' Rush-Larsen steps change
-        # them by dt/tau ~ 1e-5 of their value per step, near FP32 resolution)
-        rel_tol = 1e-9 if name == "plain" else 1e-2
+        if ea > ta:
+            failures.append((label, name, "activation", ea))
+        # state variables at 400 ms, max |d| relative to the variable's largest magnitude on the
+        # mesh: FP64 to rounding; FP32 within 1 % (the slow gates' Rush-Larsen steps change them by
+        # dt/tau ~ 1e-5 of their value per step, near FP32 resolution) or within 1e-6 absolute (a
+        # gate near zero at rest, e.g. TP06 r ~ 1e-8, whose relative error says nothing)
+        rel_tol, abs_tol = (1e-9, 0.0) if name == "plain" else (1e-2, 1e-6)
         var_err = {}
         models = sorted({int(ps.model) for ps in case.param_sets})
         for m in models:
@@ -74,9 +77,11 @@ def _beat(case, label):
                 r = o.get(v)
                 g = j.read(v, model=m)
                 sel = np.isfinite(g)
-                rel = float(np.abs(g[sel] - r[sel]).max() / np.abs(r[sel]).max())
+                d = float(np.abs(g[sel] - r[sel]).max())
+                rel = d / float(np.abs(r[sel]).max())
                 var_err[vname] = rel
-                assert rel <= rel_tol, (label, name, vname, rel)
+                if rel > rel_tol and d > abs_tol:
+                    failures.append((label, name, vname, rel, d))
         out[name] = var_err
         worst = sorted(var_err.items(), key=lambda kv: -kv[1])[:3]
         print(f"{label} {name}: |dV| over {BEAT_STEPS // EVERY} outputs x {case.n_cells} cells: "
@@ -85,6 +90,7 @@ def _beat(case, label):
               f"worst state variables (max|d|/max|ref| at 400 ms): "
               + ", ".join(f"{n} {x:.1e}" for n, x in worst))
         j.destroy()
+    assert not failures, failures
     ctx.close()
     return out
 
