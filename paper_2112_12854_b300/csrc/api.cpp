@@ -1094,7 +1094,7 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
         std::vector<Tile> nt, ct, gt, gst;
         std::vector<Work> wk;
         int max_lmax = 0;
-        int max_sub = 0, any_bido = 0, any_ab2 = 0, any_idx16 = 0, n_col16 = 0;
+        int max_sub = 0, any_bido = 0, any_ab2 = 0, any_idx16 = 0, n_col16 = 0, models = 0;
         for (int i = 0; i < n; ++i) {
             if (jobs[i]->precision != prec) continue;
             const int jid = int(tab.size());
@@ -1105,6 +1105,8 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
             if (jobs[i]->params.integrator == EP_INTEGRATOR_AB2) any_ab2 = 1;
             if (jobs[i]->dj.idx16) any_idx16 = 1;
             if (jobs[i]->dj.col16) ++n_col16;
+            for (int m = 0; m < EP_N_MODELS; ++m)
+                if (jobs[i]->mesh().model_off[m + 1] > jobs[i]->mesh().model_off[m]) models |= 1 << m;
             if (jobs[i]->bido) {
                 any_bido = 1;
                 pl->bido.push_back(jobs[i]);
@@ -1155,6 +1157,7 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
         g.L.ab2 = any_ab2;
         g.L.idx16 = any_idx16;
         g.L.node_form = n_col16 == 0 ? 0 : (n_col16 == g.n_jobs ? 1 : 2);
+        g.L.models = models;
         g.L.err = static_cast<unsigned *>(ctx->err_word.p);
         if (!gt.empty()) {
             if ((rc = upload(ctx, gt, &tmp, &p))) return rc;

@@ -164,7 +164,9 @@ __device__ __forceinline__ R node_at(const R *vn, int k) {
 // of Eq. 6) to the diffusion term; AB2: the batch holds jobs that advance the
 // non-gating variables by second-order Adams-Bashforth. Batches without them
 // compile without the code. CG: the node values come from the same launch.
-template <class R, bool XD = false, bool AB2 = false, bool CG = false>
+// MODELS: the cell models a batch holds (bit m for model m); a batch of TP06
+// cells only compiles TP06 alone, whose register demand is lower.
+template <class R, bool XD = false, bool AB2 = false, bool CG = false, int MODELS = 7>
 __device__ __forceinline__ void cell_update_from(const DevJob &J, int model, long long c, long long n, const R *V,
                                                  const CellSrc<R> &src) {
     using R4 = typename Vec4T<R>::type;
@@ -201,9 +203,13 @@ __device__ __forceinline__ void cell_update_from(const DevJob &J, int model, lon
             rt.on = n > J.ab2_from;
         }
     }
-    if (model == EP_TP06) iion = tt_step<R, false, AB2>(src.io, P, Vc, dt, is, rt);
-    else if (model == EP_STEWART) iion = tt_step<R, true, AB2>(src.io, P, Vc, dt, is, rt);
-    else iion = crn_step<R, AB2>(src.io, P, Vc, dt, rt);
+    if constexpr (MODELS == (1 << EP_TP06)) {
+        iion = tt_step<R, false, AB2>(src.io, P, Vc, dt, is, rt);
+    } else {
+        if (model == EP_TP06) iion = tt_step<R, false, AB2>(src.io, P, Vc, dt, is, rt);
+        else if (model == EP_STEWART) iion = tt_step<R, true, AB2>(src.io, P, Vc, dt, is, rt);
+        else iion = crn_step<R, AB2>(src.io, P, Vc, dt, rt);
+    }
     const R Vn = Vc + dt * rt(0, diff - iion - is - ix);
     Vnext[c] = Vn;
     if ((ps & kJunctionFlag) && (J.g.two_way || J.g.cell_nodes)) junction_cell_crossing<R>(J, c, n, Vc, Vn, jfirst, jlast);
@@ -214,11 +220,11 @@ __device__ __forceinline__ void cell_update_from(const DevJob &J, int model, lon
     }
 }
 
-template <class R, bool XD = false, bool AB2 = false, bool CG = false>
+template <class R, bool XD = false, bool AB2 = false, bool CG = false, int MODELS = 7>
 __device__ __forceinline__ void cell_update(const DevJob &J, int model, long long c) {
     const long long n = *J.step;
     const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
-    cell_update_from<R, XD, AB2, CG>(J, model, c, n, V, global_src<R>(J, model, c, V));
+    cell_update_from<R, XD, AB2, CG, MODELS>(J, model, c, n, V, global_src<R>(J, model, c, V));
 }
 
 // Conduction graph, part 1 (Sec. 3.2 / 3.3): the reaction of every graph node
@@ -385,14 +391,14 @@ __global__ void __launch_bounds__(kGraphThreads) graph_substeps_kernel(const Dev
 // the register allocator. All variants run the same per-cell arithmetic, so
 // their results are bitwise identical. Tiles hold kCellThreads cells; a
 // block narrower than a tile walks it in strides of its width.
-template <class R, int T, int MINB, bool XD, bool AB2>
+template <class R, int T, int MINB, bool XD, bool AB2, int MODELS = 7>
 __global__ void __launch_bounds__(T, MINB) cell_kernel(const DevJob *__restrict__ jobs,
                                                         const Tile *__restrict__ tiles, int n_tiles,
                                                         unsigned *done, int n_jobs) {
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const Tile tl = tiles[t];
         for (int i = threadIdx.x; i < tl.count; i += T)
-            cell_update<R, XD, AB2>(jobs[tl.job], tl.model, (long long)tl.start + i);
+            cell_update<R, XD, AB2, false, MODELS>(jobs[tl.job], tl.model, (long long)tl.start + i);
     }
     // Every block has read the step counters; the last one to finish advances them.
     __syncthreads();
@@ -906,7 +912,9 @@ cudaError_t launch_node(int precision, const StepLaunch &L, cudaStream_t s) {
 template <class R, int T, int B>
 static void launch_cell_kernel(const StepLaunch &L, cudaStream_t s) {
     auto *k = L.bido ? (L.ab2 ? cell_kernel<R, T, B, true, true> : cell_kernel<R, T, B, true, false>)
-                     : (L.ab2 ? cell_kernel<R, T, B, false, true> : cell_kernel<R, T, B, false, false>);
+                     : (L.ab2 ? cell_kernel<R, T, B, false, true>
+                              : (L.models == (1 << EP_TP06) ? cell_kernel<R, T, B, false, false, 1 << EP_TP06>
+                                                            : cell_kernel<R, T, B, false, false>));
     k<<<L.cell_grid, T, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done, L.n_jobs);
 }
 
@@ -1193,6 +1201,9 @@ cudaError_t launch_step_noalloc(int precision, const DevJob &job, const Tile *no
     L.cell_variant = cell_variant;
     L.idx16 = job.idx16;
     L.node_form = job.col16;
+    L.models = 0;
+    for (int m = 0; m < EP_N_MODELS; ++m)
+        if (job.reg[m].n > 0) L.models |= 1 << m;
     L.err = err;
     L.node_grid = std::max(1, std::min(n_node_tiles, sm_count * node_blocks_per_sm(precision)));
     L.cell_grid = std::max(1, std::min(n_cell_tiles, sm_count * cell_blocks_per_sm(precision, cell_variant)));

@@ -28,6 +28,7 @@ struct StepLaunch {
     int ab2;                   // some job integrates by AB2 (cell kernel keeps rate histories)
     int idx16;                 // some job stores 16-bit gather indices (the staged variants need 32-bit)
     int node_form;             // node -> cell entries of the batch: 0 all 32-bit, 1 all 16-bit, 2 mixed
+    int models;                // cell models of the batch's cells, bit m for model m
     unsigned *err;             // device error word of the context (bounded waits that gave up)
     const Work *work;          // fused variants: node and cell tiles in dependency order
     int n_work;
