@@ -204,15 +204,13 @@ def run_reference(args):
     import oracle
     case = wedge_case(CROP)
     s = oracle.Sim(case)
-    # The host threads take a few hundred milliseconds of work to reach their steady speed
-    # (measured on the GPU machine: 8.1 ms per step over 20 steps after 5 warm-up steps, 5.9 ms
-    # over 200): spin them up on a throwaway copy of the workload for 1 s, untimed, so that
-    # the timed steps measure the oracle, not the spin-up.
-    spin = oracle.Sim(case)
+    # A fresh simulation takes about a second of steps to reach its steady speed on the host
+    # cores (measured on the GPU machine: 8.1-8.5 ms per step over the 20 steps after 5 warm-up
+    # steps, 5.9 ms over 200, also after a second of steps on another simulation): run it
+    # for 1 s untimed first, so that the timed steps measure the oracle, not the ramp.
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < 1.0:
-        spin.run(1)
-    del spin
+        s.run(1)
     for _ in range(args.warmup):
         s.run(1)
     t0 = time.perf_counter()
@@ -223,7 +221,7 @@ def run_reference(args):
     val = case.n_cells * args.steps / el
     sample = (f"oracle (FP64 C, OpenMP) on a crop of the wedge workload: {CROP['nx']}x{CROP['ny']}x{CROP['nz']} "
               f"cubes x 6 = {case.n_cells} cells, one time step per bench step, after 1 s of untimed "
-              f"spin-up on a copy and the warm-up steps")
+              f"steps and the warm-up steps")
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
