@@ -382,9 +382,10 @@ int ep_plan_inspect(const ep_mesh_desc *desc, const ep_params *params, int64_t *
  * context's allocator) are the inputs and outputs. Everything else the step
  * needs -- a copy of the job's descriptor, its tile tables, a ticket counter
  * and the node values -- lives in one static device array of the library
- * (about 17.3 MiB: EP_NOALLOC_MAX_NODES doubles of node values plus the tile
- * tables of EP_NOALLOC_MAX_CELLS cells), held by every GPU that loads the
- * library until the process exits; the descriptor and tiles are copied in
+ * (about 18.3 MiB: EP_NOALLOC_MAX_NODES doubles of node values plus the tile
+ * tables and the fused step's work list of EP_NOALLOC_MAX_CELLS cells), held
+ * by every GPU that loads the library until the process exits; the
+ * descriptor, tiles and work list are copied in
  * from host memory on every call. The step then runs the same kernels as
  * ep_step (in the context's current launch shape, no graph replay), so the
  * results equal ep_step's bit for bit.
