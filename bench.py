@@ -65,8 +65,8 @@ SURVEY_STEP_FLOOR = 277
 SURVEY_CELL_FLOOR = 277 - 32
 
 
-# launch-shape variants from this one on do the whole step in one launch (ep_autotune)
-FUSED_VARIANT = 8
+# launch-shape variants that do the whole step in one launch (ep_autotune)
+FUSED_VARIANTS = (8, 9)
 
 
 def wedge_case(dims):
@@ -648,7 +648,7 @@ def main():
                           "index_width": iw,
                           "parallelism": f"replicas x{world}", "graph_replay": True},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-               "gpu_launches": (1 if int(chosen[0]) >= FUSED_VARIANT else 2) * args.steps, "fp64_plain": fp64,
+               "gpu_launches": (1 if int(chosen[0]) in FUSED_VARIANTS else 2) * args.steps, "fp64_plain": fp64,
                "alu_peaks": {"fp32_fma_tflops": alu["fp32_fma_flops"] / 1e12,
                              "mufu_ex2_tops": alu["mufu_ex2_ops"] / 1e12,
                              "fp64_fma_tflops": alu["fp64_fma_flops"] / 1e12,

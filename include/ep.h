@@ -313,9 +313,13 @@ int ep_job_destroy(ep_job *job);
  * Synchronises. The results equal those of ep_step. */
 int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double *node_ms, double *cell_ms);
 
-/* Autotuner of the step's launch shape. Variants 0-5: threads per block and
- * resident blocks per SM of the cell kernel, after its own node-value
- * launch; variants 6 and 7: the staged FP32 cell kernel, whose streamed
+/* Autotuner of the step's launch shape. Variants 0-5, 10 and 11: threads
+ * per block and resident blocks per SM of the cell kernel, after its own
+ * node-value launch (256 x 2, 256 x 3, 128 x 4, 128 x 5, 128 x 6, 64 x 12,
+ * 128 x 7, 128 x 8; the block count caps the registers per thread); an
+ * FP32 group of one forward-Euler monodomain job runs these shapes, and its
+ * node-value launch, with the job's descriptor passed as a kernel
+ * parameter, read from the constant bank; variants 6 and 7: the staged FP32 cell kernel, whose streamed
  * inputs are brought into shared memory by bulk asynchronous copies,
  * double-buffered (6: all of them, two blocks per SM; 7: indices,
  * coefficients, V and bytes, three blocks per SM), for jobs with 32-bit
@@ -325,7 +329,7 @@ int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double
  * 3), node tiles and cell tiles taken in dependency order with bounded
  * waits on per-tile ready flags (a wait that gives up sets the context's
  * error word, reported as EP_ETIMEOUT by ep_step and ep_check_finite).
- * Advances the jobs by 10 * steps_per_variant real time steps, timing each
+ * Advances the jobs by 12 * steps_per_variant real time steps, timing each
  * variant's whole step (node values, conduction graphs, cell update) with
  * CUDA events, and keeps the fastest variant per precision for every later
  * ep_step of the context. The variants compute the same arithmetic; TP06
@@ -333,7 +337,7 @@ int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double
  * differ in the last bits between the register-limited shapes and the
  * others. chosen[2] (may be NULL) receives the variant picked for
  * EP_FP32_MIXED and EP_FP64_PLAIN (-1 if no job of that precision);
- * variant_ms[2 * 10] (may be NULL) the mean step time per variant.
+ * variant_ms[2 * 12] (may be NULL) the mean step time per variant.
  * Synchronises. */
 int ep_autotune(ep_job *const *jobs, int32_t n_jobs, int32_t steps_per_variant, int32_t *chosen,
                 double *variant_ms);
@@ -349,7 +353,7 @@ int ep_autotune(ep_job *const *jobs, int32_t n_jobs, int32_t steps_per_variant, 
  * synchronises. */
 int ep_alu_peaks(ep_context *ctx, double *out);
 
-/* Force the step's launch-shape variant (0..9, see ep_autotune) for one
+/* Force the step's launch-shape variant (0..11, see ep_autotune) for one
  * precision. */
 int ep_set_cell_variant(ep_context *ctx, int32_t precision, int32_t variant);
 

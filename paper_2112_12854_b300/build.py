@@ -9,6 +9,7 @@ machine without a GPU.
 from __future__ import annotations
 
 import argparse
+import concurrent.futures
 import os
 import shutil
 import subprocess
@@ -52,13 +53,18 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     if verbose:
         cmd_common += ["-Xptxas", "-v"]
     cmd_common += list(extra or [])
-    objs = []
+    jobs = []
     for src in sources():
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
         cmd = cmd_common + FILE_FLAGS.get(os.path.basename(src), []) + ["-c", src, "-o", obj]
         if src.endswith(".cpp"):
             cmd = cmd_common + ["-x", "cu", "-c", src, "-o", obj]
-        r = subprocess.run(cmd, capture_output=True, text=True)
+        jobs.append((src, obj, cmd))
+    # the translation units compile independently: run them side by side
+    with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+        results = list(ex.map(lambda j: subprocess.run(j[2], capture_output=True, text=True), jobs))
+    objs = []
+    for (src, obj, _), r in zip(jobs, results):
         if r.returncode != 0 or verbose:
             sys.stderr.write(r.stderr)
         if r.returncode != 0:

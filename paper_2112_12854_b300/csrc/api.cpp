@@ -45,6 +45,7 @@ struct Plan {
         int n_jobs;
         DevBuf jobtab, node_tiles, cell_tiles, done, graph_tiles, graph_sub_tiles, work;
         StepLaunch L;
+        std::shared_ptr<DevJob> job0;   // host copy of a one-job group's descriptor (L.job0)
     };
     std::vector<Group> groups;
     std::vector<ep_job *> bido;   // jobs whose step ends with the elliptic solve
@@ -1094,7 +1095,7 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
         std::vector<Tile> nt, ct, gt, gst;
         std::vector<Work> wk;
         int max_lmax = 0;
-        int max_sub = 0, any_bido = 0, any_ab2 = 0, any_idx16 = 0, n_col16 = 0, models = 0;
+        int max_sub = 0, any_bido = 0, any_ab2 = 0, n_idx16 = 0, n_col16 = 0, models = 0;
         for (int i = 0; i < n; ++i) {
             if (jobs[i]->precision != prec) continue;
             const int jid = int(tab.size());
@@ -1103,7 +1104,7 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
             for (Tile t : jobs[i]->node_tiles) nt.push_back(Tile{jid, t.model, t.start, t.count});
             for (Tile t : jobs[i]->cell_tiles) ct.push_back(Tile{jid, t.model, t.start, t.count});
             if (jobs[i]->params.integrator == EP_INTEGRATOR_AB2) any_ab2 = 1;
-            if (jobs[i]->dj.idx16) any_idx16 = 1;
+            if (jobs[i]->dj.idx16) ++n_idx16;
             if (jobs[i]->dj.col16) ++n_col16;
             for (int m = 0; m < EP_N_MODELS; ++m)
                 if (jobs[i]->mesh().model_off[m + 1] > jobs[i]->mesh().model_off[m]) models |= 1 << m;
@@ -1155,7 +1156,8 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
         g.L.graph_grid = 1;
         g.L.bido = any_bido;
         g.L.ab2 = any_ab2;
-        g.L.idx16 = any_idx16;
+        g.L.idx16 = n_idx16 > 0;
+        g.L.sm_count = ctx->sm_count;
         g.L.node_form = n_col16 == 0 ? 0 : (n_col16 == g.n_jobs ? 1 : 2);
         g.L.models = models;
         g.L.err = static_cast<unsigned *>(ctx->err_word.p);
@@ -1177,6 +1179,10 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
         g.L.cell_grid0 = std::max(1, std::min<int>(int(ct.size()), ctx->sm_count * cell_blocks_per_sm(prec, 0)));
         g.L.cell_grid =
             std::max(1, std::min<int>(int(ct.size()), ctx->sm_count * cell_blocks_per_sm(prec, g.L.cell_variant)));
+        if (g.n_jobs == 1) {
+            g.job0 = std::make_shared<DevJob>(tab[0]);
+            g.L.job0 = g.job0.get();
+        }
         pl->groups.push_back(g);
     }
     cudaError_t e = cudaStreamSynchronize(ctx->upload);
@@ -1257,7 +1263,8 @@ int ep_step(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps) {
         Plan *pl = nullptr;
         if ((rc = get_plan(ctx, jobs, n_jobs, &pl))) return rc;
         bool staged = false;   // staged or fused: kernels with bounded waits that report through the error word
-        for (auto &gr : pl->groups) staged = staged || gr.L.cell_variant >= kStagedVariant;
+        for (auto &gr : pl->groups)
+            staged = staged || is_staged_variant(gr.L.cell_variant) || is_fused_variant(gr.L.cell_variant);
         int64_t left = n_steps;
         if (n_steps >= kGraphMinSteps && pl->bido.empty()) {   // cooperative solves launch directly
             if (!pl->exec) {
@@ -1700,7 +1707,7 @@ int ep_step_noalloc(ep_job *job, int64_t n_steps) {
     DeviceGuard g(ctx->device);
     std::vector<Work> wk;
     const int variant = ctx->cell_variant[job->precision];
-    if (variant >= kFusedVariant) append_work(job, 0, 0, &wk);
+    if (is_fused_variant(variant)) append_work(job, 0, 0, &wk);
     cudaError_t e = launch_step_noalloc(job->precision, job->dj, job->node_tiles.data(), int(job->node_tiles.size()),
                                         job->cell_tiles.data(), int(job->cell_tiles.size()), wk.data(),
                                         int(wk.size()), variant, ctx->sm_count,

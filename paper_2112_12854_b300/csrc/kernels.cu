@@ -69,8 +69,31 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const DevJob *__rest
     }
 }
 
+// The same for an FP32 batch of one job, its descriptor a kernel parameter
+// (see cell_kernel_1j).
+template <class R, int F>
+__global__ void __launch_bounds__(kNodeThreads) node_kernel_1j(const __grid_constant__ DevJob J,
+                                                               const Tile *__restrict__ tiles, int n_tiles) {
+    const long long n = *J.step;
+    const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        const int i = threadIdx.x;
+        if (i >= tl.count) continue;
+        const long long node = (long long)tl.start + i;
+        static_cast<R *>(J.vn)[node] = node_value<R, 6, F>(J, V, node);
+    }
+}
+
 template <class R>
 static void launch_node_kernel(const StepLaunch &L, cudaStream_t s) {
+    if constexpr (std::is_same<R, float>::value) {
+        if (L.n_jobs == 1 && L.job0) {
+            auto *k1 = L.node_form == 1 ? node_kernel_1j<float, 1> : node_kernel_1j<float, 0>;
+            k1<<<L.node_grid, kNodeThreads, 0, s>>>(*L.job0, L.node_tiles, L.n_node_tiles);
+            return;
+        }
+    }
     auto *k = L.node_form == 0 ? node_kernel<R, 0> : (L.node_form == 1 ? node_kernel<R, 1> : node_kernel<R, 2>);
     k<<<L.node_grid, kNodeThreads, 0, s>>>(L.jobs, L.node_tiles, L.n_node_tiles);
 }
@@ -407,6 +430,39 @@ __global__ void __launch_bounds__(T, MINB) cell_kernel(const DevJob *__restrict_
         const unsigned prev = atomicAdd(done, 1u);
         if (prev == gridDim.x - 1) {
             for (int j = 0; j < n_jobs; ++j) *jobs[j].step += 1;
+            *done = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// Single-job cell kernel (an FP32 batch of one job, any cell_kernel shape):
+// the job's descriptor is a kernel parameter (__grid_constant__), so the
+// per-cell reads of its fields -- array bases, region strides, parameter
+// sets, stimulus protocols, dt -- come from the constant bank instead of the
+// L1 / L2 path of the streamed and gathered data, and hold no registers as
+// pointers; the step counter is read once per thread. Otherwise cell_kernel:
+// the same arithmetic, bitwise the same results.
+template <class R, int T, int MINB, bool XD, bool AB2, int MODELS = 7>
+__global__ void __launch_bounds__(T, MINB) cell_kernel_1j(const __grid_constant__ DevJob J,
+                                                           const Tile *__restrict__ tiles, int n_tiles,
+                                                           unsigned *done) {
+    const long long n = *J.step;
+    const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        for (int i = threadIdx.x; i < tl.count; i += T) {
+            const long long c = (long long)tl.start + i;
+            cell_update_from<R, XD, AB2, false, MODELS>(J, tl.model, c, n, V, global_src<R>(J, tl.model, c, V));
+        }
+    }
+    // Every block has read the step counter; the last one to finish advances it.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(done, 1u);
+        if (prev == gridDim.x - 1) {
+            *J.step += 1;
             *done = 0u;
             __threadfence();
         }
@@ -853,7 +909,7 @@ cudaError_t launch_graph(int precision, const StepLaunch &L, cudaStream_t s) {
 template <class R>
 static cudaError_t step_impl(const StepLaunch &L, cudaStream_t s) {
     // the conduction graphs read no node values: with the fused variants they run first
-    if (L.cell_variant < kFusedVariant) launch_node_kernel<R>(L, s);
+    if (!is_fused_variant(L.cell_variant)) launch_node_kernel<R>(L, s);
     graph_impl<R>(L, s);
     return launch_cell(sizeof(R) == 8 ? EP_FP64_PLAIN : EP_FP32_MIXED, L, s);
 }
@@ -903,7 +959,7 @@ cudaError_t launch_reset_act(int precision, const DevJob *job, long long n_cells
 }
 
 cudaError_t launch_node(int precision, const StepLaunch &L, cudaStream_t s) {
-    if (L.cell_variant >= kFusedVariant) return cudaSuccess;   // the fused launch computes the node values
+    if (is_fused_variant(L.cell_variant)) return cudaSuccess;   // the fused launch computes the node values
     if (precision == EP_FP64_PLAIN) launch_node_kernel<double>(L, s);
     else launch_node_kernel<float>(L, s);
     return cudaGetLastError();
@@ -911,6 +967,25 @@ cudaError_t launch_node(int precision, const StepLaunch &L, cudaStream_t s) {
 
 template <class R, int T, int B>
 static void launch_cell_kernel(const StepLaunch &L, cudaStream_t s) {
+    if constexpr (std::is_same<R, float>::value) {
+        // one FP32 job (forward Euler, monodomain): its descriptor as a kernel parameter. FP32 only:
+        // the FP64 step is bound by the FP64 pipe, and its compiled rounding must not depend on the kernel
+        if (L.n_jobs == 1 && L.job0 && !L.bido && !L.ab2) {
+            const bool tt = L.models == (1 << EP_TP06);
+            auto *k1 = tt ? cell_kernel_1j<float, T, B, false, false, 1 << EP_TP06>
+                          : cell_kernel_1j<float, T, B, false, false>;
+            static int per_sm[2] = {0, 0};   // resident blocks per SM of the two instances
+            int &nb = per_sm[tt ? 1 : 0];
+            if (nb == 0) {
+                int q = 0;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k1, T, 0);
+                nb = std::max(q, 1);
+            }
+            const int grid = L.sm_count > 0 ? std::max(1, std::min(L.n_cell_tiles, L.sm_count * nb)) : L.cell_grid;
+            k1<<<grid, T, 0, s>>>(*L.job0, L.cell_tiles, L.n_cell_tiles, L.done);
+            return;
+        }
+    }
     auto *k = L.bido ? (L.ab2 ? cell_kernel<R, T, B, true, true> : cell_kernel<R, T, B, true, false>)
                      : (L.ab2 ? cell_kernel<R, T, B, false, true>
                               : (L.models == (1 << EP_TP06) ? cell_kernel<R, T, B, false, false, 1 << EP_TP06>
@@ -954,7 +1029,7 @@ static void launch_fused_kernel(const StepLaunch &L, cudaStream_t s) {
 
 template <class R>
 static cudaError_t cell_launch_variant(const StepLaunch &L, cudaStream_t s) {
-    if (L.cell_variant >= kFusedVariant) {
+    if (is_fused_variant(L.cell_variant)) {
         switch (L.cell_variant) {
 #define EP_FUSED_CASE(k, T, B)                                                                                 \
     case k:                                                                                                    \
@@ -967,7 +1042,7 @@ static cudaError_t cell_launch_variant(const StepLaunch &L, cudaStream_t s) {
         }
         return cudaGetLastError();
     }
-    if (L.cell_variant >= kStagedVariant) {
+    if (is_staged_variant(L.cell_variant)) {
         if constexpr (std::is_same<R, float>::value) {
             if (!L.ab2 && !L.idx16) {
                 cudaError_t e = staged_attributes();
@@ -1002,7 +1077,7 @@ cudaError_t launch_cell(int precision, const StepLaunch &L, cudaStream_t s) {
 template <class R>
 static int cell_blocks_variant(int variant) {
     int nb = 0;
-    if (variant >= kFusedVariant) {
+    if (is_fused_variant(variant)) {
         switch (variant) {
 #define EP_FUSED_CASE(k, T, B)                                                                              \
     case k:                                                                                                 \
@@ -1013,7 +1088,7 @@ static int cell_blocks_variant(int variant) {
         }
         return nb < 1 ? 1 : nb;
     }
-    if (variant >= kStagedVariant) {
+    if (is_staged_variant(variant)) {
         if (std::is_same<R, float>::value && staged_attributes() == cudaSuccess) {
             if (variant == kStagedVariant)
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_kernel_staged<false, true>, kCellThreads,
@@ -1045,7 +1120,7 @@ int cell_variant_threads(int variant) {
         EP_FUSED_VARIANTS(EP_CELL_CASE)
 #undef EP_CELL_CASE
     }
-    return variant >= kStagedVariant && variant < kFusedVariant ? kCellThreads : 0;
+    return is_staged_variant(variant) ? kCellThreads : 0;
 }
 
 cudaError_t launch_check_finite(int precision, const DevJob *job, long long n_cells, unsigned *count,
@@ -1166,7 +1241,7 @@ cudaError_t launch_step_noalloc(int precision, const DevJob &job, const Tile *no
     if (job.n_nodes < 1 || job.n_nodes > EP_NOALLOC_MAX_NODES || job.n_cells < 1 ||
         job.n_cells > EP_NOALLOC_MAX_CELLS || n_node_tiles > int(kMaxNodeTiles) ||
         n_cell_tiles > int(kMaxCellTiles) || n_work > int(kMaxNodeTiles + kMaxCellTiles) ||
-        (cell_variant >= kFusedVariant && n_work != n_node_tiles + n_cell_tiles))
+        (is_fused_variant(cell_variant) && n_work != n_node_tiles + n_cell_tiles))
         return cudaErrorInvalidValue;
     void *base = nullptr;
     cudaError_t e = noalloc_scratch_address(&base);
@@ -1200,6 +1275,8 @@ cudaError_t launch_step_noalloc(int precision, const DevJob &job, const Tile *no
     L.n_work = n_work;
     L.cell_variant = cell_variant;
     L.idx16 = job.idx16;
+    L.sm_count = sm_count;
+    L.job0 = &dj;
     L.node_form = job.col16;
     L.models = 0;
     for (int m = 0; m < EP_N_MODELS; ++m)

@@ -27,23 +27,30 @@ struct StepLaunch {
     int bido;                  // some job is bidomain (cell kernel adds DevJob::xdiv)
     int ab2;                   // some job integrates by AB2 (cell kernel keeps rate histories)
     int idx16;                 // some job stores 16-bit gather indices (the staged variants need 32-bit)
+    int sm_count;              // SMs of the device (grid of the one-job cell kernel, sized by its own occupancy)
     int node_form;             // node -> cell entries of the batch: 0 all 32-bit, 1 all 16-bit, 2 mixed
     int models;                // cell models of the batch's cells, bit m for model m
     unsigned *err;             // device error word of the context (bounded waits that gave up)
+    const DevJob *job0;        // host copy of the descriptor of a one-job batch (else NULL)
     const Work *work;          // fused variants: node and cell tiles in dependency order
     int n_work;
     unsigned *head;            // fused variants: next work item (device counter)
 };
 
 // Launch shapes of the cell kernel: (index, threads per block, minimum
-// resident blocks per SM). Variant 0 is the default before autotuning.
+// resident blocks per SM, which caps the registers per thread). Variant 0 is
+// the default before autotuning. An FP32 batch of one job (forward Euler,
+// monodomain) runs these shapes as cell_kernel_1j, the job's descriptor a
+// kernel parameter.
 #define EP_CELL_VARIANTS(X) \
     X(0, 256, 2)            \
     X(1, 256, 3)            \
     X(2, 128, 4)            \
     X(3, 128, 5)            \
     X(4, 128, 6)            \
-    X(5, 64, 12)
+    X(5, 64, 12)            \
+    X(10, 128, 7)           \
+    X(11, 128, 8)
 // Variants 6 and 7: cell_kernel_staged (FP32 forward Euler, 32-bit indices,
 // 256 threads; streamed inputs staged by bulk copies: 6 everything, two
 // blocks per SM; 7 indices / coefficients / V / bytes, three blocks per SM);
@@ -54,9 +61,11 @@ struct StepLaunch {
 #define EP_FUSED_VARIANTS(X) \
     X(8, 128, 6)             \
     X(9, 256, 3)
-constexpr int kNumCellVariants = 10;
+constexpr int kNumCellVariants = 12;
 constexpr int kStagedVariant = 6;
 constexpr int kFusedVariant = 8;
+constexpr bool is_staged_variant(int v) { return v >= kStagedVariant && v < kFusedVariant; }
+constexpr bool is_fused_variant(int v) { return v >= kFusedVariant && v < kFusedVariant + 2; }
 constexpr int kFusedLookahead = 8192;   // cell tiles whose node tiles are queued ahead of them
 constexpr int kFusedChunk = 8;          // node tiles per completion counter of the fused step
 int cell_variant_threads(int variant);

@@ -66,21 +66,25 @@ __device__ __forceinline__ R node_value(const DevJob &J, const R *__restrict__ V
     return node_sum<R, D>(w, J.ncol, V, b, e);
 }
 
+// The 16-bit form of cell c's gather indices: u holds the eight node
+// offsets from base (its run's nbase), o the four neighbour offsets from c.
+__device__ __forceinline__ void decode_idx16(const uint4 u, int base, const uint2 o, long long c, int4 &na, int4 &nb,
+                                             int4 &nc) {
+    na = make_int4(base + int(u.x & 0xffffu), base + int(u.x >> 16), base + int(u.y & 0xffffu),
+                   base + int(u.y >> 16));
+    nb = make_int4(base + int(u.z & 0xffffu), base + int(u.z >> 16), base + int(u.w & 0xffffu),
+                   base + int(u.w >> 16));
+    const int ci = int(c);
+    // low halves sign-extended through a 16-bit signed value, high halves by an arithmetic shift
+    nc = make_int4(ci + int(short(o.x & 0xffffu)), ci + (int(o.x) >> 16), ci + int(short(o.y & 0xffffu)),
+                   ci + (int(o.y) >> 16));
+}
+
 // The gather indices of cell c: its vertices (na), the vertex of the
 // neighbour opposite each face (nb) and the neighbours (nc).
 __device__ __forceinline__ void cell_indices(const DevJob &J, long long c, int4 &na, int4 &nb, int4 &nc) {
     if (J.idx16) {
-        const uint4 u = J.cidx16[c];
-        const int base = J.nbase[c >> 8];
-        na = make_int4(base + int(u.x & 0xffffu), base + int(u.x >> 16), base + int(u.y & 0xffffu),
-                       base + int(u.y >> 16));
-        nb = make_int4(base + int(u.z & 0xffffu), base + int(u.z >> 16), base + int(u.w & 0xffffu),
-                       base + int(u.w >> 16));
-        const uint2 o = J.nbr16[c];
-        const int ci = int(c);
-        // low halves sign-extended through a 16-bit signed value, high halves by an arithmetic shift
-        nc = make_int4(ci + int(short(o.x & 0xffffu)), ci + (int(o.x) >> 16), ci + int(short(o.y & 0xffffu)),
-                       ci + (int(o.y) >> 16));
+        decode_idx16(J.cidx16[c], J.nbase[c >> 8], J.nbr16[c], c, na, nb, nc);
     } else {
         na = J.nodes_a[c];
         nb = J.nodes_b[c];

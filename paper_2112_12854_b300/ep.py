@@ -523,7 +523,7 @@ def step_noalloc(job, n_steps: int):
     job.ctx.check(load().ep_step_noalloc(job._h, int(n_steps)))
 
 
-N_CELL_VARIANTS = 10
+N_CELL_VARIANTS = 12
 
 
 def autotune(jobs, steps_per_variant: int = 10):

@@ -233,3 +233,35 @@ def test_fused_step_batched_equals_alone(variant):
             assert np.array_equal(a.read(k), b.read(k))
     assert np.array_equal(alone[-1].ve, batch[-1].ve)
     ctx.close()
+
+
+PLAIN_SHAPES = (0, 1, 2, 3, 4, 5, 10, 11)
+
+
+@pytest.mark.parametrize("three_models", [False, True])
+def test_one_job_kernels_equal_the_batched_kernels(three_models):
+    """An FP32 group of one job runs the node and cell kernels with the job's
+    descriptor as a kernel parameter (constant bank); a group of several
+    jobs reads the descriptors from the job table in global memory. For every
+    two-launch shape, a job stepped alone is bitwise the same job stepped in a
+    batch with another (TP06-only cells, and TP06 / Courtemanche / Stewart
+    regions with two stimuli, ragged tiles)."""
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2112_12854_b300 import ep
+    case = _three_model_case() if three_models else w.slab_case(nx=13, ny=9, nz=3, h=0.25, stim_x=0.6)
+    other = w.slab_case(nx=7, ny=5, nz=3, h=0.5)
+    ctx = ep.Context()
+    for v in PLAIN_SHAPES:
+        ep.set_cell_variant(ctx, ep.EP_FP32_MIXED, v)
+        alone = ep.job_from_case(ctx, case)
+        alone.step(250)
+        a = ep.job_from_case(ctx, case)
+        b = ep.job_from_case(ctx, other)
+        ep.step([a, b], 250)
+        for x, y in zip(_state(alone), _state(a)):
+            assert np.array_equal(x, y, equal_nan=True), v
+        assert np.isfinite(_state(alone)[-1]).any()
+        for j in (alone, a, b):
+            j.destroy()
+    ctx.close()
