@@ -22,7 +22,8 @@ LIB = os.path.join(HERE, "libep.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The kernels' FP32 arithmetic uses the hardware approximations (exp2/log2/rcp/rsqrt
 # units, flush-to-zero); FP64 code is unaffected by these flags.
-FILE_FLAGS = {"kernels.cu": ["--use_fast_math"]}
+# kernels_tab.cu and kernels_f64.cu hold instances of the same step code and take the same flags.
+FILE_FLAGS = {f: ["--use_fast_math"] for f in ("kernels.cu", "kernels_tab.cu", "kernels_f64.cu")}
 
 
 def nvcc() -> str:

@@ -45,7 +45,10 @@ struct Plan {
         int n_jobs;
         DevBuf jobtab, node_tiles, cell_tiles, done, graph_tiles, graph_sub_tiles, work;
         StepLaunch L;
-        std::shared_ptr<DevJob> job0;   // host copy of a one-job group's descriptor (L.job0)
+        // host copies of the descriptors of a group of one job (L.tab1) or of at most kParamJobs
+        // jobs (L.tabk), passed to the FP32 kernels as a parameter
+        std::shared_ptr<JobTab<1>> tab1;
+        std::shared_ptr<JobTab<kParamJobs>> tabk;
     };
     std::vector<Group> groups;
     std::vector<ep_job *> bido;   // jobs whose step ends with the elliptic solve
@@ -1087,20 +1090,43 @@ int ep_job_create(ep_context *ctx, const ep_plan *plan, ep_job **out) {
     }
 }
 
+// The launch groups of a batch: the FP64 jobs in one group; the FP32 jobs
+// that step by forward Euler without the bidomain solve in groups of at most
+// kParamJobs (their kernels take the group's descriptors as a parameter),
+// the other FP32 jobs in one group.
+static std::vector<std::pair<int, std::vector<int>>> launch_groups(ep_job *const *jobs, int n) {
+    std::vector<std::pair<int, std::vector<int>>> out;
+    std::vector<int> f64, plain, other;
+    for (int i = 0; i < n; ++i) {
+        if (jobs[i]->precision == EP_FP64_PLAIN) f64.push_back(i);
+        else if (jobs[i]->params.integrator == EP_INTEGRATOR_AB2 || jobs[i]->bido) other.push_back(i);
+        else plain.push_back(i);
+    }
+    for (size_t a = 0; a < plain.size(); a += kParamJobs)
+        out.push_back({EP_FP32_MIXED, std::vector<int>(plain.begin() + a,
+                                                       plain.begin() + std::min(plain.size(), a + kParamJobs))});
+    if (!other.empty()) out.push_back({EP_FP32_MIXED, other});
+    if (!f64.empty()) out.push_back({EP_FP64_PLAIN, f64});
+    return out;
+}
+
 static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
     pl->jobs.assign(jobs, jobs + n);
     for (int i = 0; i < n; ++i) pl->versions.push_back(jobs[i]->version);
-    for (int prec : {EP_FP32_MIXED, EP_FP64_PLAIN}) {
+    for (const auto &grp : launch_groups(jobs, n)) {
+        const int prec = grp.first;
         std::vector<DevJob> tab;
         std::vector<Tile> nt, ct, gt, gst;
         std::vector<Work> wk;
+        std::vector<int> cell_begin, node_begin;   // first tile of each job
         int max_lmax = 0;
         int max_sub = 0, any_bido = 0, any_ab2 = 0, n_idx16 = 0, n_col16 = 0, models = 0;
-        for (int i = 0; i < n; ++i) {
-            if (jobs[i]->precision != prec) continue;
+        for (int i : grp.second) {
             const int jid = int(tab.size());
             tab.push_back(jobs[i]->dj);
             append_work(jobs[i], int(nt.size()), int(ct.size()), &wk);
+            cell_begin.push_back(int(ct.size()));
+            node_begin.push_back(int(nt.size()));
             for (Tile t : jobs[i]->node_tiles) nt.push_back(Tile{jid, t.model, t.start, t.count});
             for (Tile t : jobs[i]->cell_tiles) ct.push_back(Tile{jid, t.model, t.start, t.count});
             if (jobs[i]->params.integrator == EP_INTEGRATOR_AB2) any_ab2 = 1;
@@ -1179,9 +1205,24 @@ static int build_plan(ep_context *ctx, ep_job *const *jobs, int n, Plan *pl) {
         g.L.cell_grid0 = std::max(1, std::min<int>(int(ct.size()), ctx->sm_count * cell_blocks_per_sm(prec, 0)));
         g.L.cell_grid =
             std::max(1, std::min<int>(int(ct.size()), ctx->sm_count * cell_blocks_per_sm(prec, g.L.cell_variant)));
+        cell_begin.push_back(int(ct.size()));
+        node_begin.push_back(int(nt.size()));
+        auto fill = [&](auto &jt) {
+            jt.n_jobs = g.n_jobs;
+            for (int k = 0; k <= g.n_jobs; ++k) {
+                jt.cell_begin[k] = cell_begin[k];
+                jt.node_begin[k] = node_begin[k];
+            }
+            for (int k = 0; k < g.n_jobs; ++k) jt.j[k] = tab[k];
+        };
         if (g.n_jobs == 1) {
-            g.job0 = std::make_shared<DevJob>(tab[0]);
-            g.L.job0 = g.job0.get();
+            g.tab1 = std::make_shared<JobTab<1>>();
+            fill(*g.tab1);
+            g.L.tab1 = g.tab1.get();
+        } else if (g.n_jobs <= kParamJobs) {
+            g.tabk = std::make_shared<JobTab<kParamJobs>>();
+            fill(*g.tabk);
+            g.L.tabk = g.tabk.get();
         }
         pl->groups.push_back(g);
     }
@@ -1423,45 +1464,53 @@ int ep_autotune(ep_job *const *jobs, int32_t n_jobs, int32_t steps_per_variant, 
             if (chosen) chosen[p] = -1;
             for (int v = 0; v < kNumCellVariants && variant_ms; ++v) variant_ms[p * kNumCellVariants + v] = -1.0;
         }
-        for (auto &gr : pl->groups) {
+        // per precision: every variant on all of that precision's launch groups at once, timing their
+        // whole steps (node values, conduction graphs, cell update; the fused variants do the node
+        // values in their one launch); the other precision's groups step untimed in between, so all
+        // jobs stay in step
+        for (int prec : {EP_FP32_MIXED, EP_FP64_PLAIN}) {
+            bool any = false;
+            for (auto &gr : pl->groups) any = any || gr.precision == prec;
+            if (!any) continue;
             double best = 1e300;
             int best_v = 0;
             for (int v = 0; v < kNumCellVariants && e == cudaSuccess; ++v) {
-                gr.L.cell_variant = v;
-                gr.L.cell_grid = std::max(1, std::min<int>(gr.L.n_cell_tiles,
-                                                           ctx->sm_count * cell_blocks_per_sm(gr.precision, v)));
+                for (auto &gr : pl->groups)
+                    if (gr.precision == prec) {
+                        gr.L.cell_variant = v;
+                        gr.L.cell_grid = std::max(1, std::min<int>(gr.L.n_cell_tiles,
+                                                                   ctx->sm_count * cell_blocks_per_sm(prec, v)));
+                    }
                 double tot = 0.0;
                 for (int it = 0; it < steps_per_variant && e == cudaSuccess; ++it) {
-                    // every group of the plan advances together, so all jobs stay in step
-                    for (auto &other : pl->groups) {
-                        if (&other == &gr) {
-                            // the whole step: the fused variants do the node values in their one launch
-                            e = cudaEventRecord(e0, ctx->stream);
-                            if (e == cudaSuccess) e = launch_node(gr.precision, gr.L, ctx->stream);
-                            if (e == cudaSuccess) e = launch_graph(gr.precision, gr.L, ctx->stream);
-                            if (e == cudaSuccess) e = launch_cell(gr.precision, gr.L, ctx->stream);
-                            if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
-                            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                            float ms = 0.f;
-                            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                            tot += ms;
-                        } else if (e == cudaSuccess) {
-                            e = launch_step(other.precision, other.L, ctx->stream);
-                        }
+                    e = cudaEventRecord(e0, ctx->stream);
+                    for (auto &gr : pl->groups) {
+                        if (gr.precision != prec) continue;
+                        if (e == cudaSuccess) e = launch_node(prec, gr.L, ctx->stream);
+                        if (e == cudaSuccess) e = launch_graph(prec, gr.L, ctx->stream);
+                        if (e == cudaSuccess) e = launch_cell(prec, gr.L, ctx->stream);
                     }
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    tot += ms;
+                    for (auto &other : pl->groups)
+                        if (other.precision != prec && e == cudaSuccess)
+                            e = launch_step(other.precision, other.L, ctx->stream);
                     for (ep_job *j : pl->bido)
                         if (e == cudaSuccess) e = launch_bido(j->precision, j->bido->args, j->bido->grid, ctx->stream);
                 }
                 const double mean = tot / steps_per_variant;
-                if (variant_ms) variant_ms[gr.precision * kNumCellVariants + v] = mean;
+                if (variant_ms) variant_ms[prec * kNumCellVariants + v] = mean;
                 if (mean < best) {
                     best = mean;
                     best_v = v;
                 }
             }
             if (e != cudaSuccess) break;
-            apply_cell_variant(ctx, gr.precision, best_v);
-            if (chosen) chosen[gr.precision] = best_v;
+            apply_cell_variant(ctx, prec, best_v);
+            if (chosen) chosen[prec] = best_v;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);

@@ -17,40 +17,9 @@
 #include <mutex>
 #include <type_traits>
 
-#include "crncell.cuh"
-#include "kernels.h"
-#include "nodesum.cuh"
-#include "ttcells.cuh"
-#include "varmap.h"
+#include "cellstep.cuh"
 
 namespace ep {
-
-// In-place state access of local cell i of a region.
-template <class R>
-__device__ __forceinline__ CellIO<R> region_io(const DevRegion &rg, long long i) {
-    R *x = static_cast<R *>(rg.r) + i;
-    double *a = rg.a + i;
-    return CellIO<R>{x, a, rg.stride, x, a, rg.stride};
-}
-
-template <class R> struct Vec4T;
-template <> struct Vec4T<float> { using type = float4; };
-template <> struct Vec4T<double> { using type = double4_32a; };
-
-template <class R>
-__device__ __forceinline__ R stimulus(const DevJob &J, unsigned mask, long long n) {
-    R is = R(0);
-    for (int k = 0; k < J.n_stim; ++k) {
-        if (!((mask >> k) & 1u)) continue;
-        const DevStim &s = J.stim[k];
-        bool on;
-        if (n < s.n_on) on = false;
-        else if (s.n_per <= 0) on = n < s.n_on + s.n_dur;
-        else on = ((n - s.n_on) % s.n_per) < s.n_dur;
-        if (on) is += pick<R>(s.amp, s.amp_f);
-    }
-    return is;
-}
 
 // F: the form of the batch's node -> cell entries (0 all 32-bit, 1 all
 // 16-bit, 2 mixed), so that a uniform batch compiles one form only.
@@ -69,185 +38,16 @@ __global__ void __launch_bounds__(kNodeThreads) node_kernel(const DevJob *__rest
     }
 }
 
-// The same for an FP32 batch of one job, its descriptor a kernel parameter
-// (see cell_kernel_1j).
-template <class R, int F>
-__global__ void __launch_bounds__(kNodeThreads) node_kernel_1j(const __grid_constant__ DevJob J,
-                                                               const Tile *__restrict__ tiles, int n_tiles) {
-    const long long n = *J.step;
-    const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const Tile tl = tiles[t];
-        const int i = threadIdx.x;
-        if (i >= tl.count) continue;
-        const long long node = (long long)tl.start + i;
-        static_cast<R *>(J.vn)[node] = node_value<R, 6, F>(J, V, node);
-    }
-}
-
 template <class R>
 static void launch_node_kernel(const StepLaunch &L, cudaStream_t s) {
     if constexpr (std::is_same<R, float>::value) {
-        if (L.n_jobs == 1 && L.job0) {
-            auto *k1 = L.node_form == 1 ? node_kernel_1j<float, 1> : node_kernel_1j<float, 0>;
-            k1<<<L.node_grid, kNodeThreads, 0, s>>>(*L.job0, L.node_tiles, L.n_node_tiles);
+        if (tab_eligible(L)) {
+            launch_node_tab(L, s);
             return;
         }
     }
     auto *k = L.node_form == 0 ? node_kernel<R, 0> : (L.node_form == 1 ? node_kernel<R, 1> : node_kernel<R, 2>);
     k<<<L.node_grid, kNodeThreads, 0, s>>>(L.jobs, L.node_tiles, L.n_node_tiles);
-}
-
-__device__ __forceinline__ bool window_on(double t_trig, double delay, double dur, double t) {
-    return t_trig > -INFINITY && t >= t_trig + delay && t < t_trig + delay + dur;
-}
-
-// Junction terms of a cell touched by the conduction graph (Sec. 3.3): the
-// resistive current g_cell (V_m - V_p) and the triggered stimulus. The
-// cell's (cell, junction) entries are found by binary search.
-template <class R>
-__device__ void junction_cell_terms(const DevJob &J, long long c, long long n, R Vc, R &is, R &ix, int &first,
-                                    int &last) {
-    const DevGraph &G = J.g;
-    int lo = 0, hi = G.n_tgt;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (G.tgt_cell[mid] < c) lo = mid + 1;
-        else hi = mid;
-    }
-    first = lo;
-    const R *Vg = static_cast<const R *>(G.V[n & 1]);
-    const double t = double(n) * J.dt;
-    int k = lo;
-    for (; k < G.n_tgt && G.tgt_cell[k] == c; ++k) {
-        const int e = G.tgt_junc[k], j = e & (kJunctionSource - 1);
-        if (e & kJunctionSource) {   // source of a cell-to-cell node, excited back (two-way)
-            if (G.two_way && window_on(G.t_cell[j], G.delay_anti, G.duration, t))
-                is += pick<R>(G.amplitude, G.amplitude_f);
-        } else if (G.jmode[j] == EP_PMJ_RESISTIVE) {
-            ix += pick<R>(G.g_cell, G.g_cell_f) * (Vc - Vg[G.jnode[j]]);
-        } else if (window_on(G.t_graph[j], G.delay_ortho, G.duration, t)) {
-            is += pick<R>(G.amplitude, G.amplitude_f);
-        }
-    }
-    last = k;
-}
-
-// Muscle-side threshold crossing of two-way triggered junctions.
-template <class R>
-__device__ void junction_cell_crossing(const DevJob &J, long long c, long long n, R v0, R v1, int first, int last) {
-    const DevGraph &G = J.g;
-    const double th = G.threshold;
-    if (!(double(v0) < th && double(v1) >= th)) return;
-    const double tc = double(n) * J.dt + J.dt * (th - double(v0)) / (double(v1) - double(v0));
-    for (int k = first; k < last; ++k) {
-        const int e = G.tgt_junc[k], j = e & (kJunctionSource - 1);
-        if (e & kJunctionSource) G.t_graph[j] = tc;   // the source cell of a cell-to-cell node fires
-        else if (G.two_way && G.jmode[j] != EP_PMJ_RESISTIVE && G.jcell[j] == c) G.t_cell[j] = tc;
-    }
-}
-
-// A cell's streamed step inputs: its gather indices (decoded), and where the
-// rest is read -- straight from the job's arrays in global memory, or from a
-// shared-memory stage filled by bulk copies (cell_kernel_staged). The
-// gathered inputs (node values, neighbour potentials) are always read from
-// global memory.
-template <class R>
-struct CellSrc {
-    int4 na, nb, nc;
-    const typename Vec4T<R>::type *wa, *wb, *q;
-    const R *Vc;
-    const uint8_t *smask, *pset;
-    CellIO<R> io;
-};
-
-template <class R>
-__device__ __forceinline__ CellSrc<R> global_src(const DevJob &J, int model, long long c, const R *V) {
-    using R4 = typename Vec4T<R>::type;
-    const DevRegion &rg = J.reg[model];
-    int4 na, nb, nc;
-    cell_indices(J, c, na, nb, nc);
-    return CellSrc<R>{na, nb, nc, static_cast<const R4 *>(J.wa) + c, static_cast<const R4 *>(J.wb) + c,
-                      static_cast<const R4 *>(J.q) + c, V + c, J.smask + c, J.pset + c,
-                      region_io<R>(rg, c - rg.off)};
-}
-
-// Node value k for the cell update. In the fused kernel, where other warps
-// of the same launch write the node values, the loads are plain weak loads
-// (ld.global.ca), never the non-coherent read-only path: they follow the
-// warp's acquire of the node tiles, and a line of node values is first
-// loaded in a launch only after its tile is complete.
-template <class R, bool CG>
-__device__ __forceinline__ R node_at(const R *vn, int k) {
-    if constexpr (CG) return __ldca(vn + k);
-    else return vn[k];
-}
-
-// XD: the batch holds bidomain jobs, whose cells add L_i(v_e^n) (first line
-// of Eq. 6) to the diffusion term; AB2: the batch holds jobs that advance the
-// non-gating variables by second-order Adams-Bashforth. Batches without them
-// compile without the code. CG: the node values come from the same launch.
-// MODELS: the cell models a batch holds (bit m for model m); a batch of TP06
-// cells only compiles TP06 alone, whose register demand is lower.
-template <class R, bool XD = false, bool AB2 = false, bool CG = false, int MODELS = 7>
-__device__ __forceinline__ void cell_update_from(const DevJob &J, int model, long long c, long long n, const R *V,
-                                                 const CellSrc<R> &src) {
-    using R4 = typename Vec4T<R>::type;
-    R *__restrict__ Vnext = static_cast<R *>(J.V[(n & 1) ^ 1]);
-    const R *vn = static_cast<const R *>(J.vn);
-    const int4 na = src.na, nb = src.nb, nc = src.nc;
-    const R4 wa = *src.wa;
-    const R4 wb = *src.wb;
-    const R4 q = *src.q;
-    const R Vc = *src.Vc;
-    // diffusion term of Eq. 7 (S2 + S3 folded): eight node values, four neighbours
-    R diff = wa.x * node_at<R, CG>(vn, na.x) + wa.y * node_at<R, CG>(vn, na.y) + wa.z * node_at<R, CG>(vn, na.z) +
-             wa.w * node_at<R, CG>(vn, na.w);
-    diff += wb.x * node_at<R, CG>(vn, nb.x) + wb.y * node_at<R, CG>(vn, nb.y) + wb.z * node_at<R, CG>(vn, nb.z) +
-            wb.w * node_at<R, CG>(vn, nb.w);
-    diff += q.x * (V[nc.x] - Vc) + q.y * (V[nc.y] - Vc) + q.z * (V[nc.z] - Vc) + q.w * (V[nc.w] - Vc);
-    if (XD && J.xdiv) diff += static_cast<const R *>(J.xdiv)[c];
-
-    const unsigned mask = *src.smask;
-    R is = mask ? stimulus<R>(J, mask, n) : R(0);
-    const unsigned ps = *src.pset;
-    R ix = R(0);
-    int jfirst = 0, jlast = 0;
-    if (ps & kJunctionFlag) junction_cell_terms<R>(J, c, n, Vc, is, ix, jfirst, jlast);
-    const DevParams &P = J.params[ps & (EP_MAX_PARAM_SETS - 1)];
-    const R dt = pick<R>(J.dt, J.dt_f);
-    R iion;
-    Rates<R, AB2> rt;
-    if constexpr (AB2) {
-        if (J.integrator == EP_INTEGRATOR_AB2) {
-            const DevRegion &rg = J.reg[model];
-            rt.h = static_cast<R *>(rg.h) + (c - rg.off);
-            rt.st = rg.stride;
-            rt.on = n > J.ab2_from;
-        }
-    }
-    if constexpr (MODELS == (1 << EP_TP06)) {
-        iion = tt_step<R, false, AB2>(src.io, P, Vc, dt, is, rt);
-    } else {
-        if (model == EP_TP06) iion = tt_step<R, false, AB2>(src.io, P, Vc, dt, is, rt);
-        else if (model == EP_STEWART) iion = tt_step<R, true, AB2>(src.io, P, Vc, dt, is, rt);
-        else iion = crn_step<R, AB2>(src.io, P, Vc, dt, rt);
-    }
-    const R Vn = Vc + dt * rt(0, diff - iion - is - ix);
-    Vnext[c] = Vn;
-    if ((ps & kJunctionFlag) && (J.g.two_way || J.g.cell_nodes)) junction_cell_crossing<R>(J, c, n, Vc, Vn, jfirst, jlast);
-    const R th = pick<R>(J.threshold, J.threshold_f);
-    if (Vc < th && Vn >= th) {
-        R *act = static_cast<R *>(J.act);
-        if (isinf(act[c])) act[c] = R(double(n) * J.dt) + dt * (th - Vc) / (Vn - Vc);
-    }
-}
-
-template <class R, bool XD = false, bool AB2 = false, bool CG = false, int MODELS = 7>
-__device__ __forceinline__ void cell_update(const DevJob &J, int model, long long c) {
-    const long long n = *J.step;
-    const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
-    cell_update_from<R, XD, AB2, CG, MODELS>(J, model, c, n, V, global_src<R>(J, model, c, V));
 }
 
 // Conduction graph, part 1 (Sec. 3.2 / 3.3): the reaction of every graph node
@@ -406,66 +206,6 @@ __global__ void __launch_bounds__(kGraphThreads) graph_substeps_kernel(const Dev
                 }
         }
         __syncthreads();   // the shared arrays are refilled for the next tile
-    }
-}
-
-// Launch-shape variants of the cell kernel, chosen by ep_autotune: threads
-// per block and the minimum number of resident blocks per SM requested from
-// the register allocator. All variants run the same per-cell arithmetic, so
-// their results are bitwise identical. Tiles hold kCellThreads cells; a
-// block narrower than a tile walks it in strides of its width.
-template <class R, int T, int MINB, bool XD, bool AB2, int MODELS = 7>
-__global__ void __launch_bounds__(T, MINB) cell_kernel(const DevJob *__restrict__ jobs,
-                                                        const Tile *__restrict__ tiles, int n_tiles,
-                                                        unsigned *done, int n_jobs) {
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const Tile tl = tiles[t];
-        for (int i = threadIdx.x; i < tl.count; i += T)
-            cell_update<R, XD, AB2, false, MODELS>(jobs[tl.job], tl.model, (long long)tl.start + i);
-    }
-    // Every block has read the step counters; the last one to finish advances them.
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(done, 1u);
-        if (prev == gridDim.x - 1) {
-            for (int j = 0; j < n_jobs; ++j) *jobs[j].step += 1;
-            *done = 0u;
-            __threadfence();
-        }
-    }
-}
-
-// Single-job cell kernel (an FP32 batch of one job, any cell_kernel shape):
-// the job's descriptor is a kernel parameter (__grid_constant__), so the
-// per-cell reads of its fields -- array bases, region strides, parameter
-// sets, stimulus protocols, dt -- come from the constant bank instead of the
-// L1 / L2 path of the streamed and gathered data, and hold no registers as
-// pointers; the step counter is read once per thread. Otherwise cell_kernel:
-// the same arithmetic, bitwise the same results.
-template <class R, int T, int MINB, bool XD, bool AB2, int MODELS = 7>
-__global__ void __launch_bounds__(T, MINB) cell_kernel_1j(const __grid_constant__ DevJob J,
-                                                           const Tile *__restrict__ tiles, int n_tiles,
-                                                           unsigned *done) {
-    const long long n = *J.step;
-    const R *__restrict__ V = static_cast<const R *>(J.V[n & 1]);
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const Tile tl = tiles[t];
-        for (int i = threadIdx.x; i < tl.count; i += T) {
-            const long long c = (long long)tl.start + i;
-            cell_update_from<R, XD, AB2, false, MODELS>(J, tl.model, c, n, V, global_src<R>(J, tl.model, c, V));
-        }
-    }
-    // Every block has read the step counter; the last one to finish advances it.
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(done, 1u);
-        if (prev == gridDim.x - 1) {
-            *J.step += 1;
-            *done = 0u;
-            __threadfence();
-        }
     }
 }
 
@@ -965,31 +705,12 @@ cudaError_t launch_node(int precision, const StepLaunch &L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <class R, int T, int B>
+template <int T, int B>
 static void launch_cell_kernel(const StepLaunch &L, cudaStream_t s) {
-    if constexpr (std::is_same<R, float>::value) {
-        // one FP32 job (forward Euler, monodomain): its descriptor as a kernel parameter. FP32 only:
-        // the FP64 step is bound by the FP64 pipe, and its compiled rounding must not depend on the kernel
-        if (L.n_jobs == 1 && L.job0 && !L.bido && !L.ab2) {
-            const bool tt = L.models == (1 << EP_TP06);
-            auto *k1 = tt ? cell_kernel_1j<float, T, B, false, false, 1 << EP_TP06>
-                          : cell_kernel_1j<float, T, B, false, false>;
-            static int per_sm[2] = {0, 0};   // resident blocks per SM of the two instances
-            int &nb = per_sm[tt ? 1 : 0];
-            if (nb == 0) {
-                int q = 0;
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k1, T, 0);
-                nb = std::max(q, 1);
-            }
-            const int grid = L.sm_count > 0 ? std::max(1, std::min(L.n_cell_tiles, L.sm_count * nb)) : L.cell_grid;
-            k1<<<grid, T, 0, s>>>(*L.job0, L.cell_tiles, L.n_cell_tiles, L.done);
-            return;
-        }
-    }
-    auto *k = L.bido ? (L.ab2 ? cell_kernel<R, T, B, true, true> : cell_kernel<R, T, B, true, false>)
-                     : (L.ab2 ? cell_kernel<R, T, B, false, true>
-                              : (L.models == (1 << EP_TP06) ? cell_kernel<R, T, B, false, false, 1 << EP_TP06>
-                                                            : cell_kernel<R, T, B, false, false>));
+    auto *k = L.bido ? (L.ab2 ? cell_kernel<float, T, B, true, true> : cell_kernel<float, T, B, true, false>)
+                     : (L.ab2 ? cell_kernel<float, T, B, false, true>
+                              : (L.models == (1 << EP_TP06) ? cell_kernel<float, T, B, false, false, 1 << EP_TP06>
+                                                            : cell_kernel<float, T, B, false, false>));
     k<<<L.cell_grid, T, 0, s>>>(L.jobs, L.cell_tiles, L.n_cell_tiles, L.done, L.n_jobs);
 }
 
@@ -1057,17 +778,25 @@ static cudaError_t cell_launch_variant(const StepLaunch &L, cudaStream_t s) {
         L0.cell_grid = L.cell_grid0;
         return cell_launch_variant<R>(L0, s);
     }
-    switch (L.cell_variant) {
-#define EP_CELL_CASE(k, T, B)                                                                                  \
-    case k:                                                                                                    \
-        launch_cell_kernel<R, T, B>(L, s);                                                                     \
+    // the two-launch shapes: FP64 in kernels_f64.cu; a small FP32 batch with its descriptors as a
+    // kernel parameter in kernels_tab.cu (FP32 only: the FP64 step is bound by the FP64 pipe, and its
+    // compiled rounding must not depend on the kernel); else the job table in global memory
+    if constexpr (std::is_same<R, double>::value) {
+        return launch_cell_plain_f64(L, s);
+    } else {
+        if (tab_eligible(L)) return launch_cell_tab(L, s);
+        switch (L.cell_variant) {
+#define EP_CELL_CASE(k, T, B)               \
+    case k:                                 \
+        launch_cell_kernel<T, B>(L, s);     \
         break;
-        EP_CELL_VARIANTS(EP_CELL_CASE)
+            EP_CELL_VARIANTS(EP_CELL_CASE)
 #undef EP_CELL_CASE
-    default:
-        return cudaErrorInvalidValue;
+        default:
+            return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_cell(int precision, const StepLaunch &L, cudaStream_t s) {
@@ -1100,15 +829,19 @@ static int cell_blocks_variant(int variant) {
         if (nb >= 1) return nb;
         variant = 0;
     }
-    switch (variant) {
-#define EP_CELL_CASE(k, T, B)                                                                 \
-    case k:                                                                                   \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_kernel<R, T, B, false, false>, T, 0); \
+    if constexpr (std::is_same<R, double>::value) {
+        return cell_blocks_plain_f64(variant);
+    } else {
+        switch (variant) {
+#define EP_CELL_CASE(k, T, B)                                                                             \
+    case k:                                                                                               \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_kernel<float, T, B, false, false>, T, 0); \
         break;
-        EP_CELL_VARIANTS(EP_CELL_CASE)
+            EP_CELL_VARIANTS(EP_CELL_CASE)
 #undef EP_CELL_CASE
+        }
+        return nb < 1 ? 1 : nb;
     }
-    return nb < 1 ? 1 : nb;
 }
 
 int cell_variant_threads(int variant) {
@@ -1276,7 +1009,12 @@ cudaError_t launch_step_noalloc(int precision, const DevJob &job, const Tile *no
     L.cell_variant = cell_variant;
     L.idx16 = job.idx16;
     L.sm_count = sm_count;
-    L.job0 = &dj;
+    JobTab<1> tab1{};   // the descriptor as the FP32 kernels' parameter (copied at each launch)
+    tab1.n_jobs = 1;
+    tab1.cell_begin[1] = n_cell_tiles;
+    tab1.node_begin[1] = n_node_tiles;
+    tab1.j[0] = dj;
+    L.tab1 = &tab1;
     L.node_form = job.col16;
     L.models = 0;
     for (int m = 0; m < EP_N_MODELS; ++m)

@@ -6,6 +6,23 @@
 
 namespace ep {
 
+// Descriptors of a small FP32 batch passed as a kernel parameter (constant
+// bank; the parameter space holds 32 KB, room for kParamJobs descriptors):
+// the kernels read a job's fields -- array bases, region strides, parameter
+// sets, stimulus protocols, dt -- from the constant bank, as operands that
+// hold no registers, instead of loading them into registers through L1 / L2
+// from the job table. The tiles of job j are cell tiles [cell_begin[j],
+// cell_begin[j + 1]) and node tiles [node_begin[j], node_begin[j + 1]) of
+// the launch (a batch's tiles are grouped by job, in job order).
+constexpr int kParamJobs = 15;
+template <int K>
+struct JobTab {
+    int n_jobs;
+    int cell_begin[K + 1];
+    int node_begin[K + 1];
+    DevJob j[K];
+};
+
 struct StepLaunch {
     const DevJob *jobs;        // device job table
     int n_jobs;
@@ -31,7 +48,8 @@ struct StepLaunch {
     int node_form;             // node -> cell entries of the batch: 0 all 32-bit, 1 all 16-bit, 2 mixed
     int models;                // cell models of the batch's cells, bit m for model m
     unsigned *err;             // device error word of the context (bounded waits that gave up)
-    const DevJob *job0;        // host copy of the descriptor of a one-job batch (else NULL)
+    const JobTab<1> *tab1;     // host copies of the descriptors of a batch of one job,
+    const JobTab<kParamJobs> *tabk;   // or of up to kParamJobs jobs (else NULL)
     const Work *work;          // fused variants: node and cell tiles in dependency order
     int n_work;
     unsigned *head;            // fused variants: next work item (device counter)
@@ -39,9 +57,9 @@ struct StepLaunch {
 
 // Launch shapes of the cell kernel: (index, threads per block, minimum
 // resident blocks per SM, which caps the registers per thread). Variant 0 is
-// the default before autotuning. An FP32 batch of one job (forward Euler,
-// monodomain) runs these shapes as cell_kernel_1j, the job's descriptor a
-// kernel parameter.
+// the default before autotuning. An FP32 batch of at most kParamJobs jobs
+// (forward Euler, monodomain) runs these shapes as cell_kernel_tab, the
+// jobs' descriptors a kernel parameter.
 #define EP_CELL_VARIANTS(X) \
     X(0, 256, 2)            \
     X(1, 256, 3)            \
@@ -121,6 +139,16 @@ int alu_probe_threads();
 cudaError_t launch_step_noalloc(int precision, const DevJob &job, const Tile *node_tiles, int n_node_tiles,
                                 const Tile *cell_tiles, int n_cell_tiles, const Work *work, int n_work,
                                 int cell_variant, int sm_count, unsigned *err, long long n_steps, cudaStream_t s);
+
+// The two-launch cell kernel shapes of the plain FP64 step (kernels_f64.cu),
+// and of a small FP32 batch whose descriptors are a kernel parameter
+// (kernels_tab.cu: tab_eligible says whether a launch qualifies; then its
+// node kernel too).
+cudaError_t launch_cell_plain_f64(const StepLaunch &L, cudaStream_t s);
+int cell_blocks_plain_f64(int variant);
+bool tab_eligible(const StepLaunch &L);
+cudaError_t launch_cell_tab(const StepLaunch &L, cudaStream_t s);
+cudaError_t launch_node_tab(const StepLaunch &L, cudaStream_t s);
 
 // Kernel attributes for sizing persistent grids.
 int cell_blocks_per_sm(int precision, int variant);
