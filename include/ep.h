@@ -245,9 +245,12 @@ int ep_job_create(ep_context *ctx, const ep_plan *plan, ep_job **out);
 
 /* Advance n_jobs jobs of one context by n_steps time steps each. All jobs are
  * advanced together: every step is one node-value launch and one fused
- * cell launch covering every resident cell of every job of the same
- * precision. Repeated calls with the same job list replay a captured CUDA
- * graph. Asynchronous on the context's stream. Errors: EP_EINVAL (jobs of
+ * cell launch per launch group, each covering every resident cell of its
+ * jobs. The groups: FP32 jobs that step by forward Euler without the
+ * bidomain solve, at most 15 to a group (their descriptors are passed to the
+ * kernels as a parameter, read from the constant bank); the other FP32 jobs;
+ * the FP64 jobs. A job's results do not depend on its group. Repeated calls
+ * with the same job list replay a captured CUDA graph. Asynchronous on the context's stream. Errors: EP_EINVAL (jobs of
  * another context, repeated job, job without params), EP_ECUDA, and
  * EP_ETIMEOUT when a staged cell kernel (launch-shape variants 6 and 7) of an
  * earlier call gave up its bounded wait for a tile's copies: that call's

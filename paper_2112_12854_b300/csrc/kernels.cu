@@ -9,9 +9,13 @@
 //                cell model (Rush-Larsen / forward Euler at (V^n, s^n)),
 //                the stimulus of Eq. 4, V^{n+1} and the activation time.
 // Both kernels are persistent (grid-stride over tiles of one job and one
-// model) and serve every job of the batch in one launch. The last block of
-// the cell launch advances the jobs' step counters, which select the V
-// buffer (double-buffered by step parity) and the time t^n = n dt.
+// model) and serve every job of a launch group in one launch. The last block
+// of the cell launch advances the jobs' step counters, which select the V
+// buffer (double-buffered by step parity) and the time t^n = n dt. This file
+// holds the kernels that read the jobs' descriptors from the job table in
+// global memory, and the launch dispatch; kernels_tab.cu the FP32 kernels
+// whose descriptors are a kernel parameter, kernels_f64.cu the FP64 cell
+// kernel shapes, cellstep.cuh the device code they share.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
