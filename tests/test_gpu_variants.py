@@ -240,12 +240,13 @@ PLAIN_SHAPES = (0, 1, 2, 3, 4, 5, 10, 11)
 
 @pytest.mark.parametrize("three_models", [False, True])
 def test_one_job_kernels_equal_the_batched_kernels(three_models):
-    """An FP32 group of one job runs the node and cell kernels with the job's
-    descriptor as a kernel parameter (constant bank); a group of several
-    jobs reads the descriptors from the job table in global memory. For every
-    two-launch shape, a job stepped alone is bitwise the same job stepped in a
-    batch with another (TP06-only cells, and TP06 / Courtemanche / Stewart
-    regions with two stimuli, ragged tiles)."""
+    """The kernels of an FP32 group take the jobs' descriptors as a kernel
+    parameter: a one-job instance (the descriptor at a fixed place, the step
+    counter read once) and a 15-job instance (each tile's job found from the
+    group's tile bounds). For every two-launch shape, a job stepped alone is
+    bitwise the same job stepped in a batch with another (TP06-only cells,
+    and TP06 / Courtemanche / Stewart regions with two stimuli, ragged
+    tiles)."""
     import torch
     assert torch.cuda.is_available()
     from paper_2112_12854_b300 import ep
@@ -264,4 +265,37 @@ def test_one_job_kernels_equal_the_batched_kernels(three_models):
         assert np.isfinite(_state(alone)[-1]).any()
         for j in (alone, a, b):
             j.destroy()
+    ctx.close()
+
+
+def test_launch_groups_equal_alone():
+    """A batch is stepped in launch groups: FP32 forward-Euler jobs at most 15
+    to a group (descriptors as a kernel parameter), the other FP32 jobs (AB2
+    here) in one group with the job table in global memory, the FP64 jobs in
+    another. Twenty jobs of different sizes -- 17 forward Euler (groups of 15
+    and 2), one AB2, two FP64 -- each end bitwise where they end stepped
+    alone, with captured-graph replay and direct launches."""
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2112_12854_b300 import ep
+    ctx = ep.Context()
+    specs = [(w.slab_case(nx=5 + k % 6, ny=4 + k % 3, nz=3, h=0.5, stim_x=0.6), {}) for k in range(17)]
+    specs.append((w.slab_case(nx=8, ny=6, nz=3, h=0.5), {"integrator": 1}))
+    specs += [(w.slab_case(nx=7 + k, ny=5, nz=3, h=0.5), {"precision": ep.EP_FP64_PLAIN}) for k in range(2)]
+
+    def make():
+        return [ep.job_from_case(ctx, case, **kw) for case, kw in specs]
+    alone = make()
+    for j in alone:
+        j.step(130)
+    batch = make()
+    ep.step(batch, 100)       # one captured graph of the whole batch
+    ep.step(batch, 30)
+    for a, b in zip(alone, batch):
+        assert a.step_index == b.step_index == 130
+        assert np.array_equal(a.V, b.V)
+        assert np.array_equal(a.activation_times(), b.activation_times(), equal_nan=True)
+        for k in range(1, 19):
+            assert np.array_equal(a.read(k), b.read(k))
+    assert sum(np.isfinite(a.activation_times()).any() for a in alone) >= 17
     ctx.close()
