@@ -311,7 +311,7 @@ int ep_job_destroy(ep_job *job);
 /* Profiling hook: advance the jobs by n_steps with direct launches (no
  * graph), recording CUDA events on the context's stream around each launch,
  * and return the mean device time per step of the node-value kernel and of
- * the fused cell kernel (ms, summed over the jobs' precision groups).
+ * the fused cell kernel (ms, summed over the jobs' launch groups).
  * The elliptic solves of bidomain jobs run after each step, untimed.
  * Synchronises. The results equal those of ep_step. */
 int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double *node_ms, double *cell_ms);

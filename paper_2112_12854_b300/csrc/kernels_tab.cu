@@ -82,17 +82,24 @@ __global__ void __launch_bounds__(T, MINB) cell_kernel_tab(const __grid_constant
     }
 }
 
+// Resident blocks per SM of kernel instance KERN at T threads per block,
+// queried once per instance (thread-safe static initialisation).
+template <auto KERN, int T>
+static int blocks_per_sm_once() {
+    static const int nb = [] {
+        int q = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, KERN, T, 0);
+        return std::max(q, 1);
+    }();
+    return nb;
+}
+
 template <int T, int B, int K>
 static void cell_tab_impl(const StepLaunch &L, cudaStream_t s) {
     const bool tt = L.models == (1 << EP_TP06);
     auto *k = tt ? cell_kernel_tab<float, T, B, K, 1 << EP_TP06> : cell_kernel_tab<float, T, B, K>;
-    static int per_sm[2] = {0, 0};   // resident blocks per SM of the two instances
-    int &nb = per_sm[tt ? 1 : 0];
-    if (nb == 0) {
-        int q = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k, T, 0);
-        nb = std::max(q, 1);
-    }
+    const int nb = tt ? blocks_per_sm_once<cell_kernel_tab<float, T, B, K, 1 << EP_TP06>, T>()
+                      : blocks_per_sm_once<cell_kernel_tab<float, T, B, K>, T>();
     const int grid = L.sm_count > 0 ? std::max(1, std::min(L.n_cell_tiles, L.sm_count * nb)) : L.cell_grid;
     if constexpr (K == 1) k<<<grid, T, 0, s>>>(*L.tab1, L.cell_tiles, L.n_cell_tiles, L.done);
     else k<<<grid, T, 0, s>>>(*L.tabk, L.cell_tiles, L.n_cell_tiles, L.done);
