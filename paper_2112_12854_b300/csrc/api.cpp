@@ -889,7 +889,6 @@ int bido_apply(ep_job *job) {
         free_job_arrays(job, &B.bufs);
         return rc;
     }
-    a.job = static_cast<const DevJob *>(job->dj_dev.p);
     a.ve = ve;
     a.xdiv = xd;
     a.b = bb;
@@ -918,7 +917,7 @@ int bido_apply(ep_job *job) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(job->dj_dev.p, &job->dj, sizeof(DevJob), cudaMemcpyHostToDevice, ctx->upload);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->upload);
-    if (e == cudaSuccess) e = launch_bido(prec, a, B.grid, ctx->stream);   // v_e from the current V
+    if (e == cudaSuccess) e = launch_bido(prec, a, job->dj, B.grid, ctx->stream);   // v_e from the current V
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "bidomain upload");
     job->version++;
@@ -1237,7 +1236,7 @@ static cudaError_t enqueue_steps(Plan *pl, int64_t steps, cudaStream_t s) {
             if (e != cudaSuccess) return e;
         }
         for (ep_job *j : pl->bido) {   // second line of Eq. 6 for v_e^{n+1}
-            cudaError_t e = launch_bido(j->precision, j->bido->args, j->bido->grid, s);
+            cudaError_t e = launch_bido(j->precision, j->bido->args, j->dj, j->bido->grid, s);
             if (e != cudaSuccess) return e;
         }
     }
@@ -1360,7 +1359,7 @@ int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double
                 if (e == cudaSuccess) e = cudaEventRecord(ev[k++], ctx->stream);
             }
             for (ep_job *j : pl->bido)   // untimed: the elliptic solves of bidomain jobs
-                if (e == cudaSuccess) e = launch_bido(j->precision, j->bido->args, j->bido->grid, ctx->stream);
+                if (e == cudaSuccess) e = launch_bido(j->precision, j->bido->args, j->dj, j->bido->grid, ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         double tn = 0.0, tc = 0.0;
         for (size_t i = 0; i + 2 < k + 1 && e == cudaSuccess; i += 3) {
@@ -1499,7 +1498,7 @@ int ep_autotune(ep_job *const *jobs, int32_t n_jobs, int32_t steps_per_variant, 
                         if (other.precision != prec && e == cudaSuccess)
                             e = launch_step(other.precision, other.L, ctx->stream);
                     for (ep_job *j : pl->bido)
-                        if (e == cudaSuccess) e = launch_bido(j->precision, j->bido->args, j->bido->grid, ctx->stream);
+                        if (e == cudaSuccess) e = launch_bido(j->precision, j->bido->args, j->dj, j->bido->grid, ctx->stream);
                 }
                 const double mean = tot / steps_per_variant;
                 if (variant_ms) variant_ms[prec * kNumCellVariants + v] = mean;
@@ -1907,7 +1906,7 @@ static int transfer_ve(ep_job *job, double *host, int64_t n, bool write) {
         if (e == cudaSuccess)
             e = cudaMemsetAsync(reinterpret_cast<char *>(a.stats) + offsetof(BidoStats, timeout), 0, sizeof(int),
                                 ctx->stream);
-        if (e == cudaSuccess) e = launch_bido(job->precision, a, job->bido->grid, ctx->stream);
+        if (e == cudaSuccess) e = launch_bido(job->precision, a, job->dj, job->bido->grid, ctx->stream);
     } else {
         e = launch_field_gather(job->precision, job->bido->args.ve, job->perm_dev, n, buf, ctx->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(host, buf, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);

@@ -35,6 +35,7 @@ template <> struct VW<double> { using type = double2; static constexpr int n = 2
 
 constexpr int kWarps = kBidoThreads / 32;
 constexpr int KP = kBidoMaxRestart + 1;
+constexpr int kShortNP = 13;   // accumulators of the kernel instance for restarts up to 12
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -80,11 +81,11 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Block partial sums of acc[0..count) into part[i * gridDim.x + blockIdx.x].
-template <class R>
-__device__ void block_partials(const R (&acc)[KP], int count, double *part, double *red_sh) {
+template <class R, int N>
+__device__ void block_partials(const R (&acc)[N], int count, double *part, double *red_sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < KP; ++i) {
+    for (int i = 0; i < N; ++i) {
         if (i < count) {
             const double v = warp_sum(double(acc[i]));
             if (lane == 0) red_sh[warp * KP + i] = v;
@@ -148,8 +149,13 @@ __device__ __forceinline__ R flux(const DevJob &J, const void *wa_, const void *
 template <class R> struct BidoMinBlocks { static constexpr int value = 1; };
 template <> struct BidoMinBlocks<float> { static constexpr int value = 3; };
 
-template <class R>
-__global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_kernel(BidoArgs A) {
+// NP: the per-thread dot-product accumulators and basis vectors the passes
+// are unrolled for (restart + 1 at most): 13 for the default restart of 12,
+// which keeps the accumulators of longer restarts out of the registers, or
+// kBidoMaxRestart + 1.
+template <class R, int NP>
+__global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value)
+    bido_kernel(const __grid_constant__ BidoArgs A) {
     __shared__ double red_sh[kWarps * KP];
     __shared__ double tot[KP];
     __shared__ double H[KP * kBidoMaxRestart];   // H[i * kBidoMaxRestart + j]
@@ -158,7 +164,7 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
     __shared__ R coef[KP];                        // per-pass multipliers of the basis vectors
     __shared__ int flag_sh;
 
-    const DevJob &J = *A.job;
+    const DevJob &J = A.job;   // constant bank: the per-cell reads of its fields hold no registers
     const long long n = J.n_cells;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gsz = (long long)gridDim.x * blockDim.x;
@@ -177,7 +183,7 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
     const VT *__restrict__ bq = reinterpret_cast<const VT *>(basis);
     VT *__restrict__ wq = reinterpret_cast<VT *>(wv);
     const int m = A.restart;
-    R acc[KP];
+    R acc[NP];
     // Two partial-sum buffers used in turn: a block may write the next
     // reduction's partials while another still reads the previous totals, but
     // never before every block has passed the barrier that follows.
@@ -238,7 +244,7 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
                 vp[c] = x[c];
             }
         }
-        block_partials<R>(acc, 1, part_w(), red_sh);
+        block_partials<R, NP>(acc, 1, part_w(), red_sh);
         BIDO_SYNC(1);
         grid_totals(part_w(), 1, tot);
         ++red;
@@ -255,7 +261,7 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
                 basis[c] = r;
                 acc[0] += r * r;
             }
-            block_partials<R>(acc, 1, part_w(), red_sh);
+            block_partials<R, NP>(acc, 1, part_w(), red_sh);
             BIDO_SYNC(1);
             grid_totals(part_w(), 1, tot);
             ++red;
@@ -269,7 +275,7 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
             }
             if (threadIdx.x == 0) {
                 sc[0] = 1.0 / beta;
-                for (int i = 0; i < KP; ++i) g[i] = 0.0;
+                for (int i = 0; i < NP; ++i) g[i] = 0.0;
                 g[0] = beta;
             }
             __syncthreads();
@@ -281,15 +287,15 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
                 node_pass<R>(J, vj, sj, vn, gtid, gsz);
                 BIDO_SYNC(0);
 #pragma unroll
-                for (int i = 0; i < KP; ++i) acc[i] = R(0);
+                for (int i = 0; i < NP; ++i) acc[i] = R(0);
                 for (long long c = gtid; c < n; c += gsz) {
                     const R w = flux<R>(J, A.wa, A.wb, A.q, vn, vj, sj, c);
                     wv[c] = w;
 #pragma unroll
-                    for (int i = 0; i < KP; ++i)
+                    for (int i = 0; i < NP; ++i)
                         if (i <= j) acc[i] += basis[i * ld + c] * w;
                 }
-                block_partials<R>(acc, j + 1, part_w(), red_sh);
+                block_partials<R, NP>(acc, j + 1, part_w(), red_sh);
                 BIDO_SYNC(1);
                 grid_totals(part_w(), j + 1, tot);
                 ++red;
@@ -302,12 +308,12 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
                 if (A.reorth) {
                     // second pass: w' = w - V h, and the re-orthogonalisation dots
 #pragma unroll
-                    for (int i = 0; i < KP; ++i) acc[i] = R(0);
+                    for (int i = 0; i < NP; ++i) acc[i] = R(0);
                     for (long long qi = gtid; qi < lq; qi += gsz) {
                         VT w = wq[qi];
                         R *wp = reinterpret_cast<R *>(&w);
 #pragma unroll
-                        for (int i = 0; i < KP; ++i)
+                        for (int i = 0; i < NP; ++i)
                             if (i <= j) {
                                 const VT b4 = bq[i * lq + qi];
                                 const R *bp = reinterpret_cast<const R *>(&b4);
@@ -317,7 +323,7 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
                             }
                         wq[qi] = w;
 #pragma unroll
-                        for (int i = 0; i < KP; ++i)
+                        for (int i = 0; i < NP; ++i)
                             if (i <= j) {
                                 const VT b4 = bq[i * lq + qi];
                                 const R *bp = reinterpret_cast<const R *>(&b4);
@@ -327,7 +333,7 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
                                 acc[i] += d;
                             }
                     }
-                    block_partials<R>(acc, j + 1, part_w(), red_sh);
+                    block_partials<R, NP>(acc, j + 1, part_w(), red_sh);
                     BIDO_SYNC(2);
                     grid_totals(part_w(), j + 1, tot);
                     ++red;
@@ -346,7 +352,7 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
                     VT w = wq[qi];
                     R *wp = reinterpret_cast<R *>(&w);
 #pragma unroll
-                    for (int i = 0; i < KP; ++i)
+                    for (int i = 0; i < NP; ++i)
                         if (i <= j) {
                             const VT b4 = bq[i * lq + qi];
                             const R *bp = reinterpret_cast<const R *>(&b4);
@@ -358,7 +364,7 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
 #pragma unroll
                     for (int k = 0; k < NW; ++k) acc[0] += wp[k] * wp[k];
                 }
-                block_partials<R>(acc, 1, part_w(), red_sh);
+                block_partials<R, NP>(acc, 1, part_w(), red_sh);
                 BIDO_SYNC(3);
                 grid_totals(part_w(), 1, tot);
                 ++red;
@@ -402,7 +408,7 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
                 VT xv = xq[qi];
                 R *xp = reinterpret_cast<R *>(&xv);
 #pragma unroll
-                for (int i = 0; i < KP; ++i)
+                for (int i = 0; i < NP; ++i)
                     if (i < j) {
                         const VT b4 = bq[i * lq + qi];
                         const R *bp = reinterpret_cast<const R *>(&b4);
@@ -418,7 +424,7 @@ __global__ void __launch_bounds__(kBidoThreads, BidoMinBlocks<R>::value) bido_ke
         const R *__restrict__ wvol = static_cast<const R *>(A.wvol);
         acc[0] = R(0);
         for (long long c = gtid; c < n; c += gsz) acc[0] += wvol[c] * x[c];
-        block_partials<R>(acc, 1, part_w(), red_sh);
+        block_partials<R, NP>(acc, 1, part_w(), red_sh);
         BIDO_SYNC(4);
         grid_totals(part_w(), 1, tot);
         ++red;
@@ -465,10 +471,12 @@ __global__ void field_scatter_kernel(const double *__restrict__ in, const int *_
     if (c < n) dst[c] = R(in[perm[c]]);
 }
 
+// Both accumulator counts of a precision run at the same register budget
+// (BidoMinBlocks), so one grid serves both.
 template <class R>
 int grid_of(int sm_count) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bido_kernel<R>, kBidoThreads, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bido_kernel<R, KP>, kBidoThreads, 0) != cudaSuccess) {
         cudaGetLastError();
         nb = 1;
     }
@@ -483,16 +491,19 @@ int bido_grid(int precision, int sm_count, long long n_cells) {
     return int(std::max(1LL, std::min<long long>(co, want)));
 }
 
-cudaError_t launch_bido(int precision, const BidoArgs &a, int grid, cudaStream_t s) {
+cudaError_t launch_bido(int precision, const BidoArgs &a, const DevJob &dj, int grid, cudaStream_t s) {
     BidoArgs arg = a;
+    arg.job = dj;
     void *args[] = {&arg};
     const cudaError_t e = cudaMemsetAsync(a.sync, 0, sizeof(BidoSync), s);
     if (e != cudaSuccess) return e;
-    if (precision == EP_FP64_PLAIN)
-        return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(bido_kernel<double>), dim3(grid),
-                                           dim3(kBidoThreads), args, 0, s);
-    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(bido_kernel<float>), dim3(grid),
-                                       dim3(kBidoThreads), args, 0, s);
+    const bool short_restart = a.restart + 1 <= kShortNP;
+    const void *k = precision == EP_FP64_PLAIN
+                        ? (short_restart ? reinterpret_cast<const void *>(bido_kernel<double, kShortNP>)
+                                         : reinterpret_cast<const void *>(bido_kernel<double, KP>))
+                        : (short_restart ? reinterpret_cast<const void *>(bido_kernel<float, kShortNP>)
+                                         : reinterpret_cast<const void *>(bido_kernel<float, KP>));
+    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kBidoThreads), args, 0, s);
 }
 
 cudaError_t launch_field_gather(int precision, const void *src, const int *perm, long long n, double *out,

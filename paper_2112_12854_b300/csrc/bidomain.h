@@ -42,7 +42,8 @@ struct BidoSync {
 };
 
 struct BidoArgs {
-    const DevJob *job;           // device job: topology, L_i coefficients, V, node scratch, step
+    DevJob job;                  // the job's descriptor (topology, L_i coefficients, V, node scratch, step),
+                                 // set by launch_bido: the kernel reads it from the constant bank
     const void *wa, *wb, *q;     // L_ie coefficients (layout of DevJob::wa/wb/q)
     const void *wvol;            // V_c / sum V (gauge weights)
     void *ve, *w;                // [ld] each, zero past n_cells
@@ -69,8 +70,9 @@ struct BidoArgs {
 int bido_grid(int precision, int sm_count, long long n_cells);
 
 // One solve (mode 0) or flux refresh (mode 1) of one job on stream s: the
-// barrier state is zeroed, then one cooperative launch.
-cudaError_t launch_bido(int precision, const BidoArgs &a, int grid, cudaStream_t s);
+// barrier state is zeroed, then one cooperative launch, with dj (the job's
+// current descriptor) passed as part of the kernel parameter.
+cudaError_t launch_bido(int precision, const BidoArgs &a, const DevJob &dj, int grid, cudaStream_t s);
 
 // out[perm[c]] = src[c] (as double), and the reverse.
 cudaError_t launch_field_gather(int precision, const void *src, const int *perm, long long n, double *out,
