@@ -271,10 +271,24 @@ int ep_read_state(ep_job *job, int32_t model, int32_t var, double *host_out, int
  * exactly. Synchronises. */
 int ep_write_state(ep_job *job, int32_t model, int32_t var, const double *host_in, int64_t n);
 
+/* The same transfers in FP32, for an EP_FP32_MIXED job: V and the variables
+ * such a job stores in FP32 (ep_model_var_compensated() == 0) are read and
+ * written exactly, with half the bytes of ep_read_state / ep_write_state
+ * (a checkpoint of the job's compute-type state, or its upload from a
+ * caller that holds it in FP32). Errors: EP_EINVAL for an EP_FP64_PLAIN job,
+ * and for a variable stored as a compensated sum ([Na]i, [K]i, the SR
+ * calcium), whose value needs FP64: transfer those with ep_read_state /
+ * ep_write_state. Synchronise. */
+int ep_read_state_f32(ep_job *job, int32_t model, int32_t var, float *host_out, int64_t n);
+int ep_write_state_f32(ep_job *job, int32_t model, int32_t var, const float *host_in, int64_t n);
+
 /* Activation times (ms): the first upward crossing of the threshold,
  * t^n + dt (theta - V^n)/(V^{n+1} - V^n) (Sec. 4); +inf where the cell has not
  * activated. n = number of cells, caller's order. Synchronises. */
 int ep_activation_times(ep_job *job, double *host_out, int64_t n);
+/* The same as FP32 values, for an EP_FP32_MIXED job (the times it stores,
+ * exactly; EP_EINVAL for an EP_FP64_PLAIN job). */
+int ep_activation_times_f32(ep_job *job, float *host_out, int64_t n);
 
 /* Reset activation times to +inf (a new beat). Asynchronous. */
 int ep_reset_activation(ep_job *job);
@@ -582,6 +596,10 @@ int ep_bidomain_stats(ep_job *job, ep_bidomain_stats_t *out);
  * (e.g. "V", "Ca_i", "Na_i", "m"). */
 int32_t ep_model_nvar(int32_t model);
 const char *ep_model_varname(int32_t model, int32_t var);
+/* 1 if variable var of the model is stored as a compensated sum in an
+ * EP_FP32_MIXED job (an FP64 value in an EP_FP64_PLAIN one), 0 if it is
+ * stored in the job's compute type, -1 for an unknown model or variable. */
+int32_t ep_model_var_compensated(int32_t model, int32_t var);
 
 #ifdef __cplusplus
 }

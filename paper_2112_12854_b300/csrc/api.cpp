@@ -363,6 +363,11 @@ const char *ep_model_varname(int32_t model, int32_t var) {
     return model_vars(model)[var].name;
 }
 
+int32_t ep_model_var_compensated(int32_t model, int32_t var) {
+    if (model < 0 || model >= EP_N_MODELS || var < 0 || var >= model_nvar(model)) return -1;
+    return model_vars(model)[var].kind == kVarA ? 1 : 0;
+}
+
 int64_t ep_estimate_bytes(int64_t n_cells, int64_t n_nodes, int32_t precision) {
     const int64_t r = precision == EP_FP64_PLAIN ? 8 : 4;
     // topology: nodes_a/b, nbr (3 int4), pset, smask, sell columns (~4.3 per cell)
@@ -1567,6 +1572,71 @@ int ep_write_state(ep_job *job, int32_t model, int32_t var, const double *host_i
     } catch (const std::bad_alloc &) {
         return fail(job->ctx, EP_ENOMEM, "ep_write_state: out of host memory");
     }
+}
+
+// The same transfers in FP32, for jobs that compute in FP32 (EP_FP32_MIXED)
+// and the variables they store in FP32: exact, with half the bytes.
+static int transfer_state_f32(ep_job *job, int32_t model, int32_t var, float *host, int64_t n, bool write) {
+    int rc = check_io(job, n, host);
+    if (rc) return rc;
+    ep_context *ctx = job->ctx;
+    if (model < 0 || model >= EP_N_MODELS || var < 0 || var >= model_nvar(model))
+        return fail(ctx, EP_EINVAL, "unknown model or variable id");
+    if (job->precision != EP_FP32_MIXED)
+        return fail(ctx, EP_EINVAL, "FP32 state transfers need an EP_FP32_MIXED job");
+    if (model_vars(model)[var].kind == kVarA)
+        return fail(ctx, EP_EINVAL, std::string(model_vars(model)[var].name) +
+                                        " is stored as a compensated sum: use ep_read_state / ep_write_state");
+    DeviceGuard g(ctx->device);
+    DevBuf b;
+    if ((rc = dalloc(ctx, n * sizeof(float), &b))) return rc;
+    const DevJob *dj = static_cast<const DevJob *>(job->dj_dev.p);
+    float *buf = static_cast<float *>(b.p);
+    cudaError_t e = cudaSuccess;
+    if (write) {
+        e = cudaMemcpyAsync(buf, host, n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = launch_transfer_f32(dj, job->perm_dev, n, model, var, buf, 1, ctx->stream);
+    } else {
+        e = launch_transfer_f32(dj, job->perm_dev, n, model, var, buf, 0, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host, buf, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, &b);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, write ? "ep_write_state_f32" : "ep_read_state_f32");
+    return write ? restart_ab2(job) : EP_OK;
+}
+
+int ep_read_state_f32(ep_job *job, int32_t model, int32_t var, float *host_out, int64_t n) {
+    try {
+        return transfer_state_f32(job, model, var, host_out, n, false);
+    } catch (const std::bad_alloc &) {
+        return fail(job->ctx, EP_ENOMEM, "ep_read_state_f32: out of host memory");
+    }
+}
+
+int ep_write_state_f32(ep_job *job, int32_t model, int32_t var, const float *host_in, int64_t n) {
+    try {
+        return transfer_state_f32(job, model, var, const_cast<float *>(host_in), n, true);
+    } catch (const std::bad_alloc &) {
+        return fail(job->ctx, EP_ENOMEM, "ep_write_state_f32: out of host memory");
+    }
+}
+
+int ep_activation_times_f32(ep_job *job, float *host_out, int64_t n) {
+    int rc = check_io(job, n, host_out);
+    if (rc) return rc;
+    ep_context *ctx = job->ctx;
+    if (job->precision != EP_FP32_MIXED)
+        return fail(ctx, EP_EINVAL, "FP32 activation times need an EP_FP32_MIXED job");
+    DeviceGuard g(ctx->device);
+    DevBuf b;
+    if ((rc = dalloc(ctx, n * sizeof(float), &b))) return rc;
+    cudaError_t e = launch_gather_act_f32(static_cast<const DevJob *>(job->dj_dev.p), job->perm_dev, n,
+                                          static_cast<float *>(b.p), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, b.p, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, &b);
+    return e == cudaSuccess ? EP_OK : cuda_fail(ctx, e, "ep_activation_times_f32");
 }
 
 int ep_activation_times(ep_job *job, double *host_out, int64_t n) {

@@ -560,45 +560,47 @@ struct DevVarLoc {
 };
 
 // out / in are in the caller's cell order: internal cell c is caller cell perm[c].
-template <class R>
+// H: the caller's element type (double; or float for the variables an FP32
+// job stores in FP32, exactly).
+template <class R, class H = double>
 __global__ void gather_kernel(const DevJob *__restrict__ job, const int *__restrict__ perm, long long n_cells,
-                              int model, DevVarLoc loc, double *buf, int write) {
+                              int model, DevVarLoc loc, H *buf, int write) {
     const DevJob &J = *job;
     const long long n = *J.step;
     R *V = static_cast<R *>(J.V[n & 1]);
     const DevRegion &rg = J.reg[model];
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n_cells;
          c += (long long)gridDim.x * blockDim.x) {
-        double &x = buf[perm[c]];
+        H &x = buf[perm[c]];
         if (loc.kind == kVarV) {
             if (write) V[c] = R(x);
-            else x = double(V[c]);
+            else x = H(V[c]);
             continue;
         }
         if (c < rg.off || c >= rg.off + rg.n) {
-            if (!write) x = NAN;
+            if (!write) x = H(NAN);
             continue;
         }
         const long long i = c - rg.off;
         if (loc.kind == kVarR) {
             R *p = static_cast<R *>(rg.r) + loc.slot * rg.stride + i;
             if (write) *p = R(x);
-            else x = double(*p);
+            else x = H(*p);
         } else {
             double *p = rg.a + loc.slot * rg.stride + i;
-            if (write) Accum<R>::init(p, x);
-            else x = Accum<R>::read(p);
+            if (write) Accum<R>::init(p, double(x));
+            else x = H(Accum<R>::read(p));
         }
     }
 }
 
-template <class R>
+template <class R, class H = double>
 __global__ void act_kernel(const DevJob *__restrict__ job, const int *__restrict__ perm, long long n_cells,
-                           double *out) {
+                           H *out) {
     R *act = static_cast<R *>(job->act);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n_cells;
          c += (long long)gridDim.x * blockDim.x) {
-        if (out) out[perm[c]] = double(act[c]);
+        if (out) out[perm[c]] = H(act[c]);
         else act[c] = R(INFINITY);
     }
 }
@@ -695,6 +697,19 @@ cudaError_t launch_gather_act(int precision, const DevJob *job, const int *perm,
         act_kernel<double><<<grid_for(n_cells, 256), 256, 0, s>>>(job, perm, n_cells, out);
     else
         act_kernel<float><<<grid_for(n_cells, 256), 256, 0, s>>>(job, perm, n_cells, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transfer_f32(const DevJob *job, const int *perm, long long n_cells, int model, int var,
+                                float *buf, int write, cudaStream_t s) {
+    const VarLoc &v = model_vars(model)[var];
+    gather_kernel<float, float><<<grid_for(n_cells, 256), 256, 0, s>>>(job, perm, n_cells, model,
+                                                                       DevVarLoc{v.kind, v.slot}, buf, write);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_act_f32(const DevJob *job, const int *perm, long long n_cells, float *out, cudaStream_t s) {
+    act_kernel<float, float><<<grid_for(n_cells, 256), 256, 0, s>>>(job, perm, n_cells, out);
     return cudaGetLastError();
 }
 

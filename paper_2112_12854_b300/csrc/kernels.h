@@ -120,6 +120,11 @@ cudaError_t launch_scatter(int precision, const DevJob *job, const int *perm, lo
 cudaError_t launch_gather_act(int precision, const DevJob *job, const int *perm, long long n_cells, double *out,
                               cudaStream_t s);
 cudaError_t launch_reset_act(int precision, const DevJob *job, long long n_cells, cudaStream_t s);
+// The same transfers of an FP32 job in FP32 (variables stored in FP32 and
+// V; the activation times): write = 0 gathers into buf, 1 scatters from it.
+cudaError_t launch_transfer_f32(const DevJob *job, const int *perm, long long n_cells, int model, int var,
+                                float *buf, int write, cudaStream_t s);
+cudaError_t launch_gather_act_f32(const DevJob *job, const int *perm, long long n_cells, float *out, cudaStream_t s);
 
 // Count non-finite values of the job's state into *count (device int).
 cudaError_t launch_check_finite(int precision, const DevJob *job, long long n_cells, unsigned *count,

@@ -97,7 +97,8 @@ EXPORTS = ["ep_context_create", "ep_context_set_stream", "ep_context_destroy", "
            "ep_plan_info", "ep_plan_destroy", "ep_job_create", "ep_graph_attach", "ep_graph_read_state",
            "ep_graph_write_state", "ep_graph_activation_times", "ep_graph_info", "ep_alu_peaks",
            "ep_bidomain_enable", "ep_bidomain_disable", "ep_bidomain_read_ve", "ep_bidomain_write_ve",
-           "ep_bidomain_stats", "ep_clear_error", "ep_set_graph_kernel"]
+           "ep_bidomain_stats", "ep_clear_error", "ep_set_graph_kernel", "ep_read_state_f32",
+           "ep_write_state_f32", "ep_activation_times_f32", "ep_model_var_compensated"]
 
 _lib = None
 _P = ctypes.c_void_p
@@ -123,6 +124,10 @@ def load():
         "ep_read_state": ([_P, ctypes.c_int32, ctypes.c_int32, _P, _I64], ctypes.c_int),
         "ep_write_state": ([_P, ctypes.c_int32, ctypes.c_int32, _P, _I64], ctypes.c_int),
         "ep_activation_times": ([_P, _P, _I64], ctypes.c_int),
+        "ep_read_state_f32": ([_P, ctypes.c_int32, ctypes.c_int32, _P, _I64], ctypes.c_int),
+        "ep_write_state_f32": ([_P, ctypes.c_int32, ctypes.c_int32, _P, _I64], ctypes.c_int),
+        "ep_activation_times_f32": ([_P, _P, _I64], ctypes.c_int),
+        "ep_model_var_compensated": ([ctypes.c_int32, ctypes.c_int32], ctypes.c_int32),
         "ep_reset_activation": ([_P], ctypes.c_int),
         "ep_step_index": ([_P, ctypes.POINTER(_I64)], ctypes.c_int),
         "ep_set_step_index": ([_P, _I64], ctypes.c_int),
@@ -173,6 +178,13 @@ def load():
 def model_varnames(model: int) -> list[str]:
     L = load()
     return [L.ep_model_varname(model, k).decode() for k in range(L.ep_model_nvar(model))]
+
+
+def model_var_compensated(model: int) -> list:
+    """Per variable of the model: True where an FP32 job stores it as a
+    compensated sum (transferred in FP64 only)."""
+    L = load()
+    return [bool(L.ep_model_var_compensated(model, k)) for k in range(L.ep_model_nvar(model))]
 
 
 def estimate_bytes(n_cells: int, n_nodes: int, precision: int = EP_FP32_MIXED) -> int:
@@ -369,6 +381,23 @@ class Job:
         v = np.ascontiguousarray(values, dtype=np.float64)
         self.ctx.check(load().ep_write_state(self._h, model, var, _ptr(v), self.n_cells))
 
+    def read_f32(self, var, model: int = EP_TP06, out=None) -> np.ndarray:
+        """ep_read_state_f32: a variable an FP32 job stores in FP32, exactly."""
+        if isinstance(var, str):
+            var = model_varnames(model).index(var)
+        if out is None:
+            out = np.empty(self.n_cells, np.float32)
+        assert out.dtype == np.float32 and out.flags.c_contiguous and out.size == self.n_cells
+        self.ctx.check(load().ep_read_state_f32(self._h, model, var, _ptr(out), self.n_cells))
+        return out
+
+    def write_f32(self, var, values, model: int = EP_TP06):
+        """ep_write_state_f32."""
+        if isinstance(var, str):
+            var = model_varnames(model).index(var)
+        v = np.ascontiguousarray(values, dtype=np.float32)
+        self.ctx.check(load().ep_write_state_f32(self._h, model, var, _ptr(v), self.n_cells))
+
     @property
     def V(self) -> np.ndarray:
         return self.read(0)
@@ -378,6 +407,14 @@ class Job:
             out = np.empty(self.n_cells, np.float64)
         assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == self.n_cells
         self.ctx.check(load().ep_activation_times(self._h, _ptr(out), self.n_cells))
+        return out
+
+    def activation_times_f32(self, out=None) -> np.ndarray:
+        """ep_activation_times_f32 (an FP32 job)."""
+        if out is None:
+            out = np.empty(self.n_cells, np.float32)
+        assert out.dtype == np.float32 and out.flags.c_contiguous and out.size == self.n_cells
+        self.ctx.check(load().ep_activation_times_f32(self._h, _ptr(out), self.n_cells))
         return out
 
     def reset_activation(self):

@@ -170,6 +170,62 @@ def test_checkpoint_resume_exact(ctx):
     new.destroy()
 
 
+def test_fp32_state_transfers_exact(ctx):
+    """ep_read_state_f32 / ep_write_state_f32 / ep_activation_times_f32 move
+    the variables an FP32 job stores in FP32 exactly: each read equals the
+    FP64 read rounded to FP32 (the stored value), and a checkpoint taken with
+    them (the compensated concentrations through the FP64 calls) resumes bit
+    for bit, over three cell models. The compensated variables and FP64 jobs
+    are refused with EP_EINVAL."""
+    from paper_2112_12854_b300 import ep
+    xyz, tets = w.kuhn_box(12, 6, 3, 0.25)
+    c = w.tet_centroids(xyz, tets)
+    ps = np.where(c[:, 0] < 1.0, 0, np.where(c[:, 0] < 2.0, 1, 2)).astype(np.uint8)
+    case = w.TissueCase("mix3", xyz, tets, w.fibres_uniform(len(tets)), ps, (c[:, 0] < 0.6).astype(np.uint8),
+                        [w.ParamSet(model=0), w.ParamSet(model=1), w.ParamSet(model=2)],
+                        [w.Stimulus(-60.0, 0.0, 1.0)], 0.02, 0, -20.0)
+    ref = ep.job_from_case(ctx, case)
+    ref.step(140)
+    snap = {}
+    for m in range(3):
+        comp = ep.model_var_compensated(m)
+        assert any(comp) and not comp[0]
+        for v in range(len(comp)):
+            d = ref.read(v, model=m)
+            if comp[v]:
+                with pytest.raises(ep.EPError) as e:
+                    ref.read_f32(v, model=m)
+                assert e.value.code == ep.EP_EINVAL
+                snap[m, v] = d
+            else:
+                f = ref.read_f32(v, model=m)
+                assert np.array_equal(f, d.astype(np.float32), equal_nan=True), (m, v)
+                snap[m, v] = f
+    a32 = ref.activation_times_f32()
+    assert np.array_equal(a32, ref.activation_times().astype(np.float32))
+    assert np.isfinite(a32).any()
+    ref.step(160)
+    new = ep.job_from_case(ctx, case)
+    for (m, v), vals in snap.items():
+        if vals.dtype == np.float32:
+            new.write_f32(v, vals, model=m)
+        else:
+            new.write(v, vals, model=m)
+    new.step_index = 140
+    new.step(160)
+    for m in range(3):
+        for v in range(len(ep.model_varnames(m))):
+            assert np.array_equal(new.read(v, model=m), ref.read(v, model=m), equal_nan=True), (m, v)
+    plain = ep.job_from_case(ctx, case, precision=ep.EP_FP64_PLAIN)
+    for call in (lambda: plain.read_f32(0), lambda: plain.write_f32(0, np.zeros(plain.n_cells, np.float32)),
+                 lambda: plain.activation_times_f32()):
+        with pytest.raises(ep.EPError) as e:
+            call()
+        assert e.value.code == ep.EP_EINVAL
+    for j in (ref, new, plain):
+        j.destroy()
+
+
 def test_errors_reported(ctx):
     from paper_2112_12854_b300 import ep
     case = w.slab_case(nx=4, ny=4, nz=2, h=0.25)
