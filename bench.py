@@ -236,6 +236,38 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_beat(ctx, args, dims, stream, torch):
+    """The headline workload over one whole beat: a fresh FP32 job from the
+    resting state, stimulated at t = 0, stepped through args.beat_steps steps
+    (400 ms at dt = 0.02 ms) in chunks of 1000 steps timed with CUDA events;
+    reports the whole-beat rate and the steady window of the 1000 steps in
+    the middle of the beat. The launch shape is the context's (autotuned)."""
+    from paper_2112_12854_b300 import ep
+    case = wedge_case(dims)
+    job = ep.job_from_case(ctx, case, precision=ep.EP_FP32_MIXED)
+    torch.cuda.synchronize()
+    chunk = 1000                    # the first chunk includes the capture of the step graph (~1 ms)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.beat_steps // chunk + 1)]
+    evs[0].record(stream)
+    for k in range(args.beat_steps // chunk):
+        job.step(chunk)
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(len(evs) - 1)]
+    total = sum(ms)
+    mid = ms[len(ms) // 2]
+    act = job.activation_times()
+    finite = job.check_finite()
+    job.destroy()
+    n = case.n_cells
+    steps = chunk * len(ms)
+    return {"steps": steps, "simulated_ms": steps * case.dt, "ms_per_step": total / steps,
+            "cell_updates_per_s": n * steps / (total * 1e-3),
+            "mid_beat_1000_steps": {"first_step": chunk * (len(ms) // 2), "ms_per_step": mid / chunk,
+                                    "cell_updates_per_s": n * chunk / (mid * 1e-3)},
+            "activated_fraction": float(np.isfinite(act).mean()), "state_finite": finite}
+
+
 def run_sweep(ctx, args, stream, torch):
     """Batched parametric sweep: args.sweep_jobs slab jobs drawn from the
     configured distribution (sizes log-uniform 50k-2M tets, G_Ks / G_Kr
@@ -451,6 +483,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--small", action="store_true", help="debug: 1/8-volume crop instead of the full wedge")
     ap.add_argument("--heart-steps", type=int, default=200, help="timed steps of the whole-heart leg (0 = skip)")
+    ap.add_argument("--beat-steps", type=int, default=20000,
+                    help="steps of the whole-beat leg on the headline workload (400 ms; 0 = skip)")
     ap.add_argument("--sweep-jobs", type=int, default=256, help="jobs of the batched parametric sweep (0 = skip; "
                     "the configured sweep has 256)")
     ap.add_argument("--sweep-steps", type=int, default=200)
@@ -641,6 +675,10 @@ def main():
     if args.bido_steps > 0 and budget_left("bidomain", 60.0):
         bido = run_bidomain(ctx, args, dims, stream, torch, peak)
 
+    beat = None
+    if args.beat_steps > 0 and budget_left("beat", 40.0):
+        beat = run_beat(ctx, args, dims, stream, torch)
+
     heart = None
     if args.heart_steps > 0 and budget_left("whole_heart", 90.0):
         heart = run_heart(ctx, args, stream, torch)
@@ -680,7 +718,7 @@ def main():
                              "fp64_fma_tflops": alu["fp64_fma_flops"] / 1e12,
                              "source": "ep_alu_peaks: independent FMA / ex2 chains on every SM, CUDA events"},
                "speedup_vs_fp64_plain": value / world / fp64["value"], "state_finite": finite,
-               "batched_sweep": sweep, "bidomain": bido, "whole_heart": heart, "serving": serving,
+               "beat": beat, "batched_sweep": sweep, "bidomain": bido, "whole_heart": heart, "serving": serving,
                "legs_skipped_for_time": skipped, "bench_wall_s": time.perf_counter() - t_start}
         print(json.dumps(out), flush=True)
     ctx.close()
