@@ -39,6 +39,21 @@ def test_model_variable_tables():
         assert ep.model_varnames(m) == oracle.model_varnames(m)
 
 
+def test_compensated_variables_are_the_slow_concentrations():
+    """The variables an FP32 job keeps as compensated sums (and transfers in
+    FP64 only) are exactly [Na]i, [K]i and the SR calcium of each model;
+    everything else, V included, is stored in the compute type."""
+    expect = {ep.EP_TP06: {"Na_i", "K_i", "Ca_SR"}, ep.EP_STEWART: {"Na_i", "K_i", "Ca_SR"},
+              ep.EP_CRN: {"Na_i", "K_i", "Ca_up", "Ca_rel"}}
+    L = ep.load()
+    for m, names in expect.items():
+        comp = ep.model_var_compensated(m)
+        assert {n for n, c in zip(ep.model_varnames(m), comp) if c} == names
+        assert not comp[0]
+        assert L.ep_model_var_compensated(m, len(comp)) == -1 and L.ep_model_var_compensated(m, -1) == -1
+    assert L.ep_model_var_compensated(3, 0) == -1
+
+
 def _params(sets, dt=0.02):
     return ep.make_params(dt, sets, [])
 
