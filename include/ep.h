@@ -334,9 +334,10 @@ int ep_time_kernels(ep_job *const *jobs, int32_t n_jobs, int64_t n_steps, double
  * per block and resident blocks per SM of the cell kernel, after its own
  * node-value launch (256 x 2, 256 x 3, 128 x 4, 128 x 5, 128 x 6, 64 x 12,
  * 128 x 7, 128 x 8; the block count caps the registers per thread); an
- * FP32 group of one forward-Euler monodomain job runs these shapes, and its
- * node-value launch, with the job's descriptor passed as a kernel
- * parameter, read from the constant bank; variants 6 and 7: the staged FP32 cell kernel, whose streamed
+ * FP32 launch group of forward-Euler monodomain jobs (at most 15, see
+ * ep_step) runs these shapes, and its node-value launch, with the jobs'
+ * descriptors passed as a kernel parameter, read from the constant bank;
+ * variants 6 and 7: the staged FP32 cell kernel, whose streamed
  * inputs are brought into shared memory by bulk asynchronous copies,
  * double-buffered (6: all of them, two blocks per SM; 7: indices,
  * coefficients, V and bytes, three blocks per SM), for jobs with 32-bit
